@@ -1,0 +1,422 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU)."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_14933_b300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _cell_avg_monomial(m, j):
+    """Average of x^m over the unit cell [j - 1/2, j + 1/2]."""
+    return ((j + 0.5) ** (m + 1) - (j - 0.5) ** (m + 1)) / (m + 1)
+
+
+# ---------------------------------------------------------------- Eqs. 14-15: c_rj and d_r
+def test_eno_coeffs_match_textbook_and_are_exact_on_quadratics():
+    c = O.eno_coeffs(3)
+    rows = _golden_rows("eno_k3.txt")
+    gold = np.array([[float(Fraction(x)) for x in r] for r in rows[:3]])
+    np.testing.assert_allclose(c, gold, rtol=0, atol=1e-14)
+    # each candidate is exact for cell averages of polynomials of degree <= 2 (point value at i+1/2)
+    for r in range(3):
+        for m in range(3):
+            rec = sum(c[r, j] * _cell_avg_monomial(m, -r + j) for j in range(3))
+            assert abs(rec - 0.5 ** m) < 1e-13
+
+
+def test_linear_weights_reproduce_fifth_order_reconstruction():
+    d = O.linear_weights()
+    gold = [float(Fraction(x)) for x in _golden_rows("eno_k3.txt")[3]]
+    np.testing.assert_allclose(d, gold, atol=1e-14)
+    c = O.eno_coeffs(3)
+    # the combined 5-point formula is exact for cell averages of quartics
+    for m in range(5):
+        f = [_cell_avg_monomial(m, j) for j in range(-2, 3)]
+        rec = sum(d[r] * sum(c[r, j] * f[2 - r + j] for j in range(3)) for r in range(3))
+        assert abs(rec - 0.5 ** m) < 1e-12
+    # and is the textbook (2, -13, 47, 27, -3)/60 stencil
+    comb = np.zeros(5)
+    for r in range(3):
+        for j in range(3):
+            comb[2 - r + j] += d[r] * c[r, j]
+    np.testing.assert_allclose(comb, np.array([2, -13, 47, 27, -3]) / 60.0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- Eqs. 16-19: beta
+def _beta_from_definition(f):
+    """Eq. 16 for k = 3: sum over l = 1, 2 of the integral over cell i of dx^(2l-1) (q^(l))^2,
+    with q the quadratic whose cell averages equal f on the candidate stencil."""
+    betas = []
+    xg, wg = np.polynomial.legendre.leggauss(6)
+    xs = 0.5 * xg            # cell i = [-1/2, 1/2]
+    ws = 0.5 * wg
+    for r in range(3):
+        cells = [-r + j for j in range(3)]
+        A = np.array([[_cell_avg_monomial(m, j) for m in range(3)] for j in cells])
+        coef = np.linalg.solve(A, np.array([f[2 + j] for j in cells]))
+        q1 = coef[1] + 2 * coef[2] * xs
+        q2 = 2 * coef[2] * np.ones_like(xs)
+        betas.append(np.sum(ws * q1 ** 2) + np.sum(ws * q2 ** 2))
+    return np.array(betas)
+
+
+def test_smoothness_indicators_match_integral_definition():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        f = rng.normal(size=5)
+        np.testing.assert_allclose(O.smoothness5(f), _beta_from_definition(f), rtol=1e-12,
+                                   atol=1e-13)
+
+
+# ---------------------------------------------------------------- Eqs. 20-27: weights
+@pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5])
+def test_linear_data_gives_optimal_weights(scheme):
+    d = O.linear_weights()
+    for a, b in [(0.3, 1.7), (-2.0, 0.01), (5.0, -3.0)]:
+        f = a + b * np.arange(-2, 3)
+        v, w = O.recon5(f, scheme)
+        np.testing.assert_allclose(w, d, atol=1e-14)
+        assert abs(v - (a + b * 0.5)) < 1e-12
+
+
+def test_teno_cuts_discontinuous_stencils():
+    # step between i and i+1: only the upwind stencil {i-2, i-1, i} is smooth
+    v, w = O.recon5([0.0, 0.0, 0.0, 1.0, 1.0], O.TENO5, 1e-5)
+    np.testing.assert_array_equal(w, [0.0, 0.0, 1.0])
+    assert v == 0.0
+    v2, w2 = O.recon5([0.0, 0.0, 0.0, 1.0, 1.0], O.WENO5JS)
+    assert w2[2] > 0.99 and abs(v2) < 0.01
+
+
+def test_teno_cutoff_threshold():
+    # chi_r < C_T drops the stencil; chi = gamma_r / sum gamma
+    beta = np.array([1.0, 1e-3, 1e-12])
+    w, margin = O.weights5(beta, O.TENO5, 1e-5)
+    assert w[0] == 0.0 and w[2] > 0.0
+    tau = abs(beta[0] - beta[2])
+    gam = (1 + tau / (beta + 1e-16)) ** 6
+    chi = gam / gam.sum()
+    assert margin == pytest.approx(np.min(np.abs(chi - 1e-5) / 1e-5), rel=1e-12)
+
+
+# ---------------------------------------------------------------- eigensystem (Sec. 2.2 (b))
+def _jacobian(gamma, U, n, h=1e-7):
+    J = np.zeros((5, 5))
+    for k in range(5):
+        e = np.zeros(5)
+        e[k] = h * max(1.0, abs(U[k]))
+        J[:, k] = (O.flux(gamma, U + e, n) - O.flux(gamma, U - e, n)) / (2 * e[k])
+    return J
+
+
+def test_eigensystem_diagonalises_flux_jacobian():
+    rng = np.random.default_rng(2)
+    g = 1.4
+    for _ in range(10):
+        rho = rng.uniform(0.2, 2)
+        u = rng.uniform(-1, 1, 3)
+        p = rng.uniform(0.2, 2)
+        U = I.prim_to_cons(g, rho, *u, p)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        R, L, lam = O.eigensystem(g, U, U, n)
+        np.testing.assert_allclose(R @ L, np.eye(5), atol=1e-12)
+        A = _jacobian(g, U, n)
+        np.testing.assert_allclose(R @ np.diag(lam) @ L, A, atol=2e-7 * max(1, np.abs(A).max()))
+        a = math.sqrt(g * p / rho)
+        np.testing.assert_allclose(lam[[0, 4]], [u @ n - a, u @ n + a], rtol=1e-12)
+
+
+def test_roe_average_satisfies_property_u():
+    # Roe's condition: F(UR) - F(UL) = A_roe (UR - UL) (for the Roe-averaged Jacobian)
+    rng = np.random.default_rng(3)
+    g = 1.4
+    for _ in range(10):
+        UL = I.prim_to_cons(g, rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2))
+        UR = I.prim_to_cons(g, rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2))
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        R, L, lam = O.eigensystem(g, UL, UR, n)
+        A = R @ np.diag(lam) @ L
+        np.testing.assert_allclose(A @ (UR - UL), O.flux(g, UR, n) - O.flux(g, UL, n), atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5])
+def test_char_flux_consistency_and_order(scheme):
+    g = 1.4
+    # uniform data: the interface flux is the physical flux
+    U = I.prim_to_cons(g, 0.9, 0.3, -0.2, 0.1, 1.1)
+    S = np.array([0.6, 0.8, 0.0])
+    F = O.char_flux_1d(g, scheme, 1e-5, np.tile(U, (6, 1)), S)
+    np.testing.assert_allclose(F, O.flux(g, U, S), rtol=1e-13, atol=1e-13)
+    # smooth data: flux differences converge to dF/dx at 5th order
+    errs = []
+    for h in (0.08, 0.04):
+        x0 = 0.3
+        def state(x):
+            return I.prim_to_cons(g, 1 + 0.2 * math.sin(x), 0.5 + 0.1 * math.cos(x), 0.0, 0.0,
+                                  1 + 0.1 * math.sin(2 * x))
+        Sx = np.array([1.0, 0.0, 0.0])
+        pts = [state(x0 + (s - 3) * h) for s in range(7)]
+        Fp = O.char_flux_1d(g, scheme, 1e-5, np.array(pts[1:7]), Sx)
+        Fm = O.char_flux_1d(g, scheme, 1e-5, np.array(pts[0:6]), Sx)
+        dF = (Fp - Fm) / h
+        e = 1e-3   # 6th-order central difference of the exact flux
+        Fe = [O.flux(g, state(x0 + m * e), Sx) for m in (-3, -2, -1, 1, 2, 3)]
+        exact = (-Fe[0] + 9 * Fe[1] - 45 * Fe[2] + 45 * Fe[3] - 9 * Fe[4] + Fe[5]) / (60 * e)
+        errs.append(np.abs(dF - exact).max())
+    assert errs[1] < 1e-6
+    assert math.log2(errs[0] / errs[1]) > 4.5
+
+
+# ---------------------------------------------------------------- Eqs. 28-33: operators
+def test_derivative_operators_exact_on_quartics():
+    rng = np.random.default_rng(4)
+    c = rng.normal(size=5)
+    N = 9
+    x = np.arange(N, dtype=float)
+    f = sum(c[m] * x ** m for m in range(5))
+    df = sum(m * c[m] * x ** (m - 1) for m in range(1, 5))
+    for i in range(N):
+        assert abs(O.deriv4(f, i, False) - df[i]) < 1e-9 * max(1, abs(df[i]))
+
+
+# ---------------------------------------------------------------- Eqs. 36-38: RK3
+@pytest.mark.parametrize("z", [0.3, -0.7, 0.5j, -0.2 + 0.9j, -1.5 + 0.4j])
+def test_rk3_amplification_polynomial(z):
+    y = O.rk3_linear(complex(z), 1.0, 1)
+    assert abs(y - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
+
+
+def test_rk3_third_order_in_time():
+    lam = -1.0 + 2.0j
+    errs = [abs(O.rk3_linear(lam, 1.0 / n, n) - np.exp(lam)) for n in (20, 40)]
+    assert 2.8 < math.log2(errs[0] / errs[1]) < 3.2
+
+
+# ---------------------------------------------------------------- Eq. 6: Sutherland
+def test_sutherland_against_tabulated_air():
+    rows = [(float(a), float(b)) for a, b in _golden_rows("air_viscosity.txt")]
+    Tref, muref = rows[0]
+    for T, mu in rows[1:]:
+        ratio = O.sutherland(T / Tref, 110.4 / Tref)
+        assert abs(ratio - mu / muref) / (mu / muref) < 0.02
+    assert O.sutherland(1.0, 110.4 / 288.0) == pytest.approx(1.0, abs=1e-15)
+
+
+# ---------------------------------------------------------------- Sod (Sec. 5.1)
+def test_exact_riemann_star_state_matches_toro():
+    ps, us, rl, rr = [float(x) for x in _golden_rows("sod_star.txt")[0]]
+    p, u = O.riemann_star(1.4, [1, 0, 1], [0.125, 0, 0.1])
+    assert abs(p - ps) < 1e-5 and abs(u - us) < 1e-5
+    x = np.array([0.5 + u * 0.2 - 1e-3, 0.5 + u * 0.2 + 1e-3])
+    r, _, _ = O.riemann_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+    assert abs(r[0] - rl) < 1e-5 and abs(r[1] - rr) < 1e-5
+
+
+def test_exact_riemann_shock_satisfies_rankine_hugoniot():
+    g = 1.4
+    p, u = O.riemann_star(g, [1, 0, 1], [0.125, 0, 0.1])
+    x = np.linspace(0.5, 1.0, 20001)
+    r, uu, pp = O.riemann_sample(g, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+    k = np.argmax(r < 0.126)          # first point ahead of the shock
+    assert k > 0
+    s = (x[k] - 0.5) / 0.2            # shock speed
+    r2 = r[k - 1]
+    # mass: rho_R (0 - s) = rho_2 (u* - s)
+    assert abs(0.125 * (0 - s) - r2 * (u - s)) < 2e-4
+    # momentum: p_R + rho_R s^2 = p* + rho_2 (u* - s)^2
+    assert abs((0.1 + 0.125 * s * s) - (p + r2 * (u - s) ** 2)) < 2e-4
+
+
+def test_sod_weno5js_against_exact_solution():
+    cfg, U, x = I.sod()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(800)
+    rho = o.get_state()[0, 0, 0]
+    r, _, _ = O.riemann_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+    assert np.abs(rho - r).mean() < 4e-3
+    # shock position within one cell: where rho crosses the mid value of the jump
+    _, ust = O.riemann_star(1.4, [1, 0, 1], [0.125, 0, 0.1])
+    rr_star = float(_golden_rows("sod_star.txt")[0][3])
+    mid = 0.5 * (rr_star + 0.125)
+    xs_num = x[np.where((rho[:-1] >= mid) & (rho[1:] < mid))[0][-1]]
+    xs_ex = x[np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]]
+    assert abs(xs_num - xs_ex) <= 1.0 / 400 + 1e-12
+
+
+# ---------------------------------------------------------------- Eqs. 2-5: viscous terms
+def _line_cfg(N, Re, stretch=0.0):
+    L = 2 * math.pi
+    cfg = dict(n=(N, 1, 1), gamma=1.4, Re=Re, Pr=0.72, Ma=0.5, scheme=O.TENO5, teno_ct=1e-5,
+               bc=[[0, 0], [0, 0], [0, 0]], h=(L / N, 1, 1), L=(L, 0, 0))
+    xi = np.arange(N) * L / N
+    x = xi + stretch * np.sin(xi)
+    if stretch:
+        coords = np.zeros((3, 1, 1, N))
+        coords[0, 0, 0] = x
+        cfg["coords"] = coords
+    return cfg, x
+
+
+@pytest.mark.parametrize("stretch", [0.0, 0.3])
+def test_viscous_residual_closed_forms(stretch):
+    """R(Re) - R(inviscid) against the analytic viscous terms of Eqs. 2-5 (constant mu) for a
+    shear wave, a compression wave and a temperature wave at constant pressure; 4th-order."""
+    Re, A = 50.0, 0.01
+    g, Ma, Pr = 1.4, 0.5, 0.72
+    errs = []
+    for N in (32, 64):
+        cfg, x = _line_cfg(N, Re, stretch)
+        one = np.ones(N)
+        k = 1.0
+        v = A * np.sin(k * x)
+        u = A * np.cos(k * x)
+        T = 1 + A * np.sin(2 * k * x)
+        p = 1.0 / (g * Ma * Ma) * one
+        rho = g * Ma * Ma * p / T
+        U = I.prim_to_cons(g, rho, u, v, 0 * one, p).reshape(5, 1, 1, N)
+        Rv = O.Oracle(cfg)
+        Rv.set_state(U)
+        cfg0 = dict(cfg, Re=0.0)
+        Ri = O.Oracle(cfg0)
+        Ri.set_state(U)
+        dR = (Rv.residual() - Ri.residual())[:, 0, 0]
+        ux, uxx = -A * k * np.sin(k * x), -A * k * k * np.cos(k * x)
+        vx, vxx = A * k * np.cos(k * x), -A * k * k * np.sin(k * x)
+        Tx, Txx = 2 * A * k * np.cos(2 * k * x), -4 * A * k * k * np.sin(2 * k * x)
+        exact_mx = (4.0 / 3.0) / Re * uxx
+        exact_my = vxx / Re
+        kq = 1.0 / ((g - 1) * Ma * Ma * Pr * Re)
+        exact_E = (4.0 / 3.0) / Re * (ux * ux + u * uxx) + (vx * vx + v * vxx) / Re + kq * Txx
+        e = max(np.abs(dR[1] - exact_mx).max(), np.abs(dR[2] - exact_my).max(),
+                np.abs(dR[4] - exact_E).max(), np.abs(dR[0]).max(), np.abs(dR[3]).max())
+        errs.append(e)
+    assert errs[1] < 1e-5
+    assert math.log2(errs[0] / errs[1]) > 3.5
+
+
+def test_tgv_initial_kinetic_energy_and_dissipation():
+    cfg, U = I.tgv(32, Ma=0.1, scheme=O.CENTRAL4)
+    rho = U[0]
+    u = U[1:4] / rho
+    ke = 0.5 * (rho * (u ** 2).sum(0)).mean()
+    assert abs(ke - 0.125) < 2e-3
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    R = o.residual()
+    # dKE/dt = <u . R_m - |u|^2/2 R_rho>; incompressible limit: -<|omega|^2>/Re = -0.75/Re
+    dke = ((u * R[1:4]).sum(0) - 0.5 * (u ** 2).sum(0) * R[0]).mean()
+    assert dke == pytest.approx(-0.75 / cfg["Re"], rel=0.01)
+
+
+@pytest.mark.parametrize("scheme", [O.CENTRAL4, O.TENO5, O.WENO5JS])
+def test_discrete_conservation_periodic(scheme):
+    if scheme == O.CENTRAL4:
+        cfg, U = I.tgv(12, Ma=0.1, scheme=scheme)
+    else:
+        cfg, U = I.tgv(12, Ma=1.25, scheme=scheme)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    s0 = U.reshape(5, -1).sum(1)
+    o.step(3)
+    s1 = o.get_state().reshape(5, -1).sum(1)
+    scale = np.abs(U).reshape(5, -1).sum(1)
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * scale + 1e-12)
+
+
+def test_discrete_conservation_curvilinear():
+    cfg, U = I.euler_wave(16, scheme=O.TENO5, dt=2e-3)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    _, J, _ = o.metrics()
+    Jinv = 1.0 / J
+    s0 = (U * Jinv).reshape(5, -1).sum(1)
+    o.step(5)
+    s1 = (o.get_state() * Jinv).reshape(5, -1).sum(1)
+    assert np.all(np.abs(s1 - s0) <= 1e-12 * np.abs(s0) + 1e-12)
+
+
+# ---------------------------------------------------------------- Sec. 2.7 metrics, Sec. 5.3
+def test_metrics_of_sinusoidal_grid():
+    N, A = 32, 0.04
+    cfg, U = I.euler_wave(N, A=A)
+    o = O.Oracle(cfg)
+    S, J, sh = o.metrics()
+    d = 2.0 / N
+    i = np.arange(N)[None, :]
+    j = np.arange(N)[:, None]
+    x_i = d * np.ones((N, N))
+    x_j = A * 6 * math.pi * d / 2.0 * np.cos(6 * math.pi * j * d / 2.0) * np.ones((N, N))
+    y_i = A * 6 * math.pi * d / 2.0 * np.cos(6 * math.pi * i * d / 2.0) * np.ones((N, N))
+    y_j = d * np.ones((N, N))
+    Jinv = x_i * y_j - x_j * y_i
+    np.testing.assert_allclose(1.0 / J[0], Jinv, rtol=2e-3)
+    np.testing.assert_allclose(S[0, 0, 0] * sh[0], y_j, rtol=1e-12)
+    np.testing.assert_allclose(S[0, 1, 0] * sh[0], -x_j, atol=2e-3 * d)
+    np.testing.assert_allclose(S[1, 0, 0] * sh[1], -y_i, atol=2e-3 * d)
+
+
+@pytest.mark.parametrize("A,order", [(0.0, 5.0), (0.04, 4.0)])
+def test_euler_wave_order_of_convergence(A, order):
+    """Eq. 47 on the grid of Eqs. 48-49: L1 and Linf rates within 10 % of the formal order.
+    The metrics are 4th-order central (Sec. 2.7), which bounds the curvilinear order at 4."""
+    errs = []
+    for N in (32, 64):
+        cfg, U = I.euler_wave(N, scheme=O.TENO5, dt=1e-3 * 32 / N, A=A)
+        o = O.Oracle(cfg)
+        o.set_state(U)
+        ns = int(round(0.25 / cfg["dt"]))
+        o.step(ns)
+        rho = o.get_state()[0, 0]
+        ex = I.euler_wave_exact(cfg["coords"], ns * cfg["dt"])
+        errs.append((np.abs(rho - ex).mean(), np.abs(rho - ex).max()))
+    r1 = math.log2(errs[0][0] / errs[1][0])
+    ri = math.log2(errs[0][1] / errs[1][1])
+    assert r1 > 0.9 * order and ri > 0.9 * order
+
+
+# ---------------------------------------------------------------- Eqs. 40-46: wall ghosts
+def test_isothermal_wall_ghosts_continue_linear_temperature():
+    n = (4, 8, 1)
+    g, Ma, Tw = 1.4, 0.5, 1.3
+    cfg = dict(n=n, gamma=g, Re=100.0, Pr=0.72, Ma=Ma, scheme=O.TENO5,
+               bc=[[0, 0], [O.WALL, O.ZEROGRAD], [0, 0]], T_wall=Tw, h=(0.1, 0.1, 1), L=(0.4, 0, 0))
+    jj = np.arange(n[1])[None, :, None] * np.ones((1, 1, n[0]))
+    T = Tw + 0.05 * jj                 # linear temperature, wall value at j = 0
+    pw = 0.8
+    rho = g * Ma * Ma * pw / T
+    u = 0.1 * jj
+    v = 0.02 * jj
+    U = I.prim_to_cons(g, rho, u, v, 0 * u, pw + 0 * u).reshape(5, 1, n[1], n[0])
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    Ug = o.ghosted()[:, 0]
+    for gi in (1, 2, 3):
+        row = Ug[:, 3 - gi, 3:3 + n[0]]
+        r = row[0]
+        ug = row[1] / r
+        vg = row[2] / r
+        pg = (g - 1) * (row[4] - 0.5 * r * (ug ** 2 + vg ** 2))
+        Tg = g * Ma * Ma * pg / r
+        np.testing.assert_allclose(Tg, Tw - 0.05 * gi, rtol=1e-13)
+        np.testing.assert_allclose(pg, pw, rtol=1e-13)
+        np.testing.assert_allclose(ug, -0.1 * gi, rtol=1e-13)
+        np.testing.assert_allclose(vg, -0.02 * gi, rtol=1e-13)
