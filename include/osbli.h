@@ -1,0 +1,128 @@
+/*
+ * osbli.h -- C ABI of the B300-native (sm_103a) residual / RK-stage path of the OpenSBLI method
+ * (Lusher, Jammy & Sandham, arXiv:2007.14933).
+ *
+ * What one RK step computes (paper sections):
+ *   - compressible Navier-Stokes residual (Sec. 2.1, Eqs. 1-7) on a structured grid, curvilinear
+ *     through metric terms evaluated once with the 4th-order central / one-sided schemes
+ *     (Sec. 2.6-2.7, Eqs. 28-33);
+ *   - convective terms by characteristic-space WENO5-JS or TENO5 reconstruction with a
+ *     Roe-averaged eigensystem and local Lax-Friedrichs splitting (Sec. 2.2 algorithm,
+ *     Eqs. 9-27), or 4th-order central differences (Sec. 2.6);
+ *   - viscous and heat-flux terms by 4th-order central differences (Eqs. 4-5, 28-33);
+ *   - the low-storage 3-stage RK update dU = A dU + dt R, U = U + B dU (Sec. 2.8, Eqs. 36-38);
+ *   - boundary conditions through ghost points (Sec. 3.1.3, Eqs. 40-46; Sec. 6 set-up).
+ *
+ * Data layout at the boundary: the state is five conserved variables (rho, rho u, rho v, rho w,
+ * rho E) as structure of arrays [5][nz][ny][nx], FP64, x fastest, contiguous.  Pointers given to
+ * osbli_set_state / osbli_get_state / osbli_residual / osbli_set_boundary_data may be host or
+ * device pointers (unified addressing; page-locked host memory for asynchronous copies).  The
+ * library owns every buffer it allocates; the caller owns every pointer it passes in and may
+ * reuse it when the call returns.
+ *
+ * Errors: every int-returning call returns OSBLI_OK (0) or a negative code; osbli_last_error()
+ * returns a message for the last failure on that handle.  No call throws.  A handle is not
+ * thread-safe; different handles are independent.
+ */
+#ifndef OSBLI_H
+#define OSBLI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    OSBLI_OK = 0,
+    OSBLI_EINVAL = -1,     /* invalid argument or parameter combination */
+    OSBLI_ENOMEM = -2,     /* device allocation failed */
+    OSBLI_ECUDA = -3,      /* a CUDA call failed (message in osbli_last_error) */
+    OSBLI_ENONFINITE = -4, /* the state became non-finite during osbli_rk_step */
+    OSBLI_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    OSBLI_ESTATE = -6      /* stepping before osbli_set_state / missing face data */
+};
+
+/* convective scheme (Sec. 2.2-2.6) */
+enum { OSBLI_CENTRAL4 = 0, OSBLI_WENO5JS = 1, OSBLI_TENO5 = 2 };
+
+/* boundary conditions per direction and side (Sec. 3.1.3, Sec. 5-6 set-ups):
+ *   PERIODIC   both sides of a direction must be periodic together
+ *   ZEROGRAD   ghosts copy the boundary node (zero-order extrapolation; also used as outlet)
+ *   WALL       isothermal no-slip wall on the boundary node (Eqs. 40-46), temperature T_wall
+ *   DIRICHLET  ghosts and boundary node from osbli_set_boundary_data (rho, u, v, w, p)
+ *   INFLOW     ghosts and boundary node: u, v, w, T from osbli_set_boundary_data (slot 0 unused),
+ *              pressure extrapolated from the first interior node, rho = gamma Ma^2 p / T */
+enum { OSBLI_PERIODIC = 0, OSBLI_ZEROGRAD = 1, OSBLI_WALL = 2, OSBLI_DIRICHLET = 3,
+       OSBLI_INFLOW = 4 };
+
+/* arithmetic of the reconstruction (Sec. 2.2-2.5) */
+enum { OSBLI_FP64 = 0, OSBLI_MIXED = 1 };
+
+typedef struct osbli osbli_t;
+
+typedef struct {
+    int nx, ny, nz;            /* interior points; 1 marks an inactive direction (Sod: 400,1,1);
+                                  an active non-periodic direction needs >= 5 points, a periodic
+                                  one >= 3 */
+    double gamma, Re, Pr, Ma;  /* Re <= 0: inviscid (no viscous / heat-flux terms) */
+    double dt;                 /* fixed time step */
+    int scheme;                /* OSBLI_CENTRAL4 | OSBLI_WENO5JS | OSBLI_TENO5 */
+    double teno_ct;            /* TENO cut-off C_T (Eq. 24), e.g. 1e-5 */
+    int bc[3][2];              /* bc[direction][side], side 0 = low index */
+    double T_wall;             /* isothermal wall temperature (Eq. 41) */
+    double sutherland_ratio;   /* T_s/T_ref of Eq. 6; <= 0: constant mu = 1 */
+    int precision;             /* OSBLI_FP64 | OSBLI_MIXED */
+    int sensor;                /* reserved, must be 0 */
+    double h[3];               /* grid spacing per direction when coords == NULL */
+    double L[3];               /* period of each periodic direction (coordinate unwrapping) */
+} osbli_params;
+
+/* Create a solver for one grid.  coords: NULL (uniform grid, spacing h) or node coordinates of
+ * the interior points, host memory, [3][nz][ny][nx] (x, y, z components); the metric terms are
+ * computed on the device once (Sec. 2.7).  cuda_stream: the cudaStream_t every call enqueues
+ * on (NULL: the handle creates its own blocking stream, ordered with the legacy default
+ * stream).  On success *out receives the handle.  Errors: EINVAL (bad sizes/parameters),
+ * ENOMEM, ECUDA. */
+int osbli_create(const osbli_params *p, const double *coords, void *cuda_stream, osbli_t **out);
+
+/* Release every device buffer of the handle.  NULL is ignored. */
+void osbli_destroy(osbli_t *h);
+
+/* Face data of a DIRICHLET or INFLOW face: [5][plane], plane = interior points of the two other
+ * directions, lower direction fastest.  Copied in.  Errors: EINVAL (face is neither). */
+int osbli_set_boundary_data(osbli_t *h, int dir, int side, const double *prims);
+
+/* Copy a state in ([5][nz][ny][nx]).  Errors: EINVAL, ECUDA. */
+int osbli_set_state(osbli_t *h, const double *U);
+
+/* Copy the current state out (same layout).  Synchronises the handle's stream. */
+int osbli_get_state(osbli_t *h, double *U);
+
+/* Advance nsteps RK3 steps (3 stages each: ghost fill, residual, register update, boundary
+ * nodes).  The first call captures one step into a CUDA graph that later calls replay.
+ * Synchronises and checks the device error word before returning: ENONFINITE when any interior
+ * value became non-finite, ESTATE before osbli_set_state, EINVAL for nsteps < 0. */
+int osbli_rk_step(osbli_t *h, int nsteps);
+
+/* Residual R(U) (the right-hand side dU/dt of Eqs. 1-3) of the current state, written to R in
+ * the state layout.  Used for single-stage parity checks.  Synchronises. */
+int osbli_residual(osbli_t *h, double *R);
+
+/* Diagnostics of the current state (deterministic reductions over interior points):
+ * out[0..4] = sum of the conserved variables, out[5] = mean kinetic energy 1/2 rho |u|^2,
+ * out[6] = max Mach number, out[7] = min density, out[8] = min pressure, out[9..15] = 0. */
+int osbli_diagnostics(osbli_t *h, double out[16]);
+
+/* Kernel launches one RK step enqueues (for launch accounting). */
+int osbli_launches_per_step(const osbli_t *h);
+
+/* Message of the last failure on h (or of the last failed osbli_create when h is NULL). */
+const char *osbli_last_error(const osbli_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSBLI_H */

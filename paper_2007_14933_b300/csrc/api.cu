@@ -1,0 +1,382 @@
+// api.cu -- the C ABI of include/osbli.h: handle, buffers, validation, graph capture of one
+// RK step, error reporting.  No exception crosses the boundary.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "launch.h"
+#include "osbli.h"
+
+using namespace osb;
+
+struct osbli {
+    osbli_params p;
+    Dev P;
+    Bufs B;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *stage = nullptr;       // compact [5][N] staging for set/get/residual
+    double *diag_part = nullptr, *diag_out = nullptr;
+    int *h_err = nullptr;          // pinned
+    double *h_diag = nullptr;      // pinned
+    bool state_set = false;
+    bool bdata_set[6] = {false, false, false, false, false, false};
+    cudaGraphExec_t gexec = nullptr;
+    int launches_step = 0;
+    char err[512];
+};
+
+static char g_create_err[512] = "";
+
+static int seterr(osbli *h, int code, const char *fmt, ...)
+{
+    char *dst = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(h, call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return seterr((h), e_ == cudaErrorMemoryAllocation ? OSBLI_ENOMEM : OSBLI_ECUDA,     \
+                          "%s: %s", #call, cudaGetErrorString(e_));                              \
+    } while (0)
+
+static long long npoints(const Dev &P) { return (long long)P.n[0] * P.n[1] * P.n[2]; }
+
+static void free_all(osbli *h)
+{
+    if (!h) return;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    double *bufs[] = {h->B.U, h->B.dU, h->B.R, h->B.W, h->B.M, h->B.V, h->stage, h->diag_part,
+                      h->diag_out};
+    for (double *b : bufs)
+        if (b) cudaFree(b);
+    for (int f = 0; f < 6; f++)
+        if (h->B.bd[f]) cudaFree(h->B.bd[f]);
+    if (h->B.err) cudaFree(h->B.err);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->h_diag) cudaFreeHost(h->h_diag);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+static int validate(const osbli_params *p, const double *coords)
+{
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < 3; d++) {
+        if (n[d] < 1) return seterr(nullptr, OSBLI_EINVAL, "n[%d] = %d < 1", d, n[d]);
+        for (int s = 0; s < 2; s++)
+            if (p->bc[d][s] < OSBLI_PERIODIC || p->bc[d][s] > OSBLI_INFLOW)
+                return seterr(nullptr, OSBLI_EINVAL, "bc[%d][%d] = %d unknown", d, s, p->bc[d][s]);
+        if (n[d] == 1) continue;
+        const bool per0 = p->bc[d][0] == OSBLI_PERIODIC, per1 = p->bc[d][1] == OSBLI_PERIODIC;
+        if (per0 != per1)
+            return seterr(nullptr, OSBLI_EINVAL, "direction %d: periodic on one side only", d);
+        if (per0 && n[d] < 3)
+            return seterr(nullptr, OSBLI_EINVAL, "periodic direction %d needs >= 3 points", d);
+        if (!per0 && n[d] < 5)
+            return seterr(nullptr, OSBLI_EINVAL, "non-periodic direction %d needs >= 5 points", d);
+        if (!coords && !(p->h[d] > 0.0))
+            return seterr(nullptr, OSBLI_EINVAL, "h[%d] must be > 0 on a uniform grid", d);
+        if (coords && per0 && !(p->L[d] > 0.0))
+            return seterr(nullptr, OSBLI_EINVAL, "periodic direction %d needs its period L[%d]", d, d);
+    }
+    if ((long long)n[0] * n[1] * n[2] > (1LL << 31))
+        return seterr(nullptr, OSBLI_EINVAL, "grid larger than 2^31 points");
+    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_TENO5)
+        return seterr(nullptr, OSBLI_EINVAL, "scheme %d unknown", p->scheme);
+    if (!(p->gamma > 1.0) || !(p->Ma > 0.0))
+        return seterr(nullptr, OSBLI_EINVAL, "need gamma > 1 and Ma > 0");
+    if (p->Re > 0.0 && !(p->Pr > 0.0)) return seterr(nullptr, OSBLI_EINVAL, "viscous run needs Pr > 0");
+    if (!isfinite(p->dt) || p->dt < 0.0) return seterr(nullptr, OSBLI_EINVAL, "dt must be finite and >= 0");
+    if (p->scheme == OSBLI_TENO5 && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))
+        return seterr(nullptr, OSBLI_EINVAL, "teno_ct must lie in (0, 1)");
+    if (p->precision != OSBLI_FP64)
+        return seterr(nullptr, OSBLI_EINVAL, "precision %d not available in this build", p->precision);
+    if (p->sensor != 0) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0");
+    for (int d = 0; d < 3; d++)
+        for (int s = 0; s < 2; s++)
+            if (n[d] > 1 && p->bc[d][s] == OSBLI_WALL && !(p->T_wall > 0.0))
+                return seterr(nullptr, OSBLI_EINVAL, "wall needs T_wall > 0");
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_create(const osbli_params *p, const double *coords, void *cuda_stream,
+                            osbli_t **out)
+{
+    if (!p || !out) return seterr(nullptr, OSBLI_EINVAL, "null argument");
+    *out = nullptr;
+    int rc = validate(p, coords);
+    if (rc != OSBLI_OK) return rc;
+    osbli *h = new (std::nothrow) osbli();
+    if (!h) return seterr(nullptr, OSBLI_ENOMEM, "host allocation failed");
+    h->p = *p;
+    h->err[0] = 0;
+    Dev &P = h->P;
+    memset(&P, 0, sizeof(P));
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < 3; d++) {
+        P.n[d] = n[d];
+        P.active[d] = n[d] > 1;
+        P.g[d] = P.active[d] ? GH : 0;
+        P.np[d] = n[d] + 2 * P.g[d];
+        for (int s = 0; s < 2; s++) P.bc[d][s] = p->bc[d][s];
+    }
+    P.st[0] = 1;
+    P.st[1] = P.np[0];
+    P.st[2] = (long long)P.np[0] * P.np[1];
+    P.ntot = (long long)P.np[0] * P.np[1] * P.np[2];
+    P.vs = (P.ntot + 31) / 32 * 32;
+    P.scheme = p->scheme;
+    P.viscous = p->Re > 0.0;
+    P.curv = coords != nullptr;
+    P.gamma = p->gamma;
+    P.gm1 = p->gamma - 1.0;
+    P.Re = p->Re;
+    P.Pr = p->Pr;
+    P.Ma = p->Ma;
+    P.ct = p->teno_ct;
+    P.Tw = p->T_wall;
+    P.suth = p->sutherland_ratio;
+    P.gM2 = p->gamma * p->Ma * p->Ma;
+    P.kq = P.viscous ? 1.0 / ((p->gamma - 1.0) * p->Ma * p->Ma * p->Pr * p->Re) : 0.0;
+    P.dt = p->dt;
+    if (!P.curv) {
+        double hh[3];
+        for (int d = 0; d < 3; d++) hh[d] = P.active[d] ? p->h[d] : 1.0;
+        const double Jinv = hh[0] * (hh[1] * hh[2]);
+        const double S[3] = {hh[1] * hh[2], hh[2] * hh[0], hh[0] * hh[1]};
+        for (int d = 0; d < 3; d++) P.fac[d] = S[d] / Jinv;
+    }
+
+    auto fail = [&](int code) {
+        free_all(h);
+        if (code != OSBLI_OK) memcpy(g_create_err, h->err, sizeof(g_create_err));
+        delete h;
+        return code;
+    };
+#define CKC(call)                                                                                 \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(seterr(h, e_ == cudaErrorMemoryAllocation ? OSBLI_ENOMEM : OSBLI_ECUDA,   \
+                               "%s: %s", #call, cudaGetErrorString(e_)));                         \
+    } while (0)
+
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        CKC(cudaStreamCreate(&h->stream));
+        h->own_stream = true;
+    }
+    const long long N = npoints(P);
+    const size_t vsb = (size_t)P.vs * sizeof(double);
+    CKC(cudaMalloc(&h->B.U, NV * vsb));
+    CKC(cudaMalloc(&h->B.dU, NV * vsb));
+    CKC(cudaMalloc(&h->B.R, NV * vsb));
+    CKC(cudaMalloc(&h->B.W, NW * vsb));
+    CKC(cudaMemsetAsync(h->B.U, 0, NV * vsb, h->stream));
+    CKC(cudaMemsetAsync(h->B.dU, 0, NV * vsb, h->stream));
+    CKC(cudaMemsetAsync(h->B.R, 0, NV * vsb, h->stream));
+    if (P.viscous) {
+        CKC(cudaMalloc(&h->B.V, 12 * vsb));
+        CKC(cudaMemsetAsync(h->B.V, 0, 12 * vsb, h->stream));
+    }
+    CKC(cudaMalloc(&h->stage, (size_t)NV * N * sizeof(double)));
+    CKC(cudaMalloc(&h->diag_part, (size_t)diag_partial_size() * sizeof(double)));
+    CKC(cudaMalloc(&h->diag_out, 16 * sizeof(double)));
+    CKC(cudaMalloc(&h->B.err, sizeof(int)));
+    CKC(cudaMemsetAsync(h->B.err, 0, sizeof(int), h->stream));
+    CKC(cudaMallocHost(&h->h_err, sizeof(int)));
+    CKC(cudaMallocHost(&h->h_diag, 16 * sizeof(double)));
+    for (int d = 0; d < 3; d++)
+        for (int s = 0; s < 2; s++) {
+            const int bc = p->bc[d][s];
+            if (P.active[d] && (bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW)) {
+                const long long plane = (long long)n[(d == 0) ? 1 : 0] * n[(d == 2) ? 1 : 2];
+                CKC(cudaMalloc(&h->B.bd[2 * d + s], (size_t)NV * plane * sizeof(double)));
+            }
+        }
+    if (P.curv) {
+        CKC(cudaMalloc(&h->B.M, 10 * vsb));
+        double *X = nullptr, *Sraw = nullptr;
+        unsigned long long *smax = nullptr;
+        CKC(cudaMalloc(&X, (size_t)3 * N * sizeof(double)));
+        cudaError_t e = cudaMalloc(&Sraw, (size_t)10 * N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&smax, 3 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(X, coords, (size_t)3 * N * sizeof(double), cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(smax, 0, 3 * sizeof(unsigned long long), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->B.M, 0, 10 * vsb, h->stream);
+        if (e == cudaSuccess) {
+            double L[3] = {p->L[0], p->L[1], p->L[2]};
+            launch_metrics(P, X, L, Sraw, smax, h->B.M, h->stream);
+            e = cudaGetLastError();
+        }
+        unsigned long long hs[3] = {0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, smax, sizeof(hs), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(X);
+        if (Sraw) cudaFree(Sraw);
+        if (smax) cudaFree(smax);
+        if (e != cudaSuccess)
+            return fail(seterr(h, OSBLI_ECUDA, "metric set-up: %s", cudaGetErrorString(e)));
+        for (int d = 0; d < 3; d++) {
+            double v;
+            memcpy(&v, &hs[d], sizeof(v));
+            P.shat[d] = v;
+            if (!(v > 0.0) || !isfinite(v))
+                return fail(seterr(h, OSBLI_EINVAL, "degenerate grid: metric of direction %d is %g", d, v));
+        }
+    }
+    CKC(cudaStreamSynchronize(h->stream));
+    *out = h;
+    return OSBLI_OK;
+#undef CKC
+}
+
+extern "C" void osbli_destroy(osbli_t *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+extern "C" int osbli_set_boundary_data(osbli_t *h, int dir, int side, const double *prims)
+{
+    if (!h || !prims) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (dir < 0 || dir > 2 || side < 0 || side > 1) return seterr(h, OSBLI_EINVAL, "bad face");
+    double *dst = h->B.bd[2 * dir + side];
+    if (!dst) return seterr(h, OSBLI_EINVAL, "face (%d,%d) is not an active DIRICHLET/INFLOW face", dir, side);
+    const long long plane = (long long)h->P.n[(dir == 0) ? 1 : 0] * h->P.n[(dir == 2) ? 1 : 2];
+    CK(h, cudaMemcpyAsync(dst, prims, (size_t)NV * plane * sizeof(double), cudaMemcpyDefault, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->bdata_set[2 * dir + side] = true;
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_set_state(osbli_t *h, const double *U)
+{
+    if (!h || !U) return seterr(h, OSBLI_EINVAL, "null argument");
+    const long long N = npoints(h->P);
+    CK(h, cudaMemcpyAsync(h->stage, U, (size_t)NV * N * sizeof(double), cudaMemcpyDefault, h->stream));
+    launch_unpack(h->P, h->stage, h->B.U, NV, h->stream);
+    CK(h, cudaGetLastError());
+    h->state_set = true;
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_get_state(osbli_t *h, double *U)
+{
+    if (!h || !U) return seterr(h, OSBLI_EINVAL, "null argument");
+    const long long N = npoints(h->P);
+    launch_pack(h->P, h->B.U, h->stage, NV, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(U, h->stage, (size_t)NV * N * sizeof(double), cudaMemcpyDefault, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return OSBLI_OK;
+}
+
+static int check_faces(osbli *h)
+{
+    for (int f = 0; f < 6; f++)
+        if (h->B.bd[f] && !h->bdata_set[f])
+            return seterr(h, OSBLI_ESTATE, "face (%d,%d) needs osbli_set_boundary_data", f / 2, f % 2);
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_rk_step(osbli_t *h, int nsteps)
+{
+    if (!h) return seterr(h, OSBLI_EINVAL, "null handle");
+    if (nsteps < 0) return seterr(h, OSBLI_EINVAL, "nsteps < 0");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    int rc = check_faces(h);
+    if (rc != OSBLI_OK) return rc;
+    if (nsteps == 0) return OSBLI_OK;
+    if (!h->gexec) {
+        cudaGraph_t g = nullptr;
+        CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int launches = 0;
+        for (int s = 0; s < 3; s++) launches += launch_stage(h->P, h->B, s, h->stream);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return seterr(h, OSBLI_ECUDA, "graph capture: %s",
+                          cudaGetErrorString(le != cudaSuccess ? le : ce));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            h->gexec = nullptr;
+            return seterr(h, OSBLI_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+        }
+        h->launches_step = launches;
+    }
+    CK(h, cudaMemsetAsync(h->B.err, 0, sizeof(int), h->stream));
+    for (int i = 0; i < nsteps; i++) CK(h, cudaGraphLaunch(h->gexec, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_err, h->B.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (*h->h_err & 1) return seterr(h, OSBLI_ENONFINITE, "state became non-finite");
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_residual(osbli_t *h, double *R)
+{
+    if (!h || !R) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    int rc = check_faces(h);
+    if (rc != OSBLI_OK) return rc;
+    const long long N = npoints(h->P);
+    launch_residual(h->P, h->B, h->stream);
+    CK(h, cudaGetLastError());
+    launch_pack(h->P, h->B.R, h->stage, NV, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(R, h->stage, (size_t)NV * N * sizeof(double), cudaMemcpyDefault, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_diagnostics(osbli_t *h, double out[16])
+{
+    if (!h || !out) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    launch_diagnostics(h->P, h->B, h->diag_part, h->diag_out, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->h_diag, h->diag_out, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    memcpy(out, h->h_diag, 16 * sizeof(double));
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_launches_per_step(const osbli_t *h)
+{
+    if (!h) return 0;
+    if (h->launches_step) return h->launches_step;
+    // not captured yet: count the same sequence launch_stage enqueues
+    const Dev &P = h->P;
+    int per_stage = 1 /*prim*/ + 1 /*update*/;
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        per_stage += 2;   // ghost + convective direction
+        for (int s = 0; s < 2; s++) {
+            const int bc = P.bc[d][s];
+            if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;
+        }
+    }
+    if (P.viscous) per_stage++;
+    return 3 * per_stage;
+}
+
+extern "C" const char *osbli_last_error(const osbli_t *h)
+{
+    return h ? h->err : g_create_err;
+}

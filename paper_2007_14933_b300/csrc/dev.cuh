@@ -1,0 +1,115 @@
+// dev.cuh -- device-side data layout and per-point arithmetic of the residual / RK-stage path.
+//
+// Layout in HBM (all FP64, structure of arrays, x fastest):
+//   U, dU, R : [5][vs]  conserved state, RK register, residual, on the ghosted grid
+//              (n_d + 2*3 points per active direction, 1 per inactive one)
+//   W        : [8][vs]  per-node primitives (u, v, w, p, a, sqrt(rho), H, T)
+//   M        : [10][vs] curvilinear metrics: S~_d (normalised contravariant metric vector of
+//              direction d, 3 components each) and 1/Jinv   (curvilinear grids only)
+//   V        : [3][4][vs] viscous fluxes along each computational direction (interior nodes)
+// vs is the variable stride (>= padded node count, rounded up to 32 doubles = 256 B).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace osb {
+
+constexpr int NV = 5;
+constexpr int GH = 3;   // ghost width: WENO5/TENO5 stencil i-2..i+3 (Sec. 2.3-2.5)
+
+enum { W_U = 0, W_V, W_W, W_P, W_A, W_SR, W_H, W_T, NW };
+enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4 };
+
+struct Dev {
+    int n[3], g[3], np[3];
+    long long st[3];
+    long long ntot, vs;
+    int active[3];
+    int bc[3][2];
+    int scheme, viscous, curv;
+    double gamma, gm1, Re, Pr, Ma, ct, Tw, suth;
+    double gM2;        // gamma Ma^2
+    double kq;         // 1 / ((gamma-1) Ma^2 Pr Re)   (Eq. 4)
+    double fac[3];     // uniform grid: s_d / Jinv = 1/h_d
+    double shat[3];    // curvilinear grid: s_d = max |S_d|
+    double dt;
+};
+
+__host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, int j, int k)
+{
+    return ((long long)(k + P.g[2]) * P.np[1] + (j + P.g[1])) * P.np[0] + (i + P.g[0]);
+}
+
+// Cartesian unit frame of a direction: n = e_DIR, tangents t1, t2 with the same construction
+// rule as the general case (t1 = normalise(z x n) unless |n_z| >= 0.9, then normalise(n x x);
+// t2 = n x t1): x: (y, z); y: (-x, z); z: (y, -x).
+template <int DIR> struct Cart;
+template <> struct Cart<0> { static constexpr int T1 = 1, T2 = 2; static constexpr double S1 = 1.0, S2 = 1.0; };
+template <> struct Cart<1> { static constexpr int T1 = 0, T2 = 2; static constexpr double S1 = -1.0, S2 = 1.0; };
+template <> struct Cart<2> { static constexpr int T1 = 1, T2 = 0; static constexpr double S1 = 1.0, S2 = -1.0; };
+
+// Sutherland's law (Eq. 6); suth <= 0: constant viscosity 1.
+__device__ __forceinline__ double viscosity(const Dev &P, double T)
+{
+    if (P.suth <= 0.0) return 1.0;
+    return T * sqrt(T) * (1.0 + P.suth) / (T + P.suth);
+}
+
+// ------------------------------------------------------------------------------------------
+// 5th-order reconstruction at x_{i+1/2} from f0..f4 = f_{i-2..i+2}.
+// Candidates (Eq. 14, k = 3; the ENO coefficients of the cited Shu 1997 notes), Jiang-Shu
+// smoothness indicators (Eqs. 17-19, as printed), and
+//   WENO-JS weights (Eqs. 20-21, p = 2, eps = 1e-6), linear weights d = (3/10, 3/5, 1/10);
+//   TENO5 (Eqs. 23-27): gamma_r = (1 + tau5/(beta_r + 1e-16))^6, tau5 = |beta_0 - beta_2|,
+//   stencil r kept when gamma_r / sum(gamma) >= C_T, omega_r = d_r delta_r / sum d delta.
+// The three reciprocals 1/(beta_r + eps) come from one division of their product, and the
+// cut-off test is taken as gamma_r >= C_T * sum(gamma) (no division); both are algebraically
+// the paper's expressions.
+// ------------------------------------------------------------------------------------------
+template <int SCHEME, typename T>
+__device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
+{
+    const T c13_12 = T(13.0 / 12.0), q = T(0.25);
+    T a, b;
+    a = f2 - T(2) * f3 + f4;
+    b = T(3) * f2 - T(4) * f3 + f4;
+    const T b0 = c13_12 * a * a + q * b * b;
+    a = f1 - T(2) * f2 + f3;
+    b = f1 - f3;
+    const T b1 = c13_12 * a * a + q * b * b;
+    a = f0 - T(2) * f1 + f2;
+    b = f0 - T(4) * f1 + T(3) * f2;
+    const T b2 = c13_12 * a * a + q * b * b;
+
+    const T q0 = T(1.0 / 3.0) * f2 + T(5.0 / 6.0) * f3 - T(1.0 / 6.0) * f4;
+    const T q1 = -T(1.0 / 6.0) * f1 + T(5.0 / 6.0) * f2 + T(1.0 / 3.0) * f3;
+    const T q2 = T(1.0 / 3.0) * f0 - T(7.0 / 6.0) * f1 + T(11.0 / 6.0) * f2;
+
+    if (SCHEME == SCH_TENO5) {
+        const T eps = T(1e-16);
+        const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        const T tau = fabs(b0 - b2);
+        const T ip = T(1) / (e0 * e1 * e2);
+        T x0 = T(1) + tau * (ip * e1 * e2);
+        T x1 = T(1) + tau * (ip * e0 * e2);
+        T x2 = T(1) + tau * (ip * e0 * e1);
+        x0 = x0 * x0; x1 = x1 * x1; x2 = x2 * x2;
+        const T g0 = x0 * x0 * x0, g1 = x1 * x1 * x1, g2 = x2 * x2 * x2;
+        const T th = ct * (g0 + g1 + g2);
+        const bool k0 = g0 >= th, k1 = g1 >= th, k2 = g2 >= th;
+        const T w0 = k0 ? T(0.3) : T(0), w1 = k1 ? T(0.6) : T(0), w2 = k2 ? T(0.1) : T(0);
+        const T r = w0 * q0 + w1 * q1 + w2 * q2;
+        if (k0 && k1 && k2) return r;
+        return r / (w0 + w1 + w2);
+    } else {
+        const T eps = T(1e-6);
+        const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        const T ip = T(1) / (e0 * e1 * e2);
+        const T i0 = ip * e1 * e2, i1 = ip * e0 * e2, i2 = ip * e0 * e1;
+        const T a0 = T(0.3) * i0 * i0, a1 = T(0.6) * i1 * i1, a2 = T(0.1) * i2 * i2;
+        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    }
+}
+
+}  // namespace osb

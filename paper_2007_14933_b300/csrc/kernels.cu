@@ -1,0 +1,969 @@
+// kernels.cu -- sm_103a kernels of one RK stage: ghost fill, primitives, characteristic or
+// central convective flux differences, viscous fluxes and their divergence fused with the
+// low-storage RK register update, boundary nodes, metrics, diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dev.cuh"
+#include "launch.h"
+
+namespace osb {
+
+// 2N-storage RK3 of Williamson (the paper's Eqs. 36-38 leave A_i, B_i to the cited scheme).
+__constant__ double c_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+__constant__ double c_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+static int g_num_sms = 0;
+static int grid_for(long long work, int threads)
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    long long blocks = (work + threads - 1) / threads;
+    long long cap = (long long)g_num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+// ------------------------------------------------------------------------------------------
+// compact [nvar][nz][ny][nx] <-> ghosted layout
+// ------------------------------------------------------------------------------------------
+__global__ void k_unpack(Dev P, const double *__restrict__ src, double *__restrict__ dst, int nvar)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * nvar;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / N);
+        const long long r = t - v * N;
+        const int i = (int)(r % P.n[0]);
+        const long long q = r / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        dst[v * P.vs + node_index(P, i, j, k)] = src[t];
+    }
+}
+
+__global__ void k_pack(Dev P, const double *__restrict__ src, double *__restrict__ dst, int nvar)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * nvar;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / N);
+        const long long r = t - v * N;
+        const int i = (int)(r % P.n[0]);
+        const long long q = r / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        dst[t] = src[v * P.vs + node_index(P, i, j, k)];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Ghost fill of one direction, both sides (Sec. 3.1.3).  Lines run over the full padded extent
+// of the two other directions, so edges take values already filled by earlier directions.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void set_prim(const Dev &P, double *U, long long id, double rho,
+                                         double u, double v, double w, double p)
+{
+    U[0 * P.vs + id] = rho;
+    U[1 * P.vs + id] = rho * u;
+    U[2 * P.vs + id] = rho * v;
+    U[3 * P.vs + id] = rho * w;
+    U[4 * P.vs + id] = p / P.gm1 + 0.5 * rho * (u * u + v * v + w * w);
+}
+
+__device__ __forceinline__ void cons_prim(const Dev &P, const double *U, long long id,
+                                          double &rho, double &u, double &v, double &w, double &p)
+{
+    rho = U[0 * P.vs + id];
+    u = U[1 * P.vs + id] / rho;
+    v = U[2 * P.vs + id] / rho;
+    w = U[3 * P.vs + id] / rho;
+    p = P.gm1 * (U[4 * P.vs + id] - 0.5 * rho * (u * u + v * v + w * w));
+}
+
+__device__ __forceinline__ long long face_plane_index(const Dev &P, int d, int ca, int cb)
+{
+    const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+    const int na = P.n[da], nb = P.n[db];
+    ca = ca < 0 ? 0 : (ca >= na ? na - 1 : ca);
+    cb = cb < 0 ? 0 : (cb >= nb ? nb - 1 : cb);
+    return (long long)cb * na + ca;
+}
+
+__global__ void k_ghost(Dev P, double *__restrict__ U, int d, const double *__restrict__ bd0,
+                        const double *__restrict__ bd1)
+{
+    const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+    const long long npa = P.np[da], npb = P.np[db];
+    const long long tot = 2LL * GH * npa * npb;
+    const int n = P.n[d];
+    const long long plane = (long long)P.n[da] * P.n[db];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ia = (int)(t % npa);
+        long long q = t / npa;
+        const int ib = (int)(q % npb);
+        q /= npb;
+        const int gi = (int)(q % GH) + 1;
+        const int s = (int)(q / GH);
+        const int bc = P.bc[d][s];
+        int ii[3];
+        ii[da] = ia - P.g[da];
+        ii[db] = ib - P.g[db];
+        ii[d] = (s == 0) ? -gi : n - 1 + gi;
+        const long long idg = node_index(P, ii[0], ii[1], ii[2]);
+        if (bc == BC_PERIODIC || bc == BC_ZEROGRAD) {
+            if (bc == BC_PERIODIC) ii[d] = (s == 0) ? n - gi : gi - 1;
+            else ii[d] = (s == 0) ? 0 : n - 1;
+            const long long src = node_index(P, ii[0], ii[1], ii[2]);
+#pragma unroll
+            for (int v = 0; v < NV; v++) U[v * P.vs + idg] = U[v * P.vs + src];
+        } else if (bc == BC_WALL) {
+            // Eqs. 43-46: T_{-i} = (i+1) T_w - i T_1, rho_{-i} = M^2 gamma p_w / T_{-i},
+            // velocity reflected from interior node i, pressure = wall pressure p_w.
+            double r0, u0, v0, w0, pw, r1, u1, v1, w1, p1, rm, um, vm, wm, pm;
+            ii[d] = (s == 0) ? 0 : n - 1;
+            cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), r0, u0, v0, w0, pw);
+            ii[d] = (s == 0) ? 1 : n - 2;
+            cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), r1, u1, v1, w1, p1);
+            ii[d] = (s == 0) ? gi : n - 1 - gi;
+            cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), rm, um, vm, wm, pm);
+            const double T1 = P.gM2 * p1 / r1;
+            const double Tg = (gi + 1) * P.Tw - gi * T1;
+            const double rg = P.Ma * P.Ma * P.gamma * pw / Tg;
+            set_prim(P, U, idg, rg, -um, -vm, -wm, pw);
+        } else if (bc == BC_DIRICHLET) {
+            const double *bd = s ? bd1 : bd0;
+            const long long pid = face_plane_index(P, d, ii[da], ii[db]);
+            set_prim(P, U, idg, bd[0 * plane + pid], bd[1 * plane + pid], bd[2 * plane + pid],
+                     bd[3 * plane + pid], bd[4 * plane + pid]);
+        } else if (bc == BC_INFLOW) {
+            const double *bd = s ? bd1 : bd0;
+            const long long pid = face_plane_index(P, d, ii[da], ii[db]);
+            double r1, u1, v1, w1, p1;
+            ii[d] = (s == 0) ? 1 : n - 2;
+            cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), r1, u1, v1, w1, p1);
+            const double T = bd[4 * plane + pid];
+            set_prim(P, U, idg, P.gM2 * p1 / T, bd[1 * plane + pid], bd[2 * plane + pid],
+                     bd[3 * plane + pid], p1);
+        }
+    }
+}
+
+// After-stage boundary nodes: wall (rho u = 0, rho E = rho_w T_w / (M^2 gamma (gamma-1)),
+// Eq. 41), Dirichlet and inflow nodes.
+__global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const double *__restrict__ bd)
+{
+    const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+    const long long plane = (long long)P.n[da] * P.n[db];
+    const int n = P.n[d];
+    const int bc = P.bc[d][s];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
+         t += (long long)gridDim.x * blockDim.x) {
+        int ii[3];
+        ii[da] = (int)(t % P.n[da]);
+        ii[db] = (int)(t / P.n[da]);
+        ii[d] = (s == 0) ? 0 : n - 1;
+        const long long idb = node_index(P, ii[0], ii[1], ii[2]);
+        if (bc == BC_WALL) {
+            const double rw = U[idb];
+            U[1 * P.vs + idb] = 0.0;
+            U[2 * P.vs + idb] = 0.0;
+            U[3 * P.vs + idb] = 0.0;
+            U[4 * P.vs + idb] = rw * P.Tw / (P.Ma * P.Ma * P.gamma * P.gm1);
+        } else if (bc == BC_DIRICHLET) {
+            set_prim(P, U, idb, bd[0 * plane + t], bd[1 * plane + t], bd[2 * plane + t],
+                     bd[3 * plane + t], bd[4 * plane + t]);
+        } else if (bc == BC_INFLOW) {
+            double r1, u1, v1, w1, p1;
+            ii[d] = (s == 0) ? 1 : n - 2;
+            cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), r1, u1, v1, w1, p1);
+            set_prim(P, U, idb, P.gM2 * p1 / bd[4 * plane + t], bd[1 * plane + t],
+                     bd[2 * plane + t], bd[3 * plane + t], p1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Primitives per node (Eqs. 5-7): u, v, w, p, a, sqrt(rho), H, T on every padded node.
+// ------------------------------------------------------------------------------------------
+__global__ void k_prim(Dev P, const double *__restrict__ U, double *__restrict__ W)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double rho = U[0 * P.vs + t];
+        const double ir = 1.0 / rho;
+        const double u = U[1 * P.vs + t] * ir, v = U[2 * P.vs + t] * ir, w = U[3 * P.vs + t] * ir;
+        const double E = U[4 * P.vs + t];
+        const double p = P.gm1 * (E - 0.5 * rho * (u * u + v * v + w * w));
+        W[W_U * P.vs + t] = u;
+        W[W_V * P.vs + t] = v;
+        W[W_W * P.vs + t] = w;
+        W[W_P * P.vs + t] = p;
+        W[W_A * P.vs + t] = sqrt(P.gamma * p * ir);
+        W[W_SR * P.vs + t] = sqrt(rho);
+        W[W_H * P.vs + t] = (E + p) * ir;
+        W[W_T * P.vs + t] = P.gM2 * p * ir;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Characteristic interface flux (Sec. 2.2 algorithm, steps 2(a)-(f)) between node m and
+// node m + st along DIR: Roe average, eigenvectors along the interface normal, projection of
+// U_k and the contravariant flux F_k of the six stencil nodes, LLF split with
+// alpha_j = max_k |lambda_j(k)|, WENO/TENO reconstruction of g+ and g-, back-projection.
+// The left eigenvectors are applied in factored form (l_j . w built from u.w, n.w, t.w).
+// ------------------------------------------------------------------------------------------
+template <int DIR, bool CURV>
+struct Frame {
+    double n[3], t1[3], t2[3];
+    __device__ __forceinline__ double dn(double x, double y, double z) const
+    {
+        if (CURV) return n[0] * x + n[1] * y + n[2] * z;
+        const double w[3] = {x, y, z};
+        return w[DIR];
+    }
+    __device__ __forceinline__ double dt1(double x, double y, double z) const
+    {
+        if (CURV) return t1[0] * x + t1[1] * y + t1[2] * z;
+        const double w[3] = {x, y, z};
+        return Cart<DIR>::S1 * w[Cart<DIR>::T1];
+    }
+    __device__ __forceinline__ double dt2(double x, double y, double z) const
+    {
+        if (CURV) return t2[0] * x + t2[1] * y + t2[2] * z;
+        const double w[3] = {x, y, z};
+        return Cart<DIR>::S2 * w[Cart<DIR>::T2];
+    }
+};
+
+template <int DIR, int SCHEME, bool CURV>
+__device__ __forceinline__ void interface_flux(const Dev &P, const double *__restrict__ U,
+                                               const double *__restrict__ W,
+                                               const double *__restrict__ M, long long m,
+                                               long long st, double Fh[NV])
+{
+    const long long vs = P.vs;
+    const long long mr = m + st;
+    // (a) Roe average
+    const double sl = W[W_SR * vs + m], sr = W[W_SR * vs + mr];
+    const double inv = 1.0 / (sl + sr);
+    const double u0 = (sl * W[W_U * vs + m] + sr * W[W_U * vs + mr]) * inv;
+    const double u1 = (sl * W[W_V * vs + m] + sr * W[W_V * vs + mr]) * inv;
+    const double u2 = (sl * W[W_W * vs + m] + sr * W[W_W * vs + mr]) * inv;
+    const double H = (sl * W[W_H * vs + m] + sr * W[W_H * vs + mr]) * inv;
+    const double q2 = u0 * u0 + u1 * u1 + u2 * u2;
+    const double c2 = P.gm1 * (H - 0.5 * q2);
+    const double ia = rsqrt(c2);
+    const double a = c2 * ia;
+
+    Frame<DIR, CURV> fr;
+    if (CURV) {
+        double nv[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) nv[c] = 0.5 * (M[(DIR * 3 + c) * vs + m] + M[(DIR * 3 + c) * vs + mr]);
+        const double inm = rsqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+#pragma unroll
+        for (int c = 0; c < 3; c++) fr.n[c] = nv[c] * inm;
+        if (fabs(fr.n[2]) < 0.9) {
+            const double im = rsqrt(fr.n[0] * fr.n[0] + fr.n[1] * fr.n[1]);
+            fr.t1[0] = -fr.n[1] * im; fr.t1[1] = fr.n[0] * im; fr.t1[2] = 0.0;
+        } else {
+            const double im = rsqrt(fr.n[2] * fr.n[2] + fr.n[1] * fr.n[1]);
+            fr.t1[0] = 0.0; fr.t1[1] = fr.n[2] * im; fr.t1[2] = -fr.n[1] * im;
+        }
+        fr.t2[0] = fr.n[1] * fr.t1[2] - fr.n[2] * fr.t1[1];
+        fr.t2[1] = fr.n[2] * fr.t1[0] - fr.n[0] * fr.t1[2];
+        fr.t2[2] = fr.n[0] * fr.t1[1] - fr.n[1] * fr.t1[0];
+    }
+    const double un = fr.dn(u0, u1, u2);
+    const double ut1 = fr.dt1(u0, u1, u2);
+    const double ut2 = fr.dt2(u0, u1, u2);
+    const double b1 = P.gm1 * ia * ia;
+    const double b2 = 0.5 * b1 * q2;
+
+    // (d) wave speeds over the six stencil nodes
+    double al0 = 0.0, al1 = 0.0, al4 = 0.0;
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const long long id = m + (s - 2) * st;
+        double uns, cs;
+        if (CURV) {
+            const double Sx = M[(DIR * 3 + 0) * vs + id], Sy = M[(DIR * 3 + 1) * vs + id],
+                         Sz = M[(DIR * 3 + 2) * vs + id];
+            uns = Sx * W[W_U * vs + id] + Sy * W[W_V * vs + id] + Sz * W[W_W * vs + id];
+            cs = sqrt(Sx * Sx + Sy * Sy + Sz * Sz) * W[W_A * vs + id];
+        } else {
+            uns = W[(W_U + DIR) * vs + id];
+            cs = W[W_A * vs + id];
+        }
+        al0 = fmax(al0, fabs(uns - cs));
+        al1 = fmax(al1, fabs(uns));
+        al4 = fmax(al4, fabs(uns + cs));
+    }
+    const double h0 = 0.5 * al0, h1 = 0.5 * al1, h4 = 0.5 * al4;
+
+    // (c) projection and (d) splitting
+    double gp[NV][5], gm[NV][5];
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const long long id = m + (s - 2) * st;
+        const double r = U[0 * vs + id], mx = U[1 * vs + id], my = U[2 * vs + id],
+                     mz = U[3 * vs + id], E = U[4 * vs + id];
+        const double p = W[W_P * vs + id];
+        double F[NV];
+        if (CURV) {
+            const double Sx = M[(DIR * 3 + 0) * vs + id], Sy = M[(DIR * 3 + 1) * vs + id],
+                         Sz = M[(DIR * 3 + 2) * vs + id];
+            const double uns = Sx * W[W_U * vs + id] + Sy * W[W_V * vs + id] + Sz * W[W_W * vs + id];
+            F[0] = r * uns;
+            F[1] = mx * uns + Sx * p;
+            F[2] = my * uns + Sy * p;
+            F[3] = mz * uns + Sz * p;
+            F[4] = (E + p) * uns;
+        } else {
+            const double uns = W[(W_U + DIR) * vs + id];
+            F[0] = r * uns;
+            F[1] = mx * uns;
+            F[2] = my * uns;
+            F[3] = mz * uns;
+            F[1 + DIR] += p;
+            F[4] = (E + p) * uns;
+        }
+        double Vc[NV], Gc[NV];
+        {
+            const double um = u0 * mx + u1 * my + u2 * mz;
+            const double A = b2 * r + b1 * (E - um);
+            const double B = (un * r - fr.dn(mx, my, mz)) * ia;
+            Vc[0] = 0.5 * (A + B);
+            Vc[4] = 0.5 * (A - B);
+            Vc[1] = r - A;
+            Vc[2] = fr.dt1(mx, my, mz) - ut1 * r;
+            Vc[3] = fr.dt2(mx, my, mz) - ut2 * r;
+        }
+        {
+            const double um = u0 * F[1] + u1 * F[2] + u2 * F[3];
+            const double A = b2 * F[0] + b1 * (F[4] - um);
+            const double B = (un * F[0] - fr.dn(F[1], F[2], F[3])) * ia;
+            Gc[0] = 0.5 * (A + B);
+            Gc[4] = 0.5 * (A - B);
+            Gc[1] = F[0] - A;
+            Gc[2] = fr.dt1(F[1], F[2], F[3]) - ut1 * F[0];
+            Gc[3] = fr.dt2(F[1], F[2], F[3]) - ut2 * F[0];
+        }
+        const double hh[NV] = {h0, h1, h1, h1, h4};
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            if (s < 5) gp[j][s] = fma(hh[j], Vc[j], 0.5 * Gc[j]);
+            if (s > 0) gm[j][s - 1] = fma(-hh[j], Vc[j], 0.5 * Gc[j]);
+        }
+    }
+    // (e) reconstruction
+    double g[NV];
+    const double ct = P.ct;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        g[j] = recon5<SCHEME, double>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
+               recon5<SCHEME, double>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+    }
+    // (f) back-projection F = R g
+    const double s04 = g[0] + g[4], d40 = g[4] - g[0];
+    const double sm = s04 + g[1];
+    Fh[0] = sm;
+    const double uu[3] = {u0, u1, u2};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double f = uu[c] * sm;
+        if (CURV) {
+            f += a * fr.n[c] * d40 + fr.t1[c] * g[2] + fr.t2[c] * g[3];
+        } else {
+            if (c == DIR) f += a * d40;
+            if (c == Cart<DIR>::T1) f += Cart<DIR>::S1 * g[2];
+            if (c == Cart<DIR>::T2) f += Cart<DIR>::S2 * g[3];
+        }
+        Fh[1 + c] = f;
+    }
+    Fh[4] = H * s04 + a * un * d40 + 0.5 * q2 * g[1] + ut1 * g[2] + ut2 * g[3];
+}
+
+// Lines along DIR: thread (a, b) owns one line of the two cross directions and marches over a
+// chunk of nodes, carrying the left interface flux in registers; R[node] = -fac (F_{m+1/2} -
+// F_{m-1/2}) (Eq. 10, strong conservation form), first direction writes, later ones add.
+template <int DIR, int SCHEME, bool CURV>
+__global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restrict__ U,
+                                                   const double *__restrict__ W,
+                                                   const double *__restrict__ M,
+                                                   double *__restrict__ R, int accumulate, int chunk)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    if (a >= P.n[DA] || b >= P.n[DB]) return;
+    const int s0 = blockIdx.z * chunk;
+    const int s1 = min(s0 + chunk, P.n[DIR]);
+    int ii[3];
+    ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
+    const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const long long st = P.st[DIR];
+    double Fm[NV];
+    interface_flux<DIR, SCHEME, CURV>(P, U, W, M, base + (long long)(s0 - 1) * st, st, Fm);
+    for (int m = s0; m < s1; m++) {
+        const long long id = base + (long long)m * st;
+        double Fp[NV];
+        interface_flux<DIR, SCHEME, CURV>(P, U, W, M, id, st, Fp);
+        const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : P.fac[DIR];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const double r = -fac * (Fp[v] - Fm[v]);
+            R[v * P.vs + id] = accumulate ? R[v * P.vs + id] + r : r;
+            Fm[v] = Fp[v];
+        }
+    }
+}
+
+// Central 4th-order convective derivative of the contravariant flux (Sec. 2.6) with the
+// Ekaterinaris one-sided closures at the ends of non-periodic lines.
+template <int DIR, bool CURV>
+__device__ __forceinline__ void node_flux(const Dev &P, const double *__restrict__ U,
+                                          const double *__restrict__ W,
+                                          const double *__restrict__ M, long long id, double F[NV])
+{
+    const long long vs = P.vs;
+    const double r = U[0 * vs + id], p = W[W_P * vs + id];
+    if (CURV) {
+        const double Sx = M[(DIR * 3 + 0) * vs + id], Sy = M[(DIR * 3 + 1) * vs + id],
+                     Sz = M[(DIR * 3 + 2) * vs + id];
+        const double uns = Sx * W[W_U * vs + id] + Sy * W[W_V * vs + id] + Sz * W[W_W * vs + id];
+        F[0] = r * uns;
+        F[1] = U[1 * vs + id] * uns + Sx * p;
+        F[2] = U[2 * vs + id] * uns + Sy * p;
+        F[3] = U[3 * vs + id] * uns + Sz * p;
+        F[4] = (U[4 * vs + id] + p) * uns;
+    } else {
+        const double uns = W[(W_U + DIR) * vs + id];
+        F[0] = r * uns;
+        F[1] = U[1 * vs + id] * uns;
+        F[2] = U[2 * vs + id] * uns;
+        F[3] = U[3 * vs + id] * uns;
+        F[1 + DIR] += p;
+        F[4] = (U[4 * vs + id] + p) * uns;
+    }
+}
+
+template <int DIR, bool CURV>
+__global__ void __launch_bounds__(128) k_conv_central(Dev P, const double *__restrict__ U,
+                                                      const double *__restrict__ W,
+                                                      const double *__restrict__ M,
+                                                      double *__restrict__ R, int accumulate, int chunk)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    if (a >= P.n[DA] || b >= P.n[DB]) return;
+    const int n = P.n[DIR];
+    const int s0 = blockIdx.z * chunk;
+    const int s1 = min(s0 + chunk, n);
+    int ii[3];
+    ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
+    const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const long long st = P.st[DIR];
+    const bool per = P.bc[DIR][0] == BC_PERIODIC;
+    for (int m = s0; m < s1; m++) {
+        const long long id = base + (long long)m * st;
+        double D[NV];
+        if (per || (m >= 2 && m <= n - 3)) {
+            double f0[NV], f1[NV], f3[NV], f4[NV];
+            node_flux<DIR, CURV>(P, U, W, M, id - 2 * st, f0);
+            node_flux<DIR, CURV>(P, U, W, M, id - st, f1);
+            node_flux<DIR, CURV>(P, U, W, M, id + st, f3);
+            node_flux<DIR, CURV>(P, U, W, M, id + 2 * st, f4);
+#pragma unroll
+            for (int v = 0; v < NV; v++) D[v] = (f0[v] - 8.0 * f1[v] + 8.0 * f3[v] - f4[v]) / 12.0;
+        } else {
+            const int lo = (m < 2) ? 0 : n - 5;
+            double f[5][NV];
+#pragma unroll
+            for (int q = 0; q < 5; q++) node_flux<DIR, CURV>(P, U, W, M, base + (long long)(lo + q) * st, f[q]);
+            const int r = m - lo;
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                double s;
+                if (r == 0) s = -25.0 * f[0][v] + 48.0 * f[1][v] - 36.0 * f[2][v] + 16.0 * f[3][v] - 3.0 * f[4][v];
+                else if (r == 1) s = -3.0 * f[0][v] - 10.0 * f[1][v] + 18.0 * f[2][v] - 6.0 * f[3][v] + f[4][v];
+                else if (r == 3) s = -f[0][v] + 6.0 * f[1][v] - 18.0 * f[2][v] + 10.0 * f[3][v] + 3.0 * f[4][v];
+                else s = 3.0 * f[0][v] - 16.0 * f[1][v] + 36.0 * f[2][v] - 48.0 * f[3][v] + 25.0 * f[4][v];
+                D[v] = s / 12.0;
+            }
+        }
+        const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : P.fac[DIR];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const double r = -fac * D[v];
+            R[v * P.vs + id] = accumulate ? R[v * P.vs + id] + r : r;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// 4th-order first derivative along a line at interior index ie (Sec. 2.6, Eqs. 28, 30-33).
+// Periodic lines read ghost-inclusive or wrapped neighbours through f; non-periodic ends use
+// the one-sided closures.
+// ------------------------------------------------------------------------------------------
+template <typename Fetch>
+__device__ __forceinline__ double deriv_line(Fetch f, int ie, int n, bool per)
+{
+    if (per || (ie >= 2 && ie <= n - 3))
+        return (f(ie - 2) - 8.0 * f(ie - 1) + 8.0 * f(ie + 1) - f(ie + 2)) / 12.0;
+    if (ie == 0) return (-25.0 * f(0) + 48.0 * f(1) - 36.0 * f(2) + 16.0 * f(3) - 3.0 * f(4)) / 12.0;
+    if (ie == 1) return (-3.0 * f(0) - 10.0 * f(1) + 18.0 * f(2) - 6.0 * f(3) + f(4)) / 12.0;
+    if (ie == n - 2)
+        return (-f(n - 5) + 6.0 * f(n - 4) - 18.0 * f(n - 3) + 10.0 * f(n - 2) + 3.0 * f(n - 1)) / 12.0;
+    return (3.0 * f(n - 5) - 16.0 * f(n - 4) + 36.0 * f(n - 3) - 48.0 * f(n - 2) + 25.0 * f(n - 1)) / 12.0;
+}
+
+// Viscous fluxes (Eqs. 2-5) at interior nodes: V[d] = (S~_d . tau_{i.}, S~_d . (u_i tau_{i.} - q))
+template <bool CURV>
+__global__ void __launch_bounds__(128) k_visc_flux(Dev P, const double *__restrict__ W,
+                                                   const double *__restrict__ M, double *__restrict__ V)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const long long vs = P.vs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        const int ijk[3] = {i, j, k};
+        const long long id = node_index(P, i, j, k);
+        double dxi[3][4];
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+#pragma unroll
+            for (int v = 0; v < 4; v++) dxi[e][v] = 0.0;
+            if (!P.active[e]) continue;
+            const int ie = ijk[e];
+            const long long st = P.st[e];
+            const bool per = P.bc[e][0] == BC_PERIODIC;
+            const int widx[4] = {W_U, W_V, W_W, W_T};
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const double *f = W + widx[v] * vs + id;
+                dxi[e][v] = deriv_line([&](int s) { return f[(long long)(s - ie) * st]; }, ie, P.n[e], per);
+            }
+        }
+        double gr[4][3];
+        if (CURV) {
+            const double jr = M[9 * vs + id];
+#pragma unroll
+            for (int v = 0; v < 4; v++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int e = 0; e < 3; e++) s += P.shat[e] * jr * M[(e * 3 + c) * vs + id] * dxi[e][v];
+                    gr[v][c] = s;
+                }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; v++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) gr[v][c] = P.fac[c] * dxi[c][v];
+        }
+        const double T = W[W_T * vs + id];
+        const double mu = viscosity(P, T);
+        const double mr = mu / P.Re;
+        const double div = gr[0][0] + gr[1][1] + gr[2][2];
+        double tau[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+                tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? (2.0 / 3.0) * div : 0.0));
+        const double kq = mu * P.kq;
+        const double uu[3] = {W[W_U * vs + id], W[W_V * vs + id], W[W_W * vs + id]};
+        double e4[3];
+#pragma unroll
+        for (int b = 0; b < 3; b++) e4[b] = uu[0] * tau[0][b] + uu[1] * tau[1][b] + uu[2] * tau[2][b] + kq * gr[3][b];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!P.active[d]) continue;
+            double out[4];
+            if (CURV) {
+                const double S0 = M[(d * 3 + 0) * vs + id], S1 = M[(d * 3 + 1) * vs + id],
+                             S2 = M[(d * 3 + 2) * vs + id];
+#pragma unroll
+                for (int a = 0; a < 3; a++) out[a] = S0 * tau[a][0] + S1 * tau[a][1] + S2 * tau[a][2];
+                out[3] = S0 * e4[0] + S1 * e4[1] + S2 * e4[2];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; a++) out[a] = tau[a][d];
+                out[3] = e4[d];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) V[(d * 4 + c) * vs + id] = out[c];
+        }
+    }
+}
+
+// Viscous divergence (flux form) + RK register update (Eqs. 36-37), or residual output.
+// MODE 0: RK stage (STAGE selects A_i/B_i; stage 0 has dU^(0) = 0); MODE 1: R_total -> R.
+template <int MODE, int STAGE, bool VISC, bool CURV>
+__global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, double *__restrict__ dU,
+                                                double *__restrict__ R, const double *__restrict__ V,
+                                                const double *__restrict__ M, int *__restrict__ err)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const long long vs = P.vs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        const int ijk[3] = {i, j, k};
+        const long long id = node_index(P, i, j, k);
+        double r[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) r[v] = R[v * vs + id];
+        if (VISC) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (!P.active[d]) continue;
+                const int ie = ijk[d], n = P.n[d];
+                const long long st = P.st[d];
+                const bool per = P.bc[d][0] == BC_PERIODIC;
+                const double fac = CURV ? P.shat[d] * M[9 * vs + id] : P.fac[d];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const double *f = V + (d * 4 + c) * vs + id;
+                    const double D = deriv_line([&](int s) {
+                        int w = s;
+                        if (per) { w = s % n; if (w < 0) w += n; }
+                        return f[(long long)(w - ie) * st];
+                    }, ie, n, per);
+                    r[1 + c] += fac * D;
+                }
+            }
+        }
+        if (MODE == 1) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) R[v * vs + id] = r[v];
+            continue;
+        }
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            double du = P.dt * r[v];
+            if (STAGE > 0) du = c_rkA[STAGE] * dU[v * vs + id] + du;
+            dU[v * vs + id] = du;
+            const double un = U[v * vs + id] + c_rkB[STAGE] * du;
+            U[v * vs + id] = un;
+            bad |= !isfinite(un);
+        }
+        if (bad) atomicOr(err, 1);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Metric terms (Sec. 2.7): coordinate derivatives by the 4th-order central / one-sided
+// operators (periodic directions unwrap by the period along their own axis), S_d by cross
+// products, Jinv = X_0 . S_0.  Raw values at interior nodes, then scaled and spread to ghosts.
+// ------------------------------------------------------------------------------------------
+__global__ void k_metric_raw(Dev P, const double *__restrict__ X, double Lp0, double Lp1, double Lp2,
+                             double *__restrict__ Sraw, unsigned long long *__restrict__ smax)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const double Lp[3] = {Lp0, Lp1, Lp2};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        const int ijk[3] = {i, j, k};
+        double Xd[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!P.active[d]) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) Xd[d][c] = (c == d) ? 1.0 : 0.0;
+                continue;
+            }
+            const int n = P.n[d];
+            const bool per = P.bc[d][0] == BC_PERIODIC;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                auto f = [&](int s) {
+                    int w = s, sh = 0;
+                    if (per) {
+                        w = s % n;
+                        if (w < 0) w += n;
+                        sh = (s - w) / n;
+                    }
+                    int jj[3] = {ijk[0], ijk[1], ijk[2]};
+                    jj[d] = w;
+                    const long long o = ((long long)jj[2] * P.n[1] + jj[1]) * P.n[0] + jj[0];
+                    return X[c * N + o] + (c == d ? sh * Lp[d] : 0.0);
+                };
+                Xd[d][c] = deriv_line(f, ijk[d], n, per);
+            }
+        }
+        double S[3][3];
+        // S_0 = X_1 x X_2, S_1 = X_2 x X_0, S_2 = X_0 x X_1
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double *A = Xd[(d + 1) % 3], *B = Xd[(d + 2) % 3];
+            S[d][0] = A[1] * B[2] - A[2] * B[1];
+            S[d][1] = A[2] * B[0] - A[0] * B[2];
+            S[d][2] = A[0] * B[1] - A[1] * B[0];
+        }
+        const double Jv = Xd[0][0] * S[0][0] + Xd[0][1] * S[0][1] + Xd[0][2] * S[0][2];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) Sraw[(d * 3 + c) * N + t] = S[d][c];
+            const double mag = sqrt(S[d][0] * S[d][0] + S[d][1] * S[d][1] + S[d][2] * S[d][2]);
+            atomicMax(&smax[d], (unsigned long long)__double_as_longlong(mag));   // mag >= 0
+        }
+        Sraw[9 * N + t] = Jv;
+    }
+}
+
+__global__ void k_metric_spread(Dev P, const double *__restrict__ Sraw,
+                                const unsigned long long *__restrict__ smax, double *__restrict__ M)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    double sh[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) sh[d] = __longlong_as_double((long long)smax[d]);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(t % P.np[0]);
+        const long long q = t / P.np[0];
+        const int pj = (int)(q % P.np[1]);
+        const int pk = (int)(q / P.np[1]);
+        int c3[3] = {pi - P.g[0], pj - P.g[1], pk - P.g[2]};
+        // ghost nodes take the metric of the wrapped (periodic) or mirrored (non-periodic) node
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const int n = P.n[d];
+            int x = c3[d];
+            if (x < 0 || x >= n) {
+                if (P.bc[d][0] == BC_PERIODIC) { x %= n; if (x < 0) x += n; }
+                else x = (x < 0) ? -x : 2 * (n - 1) - x;
+            }
+            c3[d] = x;
+        }
+        const long long src = ((long long)c3[2] * P.n[1] + c3[1]) * P.n[0] + c3[0];
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) M[(d * 3 + c) * P.vs + t] = Sraw[(d * 3 + c) * N + src] / sh[d];
+        M[9 * P.vs + t] = 1.0 / Sraw[9 * N + src];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Diagnostics: fixed-partition block partial sums, then one block in fixed order.
+// ------------------------------------------------------------------------------------------
+constexpr int DIAG_BLOCKS = 256, DIAG_THREADS = 256, NDIAG = 9;
+
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const double *__restrict__ U,
+                                                               double *__restrict__ part)
+{
+    __shared__ double sh[NDIAG][DIAG_THREADS];
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        const long long id = node_index(P, i, j, k);
+        double rho, u, v, w, p;
+        cons_prim(P, U, id, rho, u, v, w, p);
+#pragma unroll
+        for (int c = 0; c < NV; c++) acc[c] += U[c * P.vs + id];
+        const double q2 = u * u + v * v + w * w;
+        acc[5] += 0.5 * rho * q2;
+        acc[6] = fmax(acc[6], sqrt(q2 / (P.gamma * p / rho)));
+        acc[7] = fmin(acc[7], rho);
+        acc[8] = fmin(acc[8], p);
+    }
+#pragma unroll
+    for (int c = 0; c < NDIAG; c++) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int off = DIAG_THREADS / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + off];
+            sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][threadIdx.x + off]);
+            sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][threadIdx.x + off]);
+            sh[8][threadIdx.x] = fmin(sh[8][threadIdx.x], sh[8][threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < NDIAG; c++) part[c * DIAG_BLOCKS + blockIdx.x] = sh[c][0];
+}
+
+__global__ void k_diag_final(const double *__restrict__ part, double *__restrict__ out, long long N)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+    for (int b = 0; b < DIAG_BLOCKS; b++) {
+        for (int c = 0; c < 6; c++) acc[c] += part[c * DIAG_BLOCKS + b];
+        acc[6] = fmax(acc[6], part[6 * DIAG_BLOCKS + b]);
+        acc[7] = fmin(acc[7], part[7 * DIAG_BLOCKS + b]);
+        acc[8] = fmin(acc[8], part[8 * DIAG_BLOCKS + b]);
+    }
+    for (int c = 0; c < 16; c++) out[c] = 0.0;
+    for (int c = 0; c < NV; c++) out[c] = acc[c];
+    out[5] = acc[5] / (double)N;
+    out[6] = acc[6];
+    out[7] = acc[7];
+    out[8] = acc[8];
+}
+
+// ==========================================================================================
+// host-side launchers
+// ==========================================================================================
+void launch_unpack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s)
+{
+    long long work = (long long)P.n[0] * P.n[1] * P.n[2] * nvar;
+    k_unpack<<<grid_for(work, 256), 256, 0, s>>>(P, src, dst, nvar);
+}
+
+void launch_pack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s)
+{
+    long long work = (long long)P.n[0] * P.n[1] * P.n[2] * nvar;
+    k_pack<<<grid_for(work, 256), 256, 0, s>>>(P, src, dst, nvar);
+}
+
+void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sraw,
+                    unsigned long long *smax, double *M, cudaStream_t s)
+{
+    long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    k_metric_raw<<<grid_for(N, 128), 128, 0, s>>>(P, X, L[0], L[1], L[2], Sraw, smax);
+    k_metric_spread<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, Sraw, smax, M);
+}
+
+static int conv_chunk(const Dev &P, int d)
+{
+    const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+    long long lines = (long long)P.n[da] * P.n[db];
+    int chunk = 32;
+    while (chunk > 4 && lines * ((P.n[d] + chunk - 1) / chunk) < 148LL * 256) chunk >>= 1;
+    return chunk;
+}
+
+template <int DIR>
+static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const int chunk = conv_chunk(P, DIR);
+    dim3 blk(32, 4);
+    dim3 grd((P.n[DA] + 31) / 32, (P.n[DB] + 3) / 4, (P.n[DIR] + chunk - 1) / chunk);
+    if (P.scheme == SCH_CENTRAL4) {
+        if (P.curv) k_conv_central<DIR, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+        else k_conv_central<DIR, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+    } else if (P.scheme == SCH_WENO5JS) {
+        if (P.curv) k_conv_char<DIR, SCH_WENO5JS, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+        else k_conv_char<DIR, SCH_WENO5JS, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+    } else {
+        if (P.curv) k_conv_char<DIR, SCH_TENO5, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+        else k_conv_char<DIR, SCH_TENO5, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+    }
+}
+
+template <int MODE, int STAGE>
+static void update(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    int g = grid_for(N, 128);
+    if (P.viscous) {
+        if (P.curv) k_update<MODE, STAGE, true, true><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
+        else k_update<MODE, STAGE, true, false><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
+    } else {
+        if (P.curv) k_update<MODE, STAGE, false, true><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
+        else k_update<MODE, STAGE, false, false><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
+    }
+}
+
+// ghost fill + primitives + convective + viscous fluxes: R holds the convective residual and
+// V the viscous fluxes when this returns (on the stream).  Returns the launch count.
+static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    int launches = 0;
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
+        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
+        launches++;
+    }
+    k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
+    launches++;
+    int acc = 0;
+    if (P.active[0]) { conv_dir<0>(P, B, acc, s); acc = 1; launches++; }
+    if (P.active[1]) { conv_dir<1>(P, B, acc, s); acc = 1; launches++; }
+    if (P.active[2]) { conv_dir<2>(P, B, acc, s); acc = 1; launches++; }
+    if (P.viscous) {
+        long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+        if (P.curv) k_visc_flux<true><<<grid_for(N, 128), 128, 0, s>>>(P, B.W, B.M, B.V);
+        else k_visc_flux<false><<<grid_for(N, 128), 128, 0, s>>>(P, B.W, B.M, B.V);
+        launches++;
+    }
+    return launches;
+}
+
+static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    int launches = 0;
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        for (int sd = 0; sd < 2; sd++) {
+            int bc = P.bc[d][sd];
+            if (bc != BC_WALL && bc != BC_DIRICHLET && bc != BC_INFLOW) continue;
+            long long plane = (long long)P.n[(d == 0) ? 1 : 0] * P.n[(d == 2) ? 1 : 2];
+            k_bnodes<<<grid_for(plane, 256), 256, 0, s>>>(P, B.U, d, sd, B.bd[2 * d + sd]);
+            launches++;
+        }
+    }
+    return launches;
+}
+
+int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
+{
+    int launches = residual_front(P, B, s);
+    if (stage == 0) update<0, 0>(P, B, s);
+    else if (stage == 1) update<0, 1>(P, B, s);
+    else update<0, 2>(P, B, s);
+    launches++;
+    launches += boundary_nodes(P, B, s);
+    return launches;
+}
+
+int launch_residual(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    int launches = residual_front(P, B, s);
+    update<1, 0>(P, B, s);
+    return launches + 1;
+}
+
+void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s)
+{
+    k_diag_partial<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(P, B.U, part);
+    k_diag_final<<<1, 32, 0, s>>>(part, out, (long long)P.n[0] * P.n[1] * P.n[2]);
+}
+
+int diag_partial_size() { return NDIAG * DIAG_BLOCKS; }
+
+}  // namespace osb

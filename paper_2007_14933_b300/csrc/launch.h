@@ -1,0 +1,27 @@
+// launch.h -- device buffers of a solver and the host-side launchers of kernels.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dev.cuh"
+
+namespace osb {
+
+struct Bufs {
+    double *U = nullptr, *dU = nullptr, *R = nullptr;  // [5][vs]
+    double *W = nullptr;                               // [NW][vs]
+    double *M = nullptr;                               // [10][vs] (curvilinear only)
+    double *V = nullptr;                               // [3][4][vs] (viscous only)
+    double *bd[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int *err = nullptr;                                // device error word
+};
+
+void launch_unpack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s);
+void launch_pack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s);
+void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sraw,
+                    unsigned long long *smax, double *M, cudaStream_t s);
+int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s);
+int launch_residual(const Dev &P, const Bufs &B, cudaStream_t s);
+void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s);
+int diag_partial_size();
+
+}  // namespace osb

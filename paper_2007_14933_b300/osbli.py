@@ -1,0 +1,218 @@
+"""Thin ctypes binding of include/osbli.h (argument marshalling only).
+
+Every numerical step runs in libosbli.so; this module only converts arguments.  Functions keep the
+C names (``osbli_create`` ...); ``Solver`` wraps a handle for convenience.  Arrays may be numpy
+arrays (host memory) or torch tensors (device or pinned host memory); layouts are those of the
+header: state [5][nz][ny][nx] FP64 contiguous.
+
+Loading fails loudly (OSError) when the library has not been built: there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libosbli.so")
+
+OSBLI_OK, OSBLI_EINVAL, OSBLI_ENOMEM, OSBLI_ECUDA, OSBLI_ENONFINITE, OSBLI_ETIMEOUT, OSBLI_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5 = 0, 1, 2
+OSBLI_PERIODIC, OSBLI_ZEROGRAD, OSBLI_WALL, OSBLI_DIRICHLET, OSBLI_INFLOW = 0, 1, 2, 3, 4
+OSBLI_FP64, OSBLI_MIXED = 0, 1
+
+EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_set_state",
+            "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
+            "osbli_launches_per_step", "osbli_last_error"]
+
+
+class osbli_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("Re", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("Ma", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("scheme", ctypes.c_int),
+        ("teno_ct", ctypes.c_double),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("T_wall", ctypes.c_double),
+        ("sutherland_ratio", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("sensor", ctypes.c_int),
+        ("h", ctypes.c_double * 3),
+        ("L", ctypes.c_double * 3),
+    ]
+
+
+class OsbliError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("osbli error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libosbli.so (raises OSError when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libosbli.so not built (run paper_2007_14933_b300/build.py): %s" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.osbli_create.argtypes = [ctypes.POINTER(osbli_params), vp, vp, ctypes.POINTER(vp)]
+        L.osbli_destroy.argtypes = [vp]
+        L.osbli_destroy.restype = None
+        L.osbli_set_boundary_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+        L.osbli_set_state.argtypes = [vp, vp]
+        L.osbli_get_state.argtypes = [vp, vp]
+        L.osbli_rk_step.argtypes = [vp, ctypes.c_int]
+        L.osbli_residual.argtypes = [vp, vp]
+        L.osbli_diagnostics.argtypes = [vp, vp]
+        L.osbli_launches_per_step.argtypes = [vp]
+        L.osbli_last_error.argtypes = [vp]
+        L.osbli_last_error.restype = ctypes.c_char_p
+        for name in ("osbli_create", "osbli_set_boundary_data", "osbli_set_state", "osbli_get_state",
+                     "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
+                     "osbli_launches_per_step"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous FP64 expected)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(h, rc):
+    if rc != OSBLI_OK:
+        msg = load().osbli_last_error(h)
+        raise OsbliError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def make_params(cfg, precision=OSBLI_FP64):
+    p = osbli_params()
+    p.nx, p.ny, p.nz = (int(x) for x in cfg["n"])
+    p.gamma = cfg.get("gamma", 1.4)
+    p.Re = cfg.get("Re", 0.0)
+    p.Pr = cfg.get("Pr", 0.72)
+    p.Ma = cfg.get("Ma", 1.0)
+    p.dt = cfg.get("dt", 0.0)
+    p.scheme = int(cfg.get("scheme", OSBLI_TENO5))
+    p.teno_ct = cfg.get("teno_ct", 1e-5)
+    for d in range(3):
+        for s in range(2):
+            p.bc[d][s] = int(cfg["bc"][d][s])
+        p.h[d] = float(cfg.get("h", (1.0, 1.0, 1.0))[d])
+        p.L[d] = float(cfg.get("L", (0.0, 0.0, 0.0))[d])
+    p.T_wall = cfg.get("T_wall", 1.0)
+    p.sutherland_ratio = cfg.get("suth", 0.0)
+    p.precision = int(precision)
+    p.sensor = 0
+    return p
+
+
+# ---- the C names ------------------------------------------------------------------------------
+def osbli_create(params, coords=None, cuda_stream=None):
+    h = ctypes.c_void_p()
+    c = None if coords is None else np.ascontiguousarray(coords, dtype=np.float64)
+    _check(None, load().osbli_create(ctypes.byref(params), _ptr(c), ctypes.c_void_p(cuda_stream or 0),
+                                     ctypes.byref(h)))
+    return h
+
+
+def osbli_destroy(h):
+    load().osbli_destroy(h)
+
+
+def osbli_set_boundary_data(h, d, s, prims):
+    return _check(h, load().osbli_set_boundary_data(h, int(d), int(s), _ptr(prims)))
+
+
+def osbli_set_state(h, U):
+    return _check(h, load().osbli_set_state(h, _ptr(U)))
+
+
+def osbli_get_state(h, U):
+    return _check(h, load().osbli_get_state(h, _ptr(U)))
+
+
+def osbli_rk_step(h, nsteps):
+    return _check(h, load().osbli_rk_step(h, int(nsteps)))
+
+
+def osbli_residual(h, R):
+    return _check(h, load().osbli_residual(h, _ptr(R)))
+
+
+def osbli_diagnostics(h, out):
+    return _check(h, load().osbli_diagnostics(h, _ptr(out)))
+
+
+def osbli_launches_per_step(h):
+    return load().osbli_launches_per_step(h)
+
+
+def osbli_last_error(h):
+    m = load().osbli_last_error(h)
+    return m.decode() if m else ""
+
+
+class Solver:
+    """One grid problem on the GPU.  ``cfg`` uses the keys of ``inputs`` problem dicts."""
+
+    def __init__(self, cfg, precision=OSBLI_FP64, cuda_stream=None):
+        self.h = None
+        self.cfg = cfg
+        self.n = tuple(int(x) for x in cfg["n"])
+        self.shape = (5, self.n[2], self.n[1], self.n[0])
+        self.params = make_params(cfg, precision)
+        self.h = osbli_create(self.params, cfg.get("coords"), cuda_stream)
+        for (d, s), arr in (cfg.get("bdata") or {}).items():
+            osbli_set_boundary_data(self.h, d, s, np.ascontiguousarray(arr, dtype=np.float64))
+
+    def close(self):
+        if getattr(self, "h", None):
+            osbli_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.shape)
+        osbli_set_state(self.h, U)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        osbli_get_state(self.h, out)
+        return out
+
+    def step(self, nsteps):
+        osbli_rk_step(self.h, nsteps)
+
+    def residual(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        osbli_residual(self.h, out)
+        return out
+
+    def diagnostics(self):
+        out = np.empty(16)
+        osbli_diagnostics(self.h, out)
+        return out
+
+    def launches_per_step(self):
+        return osbli_launches_per_step(self.h)

@@ -1,0 +1,277 @@
+"""GPU (libosbli, through the C ABI) against the CPU oracle, element by element.
+
+Tolerance (plain FP64 path): max over variables v and points of |X_gpu - X_oracle| divided by
+max over points |X_oracle,v| must be <= 1e-11, for single residual evaluations and after
+multi-step runs.  For TENO5 a stencil cut-off decision delta_r = [chi_r >= C_T] whose chi_r
+lies within rounding of C_T may legitimately differ between two correct FP64 evaluations; points
+whose oracle margin |chi - C_T|/C_T is below 1e-9 are checked separately (bounded deviation)
+instead of at 1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_14933_b300 import inputs as I
+from paper_2007_14933_b300 import osbli
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_14933_b300 import build
+    build.build()
+    osbli.load()
+
+
+def relerr(a, b, mask=None):
+    a = a.reshape(5, -1)
+    b = b.reshape(5, -1)
+    scale = np.abs(b).max(axis=1, keepdims=True)
+    scale[scale == 0] = 1.0
+    e = np.abs(a - b) / scale
+    if mask is not None:
+        e = e[:, mask.reshape(-1)]
+    return float(e.max()) if e.size else 0.0
+
+
+def residual_pair(cfg, U):
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    Rg = s.residual()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    Ro, margin = o.residual(with_margin=True)
+    return Rg, Ro, margin
+
+
+def check_residual(cfg, U):
+    Rg, Ro, margin = residual_pair(cfg, U)
+    safe = margin > 1e-9
+    assert relerr(Rg, Ro, safe) <= TOL
+    if (~safe).any():   # ambiguous TENO cut-offs: still bounded
+        assert relerr(Rg, Ro) < 1e-3
+    return Rg, Ro
+
+
+def wall_box(n=(16, 12, 4), scheme=I.TENO5):
+    """Small box with every non-periodic boundary type: inflow / zero-gradient in x, isothermal
+    wall / Dirichlet in y (tanh-stretched), periodic z, Sutherland viscosity."""
+    g, Ma = 1.4, 2.0
+    nx, ny, nz = n
+    Lx, Ly, Lz = 10.0, 4.0, 2.0
+    x = np.linspace(0, Lx, nx)
+    j = np.arange(ny)
+    y = Ly * (1 - np.tanh(1.5 * (1 - j / (ny - 1))) / np.tanh(1.5))
+    z = np.arange(nz) * Lz / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    coords = np.stack([X, Y, Z])
+    Tw = 1.7
+    eta = Y / 1.0
+    u = np.tanh(2 * eta) * (1 + 0.02 * np.sin(2 * math.pi * Z / Lz))
+    T = Tw + (1 - Tw) * np.tanh(2 * eta)
+    p = np.full_like(u, 1.0 / (g * Ma * Ma)) * (1 + 0.01 * np.sin(X))
+    rho = g * Ma * Ma * p / T
+    v = 0.01 * np.tanh(eta) * np.cos(X)
+    w = 0.01 * np.sin(2 * math.pi * Z / Lz) * np.tanh(eta)
+    U = I.prim_to_cons(g, rho, u, v, w, p)
+    U[1:4, :, 0, :] = 0.0
+    U[4, :, 0, :] = U[0, :, 0, :] * Tw / (Ma * Ma * g * (g - 1))
+    inflow = np.zeros((5, nz, ny))
+    inflow[1] = u[:, :, 0]
+    inflow[2] = v[:, :, 0]
+    inflow[3] = w[:, :, 0]
+    inflow[4] = T[:, :, 0]
+    top = np.zeros((5, nz, nx))
+    top[0] = rho[:, -1, :] * 1.05
+    top[1] = u[:, -1, :]
+    top[2] = -0.05
+    top[3] = 0.0
+    top[4] = p[:, -1, :] * 1.1
+    cfg = dict(n=n, gamma=g, Re=500.0, Pr=0.72, Ma=Ma, dt=2e-3, scheme=scheme, teno_ct=1e-5,
+               bc=[[I.INFLOW, I.ZEROGRAD], [I.WALL, I.DIRICHLET], [I.PERIODIC, I.PERIODIC]],
+               T_wall=Tw, suth=110.4 / 288.0, h=(1, 1, 1), L=(0, 0, Lz), coords=coords,
+               bdata={(0, 0): inflow.reshape(5, -1), (1, 1): top.reshape(5, -1)})
+    return cfg, U
+
+
+# ------------------------------------------------------------------------ single residual
+def test_residual_tgv_central_viscous():
+    cfg, U = I.tgv(16, Ma=0.1, scheme=I.CENTRAL4)
+    check_residual(cfg, U)
+
+
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+def test_residual_tgv_characteristic_viscous_ragged(scheme):
+    cfg, U = I.tgv(n=(20, 12, 9), Ma=1.25, scheme=scheme)
+    check_residual(cfg, U)
+
+
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+def test_residual_shocky_random_state(scheme):
+    n = (13, 9, 7)
+    U = I.random_state(n, seed=3, shocky=True)
+    cfg = dict(n=n, gamma=1.4, Re=0.0, Ma=1.0, scheme=scheme, teno_ct=1e-5,
+               bc=[[0, 0]] * 3, h=(0.1, 0.2, 0.3))
+    check_residual(cfg, U)
+
+
+def test_residual_sod():
+    cfg, U, _ = I.sod()
+    check_residual(cfg, U)
+
+
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.CENTRAL4])
+def test_residual_curvilinear_euler_wave(scheme):
+    cfg, U = I.euler_wave(24, scheme=scheme)
+    check_residual(cfg, U)
+
+
+@pytest.mark.parametrize("scheme", [I.TENO5, I.CENTRAL4])
+def test_residual_walls_inflow_dirichlet(scheme):
+    cfg, U = wall_box(scheme=scheme)
+    check_residual(cfg, U)
+
+
+# ------------------------------------------------------------------------ multi-step runs
+def run_pair(cfg, U, nsteps):
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    s.step(nsteps)
+    Ug = s.get_state()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(nsteps)
+    return Ug, o.get_state()
+
+
+def test_sod_800_steps_matches_oracle_and_exact():
+    cfg, U, x = I.sod()
+    Ug, Uo = run_pair(cfg, U, 800)
+    assert relerr(Ug, Uo) <= TOL
+    r, _, _ = O.riemann_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+    assert np.abs(Ug[0, 0, 0] - r).mean() < 4e-3
+
+
+def test_tgv_central_100_steps():
+    cfg, U = I.tgv(16, Ma=0.1, scheme=I.CENTRAL4)
+    Ug, Uo = run_pair(cfg, U, 100)
+    assert relerr(Ug, Uo) <= TOL
+
+
+def test_tgv_teno_100_steps():
+    cfg, U = I.tgv(12, Ma=1.25, scheme=I.TENO5)
+    Ug, Uo = run_pair(cfg, U, 100)
+    assert relerr(Ug, Uo) <= TOL
+
+
+def test_euler_wave_teno_100_steps():
+    cfg, U = I.euler_wave(32, scheme=I.TENO5)
+    Ug, Uo = run_pair(cfg, U, 100)
+    assert relerr(Ug, Uo) <= TOL
+
+
+def test_walls_20_steps():
+    cfg, U = wall_box()
+    Ug, Uo = run_pair(cfg, U, 20)
+    assert relerr(Ug, Uo) <= TOL
+
+
+# ------------------------------------------------------------------------ full-size samples
+def _sample_points(n, count, seed):
+    rng = np.random.default_rng(seed)
+    pts = np.stack([rng.integers(0, n[d], size=count) for d in range(3)], axis=1)
+    corners = np.array([[i, j, k] for i in (0, 1, n[0] - 1) for j in (0, n[1] - 2, n[1] - 1)
+                        for k in (0, n[2] - 1)])
+    return np.concatenate([pts, corners]).astype(np.int32)
+
+
+@pytest.mark.parametrize("which", ["tgv256_teno", "tgv128_central"])
+def test_full_size_residual_sampled(which):
+    if which == "tgv256_teno":
+        cfg, U = I.tgv(256, Ma=1.25, scheme=I.TENO5)
+    else:
+        cfg, U = I.tgv(128, Ma=0.1, scheme=I.CENTRAL4)
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    Rg = s.residual()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    pts = _sample_points(cfg["n"], 300, 7)
+    Ro, margin = o.residual_points(pts, with_margin=True)
+    Rgs = Rg[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    scale = np.abs(Rg).reshape(5, -1).max(axis=1)
+    err = np.abs(Rgs - Ro) / scale
+    safe = margin > 1e-9
+    assert err[safe].max() <= TOL
+
+
+def test_full_size_tgv256_teno_steps_conserve():
+    cfg, U = I.tgv(256, Ma=1.25, scheme=I.TENO5)
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    d0 = s.diagnostics()
+    s.step(5)
+    d1 = s.diagnostics()
+    scale = np.abs(U).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(d1[:5] - d0[:5]) <= 1e-12 * scale + 1e-9)
+    assert d1[5] < d0[5]          # kinetic energy decays
+    assert np.isfinite(s.get_state()).all()
+
+
+# ------------------------------------------------------------------------ determinism, errors
+def test_steps_are_deterministic_and_graph_replay_splits():
+    cfg, U = I.tgv(n=(16, 12, 8), Ma=1.25, scheme=I.TENO5)
+    a = osbli.Solver(cfg)
+    a.set_state(U)
+    a.step(10)
+    b = osbli.Solver(cfg)
+    b.set_state(U)
+    b.step(4)
+    b.step(6)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
+    c = osbli.Solver(cfg)
+    mid = osbli.Solver(cfg)
+    mid.set_state(U)
+    mid.step(3)
+    c.set_state(mid.get_state())
+    c.step(7)
+    np.testing.assert_array_equal(a.get_state(), c.get_state())
+
+
+def test_nonfinite_state_is_reported():
+    cfg, U = I.tgv(12, Ma=0.5, scheme=I.TENO5)
+    U = U.copy()
+    U[4, 3, 4, 5] = np.nan
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    with pytest.raises(osbli.OsbliError) as e:
+        s.step(1)
+    assert e.value.code == osbli.OSBLI_ENONFINITE
+
+
+def test_step_before_set_state_is_rejected():
+    cfg, U = I.tgv(12, Ma=0.5, scheme=I.TENO5)
+    s = osbli.Solver(cfg)
+    with pytest.raises(osbli.OsbliError) as e:
+        s.step(1)
+    assert e.value.code == osbli.OSBLI_ESTATE
+
+
+def test_torch_device_buffers_roundtrip():
+    import torch
+    cfg, U = I.tgv(n=(10, 8, 6), Ma=0.5, scheme=I.TENO5)
+    s = osbli.Solver(cfg, cuda_stream=torch.cuda.current_stream().cuda_stream)
+    Ud = torch.from_numpy(U).cuda()
+    s.set_state(Ud)
+    out = torch.empty_like(Ud)
+    osbli.osbli_get_state(s.h, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), U)
