@@ -52,7 +52,7 @@ typedef struct {
     double T_wall;         /* isothermal wall temperature */
     double suth;           /* T_s/T_ref for Sutherland's law; <= 0: mu = 1 */
     double h[3];           /* uniform spacing when coords == NULL */
-    double L[3];           /* period of each periodic direction (coordinate unwrapping) */
+    double L[3];           /* period of each periodic direction for given coords (uniform grid: n*h) */
     const double *coords;  /* [3][nz][ny][nx] physical coordinates or NULL */
     const double *bdata[6];/* face 2*d+s: [5][plane] Dirichlet (rho,u,v,w,p) or inflow (-,u,v,w,T) */
 } orc_params;
@@ -385,7 +385,9 @@ static double coord(const orc_ctx *c, int cc, int i, int j, int k)
         if (ii[d] < 0 || ii[d] >= n) {
             int w = wrapi(ii[d], n);
             int periods = (ii[d] - w) / n;
-            if (cc == d) shift += periods * P->L[d];
+            /* period of the direction: L_d for given coordinates, n_d h_d on a uniform grid */
+            double period = P->coords ? P->L[d] : n * P->h[d];
+            if (cc == d) shift += periods * period;
             ii[d] = w;
         }
     }
