@@ -433,12 +433,22 @@ double orc_deriv4(const double *v, int N, int i, int periodic)
 
 /* coordinate fetch along direction d for the metric derivatives */
 typedef struct { const orc_ctx *c; int cc, d, i, j, k; } crd_ud;
+/* Coordinate at line index s relative to the stencil's centre node.  The difference operator
+ * annihilates constants (its coefficients sum to zero), so this changes nothing but rounding;
+ * on a uniform grid the offsets (s - centre) h are exact and so are the metrics. */
 static double crd_fetch(const void *ud, int s)
 {
     const crd_ud *a = (const crd_ud *)ud;
+    const orc_ctx *c = a->c;
     int ii[3] = {a->i, a->j, a->k};
+    int centre = ii[a->d];
+    if (!c->p.coords) {
+        /* uniform grid: x_cc depends on index cc only */
+        return a->cc == a->d ? (double)(s - centre) * c->p.h[a->cc] : 0.0;
+    }
+    double x0 = coord(c, a->cc, ii[0], ii[1], ii[2]);
     ii[a->d] = s;
-    return coord(a->c, a->cc, ii[0], ii[1], ii[2]);
+    return coord(c, a->cc, ii[0], ii[1], ii[2]) - x0;
 }
 
 static void cross(const double *a, const double *b, double *r)

@@ -698,8 +698,12 @@ __global__ void k_metric_raw(Dev P, const double *__restrict__ X, double Lp0, do
             }
             const int n = P.n[d];
             const bool per = P.bc[d][0] == BC_PERIODIC;
+            const long long oc = ((long long)ijk[2] * P.n[1] + ijk[1]) * P.n[0] + ijk[0];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
+                // coordinates relative to the centre node: the operator annihilates constants,
+                // so only rounding changes (uniform spacing then gives exact metrics)
+                const double xc = X[c * N + oc];
                 auto f = [&](int s) {
                     int w = s, sh = 0;
                     if (per) {
@@ -710,7 +714,7 @@ __global__ void k_metric_raw(Dev P, const double *__restrict__ X, double Lp0, do
                     int jj[3] = {ijk[0], ijk[1], ijk[2]};
                     jj[d] = w;
                     const long long o = ((long long)jj[2] * P.n[1] + jj[1]) * P.n[0] + jj[0];
-                    return X[c * N + o] + (c == d ? sh * Lp[d] : 0.0);
+                    return (X[c * N + o] - xc) + (c == d ? sh * Lp[d] : 0.0);
                 };
                 Xd[d][c] = deriv_line(f, ijk[d], n, per);
             }
