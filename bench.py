@@ -1,0 +1,293 @@
+#!/usr/bin/env python
+"""Benchmark of the residual / RK-stage path: grid-point-stage updates per second.
+
+One step = one low-storage RK3 step (3 stages of: ghost fill, primitives, characteristic TENO5
+flux differences in x, y, z, viscous fluxes, viscous divergence fused with the register update)
+over the whole grid.  Workload: 3D Taylor-Green vortex, 256^3 periodic, Ma 1.25, Re 1600,
+Pr 0.72, TENO5 characteristic reconstruction in all directions + 4th-order central viscous
+terms, FP64 state and arithmetic, analytic initial field.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
+
+Prints one JSON line (rank 0).  ``value`` is device-timed (CUDA events on the solver's stream,
+inputs resident in HBM); ``e2e`` repeats the metric through the C ABI with page-locked host
+buffers, host<->device copies inside the timed region.  Under torchrun every rank runs its own
+replica on its own GPU (the method has no data exchange between replicas): ``value`` is the
+sum over ranks of points x stages / max-over-ranks time.  ``--impl reference`` times the CPU
+oracle on the host cores (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2007_14933_b300 import inputs as I  # noqa: E402
+
+METRIC = "Mpoint-stage updates/s, mixed+learned vs plain FP64 at matched L2 error"
+UNIT = "Mpoint-stage/s"
+# Algorithmic FP64 operations per grid point per direction of one convective launch (interface
+# flux + flux difference), counted from the arithmetic of the method (fma = 2, div/sqrt/rsqrt =
+# 1; comparisons and abs not counted).  Breakdown in the design notes.
+FLOPS_CONV_POINT_DIR = {I.TENO5: 1379.0, I.WENO5JS: 1279.0, I.CENTRAL4: 63.0}
+SCHEME_NAME = {I.TENO5: "TENO5", I.WENO5JS: "WENO5-JS", I.CENTRAL4: "central4"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid points per direction")
+    ap.add_argument("--scheme", type=int, default=I.TENO5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, scheme):
+    Ma = 1.25 if scheme != I.CENTRAL4 else 0.1
+    cfg, U = I.tgv(n, Ma=Ma, Re=1600.0, scheme=scheme)
+    name = "tgv%d_%s_viscous" % (n, SCHEME_NAME[scheme].lower().replace("-", ""))
+    conf = {"workload": name, "grid": [n, n, n], "points": n ** 3,
+            "scheme": "%s characteristic (Roe average, LLF) in x, y, z" % SCHEME_NAME[scheme]
+            if scheme != I.CENTRAL4 else "central 4th order",
+            "viscous": "4th-order central, Re=1600, Pr=0.72, mu=1", "Ma": Ma, "gamma": 1.4,
+            "dt": cfg["dt"], "time_integration": "low-storage RK3, 3 stages per step",
+            "precision": "fp64 state and arithmetic",
+            "l2": "inputs larger than L2: state %.0f MB, resident working set > 4 GB"
+                  % (5 * n ** 3 * 8 / 1e6),
+            "parallelism": "one replica per GPU"}
+    return cfg, U, conf
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(scheme, target_s=12.0):
+    """The oracle as it stands, on every host core, one RK step of the same TGV physics on a
+    smaller grid sized for ~10-30 s of CPU work."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    n = 24
+    Ma = 1.25 if scheme != I.CENTRAL4 else 0.1
+    cfg, U = I.tgv(n, Ma=Ma, scheme=scheme)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    t = time.perf_counter()
+    o.step(1)
+    per_pt = (time.perf_counter() - t) / n ** 3
+    n = int(min(128, max(24, round((target_s / per_pt) ** (1.0 / 3.0)))))
+    cfg, U = I.tgv(n, Ma=Ma, scheme=scheme)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    t = time.perf_counter()
+    o.step(1)
+    el = time.perf_counter() - t
+    return {"value": n ** 3 * 3 / el / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": "one RK3 step (3 stages) of the same TGV %s + viscous physics on a %d^3 grid "
+                      "(%.1f s)" % (SCHEME_NAME[scheme], n, el)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    n = 32
+    Ma = 1.25 if args.scheme != I.CENTRAL4 else 0.1
+    cfg, U = I.tgv(n, Ma=Ma, scheme=args.scheme)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(max(args.warmup, 0))
+    t = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t
+    val = n ** 3 * 3 * args.steps / el / 1e6
+    _, _, conf = workload(args.n, args.scheme)
+    sample = "each step: one RK3 step of the oracle on a %d^3 sample of the workload's physics" % n
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic (analytic TGV initial field)", "config": conf,
+                      "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    from paper_2007_14933_b300 import build, osbli
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    osbli.load()
+
+    cfg, U, conf = workload(args.n, args.scheme)
+    npts = args.n ** 3
+    stream = torch.cuda.current_stream()
+    s = osbli.Solver(cfg, cuda_stream=stream.cuda_stream)
+    s.set_state(U)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    gpu_index = torch.cuda.current_device()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except (ValueError, IndexError):
+            pass
+    with ClockSampler(gpu_index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = npts * 3 * args.steps * world / (ms_max / 1e3) / 1e6
+    clocks = clk.summary()
+    launches = s.launches_per_step() * args.steps
+
+    # per-kernel durations of one residual evaluation (CUDA events on the solver's stream)
+    prof = s.profile_residual(reps=2)
+    conv = [(nm, t_) for nm, t_ in prof if nm.startswith("conv_")]
+    dom_name, dom_ms = max(conv, key=lambda x: x[1])
+    flops = FLOPS_CONV_POINT_DIR[args.scheme] * npts
+    peak = osbli.osbli_fp64_peak()
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_conv_char (%s)" % dom_name,
+                "dtype": "fp64",
+                "peak_source": "FP64 FMA throughput measured in this run (osbli_fp64_peak); "
+                               "HBM-bound fraction for reference: 160 B/point-stage",
+                "flops_per_launch": flops}
+
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
+        Uo = torch.empty_like(Uh).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            osbli.osbli_set_state(s.h, Uh)
+            osbli.osbli_rk_step(s.h, 1)
+            osbli.osbli_get_state(s.h, Uo)
+        el = time.perf_counter() - t0
+        tt = torch.tensor([el], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+        e2e = {"value": npts * 3 * args.steps * world / el / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(Uh.numel() * 8), "d2h_bytes_per_step": int(Uo.numel() * 8),
+               "api": "osbli_set_state(host) + osbli_rk_step(1) + osbli_get_state(host)"}
+        launches_e2e = (s.launches_per_step() + 2) * args.steps
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (analytic TGV initial field)", "config": conf,
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+           "kernels_ms": {nm: t_ for nm, t_ in prof},
+           "variant": "plain FP64 (mixed-precision and learned-sensor forms not built)"}
+    if e2e:
+        out["gpu_launches_e2e"] = launches_e2e
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.scheme)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -115,8 +115,23 @@ int osbli_residual(osbli_t *h, double *R);
  * out[6] = max Mach number, out[7] = min density, out[8] = min pressure, out[9..15] = 0. */
 int osbli_diagnostics(osbli_t *h, double out[16]);
 
+/* Time each kernel launch of one residual evaluation (ghost fill per direction, primitives,
+ * convective flux difference per direction, viscous fluxes, viscous divergence) with CUDA events
+ * on the handle's stream, averaged over reps >= 1 repetitions.  ms[i] (host, max entries)
+ * receives the mean duration of launch i in milliseconds; osbli_profile_name(h, i) names it.
+ * Returns the number of launches (> 0) or a negative error code.  The state is unchanged. */
+int osbli_profile_residual(osbli_t *h, int reps, double *ms, int max);
+
+/* Name of launch i of the last osbli_profile_residual on h ("" when out of range). */
+const char *osbli_profile_name(const osbli_t *h, int i);
+
 /* Kernel launches one RK step enqueues (for launch accounting). */
 int osbli_launches_per_step(const osbli_t *h);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (independent DFMA chains; the
+ * denominator of the FP64 path's ALU roofline).  A measurement helper: the paper has no
+ * counterpart.  Uses the legacy default stream and a small temporary device buffer. */
+int osbli_fp64_peak(double *tflops);
 
 /* Message of the last failure on h (or of the last failed osbli_create when h is NULL). */
 const char *osbli_last_error(const osbli_t *h);

@@ -27,6 +27,8 @@ struct osbli {
     bool bdata_set[6] = {false, false, false, false, false, false};
     cudaGraphExec_t gexec = nullptr;
     int launches_step = 0;
+    const char *prof_names[32] = {};
+    int prof_count = 0;
     char err[512];
 };
 
@@ -355,6 +357,47 @@ extern "C" int osbli_diagnostics(osbli_t *h, double out[16])
     CK(h, cudaStreamSynchronize(h->stream));
     memcpy(out, h->h_diag, 16 * sizeof(double));
     return OSBLI_OK;
+}
+
+extern "C" int osbli_profile_residual(osbli_t *h, int reps, double *ms, int max)
+{
+    if (!h || !ms || reps < 1 || max < 1) return seterr(h, OSBLI_EINVAL, "bad argument");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    int rc = check_faces(h);
+    if (rc != OSBLI_OK) return rc;
+    const int cap = 32;
+    cudaEvent_t ev[cap + 1];
+    int made = 0;
+    for (; made <= cap; made++)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+    if (made <= cap) {
+        for (int i = 0; i < made; i++) cudaEventDestroy(ev[i]);
+        return seterr(h, OSBLI_ECUDA, "cudaEventCreate failed");
+    }
+    double acc[cap] = {};
+    int count = 0;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; r++) {
+        count = launch_residual_timed(h->P, h->B, h->stream, ev, h->prof_names, cap);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[count]);
+        for (int i = 0; i < count && e == cudaSuccess; i++) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+            acc[i] += t;
+        }
+    }
+    for (int i = 0; i <= cap; i++) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return seterr(h, OSBLI_ECUDA, "profile: %s", cudaGetErrorString(e));
+    h->prof_count = count;
+    for (int i = 0; i < count && i < max; i++) ms[i] = acc[i] / reps;
+    return count;
+}
+
+extern "C" const char *osbli_profile_name(const osbli_t *h, int i)
+{
+    if (!h || i < 0 || i >= h->prof_count || !h->prof_names[i]) return "";
+    return h->prof_names[i];
 }
 
 extern "C" int osbli_launches_per_step(const osbli_t *h)

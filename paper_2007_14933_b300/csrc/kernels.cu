@@ -902,25 +902,51 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     }
 }
 
+// Optional per-launch event taps (kernel timing): before each launch an event is recorded and
+// the launch is named; a final event closes the last one.
+struct Tap {
+    cudaEvent_t *ev = nullptr;
+    const char **names = nullptr;
+    int count = 0, max = 0;
+    void operator()(const char *name, cudaStream_t s)
+    {
+        if (!ev || count >= max) return;
+        cudaEventRecord(ev[count], s);
+        names[count] = name;
+        count++;
+    }
+};
+
 // ghost fill + primitives + convective + viscous fluxes: R holds the convective residual and
 // V the viscous fluxes when this returns (on the stream).  Returns the launch count.
-static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s)
+static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap = nullptr)
 {
+    static const char *ghost_names[3] = {"ghost_x", "ghost_y", "ghost_z"};
+    static const char *conv_names[3] = {"conv_x", "conv_y", "conv_z"};
     int launches = 0;
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
+        if (tap) (*tap)(ghost_names[d], s);
         k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
         launches++;
     }
+    if (tap) (*tap)("prim", s);
     k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
     int acc = 0;
-    if (P.active[0]) { conv_dir<0>(P, B, acc, s); acc = 1; launches++; }
-    if (P.active[1]) { conv_dir<1>(P, B, acc, s); acc = 1; launches++; }
-    if (P.active[2]) { conv_dir<2>(P, B, acc, s); acc = 1; launches++; }
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        if (tap) (*tap)(conv_names[d], s);
+        if (d == 0) conv_dir<0>(P, B, acc, s);
+        else if (d == 1) conv_dir<1>(P, B, acc, s);
+        else conv_dir<2>(P, B, acc, s);
+        acc = 1;
+        launches++;
+    }
     if (P.viscous) {
         long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+        if (tap) (*tap)("visc_flux", s);
         if (P.curv) k_visc_flux<true><<<grid_for(N, 128), 128, 0, s>>>(P, B.W, B.M, B.V);
         else k_visc_flux<false><<<grid_for(N, 128), 128, 0, s>>>(P, B.W, B.M, B.V);
         launches++;
@@ -960,6 +986,20 @@ int launch_residual(const Dev &P, const Bufs &B, cudaStream_t s)
     int launches = residual_front(P, B, s);
     update<1, 0>(P, B, s);
     return launches + 1;
+}
+
+int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent_t *ev,
+                          const char **names, int max_launches)
+{
+    Tap tap;
+    tap.ev = ev;
+    tap.names = names;
+    tap.max = max_launches;
+    residual_front(P, B, s, &tap);
+    tap("update", s);
+    update<1, 0>(P, B, s);
+    if (tap.count <= max_launches && ev) cudaEventRecord(ev[tap.count], s);
+    return tap.count;
 }
 
 void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s)

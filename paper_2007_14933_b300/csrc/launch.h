@@ -21,6 +21,10 @@ void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sr
                     unsigned long long *smax, double *M, cudaStream_t s);
 int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s);
 int launch_residual(const Dev &P, const Bufs &B, cudaStream_t s);
+// residual sequence with an event recorded before each launch and after the last one
+// (ev must hold max_launches + 1 events); returns the number of launches taped
+int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent_t *ev,
+                          const char **names, int max_launches);
 void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s);
 int diag_partial_size();
 

@@ -23,7 +23,8 @@ OSBLI_FP64, OSBLI_MIXED = 0, 1
 
 EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_set_state",
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
-            "osbli_launches_per_step", "osbli_last_error"]
+            "osbli_launches_per_step", "osbli_last_error", "osbli_profile_residual",
+            "osbli_profile_name", "osbli_fp64_peak"]
 
 
 class osbli_params(ctypes.Structure):
@@ -71,11 +72,16 @@ def load():
         L.osbli_residual.argtypes = [vp, vp]
         L.osbli_diagnostics.argtypes = [vp, vp]
         L.osbli_launches_per_step.argtypes = [vp]
+        L.osbli_profile_residual.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+        L.osbli_profile_name.argtypes = [vp, ctypes.c_int]
+        L.osbli_profile_name.restype = ctypes.c_char_p
+        L.osbli_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        L.osbli_fp64_peak.restype = ctypes.c_int
         L.osbli_last_error.argtypes = [vp]
         L.osbli_last_error.restype = ctypes.c_char_p
         for name in ("osbli_create", "osbli_set_boundary_data", "osbli_set_state", "osbli_get_state",
                      "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
-                     "osbli_launches_per_step"):
+                     "osbli_launches_per_step", "osbli_profile_residual"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -164,6 +170,21 @@ def osbli_launches_per_step(h):
     return load().osbli_launches_per_step(h)
 
 
+def osbli_profile_residual(h, reps, max_launches=32):
+    """Mean per-launch milliseconds of one residual evaluation: [(name, ms), ...]."""
+    ms = np.zeros(max_launches)
+    n = load().osbli_profile_residual(h, int(reps), _ptr(ms), max_launches)
+    if n < 0:
+        _check(h, n)
+    return [(load().osbli_profile_name(h, i).decode(), float(ms[i])) for i in range(n)]
+
+
+def osbli_fp64_peak():
+    t = ctypes.c_double()
+    _check(None, load().osbli_fp64_peak(ctypes.byref(t)))
+    return t.value
+
+
 def osbli_last_error(h):
     m = load().osbli_last_error(h)
     return m.decode() if m else ""
@@ -213,6 +234,9 @@ class Solver:
         out = np.empty(16)
         osbli_diagnostics(self.h, out)
         return out
+
+    def profile_residual(self, reps=3):
+        return osbli_profile_residual(self.h, reps)
 
     def launches_per_step(self):
         return osbli_launches_per_step(self.h)
