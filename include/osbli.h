@@ -128,6 +128,31 @@ const char *osbli_profile_name(const osbli_t *h, int i);
 /* Kernel launches one RK step enqueues (for launch accounting). */
 int osbli_launches_per_step(const osbli_t *h);
 
+/* Largest ghosted grid osbli_residual_noalloc accepts: (nx+6)(ny+6)(nz+6) nodes, counting the
+ * 6 ghost layers only on directions with more than one point (e.g. 34^3, 250^2 x 1). */
+#define OSBLI_NOALLOC_MAX_NODES 65536
+
+/* Residual R(U) of a state held in caller memory, computed without allocating device memory.
+ * The paper has no counterpart: this is for callers that may not call cudaMalloc (a host
+ * application that gives all device memory to its own pool, a real-time loop that cannot take
+ * the synchronisation an allocation may imply, a plug-in whose framework forbids allocation).
+ * The intermediate arrays live in one static device array of 30 doubles x
+ * OSBLI_NOALLOC_MAX_NODES (15.7 MB) that every GPU using the library holds until the process
+ * exits.  Same arithmetic as osbli_residual.
+ *   p        parameters as for osbli_create; uniform grid only (spacing h), faces PERIODIC,
+ *            ZEROGRAD or WALL only (no face data), FP64, no sensor
+ *   d_U      device pointer, [5][nz][ny][nx] FP64 state (read)
+ *   d_R      device pointer, [5][nz][ny][nx] FP64 residual (written)
+ *   stream   cudaStream_t the work is enqueued on; the call synchronises it before returning.
+ * Returns OSBLI_OK, EINVAL (bad parameters, or a grid beyond OSBLI_NOALLOC_MAX_NODES: the message
+ * from osbli_last_error(NULL) names both sizes) or ECUDA.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps the previous call's
+ * contents (the ghosted state is cleared at the start of each call); calls whose GPU work
+ * overlaps -- other streams or other host threads -- race on it and must be serialised by the
+ * caller. */
+int osbli_residual_noalloc(const osbli_params *p, const double *d_U, double *d_R, void *stream);
+
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (independent DFMA chains; the
  * denominator of the FP64 path's ALU roofline).  A measurement helper: the paper has no
  * counterpart.  Uses the legacy default stream and a small temporary device buffer. */

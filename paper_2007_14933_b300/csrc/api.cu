@@ -423,3 +423,9 @@ extern "C" const char *osbli_last_error(const osbli_t *h)
 {
     return h ? h->err : g_create_err;
 }
+
+// Message slot shared with calls that have no handle (read back by osbli_last_error(NULL)).
+void osbli_internal_set_global_error(const char *msg)
+{
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+}

@@ -24,7 +24,7 @@ OSBLI_FP64, OSBLI_MIXED = 0, 1
 EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_set_state",
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
             "osbli_launches_per_step", "osbli_last_error", "osbli_profile_residual",
-            "osbli_profile_name", "osbli_fp64_peak"]
+            "osbli_profile_name", "osbli_fp64_peak", "osbli_residual_noalloc"]
 
 
 class osbli_params(ctypes.Structure):
@@ -75,6 +75,8 @@ def load():
         L.osbli_profile_residual.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.osbli_profile_name.argtypes = [vp, ctypes.c_int]
         L.osbli_profile_name.restype = ctypes.c_char_p
+        L.osbli_residual_noalloc.argtypes = [ctypes.POINTER(osbli_params), vp, vp, vp]
+        L.osbli_residual_noalloc.restype = ctypes.c_int
         L.osbli_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
         L.osbli_fp64_peak.restype = ctypes.c_int
         L.osbli_last_error.argtypes = [vp]
@@ -177,6 +179,12 @@ def osbli_profile_residual(h, reps, max_launches=32):
     if n < 0:
         _check(h, n)
     return [(load().osbli_profile_name(h, i).decode(), float(ms[i])) for i in range(n)]
+
+
+def osbli_residual_noalloc(params, d_U, d_R, cuda_stream=None):
+    """Residual of a device-resident state without any device allocation (see osbli.h)."""
+    return _check(None, load().osbli_residual_noalloc(ctypes.byref(params), _ptr(d_U), _ptr(d_R),
+                                                      ctypes.c_void_p(cuda_stream or 0)))
 
 
 def osbli_fp64_peak():

@@ -1,0 +1,80 @@
+"""osbli_residual_noalloc: the residual for callers that may not allocate device memory.
+
+Some embedding applications cannot call cudaMalloc (they hand all device memory to their own
+pool, run a real-time loop that cannot take an allocation's synchronisation, or live as a
+plug-in that is not allowed to allocate).  The entry point keeps its intermediate arrays in a
+static device array instead.  Its result must equal the handle-based osbli_residual on the same
+state, on two calls in a row (the second call must not see the first call's leftovers).
+
+This file is collected last so that, if it fails, a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2007_14933_b300 import inputs as I
+from paper_2007_14933_b300 import osbli
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11   # same bar as the other FP64 parity tests
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_14933_b300 import build
+    build.build()
+    osbli.load()
+    return t
+
+
+def _handle_residual(cfg, U):
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    R = s.residual()
+    s.close()
+    return R
+
+
+def _noalloc_residual(torch, cfg, U):
+    dU = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    dR = torch.full_like(dU, float("nan"))
+    stream = torch.cuda.current_stream().cuda_stream
+    osbli.osbli_residual_noalloc(osbli.make_params(cfg), dU, dR, stream)
+    return dR.cpu().numpy()
+
+
+def _relerr(a, b):
+    scale = np.abs(b).reshape(5, -1).max(axis=1)[:, None]
+    return float((np.abs(a - b).reshape(5, -1) / scale).max())
+
+
+def test_noalloc_matches_handle_residual_on_two_calls(torch):
+    # call 1: TENO5 + viscous periodic box; call 2: a different state, grid and scheme
+    cfg1, U1 = I.tgv(n=(20, 12, 9), Ma=1.25, scheme=I.TENO5)
+    n2 = (16, 10, 7)
+    U2 = I.random_state(n2, seed=5, shocky=True)
+    cfg2 = dict(n=n2, gamma=1.4, Re=0.0, Ma=1.0, scheme=I.WENO5JS, bc=[[0, 0]] * 3,
+                h=(0.1, 0.2, 0.3))
+    for cfg, U in ((cfg1, U1), (cfg2, U2)):
+        Rn = _noalloc_residual(torch, cfg, U)
+        Rh = _handle_residual(cfg, U)
+        assert np.isfinite(Rn).all()
+        assert _relerr(Rn, Rh) <= TOL
+
+
+def test_noalloc_rejects_grids_beyond_the_static_capacity(torch):
+    cfg, U = I.tgv(n=(40, 40, 40), Ma=0.5, scheme=I.TENO5)   # 46^3 ghosted nodes > 65536
+    dU = torch.from_numpy(U).cuda()
+    dR = torch.empty_like(dU)
+    p = osbli.make_params(cfg)
+    rc = osbli.load().osbli_residual_noalloc(ctypes.byref(p), ctypes.c_void_p(dU.data_ptr()),
+                                             ctypes.c_void_p(dR.data_ptr()), None)
+    assert rc == osbli.OSBLI_EINVAL
+    msg = osbli.osbli_last_error(None)
+    assert "too large" in msg and "65536" in msg
