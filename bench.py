@@ -5,7 +5,9 @@ One step = one low-storage RK3 step (3 stages of: ghost fill, primitives, charac
 flux differences in x, y, z, viscous fluxes, viscous divergence fused with the register update)
 over the whole grid.  Workload: 3D Taylor-Green vortex, 256^3 periodic, Ma 1.25, Re 1600,
 Pr 0.72, TENO5 characteristic reconstruction in all directions + 4th-order central viscous
-terms, FP64 state and arithmetic, analytic initial field.
+terms, analytic initial field.  Two forms are timed on the same workload: the mixed-precision
+form (the headline ``value``: FP32 reconstruction arithmetic, FP64 state and RK registers) and
+the plain FP64 form, with the relative L2 difference of their states after the same steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
 
@@ -52,6 +54,8 @@ def parse():
     ap.add_argument("--scheme", type=int, default=I.TENO5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain", action="store_true", help="time the plain FP64 form only")
+    ap.add_argument("--mixed", action="store_true", help="time the mixed form only")
     return ap.parse_args()
 
 
@@ -179,6 +183,28 @@ def run_reference(args, rank):
     return 0
 
 
+def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist):
+    """Warm up, then time args.steps RK steps of one form with CUDA events on its stream."""
+    s = osbli.Solver(cfg, precision=precision, cuda_stream=stream.cuda_stream)
+    s.set_state(U)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return s, float(t.item())
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -197,17 +223,20 @@ def main():
     build.build()
     osbli.load()
 
-    cfg, U, conf = workload(args.n, args.scheme)
-    npts = args.n ** 3
-    stream = torch.cuda.current_stream()
-    s = osbli.Solver(cfg, cuda_stream=stream.cuda_stream)
-    s.set_state(U)
-    s.step(args.warmup)
-    torch.cuda.synchronize()
-
     def barrier():
         if dist:
             dist.barrier()
+
+    cfg, U, conf = workload(args.n, args.scheme)
+    npts = args.n ** 3
+    stream = torch.cuda.current_stream()
+    forms = ["mixed", "fp64"]
+    if args.plain or args.scheme == I.CENTRAL4:
+        forms = ["fp64"]
+    elif args.mixed:
+        forms = ["mixed"]
+    head = forms[0]
+    prec = {"mixed": osbli.OSBLI_MIXED, "fp64": osbli.OSBLI_FP64}
 
     gpu_index = torch.cuda.current_device()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -216,41 +245,53 @@ def main():
             gpu_index = int(vis.split(",")[local])
         except (ValueError, IndexError):
             pass
+    res = {}
     with ClockSampler(gpu_index) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(args.steps)
-        e1.record(stream)
-        e1.synchronize()
-        torch.cuda.synchronize()
-        barrier()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = npts * 3 * args.steps * world / (ms_max / 1e3) / 1e6
+        for f in forms:
+            res[f] = time_form(osbli, torch, cfg, U, prec[f], args, stream, barrier, dist)
     clocks = clk.summary()
-    launches = s.launches_per_step() * args.steps
+    sh, ms_max = res[head]
+    value = npts * 3 * args.steps * world / (ms_max / 1e3) / 1e6
+    launches = sh.launches_per_step() * args.steps
 
-    # per-kernel durations of one residual evaluation (CUDA events on the solver's stream)
-    prof = s.profile_residual(reps=2)
+    # per-kernel durations of one residual evaluation of the headline form (CUDA events)
+    prof = sh.profile_residual(reps=2)
     conv = [(nm, t_) for nm, t_ in prof if nm.startswith("conv_")]
     dom_name, dom_ms = max(conv, key=lambda x: x[1])
     flops = FLOPS_CONV_POINT_DIR[args.scheme] * npts
-    peak = osbli.osbli_fp64_peak()
+    if head == "mixed":
+        peak, pdt, kern = osbli.osbli_fp32_peak(), "fp32", "k_conv_char_mixed"
+        src = "FP32 FMA throughput measured in this run (osbli_fp32_peak)"
+    else:
+        peak, pdt, kern = osbli.osbli_fp64_peak(), "fp64", "k_conv_char"
+        src = "FP64 FMA throughput measured in this run (osbli_fp64_peak)"
     achieved = flops / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_conv_char (%s)" % dom_name,
-                "dtype": "fp64",
-                "peak_source": "FP64 FMA throughput measured in this run (osbli_fp64_peak); "
-                               "HBM-bound fraction for reference: 160 B/point-stage",
-                "flops_per_launch": flops}
+                "frac": achieved / peak, "traffic": None, "kernel": "%s (%s)" % (kern, dom_name),
+                "dtype": pdt, "peak_source": src, "flops_per_launch": flops}
+
+    out_forms = {}
+    for f in forms:
+        s_, ms_ = res[f]
+        out_forms[f] = {"value": npts * 3 * args.steps * world / (ms_ / 1e3) / 1e6,
+                        "ms_per_step": ms_ / args.steps}
+    extra = {"forms": out_forms}
+    if len(forms) == 2:
+        # accuracy at matched work: both forms advanced warmup + steps from the same state
+        Um = res["mixed"][0].get_state()
+        Up = res["fp64"][0].get_state()
+        l2 = [float(np.linalg.norm(Um[v] - Up[v]) / np.linalg.norm(Up[v])) for v in range(5)
+              if np.linalg.norm(Up[v]) > 0]
+        extra["speedup_mixed_vs_fp64"] = out_forms["mixed"]["value"] / out_forms["fp64"]["value"]
+        extra["l2_mixed_vs_fp64"] = max(l2)
+        extra["accuracy_note"] = ("relative L2 (max over conserved variables) between the mixed "
+                                  "and FP64 states after %d steps from the same initial field; "
+                                  "FP64 form is parity-checked against the CPU oracle"
+                                  % (args.warmup + args.steps))
+        del Um, Up
 
     e2e = None
+    launches_e2e = None
     if not args.no_e2e:
         Uh = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
         Uo = torch.empty_like(Uh).pin_memory()
@@ -258,9 +299,9 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            osbli.osbli_set_state(s.h, Uh)
-            osbli.osbli_rk_step(s.h, 1)
-            osbli.osbli_get_state(s.h, Uo)
+            osbli.osbli_set_state(sh.h, Uh)
+            osbli.osbli_rk_step(sh.h, 1)
+            osbli.osbli_get_state(sh.h, Uo)
         el = time.perf_counter() - t0
         tt = torch.tensor([el], dtype=torch.float64, device="cuda")
         if dist:
@@ -269,19 +310,27 @@ def main():
         e2e = {"value": npts * 3 * args.steps * world / el / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(Uh.numel() * 8), "d2h_bytes_per_step": int(Uo.numel() * 8),
                "api": "osbli_set_state(host) + osbli_rk_step(1) + osbli_get_state(host)"}
-        launches_e2e = (s.launches_per_step() + 2) * args.steps
+        launches_e2e = (sh.launches_per_step() + 2) * args.steps
+    for f in forms:
+        res[f][0].close()
     if dist:
         dist.destroy_process_group()
     if rank != 0:
         return 0
+    conf = dict(conf, precision=("mixed: FP32 reconstruction / weights / projections / viscous "
+                                 "terms, FP64 state, RK registers, metrics and strong-jump "
+                                 "interfaces" if head == "mixed" else "fp64 state and arithmetic"),
+                form=head)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
            "data": "synthetic (analytic TGV initial field)", "config": conf,
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
            "kernels_ms": {nm: t_ for nm, t_ in prof},
-           "variant": "plain FP64 (mixed-precision and learned-sensor forms not built)"}
-    if e2e:
+           "variant": ("mixed precision (learned sensor not in this measurement)" if head == "mixed"
+                       else "plain FP64")}
+    out.update(extra)
+    if launches_e2e is not None:
         out["gpu_launches_e2e"] = launches_e2e
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.scheme)

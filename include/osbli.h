@@ -158,6 +158,9 @@ int osbli_residual_noalloc(const osbli_params *p, const double *d_U, double *d_R
  * counterpart.  Uses the legacy default stream and a small temporary device buffer. */
 int osbli_fp64_peak(double *tflops);
 
+/* Same for FP32 FMAs (denominator of the mixed path's reconstruction kernels). */
+int osbli_fp32_peak(double *tflops);
+
 /* Message of the last failure on h (or of the last failed osbli_create when h is NULL). */
 const char *osbli_last_error(const osbli_t *h);
 

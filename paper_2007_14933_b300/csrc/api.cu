@@ -62,6 +62,9 @@ static void free_all(osbli *h)
                       h->diag_out};
     for (double *b : bufs)
         if (b) cudaFree(b);
+    float *fbufs[] = {h->B.Uf, h->B.Wf, h->B.Rf, h->B.Vf};
+    for (float *b : fbufs)
+        if (b) cudaFree(b);
     for (int f = 0; f < 6; f++)
         if (h->B.bd[f]) cudaFree(h->B.bd[f]);
     if (h->B.err) cudaFree(h->B.err);
@@ -101,8 +104,10 @@ static int validate(const osbli_params *p, const double *coords)
     if (!isfinite(p->dt) || p->dt < 0.0) return seterr(nullptr, OSBLI_EINVAL, "dt must be finite and >= 0");
     if (p->scheme == OSBLI_TENO5 && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))
         return seterr(nullptr, OSBLI_EINVAL, "teno_ct must lie in (0, 1)");
-    if (p->precision != OSBLI_FP64)
-        return seterr(nullptr, OSBLI_EINVAL, "precision %d not available in this build", p->precision);
+    if (p->precision != OSBLI_FP64 && p->precision != OSBLI_MIXED)
+        return seterr(nullptr, OSBLI_EINVAL, "precision %d unknown", p->precision);
+    if (p->precision == OSBLI_MIXED && p->scheme == OSBLI_CENTRAL4)
+        return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / TENO5");
     if (p->sensor != 0) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0");
     for (int d = 0; d < 3; d++)
         for (int s = 0; s < 2; s++)
@@ -151,6 +156,8 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     P.gM2 = p->gamma * p->Ma * p->Ma;
     P.kq = P.viscous ? 1.0 / ((p->gamma - 1.0) * p->Ma * p->Ma * p->Pr * p->Re) : 0.0;
     P.dt = p->dt;
+    P.mixed = p->precision == OSBLI_MIXED;
+    P.jump = 1.5f;
     if (!P.curv) {
         double hh[3];
         for (int d = 0; d < 3; d++) hh[d] = P.active[d] ? p->h[d] : 1.0;
@@ -184,13 +191,24 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     CKC(cudaMalloc(&h->B.U, NV * vsb));
     CKC(cudaMalloc(&h->B.dU, NV * vsb));
     CKC(cudaMalloc(&h->B.R, NV * vsb));
-    CKC(cudaMalloc(&h->B.W, NW * vsb));
+    if (p->precision != OSBLI_MIXED) CKC(cudaMalloc(&h->B.W, NW * vsb));
     CKC(cudaMemsetAsync(h->B.U, 0, NV * vsb, h->stream));
     CKC(cudaMemsetAsync(h->B.dU, 0, NV * vsb, h->stream));
     CKC(cudaMemsetAsync(h->B.R, 0, NV * vsb, h->stream));
-    if (P.viscous) {
+    if (P.viscous && !P.mixed) {
         CKC(cudaMalloc(&h->B.V, 12 * vsb));
         CKC(cudaMemsetAsync(h->B.V, 0, 12 * vsb, h->stream));
+    }
+    if (P.mixed) {
+        const size_t fsb = (size_t)P.vs * sizeof(float);
+        CKC(cudaMalloc(&h->B.Uf, NV * fsb));
+        CKC(cudaMalloc(&h->B.Wf, NW * fsb));
+        CKC(cudaMalloc(&h->B.Rf, NV * fsb));
+        CKC(cudaMemsetAsync(h->B.Rf, 0, NV * fsb, h->stream));
+        if (P.viscous) {
+            CKC(cudaMalloc(&h->B.Vf, 12 * fsb));
+            CKC(cudaMemsetAsync(h->B.Vf, 0, 12 * fsb, h->stream));
+        }
     }
     CKC(cudaMalloc(&h->stage, (size_t)NV * N * sizeof(double)));
     CKC(cudaMalloc(&h->diag_part, (size_t)diag_partial_size() * sizeof(double)));

@@ -34,6 +34,8 @@ struct Dev {
     double fac[3];     // uniform grid: s_d / Jinv = 1/h_d
     double shat[3];    // curvilinear grid: s_d = max |S_d|
     double dt;
+    int mixed;         // OSBLI_MIXED: FP32 reconstruction arithmetic
+    float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
 };
 
 __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, int j, int k)
@@ -56,20 +58,30 @@ __device__ __forceinline__ double viscosity(const Dev &P, double T)
     return T * sqrt(T) * (1.0 + P.suth) / (T + P.suth);
 }
 
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
 // ------------------------------------------------------------------------------------------
 // 5th-order reconstruction at x_{i+1/2} from f0..f4 = f_{i-2..i+2}.
 // Candidates (Eq. 14, k = 3; the ENO coefficients of the cited Shu 1997 notes), Jiang-Shu
 // smoothness indicators (Eqs. 17-19, as printed), and
 //   WENO-JS weights (Eqs. 20-21, p = 2, eps = 1e-6), linear weights d = (3/10, 3/5, 1/10);
-//   TENO5 (Eqs. 23-27): gamma_r = (1 + tau5/(beta_r + 1e-16))^6, tau5 = |beta_0 - beta_2|,
+//   TENO5 (Eqs. 23-27): gamma_r = (1 + tau5/(beta_r + eps))^6, tau5 = |beta_0 - beta_2|,
 //   stencil r kept when gamma_r / sum(gamma) >= C_T, omega_r = d_r delta_r / sum d delta.
-// The three reciprocals 1/(beta_r + eps) come from one division of their product, and the
-// cut-off test is taken as gamma_r >= C_T * sum(gamma) (no division); both are algebraically
+// FP64: eps = 1e-16; the three reciprocals 1/(beta_r + eps) come from one division of their
+// product and the cut-off test is gamma_r >= C_T * sum(gamma) (no division) -- algebraically
 // the paper's expressions.
+// FP32 (mixed path): eps is rescaled to 1e-12 x the stencil's mean square (FP32 rounding puts a
+// noise floor near 1e-13 f^2 under beta, which an absolute 1e-16 would let decide cut-offs),
+// and gamma is normalised by its largest member before the sixth power (x^6 of the unscaled
+// ratio overflows FP32); the cut-off test is unchanged in exact arithmetic.
 // ------------------------------------------------------------------------------------------
 template <int SCHEME, typename T>
 __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
 {
+    constexpr bool F32 = sizeof(T) == 4;
     const T c13_12 = T(13.0 / 12.0), q = T(0.25);
     T a, b;
     a = f2 - T(2) * f3 + f4;
@@ -87,13 +99,23 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
     const T q2 = T(1.0 / 3.0) * f0 - T(7.0 / 6.0) * f1 + T(11.0 / 6.0) * f2;
 
     if (SCHEME == SCH_TENO5) {
-        const T eps = T(1e-16);
-        const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
         const T tau = fabs(b0 - b2);
-        const T ip = T(1) / (e0 * e1 * e2);
-        T x0 = T(1) + tau * (ip * e1 * e2);
-        T x1 = T(1) + tau * (ip * e0 * e2);
-        T x2 = T(1) + tau * (ip * e0 * e1);
+        T x0, x1, x2;
+        if (F32) {
+            const T eps = T(1e-12) * T(0.2) * (f0 * f0 + f1 * f1 + f2 * f2 + f3 * f3 + f4 * f4) + T(1e-30);
+            x0 = T(1) + fdiv(tau, b0 + eps);
+            x1 = T(1) + fdiv(tau, b1 + eps);
+            x2 = T(1) + fdiv(tau, b2 + eps);
+            const T r = fdiv(T(1), fmax(x0, fmax(x1, x2)));
+            x0 *= r; x1 *= r; x2 *= r;
+        } else {
+            const T eps = T(1e-16);
+            const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+            const T ip = T(1) / (e0 * e1 * e2);
+            x0 = T(1) + tau * (ip * e1 * e2);
+            x1 = T(1) + tau * (ip * e0 * e2);
+            x2 = T(1) + tau * (ip * e0 * e1);
+        }
         x0 = x0 * x0; x1 = x1 * x1; x2 = x2 * x2;
         const T g0 = x0 * x0 * x0, g1 = x1 * x1 * x1, g2 = x2 * x2 * x2;
         const T th = ct * (g0 + g1 + g2);
@@ -105,10 +127,17 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
     } else {
         const T eps = T(1e-6);
         const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-        const T ip = T(1) / (e0 * e1 * e2);
-        const T i0 = ip * e1 * e2, i1 = ip * e0 * e2, i2 = ip * e0 * e1;
-        const T a0 = T(0.3) * i0 * i0, a1 = T(0.6) * i1 * i1, a2 = T(0.1) * i2 * i2;
-        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+        T a0, a1, a2;
+        if (F32) {
+            a0 = fdiv(T(0.3), e0 * e0);
+            a1 = fdiv(T(0.6), e1 * e1);
+            a2 = fdiv(T(0.1), e2 * e2);
+        } else {
+            const T ip = T(1) / (e0 * e1 * e2);
+            const T i0 = ip * e1 * e2, i1 = ip * e0 * e2, i2 = ip * e0 * e1;
+            a0 = T(0.3) * i0 * i0; a1 = T(0.6) * i1 * i1; a2 = T(0.1) * i2 * i2;
+        }
+        return fdiv(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
     }
 }
 

@@ -220,115 +220,156 @@ __global__ void k_prim(Dev P, const double *__restrict__ U, double *__restrict__
 // alpha_j = max_k |lambda_j(k)|, WENO/TENO reconstruction of g+ and g-, back-projection.
 // The left eigenvectors are applied in factored form (l_j . w built from u.w, n.w, t.w).
 // ------------------------------------------------------------------------------------------
-template <int DIR, bool CURV>
+template <int DIR, bool CURV, typename T>
 struct Frame {
-    double n[3], t1[3], t2[3];
-    __device__ __forceinline__ double dn(double x, double y, double z) const
+    T n[3], t1[3], t2[3];
+    __device__ __forceinline__ T dn(T x, T y, T z) const
     {
         if (CURV) return n[0] * x + n[1] * y + n[2] * z;
-        const double w[3] = {x, y, z};
+        const T w[3] = {x, y, z};
         return w[DIR];
     }
-    __device__ __forceinline__ double dt1(double x, double y, double z) const
+    __device__ __forceinline__ T dt1(T x, T y, T z) const
     {
         if (CURV) return t1[0] * x + t1[1] * y + t1[2] * z;
-        const double w[3] = {x, y, z};
-        return Cart<DIR>::S1 * w[Cart<DIR>::T1];
+        const T w[3] = {x, y, z};
+        return T(Cart<DIR>::S1) * w[Cart<DIR>::T1];
     }
-    __device__ __forceinline__ double dt2(double x, double y, double z) const
+    __device__ __forceinline__ T dt2(T x, T y, T z) const
     {
         if (CURV) return t2[0] * x + t2[1] * y + t2[2] * z;
-        const double w[3] = {x, y, z};
-        return Cart<DIR>::S2 * w[Cart<DIR>::T2];
+        const T w[3] = {x, y, z};
+        return T(Cart<DIR>::S2) * w[Cart<DIR>::T2];
     }
 };
 
-template <int DIR, int SCHEME, bool CURV>
-__device__ __forceinline__ void interface_flux(const Dev &P, const double *__restrict__ U,
-                                               const double *__restrict__ W,
-                                               const double *__restrict__ M, long long m,
-                                               long long st, double Fh[NV])
+// Node data for the interface flux: conserved state and primitives stored per node (FP64
+// arrays on the plain path, FP32 copies on the mixed path) ...
+template <typename S>
+struct SrcArrays {
+    const S *__restrict__ U;
+    const S *__restrict__ W;
+    long long vs;
+    __device__ __forceinline__ S rho(long long id) const { return U[id]; }
+    __device__ __forceinline__ S mom(int c, long long id) const { return U[(1 + c) * vs + id]; }
+    __device__ __forceinline__ S E(long long id) const { return U[4 * vs + id]; }
+    __device__ __forceinline__ S vel(int c, long long id) const { return W[(W_U + c) * vs + id]; }
+    __device__ __forceinline__ S p(long long id) const { return W[W_P * vs + id]; }
+    __device__ __forceinline__ S a(long long id) const { return W[W_A * vs + id]; }
+    __device__ __forceinline__ S sr(long long id) const { return W[W_SR * vs + id]; }
+    __device__ __forceinline__ S H(long long id) const { return W[W_H * vs + id]; }
+};
+
+// ... or FP64 primitives recomputed from the FP64 state (the mixed path's strong-jump fallback).
+struct SrcFromState {
+    const double *__restrict__ U;
+    long long vs;
+    double gamma, gm1;
+    __device__ __forceinline__ double rho(long long id) const { return U[id]; }
+    __device__ __forceinline__ double mom(int c, long long id) const { return U[(1 + c) * vs + id]; }
+    __device__ __forceinline__ double E(long long id) const { return U[4 * vs + id]; }
+    __device__ __forceinline__ double vel(int c, long long id) const { return mom(c, id) / rho(id); }
+    __device__ __forceinline__ double p(long long id) const
+    {
+        const double m0 = mom(0, id), m1 = mom(1, id), m2 = mom(2, id);
+        return gm1 * (E(id) - 0.5 * (m0 * m0 + m1 * m1 + m2 * m2) / rho(id));
+    }
+    __device__ __forceinline__ double a(long long id) const { return sqrt(gamma * p(id) / rho(id)); }
+    __device__ __forceinline__ double sr(long long id) const { return sqrt(rho(id)); }
+    __device__ __forceinline__ double H(long long id) const { return (E(id) + p(id)) / rho(id); }
+};
+
+// Characteristic interface flux (Sec. 2.2 algorithm, steps 2(a)-(f)) between node m and
+// node m + st along DIR: Roe average, eigenvectors along the interface normal, projection of
+// U_k and the contravariant flux F_k of the six stencil nodes, LLF split with
+// alpha_j = max_k |lambda_j(k)|, WENO/TENO reconstruction of g+ and g-, back-projection.
+// The left eigenvectors are applied in factored form (l_j . w built from u.w, n.w, t.w).
+// T is the arithmetic type (double: plain FP64 path; float: mixed path).
+template <int DIR, int SCHEME, bool CURV, typename T, typename Src>
+__device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const double *__restrict__ M,
+                                               long long m, long long st, T Fh[NV])
 {
     const long long vs = P.vs;
     const long long mr = m + st;
+    const T gm1 = T(P.gm1);
     // (a) Roe average
-    const double sl = W[W_SR * vs + m], sr = W[W_SR * vs + mr];
-    const double inv = 1.0 / (sl + sr);
-    const double u0 = (sl * W[W_U * vs + m] + sr * W[W_U * vs + mr]) * inv;
-    const double u1 = (sl * W[W_V * vs + m] + sr * W[W_V * vs + mr]) * inv;
-    const double u2 = (sl * W[W_W * vs + m] + sr * W[W_W * vs + mr]) * inv;
-    const double H = (sl * W[W_H * vs + m] + sr * W[W_H * vs + mr]) * inv;
-    const double q2 = u0 * u0 + u1 * u1 + u2 * u2;
-    const double c2 = P.gm1 * (H - 0.5 * q2);
-    const double ia = rsqrt(c2);
-    const double a = c2 * ia;
+    const T sl = T(q.sr(m)), sr = T(q.sr(mr));
+    const T inv = fdiv(T(1), sl + sr);
+    const T u0 = (sl * T(q.vel(0, m)) + sr * T(q.vel(0, mr))) * inv;
+    const T u1 = (sl * T(q.vel(1, m)) + sr * T(q.vel(1, mr))) * inv;
+    const T u2 = (sl * T(q.vel(2, m)) + sr * T(q.vel(2, mr))) * inv;
+    const T H = (sl * T(q.H(m)) + sr * T(q.H(mr))) * inv;
+    const T q2 = u0 * u0 + u1 * u1 + u2 * u2;
+    const T c2 = gm1 * (H - T(0.5) * q2);
+    const T ia = rsq(c2);
+    const T a = c2 * ia;
 
-    Frame<DIR, CURV> fr;
+    Frame<DIR, CURV, T> fr;
     if (CURV) {
-        double nv[3];
+        T nv[3];
 #pragma unroll
-        for (int c = 0; c < 3; c++) nv[c] = 0.5 * (M[(DIR * 3 + c) * vs + m] + M[(DIR * 3 + c) * vs + mr]);
-        const double inm = rsqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        for (int c = 0; c < 3; c++) nv[c] = T(0.5) * (T(M[(DIR * 3 + c) * vs + m]) + T(M[(DIR * 3 + c) * vs + mr]));
+        const T inm = rsq(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
 #pragma unroll
         for (int c = 0; c < 3; c++) fr.n[c] = nv[c] * inm;
-        if (fabs(fr.n[2]) < 0.9) {
-            const double im = rsqrt(fr.n[0] * fr.n[0] + fr.n[1] * fr.n[1]);
-            fr.t1[0] = -fr.n[1] * im; fr.t1[1] = fr.n[0] * im; fr.t1[2] = 0.0;
+        if (fabs(fr.n[2]) < T(0.9)) {
+            const T im = rsq(fr.n[0] * fr.n[0] + fr.n[1] * fr.n[1]);
+            fr.t1[0] = -fr.n[1] * im; fr.t1[1] = fr.n[0] * im; fr.t1[2] = T(0);
         } else {
-            const double im = rsqrt(fr.n[2] * fr.n[2] + fr.n[1] * fr.n[1]);
-            fr.t1[0] = 0.0; fr.t1[1] = fr.n[2] * im; fr.t1[2] = -fr.n[1] * im;
+            const T im = rsq(fr.n[2] * fr.n[2] + fr.n[1] * fr.n[1]);
+            fr.t1[0] = T(0); fr.t1[1] = fr.n[2] * im; fr.t1[2] = -fr.n[1] * im;
         }
         fr.t2[0] = fr.n[1] * fr.t1[2] - fr.n[2] * fr.t1[1];
         fr.t2[1] = fr.n[2] * fr.t1[0] - fr.n[0] * fr.t1[2];
         fr.t2[2] = fr.n[0] * fr.t1[1] - fr.n[1] * fr.t1[0];
     }
-    const double un = fr.dn(u0, u1, u2);
-    const double ut1 = fr.dt1(u0, u1, u2);
-    const double ut2 = fr.dt2(u0, u1, u2);
-    const double b1 = P.gm1 * ia * ia;
-    const double b2 = 0.5 * b1 * q2;
+    const T un = fr.dn(u0, u1, u2);
+    const T ut1 = fr.dt1(u0, u1, u2);
+    const T ut2 = fr.dt2(u0, u1, u2);
+    const T b1 = gm1 * ia * ia;
+    const T b2 = T(0.5) * b1 * q2;
 
     // (d) wave speeds over the six stencil nodes
-    double al0 = 0.0, al1 = 0.0, al4 = 0.0;
+    T al0 = T(0), al1 = T(0), al4 = T(0);
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const long long id = m + (s - 2) * st;
-        double uns, cs;
+        T uns, cs;
         if (CURV) {
-            const double Sx = M[(DIR * 3 + 0) * vs + id], Sy = M[(DIR * 3 + 1) * vs + id],
-                         Sz = M[(DIR * 3 + 2) * vs + id];
-            uns = Sx * W[W_U * vs + id] + Sy * W[W_V * vs + id] + Sz * W[W_W * vs + id];
-            cs = sqrt(Sx * Sx + Sy * Sy + Sz * Sz) * W[W_A * vs + id];
+            const T Sx = T(M[(DIR * 3 + 0) * vs + id]), Sy = T(M[(DIR * 3 + 1) * vs + id]),
+                    Sz = T(M[(DIR * 3 + 2) * vs + id]);
+            uns = Sx * T(q.vel(0, id)) + Sy * T(q.vel(1, id)) + Sz * T(q.vel(2, id));
+            cs = sqrt(Sx * Sx + Sy * Sy + Sz * Sz) * T(q.a(id));
         } else {
-            uns = W[(W_U + DIR) * vs + id];
-            cs = W[W_A * vs + id];
+            uns = T(q.vel(DIR, id));
+            cs = T(q.a(id));
         }
         al0 = fmax(al0, fabs(uns - cs));
         al1 = fmax(al1, fabs(uns));
         al4 = fmax(al4, fabs(uns + cs));
     }
-    const double h0 = 0.5 * al0, h1 = 0.5 * al1, h4 = 0.5 * al4;
+    const T h0 = T(0.5) * al0, h1 = T(0.5) * al1, h4 = T(0.5) * al4;
 
     // (c) projection and (d) splitting
-    double gp[NV][5], gm[NV][5];
+    T gp[NV][5], gm[NV][5];
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const long long id = m + (s - 2) * st;
-        const double r = U[0 * vs + id], mx = U[1 * vs + id], my = U[2 * vs + id],
-                     mz = U[3 * vs + id], E = U[4 * vs + id];
-        const double p = W[W_P * vs + id];
-        double F[NV];
+        const T r = T(q.rho(id)), mx = T(q.mom(0, id)), my = T(q.mom(1, id)), mz = T(q.mom(2, id)),
+                E = T(q.E(id));
+        const T p = T(q.p(id));
+        T F[NV];
         if (CURV) {
-            const double Sx = M[(DIR * 3 + 0) * vs + id], Sy = M[(DIR * 3 + 1) * vs + id],
-                         Sz = M[(DIR * 3 + 2) * vs + id];
-            const double uns = Sx * W[W_U * vs + id] + Sy * W[W_V * vs + id] + Sz * W[W_W * vs + id];
+            const T Sx = T(M[(DIR * 3 + 0) * vs + id]), Sy = T(M[(DIR * 3 + 1) * vs + id]),
+                    Sz = T(M[(DIR * 3 + 2) * vs + id]);
+            const T uns = Sx * T(q.vel(0, id)) + Sy * T(q.vel(1, id)) + Sz * T(q.vel(2, id));
             F[0] = r * uns;
             F[1] = mx * uns + Sx * p;
             F[2] = my * uns + Sy * p;
             F[3] = mz * uns + Sz * p;
             F[4] = (E + p) * uns;
         } else {
-            const double uns = W[(W_U + DIR) * vs + id];
+            const T uns = T(q.vel(DIR, id));
             F[0] = r * uns;
             F[1] = mx * uns;
             F[2] = my * uns;
@@ -336,60 +377,60 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const double *__res
             F[1 + DIR] += p;
             F[4] = (E + p) * uns;
         }
-        double Vc[NV], Gc[NV];
+        T Vc[NV], Gc[NV];
         {
-            const double um = u0 * mx + u1 * my + u2 * mz;
-            const double A = b2 * r + b1 * (E - um);
-            const double B = (un * r - fr.dn(mx, my, mz)) * ia;
-            Vc[0] = 0.5 * (A + B);
-            Vc[4] = 0.5 * (A - B);
+            const T um = u0 * mx + u1 * my + u2 * mz;
+            const T A = b2 * r + b1 * (E - um);
+            const T B = (un * r - fr.dn(mx, my, mz)) * ia;
+            Vc[0] = T(0.5) * (A + B);
+            Vc[4] = T(0.5) * (A - B);
             Vc[1] = r - A;
             Vc[2] = fr.dt1(mx, my, mz) - ut1 * r;
             Vc[3] = fr.dt2(mx, my, mz) - ut2 * r;
         }
         {
-            const double um = u0 * F[1] + u1 * F[2] + u2 * F[3];
-            const double A = b2 * F[0] + b1 * (F[4] - um);
-            const double B = (un * F[0] - fr.dn(F[1], F[2], F[3])) * ia;
-            Gc[0] = 0.5 * (A + B);
-            Gc[4] = 0.5 * (A - B);
+            const T um = u0 * F[1] + u1 * F[2] + u2 * F[3];
+            const T A = b2 * F[0] + b1 * (F[4] - um);
+            const T B = (un * F[0] - fr.dn(F[1], F[2], F[3])) * ia;
+            Gc[0] = T(0.5) * (A + B);
+            Gc[4] = T(0.5) * (A - B);
             Gc[1] = F[0] - A;
             Gc[2] = fr.dt1(F[1], F[2], F[3]) - ut1 * F[0];
             Gc[3] = fr.dt2(F[1], F[2], F[3]) - ut2 * F[0];
         }
-        const double hh[NV] = {h0, h1, h1, h1, h4};
+        const T hh[NV] = {h0, h1, h1, h1, h4};
 #pragma unroll
         for (int j = 0; j < NV; j++) {
-            if (s < 5) gp[j][s] = fma(hh[j], Vc[j], 0.5 * Gc[j]);
-            if (s > 0) gm[j][s - 1] = fma(-hh[j], Vc[j], 0.5 * Gc[j]);
+            if (s < 5) gp[j][s] = fma(hh[j], Vc[j], T(0.5) * Gc[j]);
+            if (s > 0) gm[j][s - 1] = fma(-hh[j], Vc[j], T(0.5) * Gc[j]);
         }
     }
     // (e) reconstruction
-    double g[NV];
-    const double ct = P.ct;
+    T g[NV];
+    const T ct = T(P.ct);
 #pragma unroll
     for (int j = 0; j < NV; j++) {
-        g[j] = recon5<SCHEME, double>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
-               recon5<SCHEME, double>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+        g[j] = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
+               recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
     }
     // (f) back-projection F = R g
-    const double s04 = g[0] + g[4], d40 = g[4] - g[0];
-    const double sm = s04 + g[1];
+    const T s04 = g[0] + g[4], d40 = g[4] - g[0];
+    const T sm = s04 + g[1];
     Fh[0] = sm;
-    const double uu[3] = {u0, u1, u2};
+    const T uu[3] = {u0, u1, u2};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        double f = uu[c] * sm;
+        T f = uu[c] * sm;
         if (CURV) {
             f += a * fr.n[c] * d40 + fr.t1[c] * g[2] + fr.t2[c] * g[3];
         } else {
             if (c == DIR) f += a * d40;
-            if (c == Cart<DIR>::T1) f += Cart<DIR>::S1 * g[2];
-            if (c == Cart<DIR>::T2) f += Cart<DIR>::S2 * g[3];
+            if (c == Cart<DIR>::T1) f += T(Cart<DIR>::S1) * g[2];
+            if (c == Cart<DIR>::T2) f += T(Cart<DIR>::S2) * g[3];
         }
         Fh[1 + c] = f;
     }
-    Fh[4] = H * s04 + a * un * d40 + 0.5 * q2 * g[1] + ut1 * g[2] + ut2 * g[3];
+    Fh[4] = H * s04 + a * un * d40 + T(0.5) * q2 * g[1] + ut1 * g[2] + ut2 * g[3];
 }
 
 // Lines along DIR: thread (a, b) owns one line of the two cross directions and marches over a
@@ -411,17 +452,124 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
     ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR];
+    const SrcArrays<double> q{U, W, P.vs};
     double Fm[NV];
-    interface_flux<DIR, SCHEME, CURV>(P, U, W, M, base + (long long)(s0 - 1) * st, st, Fm);
+    interface_flux<DIR, SCHEME, CURV, double>(P, q, M, base + (long long)(s0 - 1) * st, st, Fm);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         double Fp[NV];
-        interface_flux<DIR, SCHEME, CURV>(P, U, W, M, id, st, Fp);
+        interface_flux<DIR, SCHEME, CURV, double>(P, q, M, id, st, Fp);
         const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : P.fac[DIR];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             const double r = -fac * (Fp[v] - Fm[v]);
             R[v * P.vs + id] = accumulate ? R[v * P.vs + id] + r : r;
+            Fm[v] = Fp[v];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Mixed path (precision OSBLI_MIXED): FP32 node copies Uf, Wf; FP32 interface arithmetic and
+// FP32 residual accumulation Rf.  An interface whose stencil contains a strong jump between
+// two adjacent nodes (pressure or density ratio above P.jump) keeps FP64: its primitives are
+// recomputed from the FP64 state and its eigenvector projection and reconstruction run in FP64.
+// ------------------------------------------------------------------------------------------
+__global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restrict__ Uf,
+                             float *__restrict__ Wf)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float rho = (float)U[0 * P.vs + t];
+        const float mx = (float)U[1 * P.vs + t], my = (float)U[2 * P.vs + t],
+                    mz = (float)U[3 * P.vs + t], E = (float)U[4 * P.vs + t];
+        const float ir = 1.0f / rho;
+        const float u = mx * ir, v = my * ir, w = mz * ir;
+        const float p = (float)P.gm1 * (E - 0.5f * (mx * u + my * v + mz * w));
+        Uf[0 * P.vs + t] = rho;
+        Uf[1 * P.vs + t] = mx;
+        Uf[2 * P.vs + t] = my;
+        Uf[3 * P.vs + t] = mz;
+        Uf[4 * P.vs + t] = E;
+        Wf[W_U * P.vs + t] = u;
+        Wf[W_V * P.vs + t] = v;
+        Wf[W_W * P.vs + t] = w;
+        Wf[W_P * P.vs + t] = p;
+        Wf[W_A * P.vs + t] = sqrtf((float)P.gamma * p * ir);
+        Wf[W_SR * P.vs + t] = sqrtf(rho);
+        Wf[W_H * P.vs + t] = (E + p) * ir;
+        Wf[W_T * P.vs + t] = (float)P.gM2 * p * ir;
+    }
+}
+
+__device__ __forceinline__ bool strong_jump(const Dev &P, const float *__restrict__ Uf,
+                                            const float *__restrict__ Wf, long long m, long long st)
+{
+    bool strong = false;
+    float p0 = Wf[W_P * P.vs + m - 2 * st], r0 = Uf[m - 2 * st];
+#pragma unroll
+    for (int s = 1; s < 6; s++) {
+        const long long id = m + (s - 2) * st;
+        const float p1 = Wf[W_P * P.vs + id], r1 = Uf[id];
+        strong |= fmaxf(p0, p1) > P.jump * fminf(p0, p1);
+        strong |= fmaxf(r0, r1) > P.jump * fminf(r0, r1);
+        p0 = p1;
+        r0 = r1;
+    }
+    return strong;
+}
+
+template <int DIR, int SCHEME, bool CURV>
+__device__ __noinline__ void fallback_flux(const Dev &P, const double *__restrict__ U,
+                                           const double *__restrict__ M, long long m, long long st,
+                                           float *Fh)
+{
+    const SrcFromState q{U, P.vs, P.gamma, P.gm1};
+    double f[NV];
+    interface_flux<DIR, SCHEME, CURV, double>(P, q, M, m, st, f);
+#pragma unroll
+    for (int v = 0; v < NV; v++) Fh[v] = (float)f[v];
+}
+
+template <int DIR, int SCHEME, bool CURV>
+__device__ __forceinline__ void mixed_flux(const Dev &P, const SrcArrays<float> &qf,
+                                           const double *__restrict__ U,
+                                           const double *__restrict__ M, long long m, long long st,
+                                           float Fh[NV])
+{
+    if (strong_jump(P, qf.U, qf.W, m, st)) fallback_flux<DIR, SCHEME, CURV>(P, U, M, m, st, Fh);
+    else interface_flux<DIR, SCHEME, CURV, float>(P, qf, M, m, st, Fh);
+}
+
+template <int DIR, int SCHEME, bool CURV>
+__global__ void __launch_bounds__(128) k_conv_char_mixed(Dev P, const double *__restrict__ U,
+                                                         const float *__restrict__ Uf,
+                                                         const float *__restrict__ Wf,
+                                                         const double *__restrict__ M,
+                                                         float *__restrict__ Rf, int accumulate, int chunk)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    if (a >= P.n[DA] || b >= P.n[DB]) return;
+    const int s0 = blockIdx.z * chunk;
+    const int s1 = min(s0 + chunk, P.n[DIR]);
+    int ii[3];
+    ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
+    const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const long long st = P.st[DIR];
+    const SrcArrays<float> qf{Uf, Wf, P.vs};
+    float Fm[NV];
+    mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, base + (long long)(s0 - 1) * st, st, Fm);
+    for (int m = s0; m < s1; m++) {
+        const long long id = base + (long long)m * st;
+        float Fp[NV];
+        mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, id, st, Fp);
+        const float fac = CURV ? (float)(P.shat[DIR] * M[9 * P.vs + id]) : (float)P.fac[DIR];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const float r = -fac * (Fp[v] - Fm[v]);
+            Rf[v * P.vs + id] = accumulate ? Rf[v * P.vs + id] + r : r;
             Fm[v] = Fp[v];
         }
     }
@@ -515,22 +663,31 @@ __global__ void __launch_bounds__(128) k_conv_central(Dev P, const double *__res
 // Periodic lines read ghost-inclusive or wrapped neighbours through f; non-periodic ends use
 // the one-sided closures.
 // ------------------------------------------------------------------------------------------
-template <typename Fetch>
-__device__ __forceinline__ double deriv_line(Fetch f, int ie, int n, bool per)
+template <typename T, typename Fetch>
+__device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool per)
 {
     if (per || (ie >= 2 && ie <= n - 3))
-        return (f(ie - 2) - 8.0 * f(ie - 1) + 8.0 * f(ie + 1) - f(ie + 2)) / 12.0;
-    if (ie == 0) return (-25.0 * f(0) + 48.0 * f(1) - 36.0 * f(2) + 16.0 * f(3) - 3.0 * f(4)) / 12.0;
-    if (ie == 1) return (-3.0 * f(0) - 10.0 * f(1) + 18.0 * f(2) - 6.0 * f(3) + f(4)) / 12.0;
+        return fdiv(f(ie - 2) - T(8) * f(ie - 1) + T(8) * f(ie + 1) - f(ie + 2), T(12));
+    if (ie == 0) return fdiv(T(-25) * f(0) + T(48) * f(1) - T(36) * f(2) + T(16) * f(3) - T(3) * f(4), T(12));
+    if (ie == 1) return fdiv(T(-3) * f(0) - T(10) * f(1) + T(18) * f(2) - T(6) * f(3) + f(4), T(12));
     if (ie == n - 2)
-        return (-f(n - 5) + 6.0 * f(n - 4) - 18.0 * f(n - 3) + 10.0 * f(n - 2) + 3.0 * f(n - 1)) / 12.0;
-    return (3.0 * f(n - 5) - 16.0 * f(n - 4) + 36.0 * f(n - 3) - 48.0 * f(n - 2) + 25.0 * f(n - 1)) / 12.0;
+        return fdiv(-f(n - 5) + T(6) * f(n - 4) - T(18) * f(n - 3) + T(10) * f(n - 2) + T(3) * f(n - 1), T(12));
+    return fdiv(T(3) * f(n - 5) - T(16) * f(n - 4) + T(36) * f(n - 3) - T(48) * f(n - 2) + T(25) * f(n - 1), T(12));
 }
 
-// Viscous fluxes (Eqs. 2-5) at interior nodes: V[d] = (S~_d . tau_{i.}, S~_d . (u_i tau_{i.} - q))
-template <bool CURV>
-__global__ void __launch_bounds__(128) k_visc_flux(Dev P, const double *__restrict__ W,
-                                                   const double *__restrict__ M, double *__restrict__ V)
+// Viscous fluxes (Eqs. 2-5) at interior nodes: V[d] = (S~_d . tau_{i.}, S~_d . (u_i tau_{i.} - q)).
+// T = double (plain path) or float (mixed path: gradients, tau and q in FP32, stored as FP64).
+template <typename T>
+__device__ __forceinline__ T viscosity_t(const Dev &P, T Tm)
+{
+    if (P.suth <= 0.0) return T(1);
+    const T s = T(P.suth);
+    return Tm * sqrt(Tm) * (T(1) + s) / (Tm + s);
+}
+
+template <bool CURV, typename T, typename S>
+__global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ W,
+                                                   const double *__restrict__ M, S *__restrict__ V)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const long long vs = P.vs;
@@ -542,11 +699,11 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const double *__restri
         const int k = (int)(q / P.n[1]);
         const int ijk[3] = {i, j, k};
         const long long id = node_index(P, i, j, k);
-        double dxi[3][4];
+        T dxi[3][4];
 #pragma unroll
         for (int e = 0; e < 3; e++) {
 #pragma unroll
-            for (int v = 0; v < 4; v++) dxi[e][v] = 0.0;
+            for (int v = 0; v < 4; v++) dxi[e][v] = T(0);
             if (!P.active[e]) continue;
             const int ie = ijk[e];
             const long long st = P.st[e];
@@ -554,50 +711,50 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const double *__restri
             const int widx[4] = {W_U, W_V, W_W, W_T};
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const double *f = W + widx[v] * vs + id;
-                dxi[e][v] = deriv_line([&](int s) { return f[(long long)(s - ie) * st]; }, ie, P.n[e], per);
+                const S *f = W + widx[v] * vs + id;
+                dxi[e][v] = deriv_line<T>([&](int s) { return T(f[(long long)(s - ie) * st]); }, ie, P.n[e], per);
             }
         }
-        double gr[4][3];
+        T gr[4][3];
         if (CURV) {
             const double jr = M[9 * vs + id];
 #pragma unroll
             for (int v = 0; v < 4; v++)
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    double s = 0.0;
+                    T s = T(0);
 #pragma unroll
-                    for (int e = 0; e < 3; e++) s += P.shat[e] * jr * M[(e * 3 + c) * vs + id] * dxi[e][v];
+                    for (int e = 0; e < 3; e++) s += T(P.shat[e] * jr * M[(e * 3 + c) * vs + id]) * dxi[e][v];
                     gr[v][c] = s;
                 }
         } else {
 #pragma unroll
             for (int v = 0; v < 4; v++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) gr[v][c] = P.fac[c] * dxi[c][v];
+                for (int c = 0; c < 3; c++) gr[v][c] = T(P.fac[c]) * dxi[c][v];
         }
-        const double T = W[W_T * vs + id];
-        const double mu = viscosity(P, T);
-        const double mr = mu / P.Re;
-        const double div = gr[0][0] + gr[1][1] + gr[2][2];
-        double tau[3][3];
+        const T Tm = T(W[W_T * vs + id]);
+        const T mu = viscosity_t<T>(P, Tm);
+        const T mr = mu / T(P.Re);
+        const T div = gr[0][0] + gr[1][1] + gr[2][2];
+        T tau[3][3];
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int b = 0; b < 3; b++)
-                tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? (2.0 / 3.0) * div : 0.0));
-        const double kq = mu * P.kq;
-        const double uu[3] = {W[W_U * vs + id], W[W_V * vs + id], W[W_W * vs + id]};
-        double e4[3];
+                tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? T(2.0 / 3.0) * div : T(0)));
+        const T kq = mu * T(P.kq);
+        const T uu[3] = {T(W[W_U * vs + id]), T(W[W_V * vs + id]), T(W[W_W * vs + id])};
+        T e4[3];
 #pragma unroll
         for (int b = 0; b < 3; b++) e4[b] = uu[0] * tau[0][b] + uu[1] * tau[1][b] + uu[2] * tau[2][b] + kq * gr[3][b];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             if (!P.active[d]) continue;
-            double out[4];
+            T out[4];
             if (CURV) {
-                const double S0 = M[(d * 3 + 0) * vs + id], S1 = M[(d * 3 + 1) * vs + id],
-                             S2 = M[(d * 3 + 2) * vs + id];
+                const T S0 = T(M[(d * 3 + 0) * vs + id]), S1 = T(M[(d * 3 + 1) * vs + id]),
+                        S2 = T(M[(d * 3 + 2) * vs + id]);
 #pragma unroll
                 for (int a = 0; a < 3; a++) out[a] = S0 * tau[a][0] + S1 * tau[a][1] + S2 * tau[a][2];
                 out[3] = S0 * e4[0] + S1 * e4[1] + S2 * e4[2];
@@ -607,17 +764,20 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const double *__restri
                 out[3] = e4[d];
             }
 #pragma unroll
-            for (int c = 0; c < 4; c++) V[(d * 4 + c) * vs + id] = out[c];
+            for (int c = 0; c < 4; c++) V[(d * 4 + c) * vs + id] = (S)out[c];
         }
     }
 }
 
 // Viscous divergence (flux form) + RK register update (Eqs. 36-37), or residual output.
-// MODE 0: RK stage (STAGE selects A_i/B_i; stage 0 has dU^(0) = 0); MODE 1: R_total -> R.
-template <int MODE, int STAGE, bool VISC, bool CURV>
+// MODE 0: RK stage (STAGE selects A_i/B_i; stage 0 has dU^(0) = 0); MODE 1: R_total -> Rout.
+// RT is the storage / arithmetic type of the residual and viscous fluxes (double plain, float
+// mixed); the register update itself is FP64 on both paths.
+template <int MODE, int STAGE, bool VISC, bool CURV, typename RT>
 __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, double *__restrict__ dU,
-                                                double *__restrict__ R, const double *__restrict__ V,
-                                                const double *__restrict__ M, int *__restrict__ err)
+                                                const RT *Rin, const RT *__restrict__ V,
+                                                const double *__restrict__ M, double *Rout,
+                                                int *__restrict__ err)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const long long vs = P.vs;
@@ -629,9 +789,9 @@ __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, d
         const int k = (int)(q / P.n[1]);
         const int ijk[3] = {i, j, k};
         const long long id = node_index(P, i, j, k);
-        double r[NV];
+        RT r[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) r[v] = R[v * vs + id];
+        for (int v = 0; v < NV; v++) r[v] = Rin[v * vs + id];
         if (VISC) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
@@ -639,11 +799,11 @@ __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, d
                 const int ie = ijk[d], n = P.n[d];
                 const long long st = P.st[d];
                 const bool per = P.bc[d][0] == BC_PERIODIC;
-                const double fac = CURV ? P.shat[d] * M[9 * vs + id] : P.fac[d];
+                const RT fac = RT(CURV ? P.shat[d] * M[9 * vs + id] : P.fac[d]);
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    const double *f = V + (d * 4 + c) * vs + id;
-                    const double D = deriv_line([&](int s) {
+                    const RT *f = V + (d * 4 + c) * vs + id;
+                    const RT D = deriv_line<RT>([&](int s) {
                         int w = s;
                         if (per) { w = s % n; if (w < 0) w += n; }
                         return f[(long long)(w - ie) * st];
@@ -654,13 +814,13 @@ __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, d
         }
         if (MODE == 1) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) R[v * vs + id] = r[v];
+            for (int v = 0; v < NV; v++) Rout[v * vs + id] = (double)r[v];
             continue;
         }
         bool bad = false;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            double du = P.dt * r[v];
+            double du = P.dt * (double)r[v];
             if (STAGE > 0) du = c_rkA[STAGE] * dU[v * vs + id] + du;
             dU[v * vs + id] = du;
             const double un = U[v * vs + id] + c_rkB[STAGE] * du;
@@ -716,7 +876,7 @@ __global__ void k_metric_raw(Dev P, const double *__restrict__ X, double Lp0, do
                     const long long o = ((long long)jj[2] * P.n[1] + jj[1]) * P.n[0] + jj[0];
                     return (X[c * N + o] - xc) + (c == d ? sh * Lp[d] : 0.0);
                 };
-                Xd[d][c] = deriv_line(f, ijk[d], n, per);
+                Xd[d][c] = deriv_line<double>(f, ijk[d], n, per);
             }
         }
         double S[3][3];
@@ -869,6 +1029,14 @@ static int conv_chunk(const Dev &P, int d)
     return chunk;
 }
 
+template <int DIR, int SCHEME, bool CURV>
+static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, dim3 grd, dim3 blk, cudaStream_t s)
+{
+    if (P.mixed)
+        k_conv_char_mixed<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.Uf, B.Wf, B.M, B.Rf, acc, chunk);
+    else k_conv_char<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+}
+
 template <int DIR>
 static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
 {
@@ -880,12 +1048,21 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
         if (P.curv) k_conv_central<DIR, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
         else k_conv_central<DIR, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
     } else if (P.scheme == SCH_WENO5JS) {
-        if (P.curv) k_conv_char<DIR, SCH_WENO5JS, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
-        else k_conv_char<DIR, SCH_WENO5JS, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+        if (P.curv) conv_char_launch<DIR, SCH_WENO5JS, true>(P, B, acc, chunk, grd, blk, s);
+        else conv_char_launch<DIR, SCH_WENO5JS, false>(P, B, acc, chunk, grd, blk, s);
     } else {
-        if (P.curv) k_conv_char<DIR, SCH_TENO5, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
-        else k_conv_char<DIR, SCH_TENO5, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+        if (P.curv) conv_char_launch<DIR, SCH_TENO5, true>(P, B, acc, chunk, grd, blk, s);
+        else conv_char_launch<DIR, SCH_TENO5, false>(P, B, acc, chunk, grd, blk, s);
     }
+}
+
+template <int MODE, int STAGE, bool VISC, bool CURV>
+static void update_t(const Dev &P, const Bufs &B, int g, cudaStream_t s)
+{
+    if (P.mixed)
+        k_update<MODE, STAGE, VISC, CURV, float><<<g, 128, 0, s>>>(P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err);
+    else
+        k_update<MODE, STAGE, VISC, CURV, double><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.R, B.err);
 }
 
 template <int MODE, int STAGE>
@@ -894,11 +1071,11 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     int g = grid_for(N, 128);
     if (P.viscous) {
-        if (P.curv) k_update<MODE, STAGE, true, true><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
-        else k_update<MODE, STAGE, true, false><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
+        if (P.curv) update_t<MODE, STAGE, true, true>(P, B, g, s);
+        else update_t<MODE, STAGE, true, false>(P, B, g, s);
     } else {
-        if (P.curv) k_update<MODE, STAGE, false, true><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
-        else k_update<MODE, STAGE, false, false><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.err);
+        if (P.curv) update_t<MODE, STAGE, false, true>(P, B, g, s);
+        else update_t<MODE, STAGE, false, false>(P, B, g, s);
     }
 }
 
@@ -932,7 +1109,8 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         launches++;
     }
     if (tap) (*tap)("prim", s);
-    k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
+    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf);
+    else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
     int acc = 0;
     for (int d = 0; d < 3; d++) {
@@ -947,8 +1125,14 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     if (P.viscous) {
         long long N = (long long)P.n[0] * P.n[1] * P.n[2];
         if (tap) (*tap)("visc_flux", s);
-        if (P.curv) k_visc_flux<true><<<grid_for(N, 128), 128, 0, s>>>(P, B.W, B.M, B.V);
-        else k_visc_flux<false><<<grid_for(N, 128), 128, 0, s>>>(P, B.W, B.M, B.V);
+        const int g = grid_for(N, 128);
+        if (P.mixed) {
+            if (P.curv) k_visc_flux<true, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
+            else k_visc_flux<false, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
+        } else {
+            if (P.curv) k_visc_flux<true, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
+            else k_visc_flux<false, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
+        }
         launches++;
     }
     return launches;

@@ -24,7 +24,8 @@ OSBLI_FP64, OSBLI_MIXED = 0, 1
 EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_set_state",
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
             "osbli_launches_per_step", "osbli_last_error", "osbli_profile_residual",
-            "osbli_profile_name", "osbli_fp64_peak", "osbli_residual_noalloc"]
+            "osbli_profile_name", "osbli_fp64_peak", "osbli_residual_noalloc",
+            "osbli_fp32_peak"]
 
 
 class osbli_params(ctypes.Structure):
@@ -79,6 +80,8 @@ def load():
         L.osbli_residual_noalloc.restype = ctypes.c_int
         L.osbli_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
         L.osbli_fp64_peak.restype = ctypes.c_int
+        L.osbli_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        L.osbli_fp32_peak.restype = ctypes.c_int
         L.osbli_last_error.argtypes = [vp]
         L.osbli_last_error.restype = ctypes.c_char_p
         for name in ("osbli_create", "osbli_set_boundary_data", "osbli_set_state", "osbli_get_state",
@@ -190,6 +193,12 @@ def osbli_residual_noalloc(params, d_U, d_R, cuda_stream=None):
 def osbli_fp64_peak():
     t = ctypes.c_double()
     _check(None, load().osbli_fp64_peak(ctypes.byref(t)))
+    return t.value
+
+
+def osbli_fp32_peak():
+    t = ctypes.c_double()
+    _check(None, load().osbli_fp32_peak(ctypes.byref(t)))
     return t.value
 
 

@@ -1,0 +1,93 @@
+"""Mixed-precision path (FP32 reconstruction arithmetic, FP64 state / RK registers / metrics,
+FP64 interfaces across strong jumps) against the FP64 oracle.
+
+Bar: relative L2 error per conserved variable (||U_mixed - U_oracle||_2 / ||U_oracle||_2, max over
+the five variables) <= 1e-5 on smooth flow; shock position within one cell on the Sod problem.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_14933_b300 import inputs as I
+from paper_2007_14933_b300 import osbli
+
+pytestmark = pytest.mark.gpu
+
+L2_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_14933_b300 import build
+    build.build()
+    osbli.load()
+
+
+def l2rel(a, b):
+    a = a.reshape(5, -1)
+    b = b.reshape(5, -1)
+    return float(max(np.linalg.norm(a[v] - b[v]) / max(np.linalg.norm(b[v]), 1e-300)
+                     for v in range(5) if np.linalg.norm(b[v]) > 0))
+
+
+def mixed_vs_oracle(cfg, U, steps):
+    s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+    s.set_state(U)
+    s.step(steps)
+    Ug = s.get_state()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(steps)
+    return Ug, o.get_state()
+
+
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+def test_mixed_tgv_smooth_phase_l2(scheme):
+    # 40 steps reach t ~ 1.1, before the Ma 1.25 TGV forms shocklets (smooth flow)
+    cfg, U = I.tgv(n=(32, 28, 24), Ma=1.25, scheme=scheme)
+    Ug, Uo = mixed_vs_oracle(cfg, U, 40)
+    assert l2rel(Ug, Uo) <= L2_TOL
+
+
+def test_mixed_curvilinear_euler_wave_l2():
+    cfg, U = I.euler_wave(32, scheme=I.TENO5)
+    Ug, Uo = mixed_vs_oracle(cfg, U, 100)
+    assert l2rel(Ug, Uo) <= L2_TOL
+
+
+def test_mixed_sod_shock_position_within_one_cell():
+    cfg, U, x = I.sod()
+    Ug, Uo = mixed_vs_oracle(cfg, U, 800)
+    rg, ro = Ug[0, 0, 0], Uo[0, 0, 0]
+    mid = 0.5 * (0.26557 + 0.125)
+
+    def shock(r):
+        return x[np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]]
+    assert abs(shock(rg) - shock(ro)) <= 1.0 / 400 + 1e-12
+    assert l2rel(Ug, Uo) <= 1e-4          # discontinuous solution: recorded, looser
+
+
+def test_mixed_residual_on_jumps_and_walls():
+    from tests.test_gpu_parity import wall_box
+    for cfg, U in [wall_box()] + [(dict(n=(13, 9, 7), gamma=1.4, Re=0.0, Ma=1.0, scheme=I.TENO5,
+                                        teno_ct=1e-5, bc=[[0, 0]] * 3, h=(0.1, 0.2, 0.3)),
+                                   I.random_state((13, 9, 7), seed=3, shocky=True))]:
+        s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+        s.set_state(U)
+        Rg = s.residual()
+        o = O.Oracle(cfg)
+        o.set_state(U)
+        Ro = o.residual()
+        scale = np.abs(Ro).reshape(5, -1).max(axis=1)[:, None]
+        err = (np.abs(Rg - Ro).reshape(5, -1) / scale).max()
+        assert err < 1e-4, err
+
+
+def test_mixed_rejects_central_scheme():
+    cfg, U = I.tgv(12, Ma=0.1, scheme=I.CENTRAL4)
+    with pytest.raises(osbli.OsbliError) as e:
+        osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+    assert e.value.code == osbli.OSBLI_EINVAL
