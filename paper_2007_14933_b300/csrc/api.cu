@@ -62,7 +62,8 @@ static void free_all(osbli *h)
                       h->diag_out};
     for (double *b : bufs)
         if (b) cudaFree(b);
-    float *fbufs[] = {h->B.Uf, h->B.Wf, h->B.Rf, h->B.Vf};
+    float *fbufs[] = {h->B.Uf, h->B.Wf, h->B.Rf, h->B.Vf, h->B.Dst};
+    if (h->B.flag) cudaFree(h->B.flag);
     for (float *b : fbufs)
         if (b) cudaFree(b);
     for (int f = 0; f < 6; f++)
@@ -201,9 +202,12 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     }
     if (P.mixed) {
         const size_t fsb = (size_t)P.vs * sizeof(float);
-        CKC(cudaMalloc(&h->B.Uf, NV * fsb));
+        CKC(cudaMalloc(&h->B.Uf, 2 * NV * fsb));
         CKC(cudaMalloc(&h->B.Wf, NW * fsb));
         CKC(cudaMalloc(&h->B.Rf, NV * fsb));
+        CKC(cudaMalloc(&h->B.flag, (size_t)P.vs));
+        CKC(cudaMemsetAsync(h->B.flag, 0, (size_t)P.vs, h->stream));
+        CKC(cudaMalloc(&h->B.Dst, NV * fsb));
         CKC(cudaMemsetAsync(h->B.Rf, 0, NV * fsb, h->stream));
         if (P.viscous) {
             CKC(cudaMalloc(&h->B.Vf, 12 * fsb));
@@ -428,6 +432,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction
+        if (P.mixed && !P.curv) per_stage++;   // strong-jump patch of the direction
         for (int s = 0; s < 2; s++) {
             const int bc = P.bc[d][s];
             if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;

@@ -475,22 +475,27 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
 // two adjacent nodes (pressure or density ratio above P.jump) keeps FP64: its primitives are
 // recomputed from the FP64 state and its eigenvector projection and reconstruction run in FP64.
 // ------------------------------------------------------------------------------------------
+// FP32 node copies for the mixed path.  Uf planes 0-4 hold the state rounded to FP32 and planes
+// 5-9 the FP32 rounding of the remainder (U = hi + lo to ~48 bits), so that differences
+// between nearby nodes are formed to FP32 accuracy relative to the difference itself.  Wf holds
+// FP32 primitives (u, v, w, p, a, sqrt(rho), H, T).
 __global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restrict__ Uf,
                              float *__restrict__ Wf)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
          t += (long long)gridDim.x * blockDim.x) {
-        const float rho = (float)U[0 * P.vs + t];
-        const float mx = (float)U[1 * P.vs + t], my = (float)U[2 * P.vs + t],
-                    mz = (float)U[3 * P.vs + t], E = (float)U[4 * P.vs + t];
+        float h[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const double x = U[v * P.vs + t];
+            h[v] = (float)x;
+            Uf[v * P.vs + t] = h[v];
+            Uf[(NV + v) * P.vs + t] = (float)(x - (double)h[v]);
+        }
+        const float rho = h[0], mx = h[1], my = h[2], mz = h[3], E = h[4];
         const float ir = 1.0f / rho;
         const float u = mx * ir, v = my * ir, w = mz * ir;
         const float p = (float)P.gm1 * (E - 0.5f * (mx * u + my * v + mz * w));
-        Uf[0 * P.vs + t] = rho;
-        Uf[1 * P.vs + t] = mx;
-        Uf[2 * P.vs + t] = my;
-        Uf[3 * P.vs + t] = mz;
-        Uf[4 * P.vs + t] = E;
         Wf[W_U * P.vs + t] = u;
         Wf[W_V * P.vs + t] = v;
         Wf[W_W * P.vs + t] = w;
@@ -997,6 +1002,312 @@ __global__ void k_diag_final(const double *__restrict__ part, double *__restrict
     out[8] = acc[8];
 }
 
+// ------------------------------------------------------------------------------------------
+// Mixed path on Cartesian grids: delta form.  The reconstruction is affine (weights sum to one,
+// the smoothness indicators see only differences), so the interface flux between node m and
+// m+1 is F_m + D with D the characteristic reconstruction of the flux and state differences
+// relative to node m.  The differences are formed from the hi/lo node copies and the product
+// rule (F = u_n U + p e_n + p u_n e_E), so every FP32 operation works on numbers of the size
+// of the local variation, and the residual (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2} keeps FP32
+// accuracy relative to itself.
+// ------------------------------------------------------------------------------------------
+template <int DIR>
+__device__ __forceinline__ void node_flux_fp64(const Dev &P, const double *__restrict__ U, long long id,
+                                               double F[NV])
+{
+    const double r = U[id], E = U[4 * P.vs + id];
+    const double m0 = U[1 * P.vs + id], m1 = U[2 * P.vs + id], m2 = U[3 * P.vs + id];
+    const double mm[3] = {m0, m1, m2};
+    const double un = mm[DIR] / r;
+    const double p = P.gm1 * (E - 0.5 * (m0 * m0 + m1 * m1 + m2 * m2) / r);
+    F[0] = r * un;
+    F[1] = m0 * un;
+    F[2] = m1 * un;
+    F[3] = m2 * un;
+    F[1 + DIR] += p;
+    F[4] = (E + p) * un;
+}
+
+template <int DIR, int SCHEME>
+__device__ __noinline__ void fallback_delta(const Dev &P, const double *__restrict__ U, long long m,
+                                            long long st, float *D, float *dF1)
+{
+    const SrcFromState q{U, P.vs, P.gamma, P.gm1};
+    double Fh[NV], Fm_[NV], Fl[NV];
+    interface_flux<DIR, SCHEME, false, double>(P, q, nullptr, m, st, Fh);
+    node_flux_fp64<DIR>(P, U, m, Fm_);
+    node_flux_fp64<DIR>(P, U, m - st, Fl);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        D[v] = (float)(Fh[v] - Fm_[v]);
+        dF1[v] = (float)(Fl[v] - Fm_[v]);
+    }
+}
+
+template <int DIR, int SCHEME>
+__device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict__ Uf,
+                                           const float *__restrict__ Wf, long long m, long long st,
+                                           float D[NV], float dF1[NV])
+{
+    const long long vs = P.vs;
+    const long long mr = m + st;
+    const float gm1 = (float)P.gm1;
+    // Roe average of nodes m, m+1 (FP32 node values)
+    const float sl = Wf[W_SR * vs + m], sr = Wf[W_SR * vs + mr];
+    const float inv = __fdividef(1.f, sl + sr);
+    const float u0 = (sl * Wf[W_U * vs + m] + sr * Wf[W_U * vs + mr]) * inv;
+    const float u1 = (sl * Wf[W_V * vs + m] + sr * Wf[W_V * vs + mr]) * inv;
+    const float u2 = (sl * Wf[W_W * vs + m] + sr * Wf[W_W * vs + mr]) * inv;
+    const float H = (sl * Wf[W_H * vs + m] + sr * Wf[W_H * vs + mr]) * inv;
+    const float q2 = u0 * u0 + u1 * u1 + u2 * u2;
+    const float c2 = gm1 * (H - 0.5f * q2);
+    const float ia = rsqrtf(c2);
+    const float a = c2 * ia;
+    const Frame<DIR, false, float> fr{};
+    const float un = fr.dn(u0, u1, u2), ut1 = fr.dt1(u0, u1, u2), ut2 = fr.dt2(u0, u1, u2);
+    const float b1 = gm1 * ia * ia;
+    const float b2 = 0.5f * b1 * q2;
+
+    // wave speeds
+    float al0 = 0.f, al1 = 0.f, al4 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const long long id = m + (s - 2) * st;
+        const float uns = Wf[(W_U + DIR) * vs + id], cs = Wf[W_A * vs + id];
+        al0 = fmaxf(al0, fabsf(uns - cs));
+        al1 = fmaxf(al1, fabsf(uns));
+        al4 = fmaxf(al4, fabsf(uns + cs));
+    }
+    const float hh[NV] = {0.5f * al0, 0.5f * al1, 0.5f * al1, 0.5f * al1, 0.5f * al4};
+
+    // reference node m
+    float Uc[NV], Ul[NV], uc[3];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        Uc[v] = Uf[v * vs + m];
+        Ul[v] = Uf[(NV + v) * vs + m];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) uc[c] = Wf[(W_U + c) * vs + m];
+    const float pc = Wf[W_P * vs + m];
+
+    float gp[NV][5], gm[NV][5];
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        float Vc[NV], Gc[NV];
+        if (s == 2) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) { Vc[v] = 0.f; Gc[v] = 0.f; }
+        } else {
+            const long long id = m + (s - 2) * st;
+            float dU[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++)
+                dU[v] = (Uf[v * vs + id] - Uc[v]) + (Uf[(NV + v) * vs + id] - Ul[v]);
+            const float rk = Uf[id];
+            const float irk = __fdividef(1.f, rk);
+            float du[3], uk[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                du[c] = (dU[1 + c] - uc[c] * dU[0]) * irk;     // u_k - u_c
+                uk[c] = uc[c] + du[c];
+            }
+            // p_k - p_c = (gamma-1) (dE - d(m.u)/2), d(m.u) = dm . u_k + m_c . du
+            const float dmu = dU[1] * uk[0] + dU[2] * uk[1] + dU[3] * uk[2] +
+                              Uc[1] * du[0] + Uc[2] * du[1] + Uc[3] * du[2];
+            const float dp = gm1 * (dU[4] - 0.5f * dmu);
+            const float unk = uk[DIR], dun = du[DIR];
+            float dF[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) dF[v] = unk * dU[v] + dun * Uc[v];
+            dF[1 + DIR] += dp;
+            dF[4] += (pc + dp) * dun + dp * uc[DIR];
+            if (s == 1) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) dF1[v] = dF[v];
+            }
+            {
+                const float um = u0 * dU[1] + u1 * dU[2] + u2 * dU[3];
+                const float A = b2 * dU[0] + b1 * (dU[4] - um);
+                const float B = (un * dU[0] - fr.dn(dU[1], dU[2], dU[3])) * ia;
+                Vc[0] = 0.5f * (A + B);
+                Vc[4] = 0.5f * (A - B);
+                Vc[1] = dU[0] - A;
+                Vc[2] = fr.dt1(dU[1], dU[2], dU[3]) - ut1 * dU[0];
+                Vc[3] = fr.dt2(dU[1], dU[2], dU[3]) - ut2 * dU[0];
+            }
+            {
+                const float um = u0 * dF[1] + u1 * dF[2] + u2 * dF[3];
+                const float A = b2 * dF[0] + b1 * (dF[4] - um);
+                const float B = (un * dF[0] - fr.dn(dF[1], dF[2], dF[3])) * ia;
+                Gc[0] = 0.5f * (A + B);
+                Gc[4] = 0.5f * (A - B);
+                Gc[1] = dF[0] - A;
+                Gc[2] = fr.dt1(dF[1], dF[2], dF[3]) - ut1 * dF[0];
+                Gc[3] = fr.dt2(dF[1], dF[2], dF[3]) - ut2 * dF[0];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            if (s < 5) gp[j][s] = fmaf(hh[j], Vc[j], 0.5f * Gc[j]);
+            if (s > 0) gm[j][s - 1] = fmaf(-hh[j], Vc[j], 0.5f * Gc[j]);
+        }
+    }
+    float g[NV];
+    const float ct = (float)P.ct;
+#pragma unroll
+    for (int j = 0; j < NV; j++)
+        g[j] = recon5<SCHEME, float>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
+               recon5<SCHEME, float>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+    const float s04 = g[0] + g[4], d40 = g[4] - g[0];
+    const float sm = s04 + g[1];
+    D[0] = sm;
+    const float uu[3] = {u0, u1, u2};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float f = uu[c] * sm;
+        if (c == DIR) f += a * d40;
+        if (c == Cart<DIR>::T1) f += float(Cart<DIR>::S1) * g[2];
+        if (c == Cart<DIR>::T2) f += float(Cart<DIR>::S2) * g[3];
+        D[1 + c] = f;
+    }
+    D[4] = H * s04 + a * un * d40 + 0.5f * q2 * g[1] + ut1 * g[2] + ut2 * g[3];
+}
+
+// One interface of the delta-form mixed path.  Interfaces whose stencil holds a strong jump are
+// flagged (flag[m] = 1, m = left node) and their FP32 D kept in Dst; a later per-node pass
+// (k_patch_strong) recomputes them in FP64 and corrects the residual, so the FP32 pass carries
+// no FP64 code (and keeps its register budget).
+template <int DIR, int SCHEME>
+__device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restrict__ Uf,
+                                              const float *__restrict__ Wf, long long m, long long st,
+                                              float D[NV], float dF1[NV], unsigned char *__restrict__ flag,
+                                              float *__restrict__ Dst)
+{
+    delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, D, dF1);
+    const bool strong = strong_jump(P, Uf, Wf, m, st);
+    flag[m] = strong ? 1 : 0;
+    if (strong) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Dst[v * P.vs + m] = D[v];
+    }
+}
+
+// y and z: thread per line of the cross directions (lanes along x, coalesced), marching along DIR.
+template <int DIR, int SCHEME>
+__global__ void __launch_bounds__(128) k_conv_char_delta(Dev P, const float *__restrict__ Uf,
+                                                         const float *__restrict__ Wf,
+                                                         float *__restrict__ Rf,
+                                                         unsigned char *__restrict__ flag,
+                                                         float *__restrict__ Dst, int accumulate, int chunk)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    if (a >= P.n[DA] || b >= P.n[DB]) return;
+    const int s0 = blockIdx.z * chunk;
+    const int s1 = min(s0 + chunk, P.n[DIR]);
+    int ii[3];
+    ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
+    const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const long long st = P.st[DIR];
+    const float fac = (float)P.fac[DIR];
+    float Dm[NV], dF1[NV];
+    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, Dm, dF1, flag, Dst);
+    for (int m = s0; m < s1; m++) {
+        const long long id = base + (long long)m * st;
+        float Dp[NV];
+        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, Dp, dF1, flag, Dst);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            // F_{m+1/2} - F_{m-1/2} = (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2}
+            const float r = -fac * ((Dp[v] - Dm[v]) - dF1[v]);
+            Rf[v * P.vs + id] = accumulate ? Rf[v * P.vs + id] + r : r;
+            Dm[v] = Dp[v];
+        }
+    }
+}
+
+// x: thread per interface along a row segment of up to XSEG nodes (lanes along x, coalesced);
+// the flux difference takes the left neighbour's D from shared memory.  Thread 0 also forms
+// the segment's leftmost interface.
+constexpr int XSEG = 256;
+template <int SCHEME>
+__global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *__restrict__ Uf,
+                                                            const float *__restrict__ Wf,
+                                                            float *__restrict__ Rf,
+                                                            unsigned char *__restrict__ flag,
+                                                            float *__restrict__ Dst, int accumulate)
+{
+    __shared__ float sD[NV][XSEG + 1];
+    const int row = blockIdx.x;
+    const int j = row % P.n[1], k = row / P.n[1];
+    const int x0 = blockIdx.y * XSEG;
+    const int t = threadIdx.x;
+    const int i = x0 + t;
+    const long long base = node_index(P, 0, j, k);
+    float dF1[NV];
+    if (i < P.n[0]) {
+        float D[NV];
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, D, dF1, flag, Dst);
+#pragma unroll
+        for (int v = 0; v < NV; v++) sD[v][t + 1] = D[v];
+    }
+    if (t == 0) {
+        float D[NV], unused[NV];
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + x0 - 1, 1, D, unused, flag, Dst);
+#pragma unroll
+        for (int v = 0; v < NV; v++) sD[v][0] = D[v];
+    }
+    __syncthreads();
+    if (i >= P.n[0]) return;
+    const float fac = (float)P.fac[0];
+    const long long id = base + i;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        const float r = -fac * ((sD[v][t + 1] - sD[v][t]) - dF1[v]);
+        Rf[v * P.vs + id] = accumulate ? Rf[v * P.vs + id] + r : r;
+    }
+}
+
+// FP64 correction of flagged interfaces, one thread per interior node (deterministic):
+// node m's flux difference used D_{m+1/2} - D_{m-1/2}; replace the FP32 D of every flagged one
+// of its two interfaces by the FP64 value.
+template <int DIR, int SCHEME>
+__global__ void __launch_bounds__(128) k_patch_strong(Dev P, const double *__restrict__ U,
+                                                      float *__restrict__ Rf,
+                                                      const unsigned char *__restrict__ flag,
+                                                      const float *__restrict__ Dst)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const long long st = P.st[DIR];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        const long long id = node_index(P, i, j, k);
+        const bool fl = flag[id - st] != 0, fr = flag[id] != 0;
+        if (!fl && !fr) continue;
+        float corr[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float D64[NV], unused[NV];
+        if (fr) {
+            fallback_delta<DIR, SCHEME>(P, U, id, st, D64, unused);
+#pragma unroll
+            for (int v = 0; v < NV; v++) corr[v] += D64[v] - Dst[v * P.vs + id];
+        }
+        if (fl) {
+            fallback_delta<DIR, SCHEME>(P, U, id - st, st, D64, unused);
+#pragma unroll
+            for (int v = 0; v < NV; v++) corr[v] -= D64[v] - Dst[v * P.vs + id - st];
+        }
+        const float fac = (float)P.fac[DIR];
+#pragma unroll
+        for (int v = 0; v < NV; v++) Rf[v * P.vs + id] += -fac * corr[v];
+    }
+}
+
 // ==========================================================================================
 // host-side launchers
 // ==========================================================================================
@@ -1032,9 +1343,18 @@ static int conv_chunk(const Dev &P, int d)
 template <int DIR, int SCHEME, bool CURV>
 static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, dim3 grd, dim3 blk, cudaStream_t s)
 {
-    if (P.mixed)
+    if (P.mixed && !CURV) {
+        if (DIR == 0) {
+            dim3 g(P.n[1] * P.n[2], (P.n[0] + XSEG - 1) / XSEG);
+            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, acc);
+        } else {
+            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, acc, chunk);
+        }
+    } else if (P.mixed) {
         k_conv_char_mixed<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.Uf, B.Wf, B.M, B.Rf, acc, chunk);
-    else k_conv_char<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+    } else {
+        k_conv_char<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+    }
 }
 
 template <int DIR>
@@ -1079,6 +1399,21 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     }
 }
 
+static void launch_patch(const Dev &P, const Bufs &B, int d, cudaStream_t s)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const int g = grid_for(N, 128);
+    if (P.scheme == SCH_WENO5JS) {
+        if (d == 0) k_patch_strong<0, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+        else if (d == 1) k_patch_strong<1, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+        else k_patch_strong<2, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+    } else {
+        if (d == 0) k_patch_strong<0, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+        else if (d == 1) k_patch_strong<1, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+        else k_patch_strong<2, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+    }
+}
+
 // Optional per-launch event taps (kernel timing): before each launch an event is recorded and
 // the launch is named; a final event closes the last one.
 struct Tap {
@@ -1113,6 +1448,8 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
     int acc = 0;
+    static const char *patch_names[3] = {"patch_x", "patch_y", "patch_z"};
+    const bool patch = P.mixed && !P.curv && P.scheme != SCH_CENTRAL4;
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         if (tap) (*tap)(conv_names[d], s);
@@ -1121,6 +1458,11 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         else conv_dir<2>(P, B, acc, s);
         acc = 1;
         launches++;
+        if (patch) {
+            if (tap) (*tap)(patch_names[d], s);
+            launch_patch(P, B, d, s);
+            launches++;
+        }
     }
     if (P.viscous) {
         long long N = (long long)P.n[0] * P.n[1] * P.n[2];

@@ -12,8 +12,10 @@ struct Bufs {
     double *M = nullptr;                               // [10][vs] (curvilinear only)
     double *V = nullptr;                               // [3][4][vs] (viscous only)
     double *bd[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    float *Uf = nullptr, *Wf = nullptr;                // mixed path: FP32 node copies [5], [NW]
+    float *Uf = nullptr, *Wf = nullptr;                // mixed path: FP32 node copies [2*5] (hi, lo), [NW]
     float *Rf = nullptr, *Vf = nullptr;                // mixed path: FP32 residual [5], viscous [12]
+    unsigned char *flag = nullptr;                     // mixed path: strong-jump interface flags [vs]
+    float *Dst = nullptr;                              // mixed path: FP32 flux of flagged interfaces [5]
     int *err = nullptr;                                // device error word
 };
 
