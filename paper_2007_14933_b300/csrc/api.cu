@@ -62,7 +62,7 @@ static void free_all(osbli *h)
                       h->diag_out};
     for (double *b : bufs)
         if (b) cudaFree(b);
-    float *fbufs[] = {h->B.Uf, h->B.Wf, h->B.Rf, h->B.Vf, h->B.Dst};
+    float *fbufs[] = {h->B.Uf, h->B.Wf, h->B.Rf, h->B.Vf, h->B.Dst, h->B.Dl};
     if (h->B.flag) cudaFree(h->B.flag);
     for (float *b : fbufs)
         if (b) cudaFree(b);
@@ -208,6 +208,8 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
         CKC(cudaMalloc(&h->B.flag, (size_t)P.vs));
         CKC(cudaMemsetAsync(h->B.flag, 0, (size_t)P.vs, h->stream));
         CKC(cudaMalloc(&h->B.Dst, NV * fsb));
+        const long long lefts = (long long)n[1] * n[2] * ((n[0] + 255) / 256);
+        CKC(cudaMalloc(&h->B.Dl, (size_t)lefts * NV * sizeof(float)));
         CKC(cudaMemsetAsync(h->B.Rf, 0, NV * fsb, h->stream));
         if (P.viscous) {
             CKC(cudaMalloc(&h->B.Vf, 12 * fsb));
@@ -217,8 +219,8 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     CKC(cudaMalloc(&h->stage, (size_t)NV * N * sizeof(double)));
     CKC(cudaMalloc(&h->diag_part, (size_t)diag_partial_size() * sizeof(double)));
     CKC(cudaMalloc(&h->diag_out, 16 * sizeof(double)));
-    CKC(cudaMalloc(&h->B.err, sizeof(int)));
-    CKC(cudaMemsetAsync(h->B.err, 0, sizeof(int), h->stream));
+    CKC(cudaMalloc(&h->B.err, 4 * sizeof(int)));   // error word + strong-jump counts x, y, z
+    CKC(cudaMemsetAsync(h->B.err, 0, 4 * sizeof(int), h->stream));
     CKC(cudaMallocHost(&h->h_err, sizeof(int)));
     CKC(cudaMallocHost(&h->h_diag, 16 * sizeof(double)));
     for (int d = 0; d < 3; d++)
@@ -432,7 +434,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction
-        if (P.mixed && !P.curv) per_stage++;   // strong-jump patch of the direction
+        if (P.mixed && !P.curv) per_stage += (d == 0) ? 2 : 1;   // patch (+ x segment lefts)
         for (int s = 0; s < 2; s++) {
             const int bc = P.bc[d][s];
             if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;

@@ -480,8 +480,10 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
 // between nearby nodes are formed to FP32 accuracy relative to the difference itself.  Wf holds
 // FP32 primitives (u, v, w, p, a, sqrt(rho), H, T).
 __global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restrict__ Uf,
-                             float *__restrict__ Wf)
+                             float *__restrict__ Wf, int *__restrict__ nstrong)
 {
+    // per-direction counts of strong-jump interfaces of this stage start at zero
+    if (blockIdx.x == 0 && threadIdx.x < 3) nstrong[threadIdx.x] = 0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
          t += (long long)gridDim.x * blockDim.x) {
         float h[NV];
@@ -1182,12 +1184,13 @@ template <int DIR, int SCHEME>
 __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restrict__ Uf,
                                               const float *__restrict__ Wf, long long m, long long st,
                                               float D[NV], float dF1[NV], unsigned char *__restrict__ flag,
-                                              float *__restrict__ Dst)
+                                              float *__restrict__ Dst, int *__restrict__ nstrong)
 {
     delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, D, dF1);
     const bool strong = strong_jump(P, Uf, Wf, m, st);
     flag[m] = strong ? 1 : 0;
     if (strong) {
+        atomicAdd(nstrong + DIR, 1);
 #pragma unroll
         for (int v = 0; v < NV; v++) Dst[v * P.vs + m] = D[v];
     }
@@ -1195,11 +1198,12 @@ __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restr
 
 // y and z: thread per line of the cross directions (lanes along x, coalesced), marching along DIR.
 template <int DIR, int SCHEME>
-__global__ void __launch_bounds__(128) k_conv_char_delta(Dev P, const float *__restrict__ Uf,
+__global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf,
                                                          float *__restrict__ Rf,
                                                          unsigned char *__restrict__ flag,
-                                                         float *__restrict__ Dst, int accumulate, int chunk)
+                                                         float *__restrict__ Dst, int *__restrict__ nstrong,
+                                                         int accumulate, int chunk)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1213,11 +1217,11 @@ __global__ void __launch_bounds__(128) k_conv_char_delta(Dev P, const float *__r
     const long long st = P.st[DIR];
     const float fac = (float)P.fac[DIR];
     float Dm[NV], dF1[NV];
-    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, Dm, dF1, flag, Dst);
+    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, Dm, dF1, flag, Dst, nstrong);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         float Dp[NV];
-        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, Dp, dF1, flag, Dst);
+        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, Dp, dF1, flag, Dst, nstrong);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             // F_{m+1/2} - F_{m-1/2} = (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2}
@@ -1229,18 +1233,43 @@ __global__ void __launch_bounds__(128) k_conv_char_delta(Dev P, const float *__r
 }
 
 // x: thread per interface along a row segment of up to XSEG nodes (lanes along x, coalesced);
-// the flux difference takes the left neighbour's D from shared memory.  Thread 0 also forms
-// the segment's leftmost interface.
+// the flux difference takes the left neighbour's D from shared memory.  The segment's leftmost
+// interface comes from k_conv_left_x, so every thread forms exactly one interface.
 constexpr int XSEG = 256;
+
+template <int SCHEME>
+__global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restrict__ Uf,
+                                                     const float *__restrict__ Wf,
+                                                     unsigned char *__restrict__ flag,
+                                                     float *__restrict__ Dst, int *__restrict__ nstrong,
+                                                     float *__restrict__ Dl)
+{
+    const int nseg = (P.n[0] + XSEG - 1) / XSEG;
+    const long long total = (long long)P.n[1] * P.n[2] * nseg;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int seg = (int)(t % nseg);
+    const long long row = t / nseg;
+    const int j = (int)(row % P.n[1]), k = (int)(row / P.n[1]);
+    const long long base = node_index(P, 0, j, k);
+    float D[NV], unused[NV];
+    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, D, unused, flag, Dst, nstrong);
+#pragma unroll
+    for (int v = 0; v < NV; v++) Dl[t * NV + v] = D[v];
+}
+
 template <int SCHEME>
 __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *__restrict__ Uf,
                                                             const float *__restrict__ Wf,
                                                             float *__restrict__ Rf,
                                                             unsigned char *__restrict__ flag,
-                                                            float *__restrict__ Dst, int accumulate)
+                                                            float *__restrict__ Dst,
+                                                            int *__restrict__ nstrong,
+                                                            const float *__restrict__ Dl, int accumulate)
 {
     __shared__ float sD[NV][XSEG + 1];
     const int row = blockIdx.x;
+    const int nseg = gridDim.y;
     const int j = row % P.n[1], k = row / P.n[1];
     const int x0 = blockIdx.y * XSEG;
     const int t = threadIdx.x;
@@ -1249,16 +1278,11 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
     float dF1[NV];
     if (i < P.n[0]) {
         float D[NV];
-        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, D, dF1, flag, Dst);
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, D, dF1, flag, Dst, nstrong);
 #pragma unroll
         for (int v = 0; v < NV; v++) sD[v][t + 1] = D[v];
     }
-    if (t == 0) {
-        float D[NV], unused[NV];
-        delta_flagged<0, SCHEME>(P, Uf, Wf, base + x0 - 1, 1, D, unused, flag, Dst);
-#pragma unroll
-        for (int v = 0; v < NV; v++) sD[v][0] = D[v];
-    }
+    if (t < NV) sD[t][0] = Dl[((long long)row * nseg + blockIdx.y) * NV + t];
     __syncthreads();
     if (i >= P.n[0]) return;
     const float fac = (float)P.fac[0];
@@ -1277,8 +1301,10 @@ template <int DIR, int SCHEME>
 __global__ void __launch_bounds__(128) k_patch_strong(Dev P, const double *__restrict__ U,
                                                       float *__restrict__ Rf,
                                                       const unsigned char *__restrict__ flag,
-                                                      const float *__restrict__ Dst)
+                                                      const float *__restrict__ Dst,
+                                                      const int *__restrict__ nstrong)
 {
+    if (nstrong[DIR] == 0) return;     // nothing flagged in this direction and stage
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const long long st = P.st[DIR];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
@@ -1345,10 +1371,15 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
 {
     if (P.mixed && !CURV) {
         if (DIR == 0) {
-            dim3 g(P.n[1] * P.n[2], (P.n[0] + XSEG - 1) / XSEG);
-            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, acc);
+            const int nseg = (P.n[0] + XSEG - 1) / XSEG;
+            const long long lefts = (long long)P.n[1] * P.n[2] * nseg;
+            k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, B.flag, B.Dst,
+                                                                             B.err + 1, B.Dl);
+            dim3 g(P.n[1] * P.n[2], nseg);
+            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1,
+                                                          B.Dl, acc);
         } else {
-            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, acc, chunk);
+            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1, acc, chunk);
         }
     } else if (P.mixed) {
         k_conv_char_mixed<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.Uf, B.Wf, B.M, B.Rf, acc, chunk);
@@ -1404,13 +1435,13 @@ static void launch_patch(const Dev &P, const Bufs &B, int d, cudaStream_t s)
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const int g = grid_for(N, 128);
     if (P.scheme == SCH_WENO5JS) {
-        if (d == 0) k_patch_strong<0, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
-        else if (d == 1) k_patch_strong<1, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
-        else k_patch_strong<2, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+        if (d == 0) k_patch_strong<0, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
+        else if (d == 1) k_patch_strong<1, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
+        else k_patch_strong<2, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
     } else {
-        if (d == 0) k_patch_strong<0, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
-        else if (d == 1) k_patch_strong<1, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
-        else k_patch_strong<2, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst);
+        if (d == 0) k_patch_strong<0, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
+        else if (d == 1) k_patch_strong<1, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
+        else k_patch_strong<2, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
     }
 }
 
@@ -1444,7 +1475,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         launches++;
     }
     if (tap) (*tap)("prim", s);
-    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf);
+    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1);
     else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
     int acc = 0;
@@ -1458,6 +1489,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         else conv_dir<2>(P, B, acc, s);
         acc = 1;
         launches++;
+        if (patch && d == 0) launches++;   // the x segments' left interfaces
         if (patch) {
             if (tap) (*tap)(patch_names[d], s);
             launch_patch(P, B, d, s);

@@ -16,7 +16,8 @@ struct Bufs {
     float *Rf = nullptr, *Vf = nullptr;                // mixed path: FP32 residual [5], viscous [12]
     unsigned char *flag = nullptr;                     // mixed path: strong-jump interface flags [vs]
     float *Dst = nullptr;                              // mixed path: FP32 flux of flagged interfaces [5]
-    int *err = nullptr;                                // device error word
+    float *Dl = nullptr;                               // mixed path: left interface of each x segment [rows*segs][5]
+    int *err = nullptr;                                // device error word, then 3 strong-jump counts
 };
 
 void launch_unpack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s);
