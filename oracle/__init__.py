@@ -71,6 +71,7 @@ def lib():
         L.orc_residual.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_residual_points.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_labels.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_step.restype = ctypes.c_int
         L.orc_get_metrics.argtypes = [ctypes.c_void_p] * 4
@@ -183,6 +184,12 @@ class Oracle:
         m = np.empty(ijk.shape[0])
         lib().orc_residual_points(self._h, ijk.shape[0], _p(ijk), _p(R), _p(m))
         return (R, m) if with_margin else R
+
+    def labels(self):
+        """TENO cut-off labels of the current state ([nz][ny][nx] uint8)."""
+        lab = np.empty(self.shape[1:], dtype=np.uint8)
+        lib().orc_labels(self._h, _p(lab))
+        return lab
 
     def step(self, nsteps):
         rc = lib().orc_step(self._h, int(nsteps))

@@ -710,7 +710,22 @@ static void impose_boundary_nodes(orc_ctx *c)
  * k = m-2st .. m+3st.  Reading of step (d): alpha_j = max over those six nodes of
  * |lambda_j| evaluated from each node's own state and metric.
  * ------------------------------------------------------------------------------------------ */
-static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *margin)
+/* Sensor label of one reconstruction (no counterpart in the paper): a TENO cut-off (some
+ * omega_r = 0) that moves the reconstructed value away from the linear 5th-order value
+ * (2, -13, 47, 27, -3)/60 by more than 5 % of the range of the five stencil values. */
+static int cut_matters(const double *f, double h, const double *w)
+{
+    if (w[0] != 0.0 && w[1] != 0.0 && w[2] != 0.0) return 0;
+    double lin = (2.0 * f[0] - 13.0 * f[1] + 47.0 * f[2] + 27.0 * f[3] - 3.0 * f[4]) / 60.0;
+    double lo = f[0], hi = f[0];
+    for (int k = 1; k < 5; k++) {
+        if (f[k] < lo) lo = f[k];
+        if (f[k] > hi) hi = f[k];
+    }
+    return fabs(h - lin) > 0.05 * (hi - lo);
+}
+
+static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *margin, int *cut)
 {
     const orc_params *P = &c->p;
     long nt = c->ntot, st = c->st[d];
@@ -764,9 +779,12 @@ static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *
         }
         /* (e) reconstruct g+ from nodes m-2..m+2 and g- mirrored from m+3..m-1 */
         double fm[5] = {gm[5], gm[4], gm[3], gm[2], gm[1]};
-        double m1 = INFINITY, m2 = INFINITY;
-        double hp = orc_recon5(gp, P->scheme, P->teno_ct, NULL, &m1);
-        double hm = orc_recon5(fm, P->scheme, P->teno_ct, NULL, &m2);
+        double m1 = INFINITY, m2 = INFINITY, w1[3], w2[3];
+        double hp = orc_recon5(gp, P->scheme, P->teno_ct, w1, &m1);
+        double hm = orc_recon5(fm, P->scheme, P->teno_ct, w2, &m2);
+        if (cut && P->scheme == ORC_TENO5) {
+            if (cut_matters(gp, hp, w1) || cut_matters(fm, hm, w2)) *cut = 1;
+        }
         if (m1 < mg) mg = m1;
         if (m2 < mg) mg = m2;
         gh[j] = hp + hm;
@@ -801,7 +819,7 @@ void orc_char_flux_1d(double gamma, int scheme, double ct, const double *U6 /* [
         for (int cc = 0; cc < 3; cc++) Sbuf[(0 * 3 + cc) * 6 + s] = S[cc];
     c.U = Ubuf;
     c.S = Sbuf;
-    interface_flux(&c, 0, 2, Fh, NULL);
+    interface_flux(&c, 0, 2, Fh, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -907,7 +925,7 @@ static double cflux_fetch(const void *ud, int s)
 /* ------------------------------------------------------------------------------------------
  * Residual at one interior node: R = conv_x + conv_y + conv_z + viscous  (Eqs. 1-3, 10).
  * ------------------------------------------------------------------------------------------ */
-static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double *margin)
+static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double *margin, int *cut)
 {
     const orc_params *P = &c->p;
     long id = IDX(c, i, j, k);
@@ -924,8 +942,8 @@ static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double
             }
         } else {
             double Fp[NV], Fm[NV];
-            interface_flux(c, d, id, Fp, margin);
-            interface_flux(c, d, id - c->st[d], Fm, margin);
+            interface_flux(c, d, id, Fp, margin, cut);
+            interface_flux(c, d, id - c->st[d], Fm, margin, cut);
             for (int v = 0; v < NV; v++) R[v] -= fac * (Fp[v] - Fm[v]);
         }
     }
@@ -1018,7 +1036,7 @@ void orc_residual(void *h, double *R, double *margin)
         int j = (int)(line % P->n[1]), k = (int)(line / P->n[1]);
         for (int i = 0; i < P->n[0]; i++) {
             double r[NV], mg = INFINITY;
-            residual_at(c, i, j, k, r, &mg);
+            residual_at(c, i, j, k, r, &mg, NULL);
             long o = ((long)k * P->n[1] + j) * P->n[0] + i;
             for (int v = 0; v < NV; v++) R[v * plane + o] = r[v];
             if (margin) margin[o] = mg;
@@ -1034,9 +1052,31 @@ void orc_residual_points(void *h, int npts, const int *ijk, double *R, double *m
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < npts; q++) {
         double r[NV], mg = INFINITY;
-        residual_at(c, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r, &mg);
+        residual_at(c, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r, &mg, NULL);
         for (int v = 0; v < NV; v++) R[5 * q + v] = r[v];
         if (margin) margin[q] = mg;
+    }
+}
+
+/* Shock-sensor training labels (no counterpart in the paper; the learned sensor is an addition
+ * to the method): label 1 where the TENO5 residual of the point used an interface (either side,
+ * any characteristic field, any direction) at which a candidate stencil was cut (delta_r = 0,
+ * Eq. 24) and the cut moved the reconstruction by more than 5 % of the stencil's range (see
+ * cut_matters), else 0.  labels: [nz][ny][nx] bytes. */
+void orc_labels(void *h, unsigned char *labels)
+{
+    orc_ctx *c = (orc_ctx *)h;
+    const orc_params *P = &c->p;
+    ghost_fill(c);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long line = 0; line < (long)P->n[1] * P->n[2]; line++) {
+        int j = (int)(line % P->n[1]), k = (int)(line / P->n[1]);
+        for (int i = 0; i < P->n[0]; i++) {
+            double r[NV], mg = INFINITY;
+            int cut = 0;
+            residual_at(c, i, j, k, r, &mg, &cut);
+            labels[((long)k * P->n[1] + j) * P->n[0] + i] = (unsigned char)cut;
+        }
     }
 }
 
