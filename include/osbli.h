@@ -74,7 +74,8 @@ typedef struct {
     double T_wall;             /* isothermal wall temperature (Eq. 41) */
     double sutherland_ratio;   /* T_s/T_ref of Eq. 6; <= 0: constant mu = 1 */
     int precision;             /* OSBLI_FP64 | OSBLI_MIXED */
-    int sensor;                /* reserved, must be 0 */
+    int sensor;                /* 1: learned shock sensor gates TENO vs central fluxes (precision
+                                  OSBLI_MIXED, WENO5-JS/TENO5, uniform grid); 0: off */
     double h[3];               /* grid spacing per direction when coords == NULL */
     double L[3];               /* period of each periodic direction (coordinate unwrapping) */
 } osbli_params;
@@ -112,7 +113,9 @@ int osbli_residual(osbli_t *h, double *R);
 
 /* Diagnostics of the current state (deterministic reductions over interior points):
  * out[0..4] = sum of the conserved variables, out[5] = mean kinetic energy 1/2 rho |u|^2,
- * out[6] = max Mach number, out[7] = min density, out[8] = min pressure, out[9..15] = 0. */
+ * out[6] = max Mach number, out[7] = min density, out[8] = min pressure, out[9] = fraction of
+ * cells gated to the characteristic flux by the learned sensor at the last evaluation (0 when
+ * the sensor is off), out[10..15] = 0. */
 int osbli_diagnostics(osbli_t *h, double out[16]);
 
 /* Time each kernel launch of one residual evaluation (ghost fill per direction, primitives,
@@ -124,6 +127,52 @@ int osbli_profile_residual(osbli_t *h, int reps, double *ms, int max);
 
 /* Name of launch i of the last osbli_profile_residual on h ("" when out of range). */
 const char *osbli_profile_name(const osbli_t *h, int i);
+
+/* ---- learned shock sensor (an addition to the method: the paper has no sensor) --------------
+ * Per cell, features from the 3x3x3 neighbourhood (rho_n/rho_c - 1, (u_n - u_c)/a_c for three
+ * components, p_n/p_c - 1: 135 values, padded to 144 BF16 per row) feed an MLP
+ * 135 -> 32 -> 32 -> 1 (ReLU, ReLU, sigmoid) evaluated on BF16 tensor cores once per RK step.
+ * Cells with probability above the threshold are flagged, and an interface takes the TENO/WENO characteristic flux when either adjacent cell
+ * is gated (or its stencil holds a strong jump); otherwise the 4th-order central flux.
+ * Weights: FP32 parameter vector of OSBLI_SENSOR_NPARAM values, W1[32][135], b1[32], W2[32][32],
+ * b2[32], w3[32], b3 (host memory). */
+#define OSBLI_SENSOR_NPARAM 5441
+#define OSBLI_SENSOR_NFEAT 144
+
+/* Install weights and decision threshold (probability in (0,1)) on a handle created with
+ * params.sensor = 1; required before stepping.  Errors: EINVAL. */
+int osbli_sensor_set_weights(osbli_t *h, const float *w, float threshold);
+
+/* Training labels of the current state (TENO5 handles, any precision): 1 for a cell whose FP64
+ * TENO5 residual used an interface where a candidate stencil was cut and the cut moved the
+ * reconstruction by more than 5 % of the stencil's range.  labels: [nz][ny][nx] bytes, host or
+ * device.  Allocates temporary device memory. */
+int osbli_sensor_labels(osbli_t *h, uint8_t *labels);
+
+/* Features of the current state: d_feats device pointer, [nz*ny*nx][144] BF16 (the caller
+ * allocates nz*ny*nx*288 bytes). */
+int osbli_sensor_features(osbli_t *h, void *d_feats);
+
+/* Sensor probabilities of the current state, [nz][ny][nx] FP32, host or device pointer. */
+int osbli_sensor_probs(osbli_t *h, float *probs);
+
+/* Sensor probabilities of n feature rows: d_feats [n][144] BF16 device, w host parameter vector,
+ * d_probs [n] FP32 device.  Legacy default stream; synchronises the device. */
+int osbli_mlp_forward(const void *d_feats, long long n, const float *w, float *d_probs);
+
+/* One full-batch gradient of the mean weighted binary cross-entropy
+ * L = -mean(pos_weight y log p + (1 - y) log(1 - p)) on the GPU kernels used for training:
+ * d_feats [n][144] BF16 device, d_labels [n] bytes device, w host parameter vector, grad host
+ * (OSBLI_SENSOR_NPARAM), *loss host.  Allocates temporary device memory. */
+int osbli_mlp_grad(const void *d_feats, const uint8_t *d_labels, long long n, float pos_weight,
+                   const float *w, float *grad, double *loss);
+
+/* Train with Adam (beta 0.9 / 0.999) for `steps` mini-batches of `batch` rows (multiple of 16)
+ * drawn by a counter-based hash of (seed, step, row); w (host, in/out) holds the FP32 master
+ * parameters; loss_hist (host, steps values, may be NULL) the batch losses.  Runs on the legacy
+ * default stream.  Allocates temporary device memory. */
+int osbli_mlp_train(const void *d_feats, const uint8_t *d_labels, long long n, int steps, int batch,
+                    float lr, float pos_weight, unsigned seed, float *w, float *loss_hist);
 
 /* Kernel launches one RK step enqueues (for launch accounting). */
 int osbli_launches_per_step(const osbli_t *h);

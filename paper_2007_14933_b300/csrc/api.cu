@@ -27,6 +27,7 @@ struct osbli {
     bool bdata_set[6] = {false, false, false, false, false, false};
     cudaGraphExec_t gexec = nullptr;
     int launches_step = 0;
+    bool sensor_ready = false;
     const char *prof_names[32] = {};
     int prof_count = 0;
     char err[512];
@@ -69,6 +70,9 @@ static void free_all(osbli *h)
     for (int f = 0; f < 6; f++)
         if (h->B.bd[f]) cudaFree(h->B.bd[f]);
     if (h->B.err) cudaFree(h->B.err);
+    if (h->B.sw) cudaFree(h->B.sw);
+    if (h->B.sflag) cudaFree(h->B.sflag);
+    if (h->B.gate) cudaFree(h->B.gate);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -109,7 +113,10 @@ static int validate(const osbli_params *p, const double *coords)
         return seterr(nullptr, OSBLI_EINVAL, "precision %d unknown", p->precision);
     if (p->precision == OSBLI_MIXED && p->scheme == OSBLI_CENTRAL4)
         return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / TENO5");
-    if (p->sensor != 0) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0");
+    if (p->sensor != 0 && p->sensor != 1) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0 or 1");
+    if (p->sensor == 1 && (p->precision != OSBLI_MIXED || coords || p->scheme == OSBLI_CENTRAL4))
+        return seterr(nullptr, OSBLI_EINVAL,
+                      "the learned sensor gates the mixed-precision WENO/TENO path on Cartesian grids");
     for (int d = 0; d < 3; d++)
         for (int s = 0; s < 2; s++)
             if (n[d] > 1 && p->bc[d][s] == OSBLI_WALL && !(p->T_wall > 0.0))
@@ -158,6 +165,7 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     P.kq = P.viscous ? 1.0 / ((p->gamma - 1.0) * p->Ma * p->Ma * p->Pr * p->Re) : 0.0;
     P.dt = p->dt;
     P.mixed = p->precision == OSBLI_MIXED;
+    P.sensor = p->sensor == 1;
     P.jump = 1.5f;
     if (!P.curv) {
         double hh[3];
@@ -223,6 +231,13 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     CKC(cudaMemsetAsync(h->B.err, 0, 4 * sizeof(int), h->stream));
     CKC(cudaMallocHost(&h->h_err, sizeof(int)));
     CKC(cudaMallocHost(&h->h_diag, 16 * sizeof(double)));
+    if (P.sensor) {
+        CKC(cudaMalloc(&h->B.sw, sensor_weights_bytes()));
+        CKC(cudaMalloc(&h->B.sflag, (size_t)P.vs));
+        CKC(cudaMemsetAsync(h->B.sflag, 0, (size_t)P.vs, h->stream));
+        CKC(cudaMalloc(&h->B.gate, (size_t)P.vs));
+        CKC(cudaMemsetAsync(h->B.gate, 1, (size_t)P.vs, h->stream));
+    }
     for (int d = 0; d < 3; d++)
         for (int s = 0; s < 2; s++) {
             const int bc = p->bc[d][s];
@@ -313,6 +328,8 @@ extern "C" int osbli_get_state(osbli_t *h, double *U)
 
 static int check_faces(osbli *h)
 {
+    if (h->P.sensor && !h->sensor_ready)
+        return seterr(h, OSBLI_ESTATE, "the learned sensor needs osbli_sensor_set_weights");
     for (int f = 0; f < 6; f++)
         if (h->B.bd[f] && !h->bdata_set[f])
             return seterr(h, OSBLI_ESTATE, "face (%d,%d) needs osbli_set_boundary_data", f / 2, f % 2);
@@ -453,4 +470,76 @@ extern "C" const char *osbli_last_error(const osbli_t *h)
 void osbli_internal_set_global_error(const char *msg)
 {
     snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+}
+
+// ---------------------------------------------------------------------------------------------
+// learned sensor
+// ---------------------------------------------------------------------------------------------
+extern "C" int osbli_sensor_set_weights(osbli_t *h, const float *w, float threshold)
+{
+    if (!h || !w) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->P.sensor) return seterr(h, OSBLI_EINVAL, "handle created without the sensor (params.sensor = 0)");
+    if (!(threshold > 0.f && threshold < 1.f)) return seterr(h, OSBLI_EINVAL, "threshold must lie in (0, 1)");
+    if (sensor_upload(w, h->B.sw, h->stream) != OSBLI_OK) return seterr(h, OSBLI_ECUDA, "weight upload failed");
+    h->B.zthresh = logf(threshold / (1.f - threshold));
+    h->sensor_ready = true;
+    if (h->gexec) {   // the captured step holds the old threshold
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_sensor_labels(osbli_t *h, uint8_t *labels)
+{
+    if (!h || !labels) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    if (h->P.scheme != OSBLI_TENO5) return seterr(h, OSBLI_EINVAL, "labels are TENO5 cut-off decisions");
+    for (int f = 0; f < 6; f++)
+        if (h->B.bd[f] && !h->bdata_set[f]) return seterr(h, OSBLI_ESTATE, "face data missing");
+    const long long N = npoints(h->P);
+    unsigned char *labd = nullptr, *out = nullptr;
+    cudaError_t e = cudaMalloc(&labd, 3 * (size_t)h->P.vs);
+    if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(labd, 0, 3 * (size_t)h->P.vs, h->stream);
+    if (e == cudaSuccess) {
+        unsigned char *ld[3] = {labd, labd + h->P.vs, labd + 2 * h->P.vs};
+        launch_labels(h->P, h->B, ld, out, h->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(labels, out, (size_t)N, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (labd) cudaFree(labd);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess) return seterr(h, OSBLI_ECUDA, "labels: %s", cudaGetErrorString(e));
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_sensor_features(osbli_t *h, void *d_feats)
+{
+    if (!h || !d_feats) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    launch_ghosts(h->P, h->B, h->stream);
+    launch_features(h->P, h->B, d_feats, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_sensor_probs(osbli_t *h, float *probs)
+{
+    if (!h || !probs) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->P.sensor || !h->sensor_ready) return seterr(h, OSBLI_ESTATE, "sensor weights not set");
+    if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
+    const long long N = npoints(h->P);
+    float *d = nullptr;
+    CK(h, cudaMalloc(&d, sizeof(float) * (size_t)N));
+    launch_ghosts(h->P, h->B, h->stream);
+    launch_sensor_probs(h->P, h->B, d, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(probs, d, sizeof(float) * (size_t)N, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return seterr(h, OSBLI_ECUDA, "probs: %s", cudaGetErrorString(e));
+    return OSBLI_OK;
 }

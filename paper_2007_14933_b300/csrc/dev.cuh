@@ -36,6 +36,7 @@ struct Dev {
     double dt;
     int mixed;         // OSBLI_MIXED: FP32 reconstruction arithmetic
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
+    int sensor;        // learned gate active (mixed path, Cartesian grids)
 };
 
 __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, int j, int k)
@@ -79,7 +80,7 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // ratio overflows FP32); the cut-off test is unchanged in exact arithmetic.
 // ------------------------------------------------------------------------------------------
 template <int SCHEME, typename T>
-__device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
+__device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, bool *allkept = nullptr)
 {
     constexpr bool F32 = sizeof(T) == 4;
     const T c13_12 = T(13.0 / 12.0), q = T(0.25);
@@ -120,6 +121,7 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
         const T g0 = x0 * x0 * x0, g1 = x1 * x1 * x1, g2 = x2 * x2 * x2;
         const T th = ct * (g0 + g1 + g2);
         const bool k0 = g0 >= th, k1 = g1 >= th, k2 = g2 >= th;
+        if (allkept) *allkept = k0 && k1 && k2;
         const T w0 = k0 ? T(0.3) : T(0), w1 = k1 ? T(0.6) : T(0), w2 = k2 ? T(0.1) : T(0);
         const T r = w0 * q0 + w1 * q1 + w2 * q2;
         if (k0 && k1 && k2) return r;
@@ -139,6 +141,19 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct)
         }
         return fdiv(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
     }
+}
+
+// Sensor label of one TENO reconstruction (an addition to the method; the paper has none): the
+// cut-off removed a candidate stencil and moved the value away from the linear 5th-order
+// reconstruction by more than 5 % of the range of the five stencil values.
+__device__ __forceinline__ bool cut_matters(double f0, double f1, double f2, double f3, double f4,
+                                            double val, bool allkept)
+{
+    if (allkept) return false;
+    const double lin = (2.0 * f0 - 13.0 * f1 + 47.0 * f2 + 27.0 * f3 - 3.0 * f4) / 60.0;
+    const double lo = fmin(fmin(fmin(f0, f1), fmin(f2, f3)), f4);
+    const double hi = fmax(fmax(fmax(f0, f1), fmax(f2, f3)), f4);
+    return fabs(val - lin) > 0.05 * (hi - lo);
 }
 
 }  // namespace osb

@@ -285,9 +285,9 @@ struct SrcFromState {
 // alpha_j = max_k |lambda_j(k)|, WENO/TENO reconstruction of g+ and g-, back-projection.
 // The left eigenvectors are applied in factored form (l_j . w built from u.w, n.w, t.w).
 // T is the arithmetic type (double: plain FP64 path; float: mixed path).
-template <int DIR, int SCHEME, bool CURV, typename T, typename Src>
+template <int DIR, int SCHEME, bool CURV, typename T, typename Src, bool LABEL = false>
 __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const double *__restrict__ M,
-                                               long long m, long long st, T Fh[NV])
+                                               long long m, long long st, T Fh[NV], bool *label = nullptr)
 {
     const long long vs = P.vs;
     const long long mr = m + st;
@@ -410,8 +410,17 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
     const T ct = T(P.ct);
 #pragma unroll
     for (int j = 0; j < NV; j++) {
-        g[j] = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
-               recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+        if (LABEL) {
+            bool kp = true, km = true;
+            const T vp = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, &kp);
+            const T vm = recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, &km);
+            g[j] = vp + vm;
+            *label = *label || cut_matters(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], vp, kp) ||
+                     cut_matters(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], vm, km);
+        } else {
+            g[j] = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
+                   recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+        }
     }
     // (f) back-projection F = R g
     const T s04 = g[0] + g[4], d40 = g[4] - g[0];
@@ -944,14 +953,15 @@ __global__ void k_metric_spread(Dev P, const double *__restrict__ Sraw,
 // ------------------------------------------------------------------------------------------
 // Diagnostics: fixed-partition block partial sums, then one block in fixed order.
 // ------------------------------------------------------------------------------------------
-constexpr int DIAG_BLOCKS = 256, DIAG_THREADS = 256, NDIAG = 9;
+constexpr int DIAG_BLOCKS = 256, DIAG_THREADS = 256, NDIAG = 10;
 
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const double *__restrict__ U,
+                                                               const unsigned char *__restrict__ gate,
                                                                double *__restrict__ part)
 {
     __shared__ double sh[NDIAG][DIAG_THREADS];
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300, 0};
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % P.n[0]);
@@ -968,6 +978,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
         acc[6] = fmax(acc[6], sqrt(q2 / (P.gamma * p / rho)));
         acc[7] = fmin(acc[7], rho);
         acc[8] = fmin(acc[8], p);
+        if (gate) acc[9] += gate[id] ? 1.0 : 0.0;
     }
 #pragma unroll
     for (int c = 0; c < NDIAG; c++) sh[c][threadIdx.x] = acc[c];
@@ -979,6 +990,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
             sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][threadIdx.x + off]);
             sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][threadIdx.x + off]);
             sh[8][threadIdx.x] = fmin(sh[8][threadIdx.x], sh[8][threadIdx.x + off]);
+            sh[9][threadIdx.x] += sh[9][threadIdx.x + off];
         }
         __syncthreads();
     }
@@ -989,12 +1001,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
 __global__ void k_diag_final(const double *__restrict__ part, double *__restrict__ out, long long N)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300, 0};
     for (int b = 0; b < DIAG_BLOCKS; b++) {
         for (int c = 0; c < 6; c++) acc[c] += part[c * DIAG_BLOCKS + b];
         acc[6] = fmax(acc[6], part[6 * DIAG_BLOCKS + b]);
         acc[7] = fmin(acc[7], part[7 * DIAG_BLOCKS + b]);
         acc[8] = fmin(acc[8], part[8 * DIAG_BLOCKS + b]);
+        acc[9] += part[9 * DIAG_BLOCKS + b];
     }
     for (int c = 0; c < 16; c++) out[c] = 0.0;
     for (int c = 0; c < NV; c++) out[c] = acc[c];
@@ -1002,6 +1015,7 @@ __global__ void k_diag_final(const double *__restrict__ part, double *__restrict
     out[6] = acc[6];
     out[7] = acc[7];
     out[8] = acc[8];
+    out[9] = acc[9] / (double)N;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1176,6 +1190,50 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
     D[4] = H * s04 + a * un * d40 + 0.5f * q2 * g[1] + ut1 * g[2] + ut2 * g[3];
 }
 
+// Central 4th-order interface flux in delta form (the cheap flux of interfaces the learned
+// sensor leaves ungated): F_{m+1/2} = [7 (F_m + F_{m+1}) - (F_{m-1} + F_{m+2})] / 12, i.e.
+// D = (7 dF_{m+1} - dF_{m-1} - dF_{m+2}) / 12 with dF_k = F_k - F_m from the product rule.
+template <int DIR>
+__device__ __forceinline__ void node_dflux(const Dev &P, const float *__restrict__ Uf,
+                                           const float *__restrict__ Wf, long long m, long long id,
+                                           float dF[NV])
+{
+    const long long vs = P.vs;
+    const float gm1 = (float)P.gm1;
+    float dU[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) dU[v] = (Uf[v * vs + id] - Uf[v * vs + m]) + (Uf[(NV + v) * vs + id] - Uf[(NV + v) * vs + m]);
+    const float irk = __fdividef(1.f, Uf[id]);
+    float du[3], uk[3], uc[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        uc[c] = Wf[(W_U + c) * vs + m];
+        du[c] = (dU[1 + c] - uc[c] * dU[0]) * irk;
+        uk[c] = uc[c] + du[c];
+    }
+    const float dmu = dU[1] * uk[0] + dU[2] * uk[1] + dU[3] * uk[2] + Uf[1 * vs + m] * du[0] +
+                      Uf[2 * vs + m] * du[1] + Uf[3 * vs + m] * du[2];
+    const float dp = gm1 * (dU[4] - 0.5f * dmu);
+    const float unk = uk[DIR], dun = du[DIR];
+#pragma unroll
+    for (int v = 0; v < NV; v++) dF[v] = unk * dU[v] + dun * Uf[v * vs + m];
+    dF[1 + DIR] += dp;
+    dF[4] += (Wf[W_P * vs + m] + dp) * dun + dp * uc[DIR];
+}
+
+template <int DIR>
+__device__ __forceinline__ void central_delta(const Dev &P, const float *__restrict__ Uf,
+                                              const float *__restrict__ Wf, long long m, long long st,
+                                              float D[NV], float dF1[NV])
+{
+    float fp1[NV], fp2[NV];
+    node_dflux<DIR>(P, Uf, Wf, m, m - st, dF1);
+    node_dflux<DIR>(P, Uf, Wf, m, m + st, fp1);
+    node_dflux<DIR>(P, Uf, Wf, m, m + 2 * st, fp2);
+#pragma unroll
+    for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - dF1[v] - fp2[v]) * (1.f / 12.f);
+}
+
 // One interface of the delta-form mixed path.  Interfaces whose stencil holds a strong jump are
 // flagged (flag[m] = 1, m = left node) and their FP32 D kept in Dst; a later per-node pass
 // (k_patch_strong) recomputes them in FP64 and corrects the residual, so the FP32 pass carries
@@ -1184,10 +1242,12 @@ template <int DIR, int SCHEME>
 __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restrict__ Uf,
                                               const float *__restrict__ Wf, long long m, long long st,
                                               float D[NV], float dF1[NV], unsigned char *__restrict__ flag,
-                                              float *__restrict__ Dst, int *__restrict__ nstrong)
+                                              float *__restrict__ Dst, int *__restrict__ nstrong,
+                                              const unsigned char *__restrict__ gate)
 {
-    delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, D, dF1);
     const bool strong = strong_jump(P, Uf, Wf, m, st);
+    if (!gate || strong || gate[m] || gate[m + st]) delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, D, dF1);
+    else central_delta<DIR>(P, Uf, Wf, m, st, D, dF1);
     flag[m] = strong ? 1 : 0;
     if (strong) {
         atomicAdd(nstrong + DIR, 1);
@@ -1203,6 +1263,7 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
                                                          float *__restrict__ Rf,
                                                          unsigned char *__restrict__ flag,
                                                          float *__restrict__ Dst, int *__restrict__ nstrong,
+                                                         const unsigned char *__restrict__ gate,
                                                          int accumulate, int chunk)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
@@ -1217,11 +1278,11 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
     const long long st = P.st[DIR];
     const float fac = (float)P.fac[DIR];
     float Dm[NV], dF1[NV];
-    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, Dm, dF1, flag, Dst, nstrong);
+    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, Dm, dF1, flag, Dst, nstrong, gate);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         float Dp[NV];
-        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, Dp, dF1, flag, Dst, nstrong);
+        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, Dp, dF1, flag, Dst, nstrong, gate);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             // F_{m+1/2} - F_{m-1/2} = (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2}
@@ -1242,6 +1303,7 @@ __global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restr
                                                      const float *__restrict__ Wf,
                                                      unsigned char *__restrict__ flag,
                                                      float *__restrict__ Dst, int *__restrict__ nstrong,
+                                                     const unsigned char *__restrict__ gate,
                                                      float *__restrict__ Dl)
 {
     const int nseg = (P.n[0] + XSEG - 1) / XSEG;
@@ -1253,7 +1315,7 @@ __global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restr
     const int j = (int)(row % P.n[1]), k = (int)(row / P.n[1]);
     const long long base = node_index(P, 0, j, k);
     float D[NV], unused[NV];
-    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, D, unused, flag, Dst, nstrong);
+    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, D, unused, flag, Dst, nstrong, gate);
 #pragma unroll
     for (int v = 0; v < NV; v++) Dl[t * NV + v] = D[v];
 }
@@ -1265,6 +1327,7 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
                                                             unsigned char *__restrict__ flag,
                                                             float *__restrict__ Dst,
                                                             int *__restrict__ nstrong,
+                                                            const unsigned char *__restrict__ gate,
                                                             const float *__restrict__ Dl, int accumulate)
 {
     __shared__ float sD[NV][XSEG + 1];
@@ -1278,7 +1341,7 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
     float dF1[NV];
     if (i < P.n[0]) {
         float D[NV];
-        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, D, dF1, flag, Dst, nstrong);
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, D, dF1, flag, Dst, nstrong, gate);
 #pragma unroll
         for (int v = 0; v < NV; v++) sD[v][t + 1] = D[v];
     }
@@ -1334,6 +1397,87 @@ __global__ void __launch_bounds__(128) k_patch_strong(Dev P, const double *__res
     }
 }
 
+int conv_chunk(const Dev &P, int d);
+
+// ------------------------------------------------------------------------------------------
+// Sensor labels (an addition to the method): the FP64 TENO5 interface fluxes of the current
+// state, recording per interface whether a material cut-off happened (cut_matters), then per
+// cell the OR over its two interfaces in every direction.  Primitives come from the FP64 state.
+// ------------------------------------------------------------------------------------------
+template <int DIR, bool CURV>
+__global__ void __launch_bounds__(128) k_label_dir(Dev P, const double *__restrict__ U,
+                                                   const double *__restrict__ M,
+                                                   unsigned char *__restrict__ lab, int chunk)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    if (a >= P.n[DA] || b >= P.n[DB]) return;
+    const int s0 = blockIdx.z * chunk;
+    const int s1 = min(s0 + chunk, P.n[DIR]);
+    int ii[3];
+    ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
+    const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const long long st = P.st[DIR];
+    const SrcFromState q{U, P.vs, P.gamma, P.gm1};
+    for (int m = s0 - (s0 == 0 ? 1 : 0); m < s1; m++) {
+        const long long id = base + (long long)m * st;
+        double F[NV];
+        bool l = false;
+        interface_flux<DIR, SCH_TENO5, CURV, double, SrcFromState, true>(P, q, M, id, st, F, &l);
+        lab[id] = l ? 1 : 0;
+    }
+}
+
+__global__ void k_cell_labels(Dev P, const unsigned char *__restrict__ lab0,
+                              const unsigned char *__restrict__ lab1,
+                              const unsigned char *__restrict__ lab2, unsigned char *__restrict__ out)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const unsigned char *lab[3] = {lab0, lab1, lab2};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]);
+        const int k = (int)(q / P.n[1]);
+        const long long id = node_index(P, i, j, k);
+        unsigned char v = 0;
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            if (P.active[d]) v |= lab[d][id] | lab[d][id - P.st[d]];
+        out[t] = v;
+    }
+}
+
+void launch_labels(const Dev &P, const Bufs &B, unsigned char *labd[3], unsigned char *out, cudaStream_t s)
+{
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
+        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
+    }
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+        const int chunk = conv_chunk(P, d);
+        dim3 blk(32, 4);
+        dim3 grd((P.n[da] + 31) / 32, (P.n[db] + 3) / 4, (P.n[d] + chunk - 1) / chunk);
+        if (d == 0) {
+            if (P.curv) k_label_dir<0, true><<<grd, blk, 0, s>>>(P, B.U, B.M, labd[0], chunk);
+            else k_label_dir<0, false><<<grd, blk, 0, s>>>(P, B.U, B.M, labd[0], chunk);
+        } else if (d == 1) {
+            if (P.curv) k_label_dir<1, true><<<grd, blk, 0, s>>>(P, B.U, B.M, labd[1], chunk);
+            else k_label_dir<1, false><<<grd, blk, 0, s>>>(P, B.U, B.M, labd[1], chunk);
+        } else {
+            if (P.curv) k_label_dir<2, true><<<grd, blk, 0, s>>>(P, B.U, B.M, labd[2], chunk);
+            else k_label_dir<2, false><<<grd, blk, 0, s>>>(P, B.U, B.M, labd[2], chunk);
+        }
+    }
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    k_cell_labels<<<grid_for(N, 256), 256, 0, s>>>(P, labd[0], labd[1], labd[2], out);
+}
+
 // ==========================================================================================
 // host-side launchers
 // ==========================================================================================
@@ -1357,7 +1501,7 @@ void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sr
     k_metric_spread<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, Sraw, smax, M);
 }
 
-static int conv_chunk(const Dev &P, int d)
+int conv_chunk(const Dev &P, int d)
 {
     const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
     long long lines = (long long)P.n[da] * P.n[db];
@@ -1369,17 +1513,18 @@ static int conv_chunk(const Dev &P, int d)
 template <int DIR, int SCHEME, bool CURV>
 static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, dim3 grd, dim3 blk, cudaStream_t s)
 {
+    const unsigned char *gate = P.sensor ? B.gate : nullptr;
     if (P.mixed && !CURV) {
         if (DIR == 0) {
             const int nseg = (P.n[0] + XSEG - 1) / XSEG;
             const long long lefts = (long long)P.n[1] * P.n[2] * nseg;
             k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, B.flag, B.Dst,
-                                                                             B.err + 1, B.Dl);
+                                                                             B.err + 1, gate, B.Dl);
             dim3 g(P.n[1] * P.n[2], nseg);
             k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1,
-                                                          B.Dl, acc);
+                                                          gate, B.Dl, acc);
         } else {
-            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1, acc, chunk);
+            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1, gate, acc, chunk);
         }
     } else if (P.mixed) {
         k_conv_char_mixed<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.Uf, B.Wf, B.M, B.Rf, acc, chunk);
@@ -1462,7 +1607,7 @@ struct Tap {
 
 // ghost fill + primitives + convective + viscous fluxes: R holds the convective residual and
 // V the viscous fluxes when this returns (on the stream).  Returns the launch count.
-static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap = nullptr)
+static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap = nullptr, bool sensor_now = true)
 {
     static const char *ghost_names[3] = {"ghost_x", "ghost_y", "ghost_z"};
     static const char *conv_names[3] = {"conv_x", "conv_y", "conv_z"};
@@ -1478,6 +1623,10 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1);
     else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
+    if (P.sensor && sensor_now) {
+        if (tap) (*tap)("sensor", s);
+        launches += launch_sensor_gate(P, B, s);
+    }
     int acc = 0;
     static const char *patch_names[3] = {"patch_x", "patch_y", "patch_z"};
     const bool patch = P.mixed && !P.curv && P.scheme != SCH_CENTRAL4;
@@ -1530,7 +1679,8 @@ static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s)
 
 int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
 {
-    int launches = residual_front(P, B, s);
+    // the learned gate is evaluated once per RK step, at its first stage
+    int launches = residual_front(P, B, s, nullptr, stage == 0);
     if (stage == 0) update<0, 0>(P, B, s);
     else if (stage == 1) update<0, 1>(P, B, s);
     else update<0, 2>(P, B, s);
@@ -1560,9 +1710,18 @@ int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent
     return tap.count;
 }
 
+void launch_ghosts(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
+        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
+    }
+}
+
 void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s)
 {
-    k_diag_partial<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(P, B.U, part);
+    k_diag_partial<<<DIAG_BLOCKS, DIAG_THREADS, 0, s>>>(P, B.U, P.sensor ? B.gate : nullptr, part);
     k_diag_final<<<1, 32, 0, s>>>(part, out, (long long)P.n[0] * P.n[1] * P.n[2]);
 }
 

@@ -17,6 +17,9 @@ struct Bufs {
     unsigned char *flag = nullptr;                     // mixed path: strong-jump interface flags [vs]
     float *Dst = nullptr;                              // mixed path: FP32 flux of flagged interfaces [5]
     float *Dl = nullptr;                               // mixed path: left interface of each x segment [rows*segs][5]
+    void *sw = nullptr;                                // sensor: device weights (BF16 / FP32)
+    unsigned char *sflag = nullptr, *gate = nullptr;   // sensor: cell flags, dilated gate [vs]
+    float zthresh = 0.f;                               // sensor: logit of the decision threshold
     int *err = nullptr;                                // device error word, then 3 strong-jump counts
 };
 
@@ -32,5 +35,15 @@ int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent
                           const char **names, int max_launches);
 void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s);
 int diag_partial_size();
+void launch_ghosts(const Dev &P, const Bufs &B, cudaStream_t s);
+// sensor (sensor.cu)
+int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s);
+void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s);
+void launch_features(const Dev &P, const Bufs &B, void *X, cudaStream_t s);
+size_t sensor_weights_bytes();
+int sensor_upload(const float *w, void *d_sw, cudaStream_t s);
+// sensor labels of the current state: ghost fill, per-direction interface labels labd[d] ([vs]
+// bytes each), per-cell OR into out ([N] bytes, compact)
+void launch_labels(const Dev &P, const Bufs &B, unsigned char *labd[3], unsigned char *out, cudaStream_t s);
 
 }  // namespace osb

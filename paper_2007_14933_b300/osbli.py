@@ -25,7 +25,11 @@ EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_s
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
             "osbli_launches_per_step", "osbli_last_error", "osbli_profile_residual",
             "osbli_profile_name", "osbli_fp64_peak", "osbli_residual_noalloc",
-            "osbli_fp32_peak"]
+            "osbli_fp32_peak", "osbli_sensor_set_weights", "osbli_sensor_labels",
+            "osbli_sensor_features", "osbli_sensor_probs", "osbli_mlp_grad", "osbli_mlp_train",
+            "osbli_mlp_forward"]
+SENSOR_NPARAM = 5441
+SENSOR_NFEAT = 144
 
 
 class osbli_params(ctypes.Structure):
@@ -78,6 +82,19 @@ def load():
         L.osbli_profile_name.restype = ctypes.c_char_p
         L.osbli_residual_noalloc.argtypes = [ctypes.POINTER(osbli_params), vp, vp, vp]
         L.osbli_residual_noalloc.restype = ctypes.c_int
+        L.osbli_sensor_set_weights.argtypes = [vp, vp, ctypes.c_float]
+        L.osbli_sensor_labels.argtypes = [vp, vp]
+        L.osbli_sensor_features.argtypes = [vp, vp]
+        L.osbli_sensor_probs.argtypes = [vp, vp]
+        L.osbli_mlp_grad.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_float, vp, vp,
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.osbli_mlp_train.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_uint, vp, vp]
+        L.osbli_mlp_forward.argtypes = [vp, ctypes.c_longlong, vp, vp]
+        L.osbli_mlp_forward.restype = ctypes.c_int
+        for name in ("osbli_sensor_set_weights", "osbli_sensor_labels", "osbli_sensor_features",
+                     "osbli_sensor_probs", "osbli_mlp_grad", "osbli_mlp_train"):
+            getattr(L, name).restype = ctypes.c_int
         L.osbli_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
         L.osbli_fp64_peak.restype = ctypes.c_int
         L.osbli_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
@@ -130,7 +147,7 @@ def make_params(cfg, precision=OSBLI_FP64):
     p.T_wall = cfg.get("T_wall", 1.0)
     p.sutherland_ratio = cfg.get("suth", 0.0)
     p.precision = int(precision)
-    p.sensor = 0
+    p.sensor = int(cfg.get("sensor", 0))
     return p
 
 
@@ -202,6 +219,47 @@ def osbli_fp32_peak():
     return t.value
 
 
+def osbli_sensor_set_weights(h, w, threshold):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.size == SENSOR_NPARAM
+    return _check(h, load().osbli_sensor_set_weights(h, _ptr(w), float(threshold)))
+
+
+def osbli_sensor_labels(h, labels):
+    return _check(h, load().osbli_sensor_labels(h, _ptr(labels)))
+
+
+def osbli_sensor_features(h, d_feats):
+    return _check(h, load().osbli_sensor_features(h, _ptr(d_feats)))
+
+
+def osbli_sensor_probs(h, probs):
+    return _check(h, load().osbli_sensor_probs(h, _ptr(probs)))
+
+
+def osbli_mlp_forward(d_feats, n, w, d_probs):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    return _check(None, load().osbli_mlp_forward(_ptr(d_feats), int(n), _ptr(w), _ptr(d_probs)))
+
+
+def osbli_mlp_grad(d_feats, d_labels, n, pos_weight, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    g = np.zeros(SENSOR_NPARAM, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(None, load().osbli_mlp_grad(_ptr(d_feats), _ptr(d_labels), int(n), float(pos_weight),
+                                       _ptr(w), _ptr(g), ctypes.byref(loss)))
+    return loss.value, g
+
+
+def osbli_mlp_train(d_feats, d_labels, n, steps, batch, lr, pos_weight, seed, w):
+    w = np.array(w, dtype=np.float32, copy=True)
+    hist = np.zeros(max(int(steps), 1), dtype=np.float32)
+    _check(None, load().osbli_mlp_train(_ptr(d_feats), _ptr(d_labels), int(n), int(steps), int(batch),
+                                        float(lr), float(pos_weight), int(seed) & 0xFFFFFFFF,
+                                        _ptr(w), _ptr(hist)))
+    return w, hist[:int(steps)]
+
+
 def osbli_last_error(h):
     m = load().osbli_last_error(h)
     return m.decode() if m else ""
@@ -254,6 +312,14 @@ class Solver:
 
     def profile_residual(self, reps=3):
         return osbli_profile_residual(self.h, reps)
+
+    def labels(self):
+        lab = np.empty(self.shape[1:], dtype=np.uint8)
+        osbli_sensor_labels(self.h, lab)
+        return lab
+
+    def set_sensor(self, w, threshold=0.5):
+        osbli_sensor_set_weights(self.h, w, threshold)
 
     def launches_per_step(self):
         return osbli_launches_per_step(self.h)

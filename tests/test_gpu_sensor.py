@@ -1,0 +1,151 @@
+"""Learned shock sensor on the GPU against the oracle's sensor reference and TENO labels.
+
+Bars: BF16 features within one BF16 rounding of the FP64 features; labels identical to the
+oracle's (ambiguous cut-offs within 1e-9 of C_T excepted); MLP gradients within 2e-2 (relative
+2-norm per parameter block) of the FP64 gradient taken with BF16-rounded inputs and weights;
+probabilities within 2e-2.  Gain: the trained gate sends most interfaces to the central flux
+and stays close to full TENO.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import sensor as S
+from paper_2007_14933_b300 import inputs as I
+from paper_2007_14933_b300 import osbli
+from paper_2007_14933_b300 import sensor as SN
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_14933_b300 import build
+    build.build()
+    osbli.load()
+    return t
+
+
+def _bf16_to_f32(t):
+    return t.float().cpu().numpy()
+
+
+def _state(n=(20, 16, 12), Ma=1.25, steps=30):
+    cfg, U = I.tgv(n=n, Ma=Ma, scheme=I.TENO5)
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    s.step(steps)
+    U = s.get_state()
+    s.close()
+    return cfg, U
+
+
+def test_features_match_oracle(torch):
+    cfg, U = _state()
+    N = int(np.prod(cfg["n"]))
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    f = torch.empty((N, 144), dtype=torch.bfloat16, device="cuda")
+    osbli.osbli_sensor_features(s.h, f)
+    Fg = _bf16_to_f32(f)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    Fo = S.features(o.ghosted(), cfg["n"], cfg["gamma"])
+    assert np.all(Fg[:, 135:] == 0)
+    err = np.abs(Fg[:, :135] - Fo)
+    assert np.all(err <= 2.0 ** -7 * np.abs(Fo) + 1e-6)
+
+
+def test_labels_match_oracle(torch):
+    cfg, U = _state(steps=60)
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    lg = s.labels()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    lo = o.labels()
+    assert lo.mean() > 0.01
+    assert (lg != lo).mean() <= 0.002
+
+
+def test_mlp_gradient_matches_oracle(torch):
+    cfg, U = _state()
+    N = int(np.prod(cfg["n"]))
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    f = torch.empty((N, 144), dtype=torch.bfloat16, device="cuda")
+    osbli.osbli_sensor_features(s.h, f)
+    lab = torch.from_numpy(s.labels().ravel().copy()).cuda()
+    w = S.init_weights(4)
+    rng = np.random.default_rng(5)
+    w = (w + rng.normal(0, 0.02, w.size)).astype(np.float32)
+    loss, g = osbli.osbli_mlp_grad(f, lab, N, 2.0, w)
+    X = _bf16_to_f32(f)[:, :135].astype(np.float64)
+    wr = w.astype(np.float64).copy()
+    o = 0
+    for size, is_matrix in ((32 * 135, True), (32, False), (32 * 32, True), (32, False), (32, False), (1, False)):
+        if is_matrix:
+            wr[o:o + size] = S.bf16_round(w[o:o + size])
+        o += size
+    Lo, go = S.loss_and_grad(wr, X, lab.cpu().numpy().astype(np.float64), pos_weight=2.0)
+    assert abs(loss - Lo) <= 2e-2 * abs(Lo)
+    o = 0
+    for size in (32 * 135, 32, 32 * 32, 32, 32, 1):
+        a, b = g[o:o + size], go[o:o + size]
+        assert np.linalg.norm(a - b) <= 2e-2 * max(np.linalg.norm(b), 1e-6), o
+        o += size
+
+
+def test_probs_match_oracle_and_training_lowers_loss(torch):
+    feats, labels, _ = SN.tgv_training_set(N=32, nsnap=3, steps_between=20)
+    w, hist = SN.train(feats, labels, steps=600, batch=2048)
+    # the balanced weighted BCE of the best constant predictor is ln 2 = 0.693
+    assert hist[-20:].mean() < 0.85 * hist[:20].mean()
+    cfg, U = _state(n=(16, 16, 16), steps=40)
+    s = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    s.set_state(U)
+    s.set_sensor(w, 0.5)
+    p = np.empty(s.shape[1:], dtype=np.float32)
+    osbli.osbli_sensor_probs(s.h, p)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    X = S.bf16_round(S.features(o.ghosted(), cfg["n"], cfg["gamma"]).astype(np.float32)).astype(np.float64)
+    wr = w.astype(np.float64)
+    _, po = S.forward(wr, X)
+    assert np.abs(p.ravel() - po).max() <= 2e-2
+
+
+def test_learned_gate_gain_over_full_teno(torch):
+    """Train on 48^3 TGV snapshots, then run 64^3 from the analytic field: the gate keeps the
+    characteristic flux on a minority of cells while the state stays close to the full-TENO
+    (mixed) result; gating nothing (central everywhere but at strong jumps) drifts further."""
+    feats, labels, _ = SN.tgv_training_set(N=48, nsnap=6, steps_between=12)
+    w, _ = SN.train(feats, labels, steps=800, batch=4096)
+    cfg, U = I.tgv(64, Ma=1.25, scheme=I.TENO5)
+    steps = 40
+    base = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+    base.set_state(U)
+    base.step(steps)
+    Ut = base.get_state()
+
+    def hybrid(threshold):
+        hyb = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+        hyb.set_state(U)
+        hyb.set_sensor(w, threshold)
+        hyb.step(steps)
+        Uh = hyb.get_state()
+        l2 = max(np.linalg.norm(Uh[v] - Ut[v]) / np.linalg.norm(Ut[v]) for v in range(5))
+        return l2, hyb.diagnostics()[9], Uh
+
+    thr = SN.calibrate_threshold(w, feats, labels, recall=0.9)
+    l2, frac, Uh = hybrid(thr)
+    l2_none, frac_none, _ = hybrid(0.999999)
+    print("learned gate: threshold %.3f gated fraction %.3f, L2 vs full TENO %.2e; no gate: %.3f, %.2e"
+          % (thr, frac, l2, frac_none, l2_none))
+    assert np.isfinite(Uh).all()
+    assert frac < 0.7
+    assert l2 < 5e-3
+    assert l2 < l2_none
