@@ -5,9 +5,11 @@ One step = one low-storage RK3 step (3 stages of: ghost fill, primitives, charac
 flux differences in x, y, z, viscous fluxes, viscous divergence fused with the register update)
 over the whole grid.  Workload: 3D Taylor-Green vortex, 256^3 periodic, Ma 1.25, Re 1600,
 Pr 0.72, TENO5 characteristic reconstruction in all directions + 4th-order central viscous
-terms, analytic initial field.  Two forms are timed on the same workload: the mixed-precision
-form (the headline ``value``: FP32 reconstruction arithmetic, FP64 state and RK registers) and
-the plain FP64 form, with the relative L2 difference of their states after the same steps.
+terms, analytic initial field.  Three forms are timed on the same workload: mixed precision with
+the learned TENO/central gate (the headline ``value``; the sensor is first trained on the GPU from
+TENO labels of coarse TGV snapshots), mixed precision alone (FP32 reconstruction arithmetic, FP64
+state and RK registers), and plain FP64, with the relative L2 difference of each state against the
+FP64 state after the same steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
 
@@ -41,6 +43,9 @@ UNIT = "Mpoint-stage/s"
 # flux + flux difference), counted from the arithmetic of the method (fma = 2, div/sqrt/rsqrt =
 # 1; comparisons and abs not counted).  Breakdown in the design notes.
 FLOPS_CONV_POINT_DIR = {I.TENO5: 1379.0, I.WENO5JS: 1279.0, I.CENTRAL4: 63.0}
+# central 4th-order interface flux in delta form (three node flux differences by the product
+# rule, the 5-point combination) + flux difference
+FLOPS_CENTRAL_DELTA = 135.0
 SCHEME_NAME = {I.TENO5: "TENO5", I.WENO5JS: "WENO5-JS", I.CENTRAL4: "central4"}
 
 
@@ -56,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain", action="store_true", help="time the plain FP64 form only")
     ap.add_argument("--mixed", action="store_true", help="time the mixed form only")
+    ap.add_argument("--no-sensor", action="store_true", help="skip the learned-sensor form")
+    ap.add_argument("--sensor-steps", type=int, default=800, help="Adam steps of the sensor training")
     return ap.parse_args()
 
 
@@ -183,9 +190,12 @@ def run_reference(args, rank):
     return 0
 
 
-def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist):
+def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sensor=None):
     """Warm up, then time args.steps RK steps of one form with CUDA events on its stream."""
-    s = osbli.Solver(cfg, precision=precision, cuda_stream=stream.cuda_stream)
+    s = osbli.Solver(dict(cfg, sensor=1 if sensor else 0), precision=precision,
+                     cuda_stream=stream.cuda_stream)
+    if sensor:
+        s.set_sensor(sensor[0], sensor[1])
     s.set_state(U)
     s.step(args.warmup)
     torch.cuda.synchronize()
@@ -230,13 +240,32 @@ def main():
     cfg, U, conf = workload(args.n, args.scheme)
     npts = args.n ** 3
     stream = torch.cuda.current_stream()
-    forms = ["mixed", "fp64"]
+    forms = ["learned", "mixed", "fp64"]
     if args.plain or args.scheme == I.CENTRAL4:
         forms = ["fp64"]
     elif args.mixed:
         forms = ["mixed"]
+    elif args.no_sensor:
+        forms = ["mixed", "fp64"]
     head = forms[0]
-    prec = {"mixed": osbli.OSBLI_MIXED, "fp64": osbli.OSBLI_FP64}
+    prec = {"learned": osbli.OSBLI_MIXED, "mixed": osbli.OSBLI_MIXED, "fp64": osbli.OSBLI_FP64}
+    sensor = None
+    sensor_info = None
+    if "learned" in forms:
+        # train the sensor on the GPU from TENO labels of coarse TGV snapshots (same physics)
+        from paper_2007_14933_b300 import sensor as SN
+        t0 = time.perf_counter()
+        feats, labels, _ = SN.tgv_training_set(N=64, Ma=conf["Ma"], nsnap=6, steps_between=12)
+        w, hist = SN.train(feats, labels, steps=args.sensor_steps, batch=4096)
+        thr = SN.calibrate_threshold(w, feats, labels, recall=0.9)
+        sensor = (w, thr)
+        sensor_info = {"train_set": "TGV 64^3 Ma %.2f, 6 snapshots every 12 steps, %d cells, "
+                                    "label fraction %.3f" % (conf["Ma"], int(labels.numel()),
+                                                             float(labels.float().mean().item())),
+                       "train_steps": args.sensor_steps, "batch": 4096, "loss_first": float(hist[:20].mean()),
+                       "loss_last": float(hist[-20:].mean()), "threshold": thr,
+                       "recall_target": 0.9, "train_s": time.perf_counter() - t0}
+        del feats, labels
 
     gpu_index = torch.cuda.current_device()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -248,7 +277,8 @@ def main():
     res = {}
     with ClockSampler(gpu_index) as clk:
         for f in forms:
-            res[f] = time_form(osbli, torch, cfg, U, prec[f], args, stream, barrier, dist)
+            res[f] = time_form(osbli, torch, cfg, U, prec[f], args, stream, barrier, dist,
+                               sensor if f == "learned" else None)
     clocks = clk.summary()
     sh, ms_max = res[head]
     value = npts * 3 * args.steps * world / (ms_max / 1e3) / 1e6
@@ -259,8 +289,16 @@ def main():
     conv = [(nm, t_) for nm, t_ in prof if nm.startswith("conv_")]
     dom_name, dom_ms = max(conv, key=lambda x: x[1])
     flops = FLOPS_CONV_POINT_DIR[args.scheme] * npts
-    if head == "mixed":
-        peak, pdt, kern = osbli.osbli_fp32_peak(), "fp32", "k_conv_char_mixed"
+    gated = None
+    if head == "learned":
+        dg = sh.diagnostics()
+        gated = {"cells": float(dg[9]), "interfaces_x": float(dg[10]),
+                 "interfaces_y": float(dg[11]), "interfaces_z": float(dg[12])}
+        f_int = float(dg[10 + "xyz".index(dom_name[-1])])
+        flops = (f_int * FLOPS_CONV_POINT_DIR[args.scheme] + (1.0 - f_int) * FLOPS_CENTRAL_DELTA) * npts
+    if head in ("mixed", "learned"):
+        peak, pdt = osbli.osbli_fp32_peak(), "fp32"
+        kern = "k_conv_char_delta" if dom_name != "conv_x" else "k_conv_char_delta_x"
         src = "FP32 FMA throughput measured in this run (osbli_fp32_peak)"
     else:
         peak, pdt, kern = osbli.osbli_fp64_peak(), "fp64", "k_conv_char"
@@ -276,19 +314,26 @@ def main():
         out_forms[f] = {"value": npts * 3 * args.steps * world / (ms_ / 1e3) / 1e6,
                         "ms_per_step": ms_ / args.steps}
     extra = {"forms": out_forms}
-    if len(forms) == 2:
-        # accuracy at matched work: both forms advanced warmup + steps from the same state
-        Um = res["mixed"][0].get_state()
+    if "fp64" in forms and len(forms) > 1:
+        # accuracy at matched work: every form advanced warmup + steps from the same state
         Up = res["fp64"][0].get_state()
-        l2 = [float(np.linalg.norm(Um[v] - Up[v]) / np.linalg.norm(Up[v])) for v in range(5)
-              if np.linalg.norm(Up[v]) > 0]
-        extra["speedup_mixed_vs_fp64"] = out_forms["mixed"]["value"] / out_forms["fp64"]["value"]
-        extra["l2_mixed_vs_fp64"] = max(l2)
-        extra["accuracy_note"] = ("relative L2 (max over conserved variables) between the mixed "
-                                  "and FP64 states after %d steps from the same initial field; "
-                                  "FP64 form is parity-checked against the CPU oracle"
+        for f in forms:
+            if f == "fp64":
+                continue
+            Uf = res[f][0].get_state()
+            l2 = [float(np.linalg.norm(Uf[v] - Up[v]) / np.linalg.norm(Up[v])) for v in range(5)
+                  if np.linalg.norm(Up[v]) > 0]
+            extra["l2_%s_vs_fp64" % f] = max(l2)
+            extra["speedup_%s_vs_fp64" % f] = out_forms[f]["value"] / out_forms["fp64"]["value"]
+            del Uf
+        extra["accuracy_note"] = ("relative L2 (max over conserved variables) of each form's state "
+                                  "against the FP64 form after %d steps from the same initial "
+                                  "field; the FP64 form is parity-checked against the CPU oracle"
                                   % (args.warmup + args.steps))
-        del Um, Up
+        del Up
+    if sensor_info:
+        sensor_info["gated"] = gated
+        extra["sensor"] = sensor_info
 
     e2e = None
     launches_e2e = None
@@ -317,18 +362,20 @@ def main():
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    conf = dict(conf, precision=("mixed: FP32 reconstruction / weights / projections / viscous "
-                                 "terms, FP64 state, RK registers, metrics and strong-jump "
-                                 "interfaces" if head == "mixed" else "fp64 state and arithmetic"),
-                form=head)
+    mixed_desc = ("mixed: FP32 reconstruction / weights / projections / viscous terms, FP64 state, "
+                  "RK registers, metrics and strong-jump interfaces")
+    conf = dict(conf, precision=mixed_desc if head in ("mixed", "learned") else "fp64 state and arithmetic",
+                form={"learned": "mixed precision + learned TENO/central gate", "mixed": "mixed precision",
+                      "fp64": "plain FP64"}[head])
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if head in ("mixed", "learned") else "f64",
            "data": "synthetic (analytic TGV initial field)", "config": conf,
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
            "kernels_ms": {nm: t_ for nm, t_ in prof},
-           "variant": ("mixed precision (learned sensor not in this measurement)" if head == "mixed"
-                       else "plain FP64")}
+           "variant": {"learned": "mixed precision + learned sensor (headline form)",
+                       "mixed": "mixed precision", "fp64": "plain FP64"}[head]}
     out.update(extra)
     if launches_e2e is not None:
         out["gpu_launches_e2e"] = launches_e2e

@@ -115,7 +115,8 @@ int osbli_residual(osbli_t *h, double *R);
  * out[0..4] = sum of the conserved variables, out[5] = mean kinetic energy 1/2 rho |u|^2,
  * out[6] = max Mach number, out[7] = min density, out[8] = min pressure, out[9] = fraction of
  * cells gated to the characteristic flux by the learned sensor at the last evaluation (0 when
- * the sensor is off), out[10..15] = 0. */
+ * the sensor is off), out[10..12] = fraction of interfaces along x, y, z taking the
+ * characteristic flux under the sensor's gate (strong jumps aside), out[13..15] = 0. */
 int osbli_diagnostics(osbli_t *h, double out[16]);
 
 /* Time each kernel launch of one residual evaluation (ghost fill per direction, primitives,

@@ -953,7 +953,7 @@ __global__ void k_metric_spread(Dev P, const double *__restrict__ Sraw,
 // ------------------------------------------------------------------------------------------
 // Diagnostics: fixed-partition block partial sums, then one block in fixed order.
 // ------------------------------------------------------------------------------------------
-constexpr int DIAG_BLOCKS = 256, DIAG_THREADS = 256, NDIAG = 10;
+constexpr int DIAG_BLOCKS = 256, DIAG_THREADS = 256, NDIAG = 13;
 
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const double *__restrict__ U,
                                                                const unsigned char *__restrict__ gate,
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
 {
     __shared__ double sh[NDIAG][DIAG_THREADS];
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300, 0};
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300, 0, 0, 0, 0};
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % P.n[0]);
@@ -978,7 +978,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
         acc[6] = fmax(acc[6], sqrt(q2 / (P.gamma * p / rho)));
         acc[7] = fmin(acc[7], rho);
         acc[8] = fmin(acc[8], p);
-        if (gate) acc[9] += gate[id] ? 1.0 : 0.0;
+        if (gate) {
+            acc[9] += gate[id] ? 1.0 : 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+                if (P.active[d]) acc[10 + d] += (gate[id] | gate[id + P.st[d]]) ? 1.0 : 0.0;
+        }
     }
 #pragma unroll
     for (int c = 0; c < NDIAG; c++) sh[c][threadIdx.x] = acc[c];
@@ -990,7 +995,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
             sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][threadIdx.x + off]);
             sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][threadIdx.x + off]);
             sh[8][threadIdx.x] = fmin(sh[8][threadIdx.x], sh[8][threadIdx.x + off]);
-            sh[9][threadIdx.x] += sh[9][threadIdx.x + off];
+#pragma unroll
+            for (int c = 9; c < NDIAG; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + off];
         }
         __syncthreads();
     }
@@ -1001,13 +1007,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dev P, const doub
 __global__ void k_diag_final(const double *__restrict__ part, double *__restrict__ out, long long N)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300, 0};
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 1e300, 1e300, 0, 0, 0, 0};
     for (int b = 0; b < DIAG_BLOCKS; b++) {
         for (int c = 0; c < 6; c++) acc[c] += part[c * DIAG_BLOCKS + b];
         acc[6] = fmax(acc[6], part[6 * DIAG_BLOCKS + b]);
         acc[7] = fmin(acc[7], part[7 * DIAG_BLOCKS + b]);
         acc[8] = fmin(acc[8], part[8 * DIAG_BLOCKS + b]);
-        acc[9] += part[9 * DIAG_BLOCKS + b];
+        for (int c = 9; c < NDIAG; c++) acc[c] += part[c * DIAG_BLOCKS + b];
     }
     for (int c = 0; c < 16; c++) out[c] = 0.0;
     for (int c = 0; c < NV; c++) out[c] = acc[c];
@@ -1015,7 +1021,7 @@ __global__ void k_diag_final(const double *__restrict__ part, double *__restrict
     out[6] = acc[6];
     out[7] = acc[7];
     out[8] = acc[8];
-    out[9] = acc[9] / (double)N;
+    for (int c = 9; c < NDIAG; c++) out[c] = acc[c] / (double)N;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1708,6 +1714,12 @@ int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent
     update<1, 0>(P, B, s);
     if (tap.count <= max_launches && ev) cudaEventRecord(ev[tap.count], s);
     return tap.count;
+}
+
+void launch_prim(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1);
+    else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
 }
 
 void launch_ghosts(const Dev &P, const Bufs &B, cudaStream_t s)

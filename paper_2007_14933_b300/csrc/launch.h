@@ -36,6 +36,7 @@ int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent
 void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, cudaStream_t s);
 int diag_partial_size();
 void launch_ghosts(const Dev &P, const Bufs &B, cudaStream_t s);
+void launch_prim(const Dev &P, const Bufs &B, cudaStream_t s);
 // sensor (sensor.cu)
 int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s);
 void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s);

@@ -173,6 +173,23 @@ __device__ __forceinline__ void neighbour_features(const Dev &P, const double *_
     f[4] = p / pc - 1.f;
 }
 
+// the same from the mixed path's FP32 node arrays (rho in Uf plane 0, u, v, w, p, a in Wf)
+__device__ __forceinline__ void neighbour_features_f(const Dev &P, const float *__restrict__ Uf,
+                                                     const float *__restrict__ Wf, long long id, int nb,
+                                                     float irc, float uc, float vc, float wc, float ipc,
+                                                     float iac, float f[5])
+{
+    const int di = P.active[0] ? nb % 3 - 1 : 0;
+    const int dj = P.active[1] ? (nb / 3) % 3 - 1 : 0;
+    const int dk = P.active[2] ? nb / 9 - 1 : 0;
+    const long long nid = id + di * P.st[0] + dj * P.st[1] + dk * P.st[2];
+    f[0] = Uf[nid] * irc - 1.f;
+    f[1] = (Wf[W_U * P.vs + nid] - uc) * iac;
+    f[2] = (Wf[W_V * P.vs + nid] - vc) * iac;
+    f[3] = (Wf[W_W * P.vs + nid] - wc) * iac;
+    f[4] = Wf[W_P * P.vs + nid] * ipc - 1.f;
+}
+
 __global__ void k_features(Dev P, const double *__restrict__ U, __nv_bfloat16 *__restrict__ X)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -199,66 +216,96 @@ __global__ void k_features(Dev P, const double *__restrict__ U, __nv_bfloat16 *_
 // ------------------------------------------------------------------------------------------
 constexpr int INF_WARPS = 4;
 
-__global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const double *__restrict__ U,
+// A warp handles 16 consecutive x-cells of one grid row.  The 9 neighbouring rows (dj, dk in
+// {-1,0,1}) of x-positions x0-1 .. x0+16 are staged in shared memory with coalesced loads
+// (rho, u, v, w, p).  Each lane then forms exactly the feature values of its tensor-core A
+// fragments: column c of a cell is (neighbour row, x offset, quantity) from a table, and
+// feature = staged value * scale - offset with per-cell scale/offset (1/rho_c and 1; 1/a_c and
+// u_c/a_c; 1/p_c and 1), so no feature tile is written.
+constexpr int SEG = 16;
+__global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const float *__restrict__ Uf,
+                                                                 const float *__restrict__ Wf,
                                                                  const SensorW *__restrict__ W,
                                                                  float zthresh,
                                                                  unsigned char *__restrict__ flag,
                                                                  float *__restrict__ probs)
 {
     __shared__ SensorSmem S;
-    __shared__ __nv_bfloat16 sF[INF_WARPS][16][FS];
-    __shared__ float sC[INF_WARPS][16][6];   // centre rho, u, v, w, p, 1/a
+    __shared__ float sQ[INF_WARPS][9][5][SEG + 2];
+    __shared__ float sM[INF_WARPS][SEG][5], sA[INF_WARPS][SEG][5];
+    __shared__ unsigned short sCol[SK];
     load_weights(S, W);
+    for (int c = threadIdx.x; c < SK; c += blockDim.x) {
+        unsigned short v = 0xFFFF;
+        if (c < SF) {
+            const int nb = c / 5, q = c % 5;
+            v = (unsigned short)(((nb / 3) << 8) | ((nb % 3) << 4) | q);
+        }
+        sCol[c] = v;
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    const long long ntiles = (N + 15) / 16;
+    const int nseg = (P.n[0] + SEG - 1) / SEG;
+    const long long ntiles = (long long)nseg * P.n[1] * P.n[2];
+    const long long vs = P.vs;
     for (long long tile = blockIdx.x * (long long)INF_WARPS + warp; tile < ntiles;
          tile += (long long)gridDim.x * INF_WARPS) {
-        const long long c0 = tile * 16;
-        if (lane < 16) {
-            const long long c = c0 + lane;
-            float r = 1.f, u = 0.f, v = 0.f, w = 0.f, p = 1.f;
-            if (c < N) {
-                int i, j, k;
-                prims_f(P, U, cell_node(P, c, i, j, k), r, u, v, w, p);
-            }
-            sC[warp][lane][0] = r; sC[warp][lane][1] = u; sC[warp][lane][2] = v;
-            sC[warp][lane][3] = w; sC[warp][lane][4] = p;
-            sC[warp][lane][5] = rsqrtf((float)P.gamma * p / r);
-        }
-        __syncwarp();
-        for (int pr = lane; pr < 16 * 27; pr += 32) {
-            const int row = pr / 27, nb = pr % 27;
-            const long long c = c0 + row;
-            float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-            if (c < N) {
-                int i, j, k;
-                const long long id = cell_node(P, c, i, j, k);
-                const float *cc = sC[warp][row];
-                neighbour_features(P, U, id, nb, cc[0], cc[1], cc[2], cc[3], cc[4], cc[5], f);
-            }
+        const int seg = (int)(tile % nseg);
+        const long long row = tile / nseg;
+        const int j = (int)(row % P.n[1]), k = (int)(row / P.n[1]);
+        const int x0 = seg * SEG;
+        const int ncell = min(SEG, P.n[0] - x0);
+        const long long base = node_index(P, x0, j, k);
+        if (lane < SEG + 2) {
+            int dx = lane - 1;
+            if (!P.active[0]) dx = 0;
+            else if (x0 + dx > P.n[0]) dx = P.n[0] - x0;     // past the first ghost: unused
 #pragma unroll
-            for (int q = 0; q < 5; q++) sF[warp][row][5 * nb + q] = __float2bfloat16_rn(f[q]);
+            for (int r = 0; r < 9; r++) {
+                const int dj = P.active[1] ? r % 3 - 1 : 0, dk = P.active[2] ? r / 3 - 1 : 0;
+                const long long id = base + dx + dj * P.st[1] + dk * P.st[2];
+                sQ[warp][r][0][lane] = Uf[id];
+                sQ[warp][r][1][lane] = Wf[W_U * vs + id];
+                sQ[warp][r][2][lane] = Wf[W_V * vs + id];
+                sQ[warp][r][3][lane] = Wf[W_W * vs + id];
+                sQ[warp][r][4][lane] = Wf[W_P * vs + id];
+            }
         }
-        for (int q = lane; q < 16 * (SK - SF); q += 32) sF[warp][q / (SK - SF)][SF + q % (SK - SF)] = __float2bfloat16_rn(0.f);
         __syncwarp();
+        if (lane < SEG) {
+            const float r = sQ[warp][4][0][lane + 1], p = sQ[warp][4][4][lane + 1];
+            const float irc = 1.f / r, ipc = 1.f / p;
+            const float iac = rsqrtf((float)P.gamma * p * irc);
+            sM[warp][lane][0] = irc; sA[warp][lane][0] = 1.f;
+            sM[warp][lane][4] = ipc; sA[warp][lane][4] = 1.f;
+#pragma unroll
+            for (int c = 1; c < 4; c++) {
+                sM[warp][lane][c] = iac;
+                sA[warp][lane][c] = sQ[warp][4][c][lane + 1] * iac;
+            }
+        }
+        __syncwarp();
+        auto feat = [&](int cell, int col) -> float {
+            const unsigned short m = sCol[col];
+            if (m == 0xFFFF || cell >= ncell) return 0.f;
+            const int q = m & 15, di = (m >> 4) & 15, rn = m >> 8;
+            return fmaf(sQ[warp][rn][q][cell + di], sM[warp][cell][q], -sA[warp][cell][q]);
+        };
         TileOut o;
         mlp_tile(S, [&](int kt, uint32_t a[4]) {
-            a[0] = ld32(&sF[warp][g][16 * kt + 2 * t]);
-            a[1] = ld32(&sF[warp][g + 8][16 * kt + 2 * t]);
-            a[2] = ld32(&sF[warp][g][16 * kt + 8 + 2 * t]);
-            a[3] = ld32(&sF[warp][g + 8][16 * kt + 8 + 2 * t]);
+            const int c0 = 16 * kt + 2 * t, c1 = c0 + 8;
+            a[0] = pack2(feat(g, c0), feat(g, c0 + 1));
+            a[1] = pack2(feat(g + 8, c0), feat(g + 8, c0 + 1));
+            a[2] = pack2(feat(g, c1), feat(g, c1 + 1));
+            a[3] = pack2(feat(g + 8, c1), feat(g + 8, c1 + 1));
         }, o);
         if (t == 0) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const long long c = c0 + g + 8 * h;
-                if (c < N) {
-                    int i, j, k;
-                    const long long id = cell_node(P, c, i, j, k);
-                    if (flag) flag[id] = o.z[h] > zthresh ? 1 : 0;
-                    if (probs) probs[c] = 1.f / (1.f + __expf(-o.z[h]));
+                const int ci = g + 8 * h;
+                if (ci < ncell) {
+                    if (flag) flag[base + ci] = o.z[h] > zthresh ? 1 : 0;
+                    if (probs) probs[(row * P.n[0]) + x0 + ci] = 1.f / (1.f + __expf(-o.z[h]));
                 }
             }
         }
@@ -310,11 +357,10 @@ static int sm_count()
 
 int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s)
 {
-    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    const long long tiles = (N + 15) / 16;
+    const long long tiles = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[1] * P.n[2];
     long long blocks = (tiles + INF_WARPS - 1) / INF_WARPS;
     if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
-    k_sensor_infer<<<(int)blocks, 32 * INF_WARPS, 0, s>>>(P, B.U, (const SensorW *)B.sw, B.zthresh, B.sflag, nullptr);
+    k_sensor_infer<<<(int)blocks, 32 * INF_WARPS, 0, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw, B.zthresh, B.sflag, nullptr);
     long long db = (P.ntot + 255) / 256;
     if (db > (long long)sm_count() * 16) db = (long long)sm_count() * 16;
     k_dilate<<<(int)db, 256, 0, s>>>(P, B.sflag, B.gate, 0);
@@ -323,11 +369,11 @@ int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s)
 
 void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s)
 {
-    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    const long long tiles = (N + 15) / 16;
+    launch_prim(P, B, s);
+    const long long tiles = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[1] * P.n[2];
     long long blocks = (tiles + INF_WARPS - 1) / INF_WARPS;
     if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
-    k_sensor_infer<<<(int)blocks, 32 * INF_WARPS, 0, s>>>(P, B.U, (const SensorW *)B.sw, B.zthresh, nullptr, probs);
+    k_sensor_infer<<<(int)blocks, 32 * INF_WARPS, 0, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw, B.zthresh, nullptr, probs);
 }
 
 void launch_features(const Dev &P, const Bufs &B, void *X, cudaStream_t s)
