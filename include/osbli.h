@@ -146,7 +146,8 @@ int osbli_sensor_set_weights(osbli_t *h, const float *w, float threshold);
 
 /* Training labels of the current state (TENO5 handles, any precision): 1 for a cell whose FP64
  * TENO5 residual used an interface where a candidate stencil was cut and the cut moved the
- * reconstruction by more than 5 % of the stencil's range.  labels: [nz][ny][nx] bytes, host or
+ * reconstruction by more than 5 % of the stencil's range and by more than 1e-5 x the interface's
+ * mean density x its largest acoustic speed (a floor against rounding-noise cut-offs).  labels: [nz][ny][nx] bytes, host or
  * device.  Allocates temporary device memory. */
 int osbli_sensor_labels(osbli_t *h, uint8_t *labels);
 

@@ -712,8 +712,10 @@ static void impose_boundary_nodes(orc_ctx *c)
  * ------------------------------------------------------------------------------------------ */
 /* Sensor label of one reconstruction (no counterpart in the paper): a TENO cut-off (some
  * omega_r = 0) that moves the reconstructed value away from the linear 5th-order value
- * (2, -13, 47, 27, -3)/60 by more than 5 % of the range of the five stencil values. */
-static int cut_matters(const double *f, double h, const double *w)
+ * (2, -13, 47, 27, -3)/60 by more than 5 % of the range of the five stencil values and by more
+ * than `noise` (1e-5 of the interface's mean density times its largest acoustic speed), so that
+ * cut-offs decided by rounding noise in near-uniform flow do not count. */
+static int cut_matters(const double *f, double h, const double *w, double noise)
 {
     if (w[0] != 0.0 && w[1] != 0.0 && w[2] != 0.0) return 0;
     double lin = (2.0 * f[0] - 13.0 * f[1] + 47.0 * f[2] + 27.0 * f[3] - 3.0 * f[4]) / 60.0;
@@ -722,7 +724,8 @@ static int cut_matters(const double *f, double h, const double *w)
         if (f[k] < lo) lo = f[k];
         if (f[k] > hi) hi = f[k];
     }
-    return fabs(h - lin) > 0.05 * (hi - lo);
+    double dev = fabs(h - lin);
+    return dev > 0.05 * (hi - lo) && dev > noise;
 }
 
 static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *margin, int *cut)
@@ -759,6 +762,12 @@ static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *
     eigensystem(P->gamma, u, H, a, nv, R, L);
     double gh[NV];
     double mg = INFINITY;
+    double acoustic = 0.0;
+    for (int s = 0; s < 6; s++) {
+        if (fabs(lam[s][0]) > acoustic) acoustic = fabs(lam[s][0]);
+        if (fabs(lam[s][2]) > acoustic) acoustic = fabs(lam[s][2]);
+    }
+    const double floor_ = 1e-5 * 0.5 * (Uk[2][0] + Uk[3][0]) * acoustic;
     for (int j = 0; j < NV; j++) {
         int lj = (j == 0) ? 0 : (j == 4 ? 2 : 1);
         double alpha = 0.0;
@@ -783,7 +792,7 @@ static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *
         double hp = orc_recon5(gp, P->scheme, P->teno_ct, w1, &m1);
         double hm = orc_recon5(fm, P->scheme, P->teno_ct, w2, &m2);
         if (cut && P->scheme == ORC_TENO5) {
-            if (cut_matters(gp, hp, w1) || cut_matters(fm, hm, w2)) *cut = 1;
+            if (cut_matters(gp, hp, w1, floor_) || cut_matters(fm, hm, w2, floor_)) *cut = 1;
         }
         if (m1 < mg) mg = m1;
         if (m2 < mg) mg = m2;
@@ -1061,8 +1070,8 @@ void orc_residual_points(void *h, int npts, const int *ijk, double *R, double *m
 /* Shock-sensor training labels (no counterpart in the paper; the learned sensor is an addition
  * to the method): label 1 where the TENO5 residual of the point used an interface (either side,
  * any characteristic field, any direction) at which a candidate stencil was cut (delta_r = 0,
- * Eq. 24) and the cut moved the reconstruction by more than 5 % of the stencil's range (see
- * cut_matters), else 0.  labels: [nz][ny][nx] bytes. */
+ * Eq. 24) and the cut moved the reconstruction by more than 5 % of the stencil's range and
+ * above the noise floor (see cut_matters), else 0.  labels: [nz][ny][nx] bytes. */
 void orc_labels(void *h, unsigned char *labels)
 {
     orc_ctx *c = (orc_ctx *)h;

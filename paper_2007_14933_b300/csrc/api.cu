@@ -28,6 +28,8 @@ struct osbli {
     cudaGraphExec_t gexec = nullptr;
     int launches_step = 0;
     bool sensor_ready = false;
+    double *lfac[3] = {nullptr, nullptr, nullptr};   // rectilinear grids: per-line factors
+    double *lesc[3] = {nullptr, nullptr, nullptr};   // and per-line epsilon scales
     const char *prof_names[32] = {};
     int prof_count = 0;
     char err[512];
@@ -73,6 +75,10 @@ static void free_all(osbli *h)
     if (h->B.sw) cudaFree(h->B.sw);
     if (h->B.sflag) cudaFree(h->B.sflag);
     if (h->B.gate) cudaFree(h->B.gate);
+    for (int d = 0; d < 3; d++) {
+        if (h->lfac[d]) cudaFree(h->lfac[d]);
+        if (h->lesc[d]) cudaFree(h->lesc[d]);
+    }
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -114,9 +120,8 @@ static int validate(const osbli_params *p, const double *coords)
     if (p->precision == OSBLI_MIXED && p->scheme == OSBLI_CENTRAL4)
         return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / TENO5");
     if (p->sensor != 0 && p->sensor != 1) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0 or 1");
-    if (p->sensor == 1 && (p->precision != OSBLI_MIXED || coords || p->scheme == OSBLI_CENTRAL4))
-        return seterr(nullptr, OSBLI_EINVAL,
-                      "the learned sensor gates the mixed-precision WENO/TENO path on Cartesian grids");
+    if (p->sensor == 1 && (p->precision != OSBLI_MIXED || p->scheme == OSBLI_CENTRAL4))
+        return seterr(nullptr, OSBLI_EINVAL, "the learned sensor gates the mixed-precision WENO/TENO path");
     for (int d = 0; d < 3; d++)
         for (int s = 0; s < 2; s++)
             if (n[d] > 1 && p->bc[d][s] == OSBLI_WALL && !(p->T_wall > 0.0))
@@ -261,8 +266,22 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
             launch_metrics(P, X, L, Sraw, smax, h->B.M, h->stream);
             e = cudaGetLastError();
         }
+        // rectilinear detection: per-line factors and a flag raised by any non-rectilinear node
+        for (int d = 0; d < 3 && e == cudaSuccess; d++) {
+            e = cudaMalloc(&h->lfac[d], (size_t)n[d] * sizeof(double));
+            const size_t lines = (size_t)n[(d == 0) ? 1 : 0] * n[(d == 2) ? 1 : 2];
+            if (e == cudaSuccess) e = cudaMalloc(&h->lesc[d], lines * sizeof(double));
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->B.err, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) {
+            launch_rect(P, Sraw, smax, h->lfac, h->lesc, h->B.err, h->stream);
+            e = cudaGetLastError();
+        }
         unsigned long long hs[3] = {0, 0, 0};
+        int general_grid = 1;
         if (e == cudaSuccess) e = cudaMemcpyAsync(hs, smax, sizeof(hs), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&general_grid, h->B.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->B.err, 0, sizeof(int), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         cudaFree(X);
         if (Sraw) cudaFree(Sraw);
@@ -276,6 +295,13 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
             if (!(v > 0.0) || !isfinite(v))
                 return fail(seterr(h, OSBLI_EINVAL, "degenerate grid: metric of direction %d is %g", d, v));
         }
+        P.rect = general_grid == 0;
+        for (int d = 0; d < 3; d++) {
+            P.lfac[d] = P.rect ? h->lfac[d] : nullptr;
+            P.lesc[d] = P.rect ? h->lesc[d] : nullptr;
+        }
+        if (P.sensor && !P.rect)
+            return fail(seterr(h, OSBLI_EINVAL, "the learned sensor needs a Cartesian or rectilinear grid"));
     }
     CKC(cudaStreamSynchronize(h->stream));
     *out = h;
@@ -451,7 +477,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction
-        if (P.mixed && !P.curv) per_stage += (d == 0) ? 2 : 1;   // patch (+ x segment lefts)
+        if (P.mixed && !general(P)) per_stage += (d == 0) ? 2 : 1;   // patch (+ x segment lefts)
         for (int s = 0; s < 2; s++) {
             const int bc = P.bc[d][s];
             if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;

@@ -36,8 +36,39 @@ struct Dev {
     double dt;
     int mixed;         // OSBLI_MIXED: FP32 reconstruction arithmetic
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
-    int sensor;        // learned gate active (mixed path, Cartesian grids)
+    int sensor;        // learned gate active (mixed path, Cartesian or rectilinear grids)
+    int rect;          // rectilinear grid: Cartesian kernels with per-line factors lfac
+    const double *lfac[3];   // rect: S_dd / Jinv of each line position along direction d
+    const double *lesc[3];   // rect: 1 / |S~_d|^2 of each line of direction d ([n_DB][n_DA])
 };
+
+// Grids that need the general curvilinear kernels (metric vectors read per node).
+__host__ __device__ __forceinline__ bool general(const Dev &P) { return P.curv && !P.rect; }
+
+// Residual factor of the divergence along DIR at line position s.  Uniform grids: s_d / Jinv =
+// 1/h_d.  Rectilinear grids (coordinate c a function of xi_c alone): the metric vector S_d is
+// axis-aligned and constant along its own lines, so the strong-conservation divergence
+// (Sec. 2.7) is the Cartesian one scaled by S_dd / Jinv of the line position (1/(dx_d/dxi_d)).
+template <int DIR>
+__device__ __forceinline__ double line_fac(const Dev &P, int s)
+{
+    return P.rect ? __ldg(P.lfac[DIR] + s) : P.fac[DIR];
+}
+__device__ __forceinline__ double line_fac(const Dev &P, int d, int s)
+{
+    return P.rect ? __ldg(P.lfac[d] + s) : P.fac[d];
+}
+
+// Epsilon scale of the reconstructions along a line of direction DIR through cross indices
+// (a, b) (a: lower cross direction).  The curvilinear form reconstructs the metric-scaled flux
+// |S~_d| F; on rectilinear grids the Cartesian kernels reconstruct F itself, and eps / |S~_d|^2
+// in place of eps gives exactly the same WENO / TENO weights.  1 on uniform grids (|S~_d| = 1).
+template <int DIR>
+__device__ __forceinline__ double line_eps(const Dev &P, int a, int b)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0;
+    return P.rect ? __ldg(P.lesc[DIR] + (long long)b * P.n[DA] + a) : 1.0;
+}
 
 __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, int j, int k)
 {
@@ -79,8 +110,9 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // and gamma is normalised by its largest member before the sixth power (x^6 of the unscaled
 // ratio overflows FP32); the cut-off test is unchanged in exact arithmetic.
 // ------------------------------------------------------------------------------------------
+// es scales the absolute epsilons (WENO-JS 1e-6, FP64 TENO 1e-16): see line_eps.
 template <int SCHEME, typename T>
-__device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, bool *allkept = nullptr)
+__device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, T es, bool *allkept = nullptr)
 {
     constexpr bool F32 = sizeof(T) == 4;
     const T c13_12 = T(13.0 / 12.0), q = T(0.25);
@@ -110,7 +142,7 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, bool *al
             const T r = fdiv(T(1), fmax(x0, fmax(x1, x2)));
             x0 *= r; x1 *= r; x2 *= r;
         } else {
-            const T eps = T(1e-16);
+            const T eps = T(1e-16) * es;
             const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
             const T ip = T(1) / (e0 * e1 * e2);
             x0 = T(1) + tau * (ip * e1 * e2);
@@ -127,7 +159,7 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, bool *al
         if (k0 && k1 && k2) return r;
         return r / (w0 + w1 + w2);
     } else {
-        const T eps = T(1e-6);
+        const T eps = T(1e-6) * es;
         const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
         T a0, a1, a2;
         if (F32) {
@@ -145,15 +177,18 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, bool *al
 
 // Sensor label of one TENO reconstruction (an addition to the method; the paper has none): the
 // cut-off removed a candidate stencil and moved the value away from the linear 5th-order
-// reconstruction by more than 5 % of the range of the five stencil values.
+// reconstruction by more than 5 % of the range of the five stencil values and by more than
+// `floor` (1e-5 x the interface's mean density x its largest acoustic speed, which keeps
+// rounding-noise cut-offs in near-uniform flow out).
 __device__ __forceinline__ bool cut_matters(double f0, double f1, double f2, double f3, double f4,
-                                            double val, bool allkept)
+                                            double val, bool allkept, double floor)
 {
     if (allkept) return false;
     const double lin = (2.0 * f0 - 13.0 * f1 + 47.0 * f2 + 27.0 * f3 - 3.0 * f4) / 60.0;
     const double lo = fmin(fmin(fmin(f0, f1), fmin(f2, f3)), f4);
     const double hi = fmax(fmax(fmax(f0, f1), fmax(f2, f3)), f4);
-    return fabs(val - lin) > 0.05 * (hi - lo);
+    const double dev = fabs(val - lin);
+    return dev > 0.05 * (hi - lo) && dev > floor;
 }
 
 }  // namespace osb

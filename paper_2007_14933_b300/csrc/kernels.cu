@@ -287,7 +287,7 @@ struct SrcFromState {
 // T is the arithmetic type (double: plain FP64 path; float: mixed path).
 template <int DIR, int SCHEME, bool CURV, typename T, typename Src, bool LABEL = false>
 __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const double *__restrict__ M,
-                                               long long m, long long st, T Fh[NV], bool *label = nullptr)
+                                               long long m, long long st, T es, T Fh[NV], bool *label = nullptr)
 {
     const long long vs = P.vs;
     const long long mr = m + st;
@@ -408,18 +408,19 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
     // (e) reconstruction
     T g[NV];
     const T ct = T(P.ct);
+    const double floor_ = LABEL ? 1e-5 * 0.5 * (q.rho(m) + q.rho(mr)) * fmax(al0, al4) : 0.0;
 #pragma unroll
     for (int j = 0; j < NV; j++) {
         if (LABEL) {
             bool kp = true, km = true;
-            const T vp = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, &kp);
-            const T vm = recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, &km);
+            const T vp = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, es, &kp);
+            const T vm = recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, es, &km);
             g[j] = vp + vm;
-            *label = *label || cut_matters(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], vp, kp) ||
-                     cut_matters(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], vm, km);
+            *label = *label || cut_matters(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], vp, kp, floor_) ||
+                     cut_matters(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], vm, km, floor_);
         } else {
-            g[j] = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
-                   recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+            g[j] = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, es) +
+                   recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, es);
         }
     }
     // (f) back-projection F = R g
@@ -462,13 +463,14 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR];
     const SrcArrays<double> q{U, W, P.vs};
+    const double es = CURV ? 1.0 : line_eps<DIR>(P, a, b);
     double Fm[NV];
-    interface_flux<DIR, SCHEME, CURV, double>(P, q, M, base + (long long)(s0 - 1) * st, st, Fm);
+    interface_flux<DIR, SCHEME, CURV, double>(P, q, M, base + (long long)(s0 - 1) * st, st, es, Fm);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         double Fp[NV];
-        interface_flux<DIR, SCHEME, CURV, double>(P, q, M, id, st, Fp);
-        const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : P.fac[DIR];
+        interface_flux<DIR, SCHEME, CURV, double>(P, q, M, id, st, es, Fp);
+        const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : line_fac<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             const double r = -fac * (Fp[v] - Fm[v]);
@@ -538,11 +540,11 @@ __device__ __forceinline__ bool strong_jump(const Dev &P, const float *__restric
 template <int DIR, int SCHEME, bool CURV>
 __device__ __noinline__ void fallback_flux(const Dev &P, const double *__restrict__ U,
                                            const double *__restrict__ M, long long m, long long st,
-                                           float *Fh)
+                                           double es, float *Fh)
 {
     const SrcFromState q{U, P.vs, P.gamma, P.gm1};
     double f[NV];
-    interface_flux<DIR, SCHEME, CURV, double>(P, q, M, m, st, f);
+    interface_flux<DIR, SCHEME, CURV, double>(P, q, M, m, st, es, f);
 #pragma unroll
     for (int v = 0; v < NV; v++) Fh[v] = (float)f[v];
 }
@@ -551,10 +553,10 @@ template <int DIR, int SCHEME, bool CURV>
 __device__ __forceinline__ void mixed_flux(const Dev &P, const SrcArrays<float> &qf,
                                            const double *__restrict__ U,
                                            const double *__restrict__ M, long long m, long long st,
-                                           float Fh[NV])
+                                           double es, float Fh[NV])
 {
-    if (strong_jump(P, qf.U, qf.W, m, st)) fallback_flux<DIR, SCHEME, CURV>(P, U, M, m, st, Fh);
-    else interface_flux<DIR, SCHEME, CURV, float>(P, qf, M, m, st, Fh);
+    if (strong_jump(P, qf.U, qf.W, m, st)) fallback_flux<DIR, SCHEME, CURV>(P, U, M, m, st, es, Fh);
+    else interface_flux<DIR, SCHEME, CURV, float>(P, qf, M, m, st, (float)es, Fh);
 }
 
 template <int DIR, int SCHEME, bool CURV>
@@ -575,13 +577,14 @@ __global__ void __launch_bounds__(128) k_conv_char_mixed(Dev P, const double *__
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR];
     const SrcArrays<float> qf{Uf, Wf, P.vs};
+    const double es = CURV ? 1.0 : line_eps<DIR>(P, a, b);
     float Fm[NV];
-    mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, base + (long long)(s0 - 1) * st, st, Fm);
+    mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, base + (long long)(s0 - 1) * st, st, es, Fm);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         float Fp[NV];
-        mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, id, st, Fp);
-        const float fac = CURV ? (float)(P.shat[DIR] * M[9 * P.vs + id]) : (float)P.fac[DIR];
+        mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, id, st, es, Fp);
+        const float fac = CURV ? (float)(P.shat[DIR] * M[9 * P.vs + id]) : (float)line_fac<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             const float r = -fac * (Fp[v] - Fm[v]);
@@ -665,7 +668,7 @@ __global__ void __launch_bounds__(128) k_conv_central(Dev P, const double *__res
                 D[v] = s / 12.0;
             }
         }
-        const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : P.fac[DIR];
+        const double fac = CURV ? P.shat[DIR] * M[9 * P.vs + id] : line_fac<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             const double r = -fac * D[v];
@@ -747,7 +750,7 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
 #pragma unroll
             for (int v = 0; v < 4; v++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) gr[v][c] = T(P.fac[c]) * dxi[c][v];
+                for (int c = 0; c < 3; c++) gr[v][c] = T(line_fac(P, c, ijk[c])) * dxi[c][v];
         }
         const T Tm = T(W[W_T * vs + id]);
         const T mu = viscosity_t<T>(P, Tm);
@@ -815,7 +818,7 @@ __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, d
                 const int ie = ijk[d], n = P.n[d];
                 const long long st = P.st[d];
                 const bool per = P.bc[d][0] == BC_PERIODIC;
-                const RT fac = RT(CURV ? P.shat[d] * M[9 * vs + id] : P.fac[d]);
+                const RT fac = RT(CURV ? P.shat[d] * M[9 * vs + id] : line_fac(P, d, ie));
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
                     const RT *f = V + (d * 4 + c) * vs + id;
@@ -1052,11 +1055,11 @@ __device__ __forceinline__ void node_flux_fp64(const Dev &P, const double *__res
 
 template <int DIR, int SCHEME>
 __device__ __noinline__ void fallback_delta(const Dev &P, const double *__restrict__ U, long long m,
-                                            long long st, float *D, float *dF1)
+                                            long long st, double es, float *D, float *dF1)
 {
     const SrcFromState q{U, P.vs, P.gamma, P.gm1};
     double Fh[NV], Fm_[NV], Fl[NV];
-    interface_flux<DIR, SCHEME, false, double>(P, q, nullptr, m, st, Fh);
+    interface_flux<DIR, SCHEME, false, double>(P, q, nullptr, m, st, es, Fh);
     node_flux_fp64<DIR>(P, U, m, Fm_);
     node_flux_fp64<DIR>(P, U, m - st, Fl);
 #pragma unroll
@@ -1069,7 +1072,7 @@ __device__ __noinline__ void fallback_delta(const Dev &P, const double *__restri
 template <int DIR, int SCHEME>
 __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict__ Uf,
                                            const float *__restrict__ Wf, long long m, long long st,
-                                           float D[NV], float dF1[NV])
+                                           float es, float D[NV], float dF1[NV])
 {
     const long long vs = P.vs;
     const long long mr = m + st;
@@ -1179,8 +1182,8 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
     const float ct = (float)P.ct;
 #pragma unroll
     for (int j = 0; j < NV; j++)
-        g[j] = recon5<SCHEME, float>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct) +
-               recon5<SCHEME, float>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct);
+        g[j] = recon5<SCHEME, float>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, es) +
+               recon5<SCHEME, float>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, es);
     const float s04 = g[0] + g[4], d40 = g[4] - g[0];
     const float sm = s04 + g[1];
     D[0] = sm;
@@ -1247,12 +1250,13 @@ __device__ __forceinline__ void central_delta(const Dev &P, const float *__restr
 template <int DIR, int SCHEME>
 __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restrict__ Uf,
                                               const float *__restrict__ Wf, long long m, long long st,
-                                              float D[NV], float dF1[NV], unsigned char *__restrict__ flag,
+                                              float es, float D[NV], float dF1[NV],
+                                              unsigned char *__restrict__ flag,
                                               float *__restrict__ Dst, int *__restrict__ nstrong,
                                               const unsigned char *__restrict__ gate)
 {
     const bool strong = strong_jump(P, Uf, Wf, m, st);
-    if (!gate || strong || gate[m] || gate[m + st]) delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, D, dF1);
+    if (!gate || strong || gate[m] || gate[m + st]) delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, es, D, dF1);
     else central_delta<DIR>(P, Uf, Wf, m, st, D, dF1);
     flag[m] = strong ? 1 : 0;
     if (strong) {
@@ -1282,13 +1286,14 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
     ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR];
-    const float fac = (float)P.fac[DIR];
+    const float es = (float)line_eps<DIR>(P, a, b);
     float Dm[NV], dF1[NV];
-    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, Dm, dF1, flag, Dst, nstrong, gate);
+    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, es, Dm, dF1, flag, Dst, nstrong, gate);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         float Dp[NV];
-        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, Dp, dF1, flag, Dst, nstrong, gate);
+        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, flag, Dst, nstrong, gate);
+        const float fac = (float)line_fac<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             // F_{m+1/2} - F_{m-1/2} = (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2}
@@ -1321,7 +1326,8 @@ __global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restr
     const int j = (int)(row % P.n[1]), k = (int)(row / P.n[1]);
     const long long base = node_index(P, 0, j, k);
     float D[NV], unused[NV];
-    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, D, unused, flag, Dst, nstrong, gate);
+    const float es = (float)line_eps<0>(P, j, k);
+    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, es, D, unused, flag, Dst, nstrong, gate);
 #pragma unroll
     for (int v = 0; v < NV; v++) Dl[t * NV + v] = D[v];
 }
@@ -1347,14 +1353,15 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
     float dF1[NV];
     if (i < P.n[0]) {
         float D[NV];
-        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, D, dF1, flag, Dst, nstrong, gate);
+        const float es = (float)line_eps<0>(P, j, k);
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, es, D, dF1, flag, Dst, nstrong, gate);
 #pragma unroll
         for (int v = 0; v < NV; v++) sD[v][t + 1] = D[v];
     }
     if (t < NV) sD[t][0] = Dl[((long long)row * nseg + blockIdx.y) * NV + t];
     __syncthreads();
     if (i >= P.n[0]) return;
-    const float fac = (float)P.fac[0];
+    const float fac = (float)line_fac<0>(P, i);
     const long long id = base + i;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -1385,19 +1392,22 @@ __global__ void __launch_bounds__(128) k_patch_strong(Dev P, const double *__res
         const long long id = node_index(P, i, j, k);
         const bool fl = flag[id - st] != 0, fr = flag[id] != 0;
         if (!fl && !fr) continue;
+        constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+        const int ijk[3] = {i, j, k};
+        const double es = line_eps<DIR>(P, ijk[DA], ijk[DB]);
         float corr[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
         float D64[NV], unused[NV];
         if (fr) {
-            fallback_delta<DIR, SCHEME>(P, U, id, st, D64, unused);
+            fallback_delta<DIR, SCHEME>(P, U, id, st, es, D64, unused);
 #pragma unroll
             for (int v = 0; v < NV; v++) corr[v] += D64[v] - Dst[v * P.vs + id];
         }
         if (fl) {
-            fallback_delta<DIR, SCHEME>(P, U, id - st, st, D64, unused);
+            fallback_delta<DIR, SCHEME>(P, U, id - st, st, es, D64, unused);
 #pragma unroll
             for (int v = 0; v < NV; v++) corr[v] -= D64[v] - Dst[v * P.vs + id - st];
         }
-        const float fac = (float)P.fac[DIR];
+        const float fac = (float)line_fac<DIR>(P, ijk[DIR]);
 #pragma unroll
         for (int v = 0; v < NV; v++) Rf[v * P.vs + id] += -fac * corr[v];
     }
@@ -1426,11 +1436,12 @@ __global__ void __launch_bounds__(128) k_label_dir(Dev P, const double *__restri
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR];
     const SrcFromState q{U, P.vs, P.gamma, P.gm1};
+    const double es = CURV ? 1.0 : line_eps<DIR>(P, a, b);
     for (int m = s0 - (s0 == 0 ? 1 : 0); m < s1; m++) {
         const long long id = base + (long long)m * st;
         double F[NV];
         bool l = false;
-        interface_flux<DIR, SCH_TENO5, CURV, double, SrcFromState, true>(P, q, M, id, st, F, &l);
+        interface_flux<DIR, SCH_TENO5, CURV, double, SrcFromState, true>(P, q, M, id, st, es, F, &l);
         lab[id] = l ? 1 : 0;
     }
 }
@@ -1507,6 +1518,72 @@ void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sr
     k_metric_spread<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, Sraw, smax, M);
 }
 
+// Rectilinear grids (coordinate c a function of xi_c alone): every metric vector is
+// axis-aligned, S_d = S_dd e_d, and S_dd / Jinv depends on the position along d only.  The line
+// factors come from the nodes with the other two indices 0; a check marks the grid general when
+// any off-diagonal metric is non-zero or a node's factor differs from its line's by more than
+// 1e-13 (relative).
+__global__ void k_rect_lines(Dev P, const double *__restrict__ Sraw, const unsigned long long *__restrict__ smax,
+                             double *l0, double *l1, double *l2, double *e0, double *e1, double *e2)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    double *out[3] = {l0, l1, l2}, *eout[3] = {e0, e1, e2};
+    const int d = blockIdx.y;
+    const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+    const long long stv[3] = {1, P.n[0], (long long)P.n[0] * P.n[1]};
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n[d]; s += gridDim.x * blockDim.x) {
+        const long long o = (long long)s * stv[d];
+        out[d][s] = Sraw[(d * 3 + d) * N + o] / Sraw[9 * N + o];
+    }
+    // 1 / |S~_d|^2 of every line of direction d, from its first node
+    const double sh = __longlong_as_double((long long)smax[d]);
+    const long long lines = (long long)P.n[da] * P.n[db];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < lines;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t % P.n[da]), b = (int)(t / P.n[da]);
+        const long long o = a * stv[da] + b * stv[db];
+        const double sn = fabs(Sraw[(d * 3 + d) * N + o]) / sh;
+        eout[d][t] = 1.0 / (sn * sn);
+    }
+}
+
+__global__ void k_rect_check(Dev P, const double *__restrict__ Sraw, const double *l0, const double *l1,
+                             const double *l2, const double *e0, const double *e1, const double *e2,
+                             const unsigned long long *__restrict__ smax, int *__restrict__ general_grid)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    const double *lf[3] = {l0, l1, l2}, *le[3] = {e0, e1, e2};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int ijk[3] = {i, (int)(q % P.n[1]), (int)(q / P.n[1])};
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                if (c != d) bad |= Sraw[(d * 3 + c) * N + t] != 0.0;
+            const double f = Sraw[(d * 3 + d) * N + t] / Sraw[9 * N + t], g = lf[d][ijk[d]];
+            bad |= !(fabs(f - g) <= 1e-13 * fabs(g));
+            const double sn = fabs(Sraw[(d * 3 + d) * N + t]) / __longlong_as_double((long long)smax[d]);
+            const double e = 1.0 / (sn * sn), ge = le[d][(long long)ijk[db] * P.n[da] + ijk[da]];
+            bad |= !(fabs(e - ge) <= 1e-12 * fabs(ge));
+        }
+        if (bad) atomicOr(general_grid, 1);
+    }
+}
+
+void launch_rect(const Dev &P, const double *Sraw, const unsigned long long *smax, double *const lfac[3],
+                 double *const lesc[3], int *general_grid, cudaStream_t s)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    k_rect_lines<<<dim3(256, 3), 128, 0, s>>>(P, Sraw, smax, lfac[0], lfac[1], lfac[2], lesc[0], lesc[1], lesc[2]);
+    k_rect_check<<<grid_for(N, 256), 256, 0, s>>>(P, Sraw, lfac[0], lfac[1], lfac[2], lesc[0], lesc[1],
+                                                  lesc[2], smax, general_grid);
+}
+
 int conv_chunk(const Dev &P, int d)
 {
     const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
@@ -1547,13 +1624,13 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
     dim3 blk(32, 4);
     dim3 grd((P.n[DA] + 31) / 32, (P.n[DB] + 3) / 4, (P.n[DIR] + chunk - 1) / chunk);
     if (P.scheme == SCH_CENTRAL4) {
-        if (P.curv) k_conv_central<DIR, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
+        if (general(P)) k_conv_central<DIR, true><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
         else k_conv_central<DIR, false><<<grd, blk, 0, s>>>(P, B.U, B.W, B.M, B.R, acc, chunk);
     } else if (P.scheme == SCH_WENO5JS) {
-        if (P.curv) conv_char_launch<DIR, SCH_WENO5JS, true>(P, B, acc, chunk, grd, blk, s);
+        if (general(P)) conv_char_launch<DIR, SCH_WENO5JS, true>(P, B, acc, chunk, grd, blk, s);
         else conv_char_launch<DIR, SCH_WENO5JS, false>(P, B, acc, chunk, grd, blk, s);
     } else {
-        if (P.curv) conv_char_launch<DIR, SCH_TENO5, true>(P, B, acc, chunk, grd, blk, s);
+        if (general(P)) conv_char_launch<DIR, SCH_TENO5, true>(P, B, acc, chunk, grd, blk, s);
         else conv_char_launch<DIR, SCH_TENO5, false>(P, B, acc, chunk, grd, blk, s);
     }
 }
@@ -1573,10 +1650,10 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     int g = grid_for(N, 128);
     if (P.viscous) {
-        if (P.curv) update_t<MODE, STAGE, true, true>(P, B, g, s);
+        if (general(P)) update_t<MODE, STAGE, true, true>(P, B, g, s);
         else update_t<MODE, STAGE, true, false>(P, B, g, s);
     } else {
-        if (P.curv) update_t<MODE, STAGE, false, true>(P, B, g, s);
+        if (general(P)) update_t<MODE, STAGE, false, true>(P, B, g, s);
         else update_t<MODE, STAGE, false, false>(P, B, g, s);
     }
 }
@@ -1635,7 +1712,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     }
     int acc = 0;
     static const char *patch_names[3] = {"patch_x", "patch_y", "patch_z"};
-    const bool patch = P.mixed && !P.curv && P.scheme != SCH_CENTRAL4;
+    const bool patch = P.mixed && !general(P) && P.scheme != SCH_CENTRAL4;
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         if (tap) (*tap)(conv_names[d], s);
@@ -1656,10 +1733,10 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         if (tap) (*tap)("visc_flux", s);
         const int g = grid_for(N, 128);
         if (P.mixed) {
-            if (P.curv) k_visc_flux<true, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
+            if (general(P)) k_visc_flux<true, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
             else k_visc_flux<false, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
         } else {
-            if (P.curv) k_visc_flux<true, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
+            if (general(P)) k_visc_flux<true, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
             else k_visc_flux<false, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
         }
         launches++;

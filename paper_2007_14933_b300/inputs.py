@@ -151,3 +151,147 @@ def random_state(n, seed, gamma=1.4, Ma=1.0, amp=0.1, shocky=False):
         rho = np.where(jump, rho * 0.35, rho)
         p = np.where(jump, p * 0.3, p)
     return prim_to_cons(gamma, rho, u, v, w, p)
+
+
+# ---------------------------------------------------------------------------------------------
+# Shock / boundary-layer box (config of the learned-sensor workload): Mach 2 freestream over an
+# isothermal wall, laminar similarity inflow, oblique shock imposed on the top boundary.
+# ---------------------------------------------------------------------------------------------
+def _rk4(fun, y0, t):
+    y = np.zeros((len(t), len(y0)))
+    y[0] = y0
+    for i in range(len(t) - 1):
+        h = t[i + 1] - t[i]
+        k1 = fun(y[i])
+        k2 = fun(y[i] + 0.5 * h * k1)
+        k3 = fun(y[i] + 0.5 * h * k2)
+        k4 = fun(y[i] + h * k3)
+        y[i + 1] = y[i] + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return y
+
+
+def similarity_profile(Ma=2.0, Pr=0.72, gamma=1.4, eta_max=12.0, npts=6001):
+    """Compressible laminar boundary layer, Chapman-Rubesin constant C = 1, Howarth variable
+    eta = Y / sqrt(2 nu x / U) (textbook similarity form): f''' + f f'' = 0 and
+    T'' + Pr f T' + Pr (gamma-1) Ma^2 f''^2 = 0 with T'(0) = 0 (adiabatic wall), T(inf) = 1.
+    Returns eta, f, f', T (T nondimensionalised by the freestream)."""
+    eta = np.linspace(0.0, eta_max, npts)
+    rhs = lambda v: np.array([v[1], v[2], -v[0] * v[2]])
+    # scaling invariance of the Blasius equation: with F''(0) = 1 and F'(inf) = c,
+    # f(eta) = c^(-1/2) F(c^(-1/2) eta) has f'(inf) = 1 and f''(0) = c^(-3/2)
+    y1 = _rk4(rhs, np.array([0.0, 0.0, 1.0]), np.linspace(0.0, 2.0 * eta_max, npts))
+    s = y1[-1, 1] ** -1.5
+    y = _rk4(rhs, np.array([0.0, 0.0, s]), eta)
+    f, fp, fpp = y[:, 0], y[:, 1], y[:, 2]
+    # particular solution with T(0) = 0, T'(0) = 0; T = Tp + const satisfies T'(0) = 0
+    c = Pr * (gamma - 1.0) * Ma * Ma
+    z = np.zeros((npts, 2))
+    for i in range(npts - 1):
+        h = eta[i + 1] - eta[i]
+        fi, fm, fe = f[i], 0.5 * (f[i] + f[i + 1]), f[i + 1]
+        gi, gm, ge = fpp[i] ** 2, (0.5 * (fpp[i] + fpp[i + 1])) ** 2, fpp[i + 1] ** 2
+        rhs = lambda v, ff, gg: np.array([v[1], -Pr * ff * v[1] - c * gg])
+        k1 = rhs(z[i], fi, gi)
+        k2 = rhs(z[i] + 0.5 * h * k1, fm, gm)
+        k3 = rhs(z[i] + 0.5 * h * k2, fm, gm)
+        k4 = rhs(z[i] + h * k3, fe, ge)
+        z[i + 1] = z[i] + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    T = z[:, 0] + (1.0 - z[-1, 0])
+    return eta, f, fp, T
+
+
+def boundary_layer(y, Re, Ma=2.0, Pr=0.72, gamma=1.4):
+    """u, v, T at wall distances y of the similarity layer scaled so that its displacement
+    thickness is 1 (the length unit; Re = U delta* / nu)."""
+    eta, f, fp, T = similarity_profile(Ma, Pr, gamma)
+    d = np.diff(eta)
+    I = np.sum(0.5 * ((T - fp)[1:] + (T - fp)[:-1]) * d)            # delta* = l I
+    l = 1.0 / I
+    G = np.concatenate([[0.0], np.cumsum(0.5 * (T[1:] + T[:-1]) * d)])
+    ys = l * G
+    u = np.interp(y, ys, fp, right=1.0)
+    Ti = np.interp(y, ys, T, right=1.0)
+    vv = -(T * f - fp * G) / (l * Re)                                 # v = T rho v
+    v = np.interp(y, ys, vv, right=vv[-1])
+    return u, v, Ti, T[0]
+
+
+def oblique_shock(Ma, theta_deg, gamma=1.4):
+    """Weak oblique shock for deflection theta (theta-beta-Ma relation) and the Rankine-Hugoniot
+    post-shock state relative to a freestream rho = 1, |u| = 1, p = 1/(gamma Ma^2).  Returns
+    beta (rad), rho2, p2, speed2 (the post-shock flow is turned by theta)."""
+    th = np.radians(theta_deg)
+    g = gamma
+
+    def tan_theta(b):
+        return 2.0 / np.tan(b) * (Ma ** 2 * np.sin(b) ** 2 - 1.0) / (Ma ** 2 * (g + np.cos(2 * b)) + 2.0)
+    lo, hi = np.arcsin(1.0 / Ma) + 1e-9, np.radians(64.0)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if tan_theta(mid) < np.tan(th):
+            lo = mid
+        else:
+            hi = mid
+    b = 0.5 * (lo + hi)
+    mn1 = Ma * np.sin(b)
+    p21 = 1.0 + 2.0 * g / (g + 1.0) * (mn1 ** 2 - 1.0)
+    r21 = (g + 1.0) * mn1 ** 2 / ((g - 1.0) * mn1 ** 2 + 2.0)
+    mn2 = np.sqrt((1.0 + 0.5 * (g - 1.0) * mn1 ** 2) / (g * mn1 ** 2 - 0.5 * (g - 1.0)))
+    M2 = mn2 / np.sin(b - th)
+    T21 = p21 / r21
+    speed2 = M2 / Ma * np.sqrt(T21)
+    return b, r21, p21 / (g * Ma * Ma), speed2
+
+
+def sbli(n=(512, 256, 64), Ma=2.0, Re=1e4, Pr=0.72, theta=10.0, stretch=3.0, L=(300.0, 60.0, 20.0),
+         x_shock=20.0, scheme=TENO5, cfl=0.4, Tref=288.0):
+    """Shock / boundary-layer box: uniform x in [0, Lx], wall-normal y_j = Ly (1 - tanh(s (1 -
+    j/(Ny-1))) / tanh s), periodic z.  Isothermal wall at the similarity layer's adiabatic-wall
+    temperature, inflow u, v, T from the similarity layer (pressure extrapolated), zero-gradient
+    outlet, top Dirichlet: the inflow's outer state for x < x_shock, the Rankine-Hugoniot
+    post-shock state of a theta-degree deflection of the freestream beyond.  Sutherland viscosity, T_s/T_ref = 110.4 / Tref."""
+    g = 1.4
+    nx, ny, nz = n
+    Lx, Ly, Lz = L
+    x = np.linspace(0.0, Lx, nx)
+    j = np.arange(ny)
+    y = Ly * (1.0 - np.tanh(stretch * (1.0 - j / (ny - 1))) / np.tanh(stretch))
+    z = np.arange(nz) * Lz / nz if nz > 1 else np.zeros(1)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    coords = np.stack([X, Y, Z])
+    u1, v1, T1, Tw = boundary_layer(y, Re, Ma, Pr, g)
+    p0 = 1.0 / (g * Ma * Ma)
+    shape = (nz, ny, nx)
+    u = np.broadcast_to(u1[None, :, None], shape).copy()
+    v = np.broadcast_to(v1[None, :, None], shape).copy()
+    T = np.broadcast_to(T1[None, :, None], shape).copy()
+    p = np.full(shape, p0)
+    rho = g * Ma * Ma * p / T
+    U = prim_to_cons(g, rho, u, v, np.zeros(shape), p)
+    U[1:4, :, 0, :] = 0.0
+    U[4, :, 0, :] = U[0, :, 0, :] * Tw / (Ma * Ma * g * (g - 1.0))
+    inflow = np.zeros((5, nz, ny))
+    inflow[1] = u1[None, :]
+    inflow[2] = v1[None, :]
+    inflow[4] = T1[None, :]
+    b, r2, p2, s2 = oblique_shock(Ma, theta, g)
+    th = np.radians(theta)
+    # top: the inflow's outer state upstream of x_shock (no spurious jump), the Rankine-Hugoniot
+    # state of the turned freestream beyond
+    top = np.zeros((5, nz, nx))
+    after = (x >= x_shock)[None, :]
+    top[0] = np.where(after, r2, 1.0 / T1[-1])
+    top[1] = np.where(after, s2 * np.cos(th), u1[-1])
+    top[2] = np.where(after, -s2 * np.sin(th), v1[-1])
+    top[4] = np.where(after, p2, p0)
+    cfg = _base(n, scheme=scheme, Re=Re, Pr=Pr, Ma=Ma, T_wall=Tw, suth=110.4 / Tref,
+                bc=[[INFLOW, ZEROGRAD], [WALL, DIRICHLET], [PERIODIC, PERIODIC]],
+                coords=coords, h=(1.0, 1.0, 1.0), L=(0.0, 0.0, Lz),
+                bdata={(0, 0): inflow.reshape(5, -1), (1, 1): top.reshape(5, -1)})
+    a = np.sqrt(g * p / rho)
+    dx = Lx / (nx - 1)
+    dy = np.diff(y).min()
+    dz = Lz / nz if nz > 1 else np.inf
+    cfg["dt"] = float(cfl / ((np.abs(u) + a).max() / dx + (np.abs(v) + a).max() / dy + a.max() / dz))
+    cfg["beta_shock"] = float(np.degrees(b))
+    return cfg, U
