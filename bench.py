@@ -12,6 +12,16 @@ state and RK registers), and plain FP64, with the relative L2 difference of each
 FP64 state after the same steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
+                    [--workload tgv|sbli]
+
+``--workload ensemble`` times 64 seeded four-quadrant 2D Riemann problems (sizes drawn from
+128^2..1024^2, TENO5, mixed precision) advanced together through osbli_ensemble_* (one launch per
+phase over all members, one graph per step, autotuned chunk), beside the same members stepped on
+their own handles one after another and the batched plain FP64 form.
+
+``--workload sbli`` times the shock / boundary-layer box instead (512x256x64, Mach 2, Re 1e4,
+tanh-stretched wall-normal grid, isothermal wall, similarity inflow, 10-degree oblique shock on
+the top boundary, periodic span), with the sensor trained on TGV and reduced-box snapshots.
 
 Prints one JSON line (rank 0).  ``value`` is device-timed (CUDA events on the solver's stream,
 inputs resident in HBM); ``e2e`` repeats the metric through the C ABI with page-locked host
@@ -55,7 +65,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256, help="grid points per direction")
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "sbli", "ensemble"],
+                    help="tgv: Taylor-Green vortex n^3 (headline); sbli: shock / boundary-layer box "
+                         "512x256x64; ensemble: 64 seeded 2D Riemann problems 128^2..1024^2")
+    ap.add_argument("--seed", type=int, default=0, help="ensemble seed")
+    ap.add_argument("--n", type=int, default=256, help="TGV grid points per direction")
     ap.add_argument("--scheme", type=int, default=I.TENO5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -66,7 +80,27 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n, scheme):
+SBLI_N = (512, 256, 64)
+
+
+def workload(n, scheme, kind="tgv"):
+    if kind == "sbli":
+        cfg, U = I.sbli(n=SBLI_N, scheme=scheme)
+        name = "sbli%dx%dx%d_%s_viscous" % (SBLI_N + (SCHEME_NAME[scheme].lower().replace("-", ""),))
+        conf = {"workload": name, "grid": list(SBLI_N), "points": int(np.prod(SBLI_N)),
+                "scheme": "%s characteristic (Roe average, LLF) in x, y, z" % SCHEME_NAME[scheme],
+                "viscous": "4th-order central, Re=1e4 (displacement thickness), Pr=0.72, Sutherland "
+                           "110.4 K / 288 K",
+                "Ma": 2.0, "gamma": 1.4, "dt": cfg["dt"],
+                "domain": "300 x 60 x 20, tanh wall-normal stretching 3.0 (rectilinear)",
+                "boundaries": "similarity inflow / zero-gradient outlet, isothermal wall at the "
+                              "adiabatic-wall temperature / Dirichlet top with a 10 deg oblique "
+                              "shock from x=20, periodic span",
+                "initial": "similarity profile everywhere (analytic)",
+                "time_integration": "low-storage RK3, 3 stages per step",
+                "l2": "inputs larger than L2: state %.0f MB" % (5 * np.prod(SBLI_N) * 8 / 1e6),
+                "parallelism": "one replica per GPU"}
+        return cfg, U, conf
     Ma = 1.25 if scheme != I.CENTRAL4 else 0.1
     cfg, U = I.tgv(n, Ma=Ma, Re=1600.0, scheme=scheme)
     name = "tgv%d_%s_viscous" % (n, SCHEME_NAME[scheme].lower().replace("-", ""))
@@ -134,6 +168,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_baseline_sbli(scheme, target_s=12.0):
+    """The oracle on every host core, one RK step of the shock / boundary-layer physics on a box
+    with the same domain and set-up at reduced resolution (~10-30 s of CPU work)."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    f = 8
+    while True:
+        n = tuple(max(8, v // f) for v in SBLI_N)
+        cfg, U = I.sbli(n=n, scheme=scheme)
+        o = O.Oracle(cfg)
+        o.set_state(U)
+        t = time.perf_counter()
+        o.step(1)
+        el = time.perf_counter() - t
+        if el > target_s / 8 or f <= 2:
+            break
+        f //= 2
+    npts = int(np.prod(n))
+    return {"value": npts * 3 / el / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": "one RK3 step (3 stages) of the same %s shock / boundary-layer set-up on a "
+                      "%dx%dx%d grid (%.1f s)" % ((SCHEME_NAME[scheme],) + n + (el,))}
+
+
 def cpu_baseline(scheme, target_s=12.0):
     """The oracle as it stands, on every host core, one RK step of the same TGV physics on a
     smaller grid sized for ~10-30 s of CPU work."""
@@ -166,27 +224,181 @@ def run_reference(args, rank):
     import oracle as O
     cores = len(os.sched_getaffinity(0))
     O.set_threads(cores)
-    n = 32
-    Ma = 1.25 if args.scheme != I.CENTRAL4 else 0.1
-    cfg, U = I.tgv(n, Ma=Ma, scheme=args.scheme)
+    if args.workload == "ensemble":
+        mem = I.riemann_ensemble(args.seed, scheme=args.scheme)
+        cfg, U = min(mem, key=lambda m: int(np.prod(m[0]["n"])))
+        nn = tuple(int(x) for x in cfg["n"])
+        sample = "each step: one RK3 step of the oracle on the smallest ensemble member (%dx%d)" % nn[:2]
+    elif args.workload == "sbli":
+        nn = tuple(v // 8 for v in SBLI_N)
+        cfg, U = I.sbli(n=nn, scheme=args.scheme)
+        sample = ("each step: one RK3 step of the oracle on the same shock / boundary-layer set-up "
+                  "at %dx%dx%d" % nn)
+    else:
+        n = 32
+        nn = (n, n, n)
+        Ma = 1.25 if args.scheme != I.CENTRAL4 else 0.1
+        cfg, U = I.tgv(n, Ma=Ma, scheme=args.scheme)
+        sample = "each step: one RK3 step of the oracle on a %d^3 sample of the workload's physics" % n
     o = O.Oracle(cfg)
     o.set_state(U)
     o.step(max(args.warmup, 0))
     t = time.perf_counter()
     o.step(args.steps)
     el = time.perf_counter() - t
-    val = n ** 3 * 3 * args.steps / el / 1e6
-    _, _, conf = workload(args.n, args.scheme)
-    sample = "each step: one RK3 step of the oracle on a %d^3 sample of the workload's physics" % n
+    val = int(np.prod(nn)) * 3 * args.steps / el / 1e6
+    if args.workload == "ensemble":
+        conf = {"workload": "riemann2d_ensemble64_seed%d_%s" % (args.seed, SCHEME_NAME[args.scheme].lower().replace("-", "")),
+                "members": len(mem), "points": int(sum(np.prod(c["n"]) for c, _ in mem))}
+    else:
+        _, _, conf = workload(args.n, args.scheme, args.workload)
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
                       "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic (analytic TGV initial field)", "config": conf,
+                      "data": "synthetic (analytic initial field)", "config": conf,
                       "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
+    return 0
+
+
+def run_ensemble(args, world, rank, local):
+    """64 seeded 2D Riemann problems: batched mixed (headline), separate handles, batched FP64."""
+    import torch
+    from paper_2007_14933_b300 import build, osbli
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    osbli.load()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+    mem = I.riemann_ensemble(args.seed, scheme=args.scheme)
+    cfgs = [c for c, _ in mem]
+    npts = int(sum(np.prod(c["n"]) for c in cfgs))
+    stream = torch.cuda.current_stream()
+    sizes = [int(c["n"][0]) for c in cfgs]
+    conf = {"workload": "riemann2d_ensemble64_seed%d_%s" % (args.seed, SCHEME_NAME[args.scheme].lower().replace("-", "")),
+            "members": len(cfgs), "points": npts, "sizes": sizes,
+            "scheme": "%s characteristic (Roe average, LLF) in x, y, inviscid" % SCHEME_NAME[args.scheme],
+            "states": "four quadrants, rho, p ~ U[0.1, 1.5], u, v ~ U[-1, 1] (numpy PCG64, seed %d)" % args.seed,
+            "dt": "per member, CFL 0.4 on the initial state", "boundaries": "zero-gradient",
+            "time_integration": "low-storage RK3, 3 stages per step",
+            "l2": "inputs larger than L2: states %.0f MB" % (5 * npts * 8 / 1e6),
+            "parallelism": "one replica per GPU"}
+
+    def make(prec):
+        e = osbli.Ensemble(cfgs, precision=prec, cuda_stream=stream.cuda_stream)
+        for p, (_, U) in enumerate(mem):
+            e.set_state(p, U)
+        return e
+
+    def timed(fn):
+        fn(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    gpu_index = torch.cuda.current_device()
+    res = {}
+    with ClockSampler(gpu_index) as clk:
+        ens = make(osbli.OSBLI_MIXED)
+        chunk, _ = ens.autotune(reps=2)
+        res["ensemble"] = timed(ens.step)
+        launches = ens.launches_per_step() * args.steps
+        sep = [osbli.Solver(c, precision=osbli.OSBLI_MIXED, cuda_stream=stream.cuda_stream) for c in cfgs]
+        for s_, (_, U) in zip(sep, mem):
+            s_.set_state(U)
+
+        def sep_step(k):
+            for _ in range(k):
+                for s_ in sep:
+                    s_.step(1)
+        res["separate"] = timed(sep_step)
+        sep_launches = sum(s_.launches_per_step() for s_ in sep)
+        for s_ in sep:
+            s_.close()
+        e64 = make(osbli.OSBLI_FP64)
+        res["fp64"] = timed(e64.step)
+    clocks = clk.summary()
+    forms = {f: {"value": npts * 3 * args.steps * world / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps}
+             for f, ms in res.items()}
+    l2 = 0.0
+    for p in range(len(cfgs)):
+        a, b = ens.get_state(p), e64.get_state(p)
+        nb = [float(np.linalg.norm(b[v])) for v in range(5)]
+        nb[1] = nb[2] = nb[3] = max(nb[1:4])
+        l2 = max(l2, max(float(np.linalg.norm(a[v] - b[v])) / nb[v] for v in range(5) if nb[v] > 0))
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.from_numpy(np.ascontiguousarray(U)).pin_memory() for _, U in mem]
+        outs = [torch.empty_like(h) .pin_memory() for h in hosts]
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for p, h in enumerate(hosts):
+                osbli.osbli_ensemble_set_state(ens.e, p, h)
+            ens.step(1)
+            for p, o in enumerate(outs):
+                osbli.osbli_ensemble_get_state(ens.e, p, o)
+        el = time.perf_counter() - t0
+        byt = int(sum(h.numel() for h in hosts) * 8)
+        e2e = {"value": npts * 3 * args.steps * world / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": byt,
+               "d2h_bytes_per_step": byt,
+               "api": "osbli_ensemble_set_state(host) x64 + osbli_ensemble_step(1) + osbli_ensemble_get_state(host) x64"}
+    ens.close()
+    e64.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    out = {"metric": METRIC, "value": forms["ensemble"]["value"], "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms["ensemble"]["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic (seeded four-quadrant Riemann states)", "config": conf,
+           "roofline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+           "forms": forms, "autotuned_chunk": chunk,
+           "gpu_launches_separate_per_step": sep_launches,
+           "speedup_ensemble_vs_separate": forms["ensemble"]["value"] / forms["separate"]["value"],
+           "speedup_ensemble_vs_fp64": forms["ensemble"]["value"] / forms["fp64"]["value"],
+           "l2_ensemble_vs_fp64": l2,
+           "variant": "mixed precision, batched members (osbli_ensemble_step)"}
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        cores = len(os.sched_getaffinity(0))
+        O.set_threads(cores)
+        done, el, used = 0, 0.0, []
+        for cfg, U in sorted(mem, key=lambda m: int(np.prod(m[0]["n"]))):
+            o = O.Oracle(cfg)
+            o.set_state(U)
+            t = time.perf_counter()
+            o.step(1)
+            el += time.perf_counter() - t
+            done += int(np.prod(cfg["n"]))
+            used.append(int(cfg["n"][0]))
+            if el > 10.0:
+                break
+        out["cpu_baseline"] = {"value": done * 3 / el / 1e6, "unit": UNIT, "cores": O.get_threads(),
+                               "kind": "oracle", "sample": "one RK3 step of the %d smallest members (N = %s), %.1f s"
+                               % (len(used), used, el)}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -222,6 +434,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "ensemble":
+        return run_ensemble(args, world, rank, local)
 
     import torch
     from paper_2007_14933_b300 import build, osbli
@@ -237,8 +451,8 @@ def main():
         if dist:
             dist.barrier()
 
-    cfg, U, conf = workload(args.n, args.scheme)
-    npts = args.n ** 3
+    cfg, U, conf = workload(args.n, args.scheme, args.workload)
+    npts = int(conf["points"])
     stream = torch.cuda.current_stream()
     forms = ["learned", "mixed", "fp64"]
     if args.plain or args.scheme == I.CENTRAL4:
@@ -255,13 +469,18 @@ def main():
         # train the sensor on the GPU from TENO labels of coarse TGV snapshots (same physics)
         from paper_2007_14933_b300 import sensor as SN
         t0 = time.perf_counter()
-        feats, labels, _ = SN.tgv_training_set(N=64, Ma=conf["Ma"], nsnap=6, steps_between=12)
+        feats, labels, _ = SN.tgv_training_set(N=64, Ma=1.25, nsnap=6, steps_between=12)
+        train_set = "TGV 64^3 Ma 1.25, 6 snapshots every 12 steps"
+        if args.workload == "sbli":
+            f2, l2_, _ = SN.sbli_training_set()
+            feats, labels = torch.cat([feats, f2]), torch.cat([labels, l2_])
+            train_set += " + " + SN.SBLI_TRAIN_DESC
+            del f2, l2_
         w, hist = SN.train(feats, labels, steps=args.sensor_steps, batch=4096)
         thr = SN.calibrate_threshold(w, feats, labels, recall=0.9)
         sensor = (w, thr)
-        sensor_info = {"train_set": "TGV 64^3 Ma %.2f, 6 snapshots every 12 steps, %d cells, "
-                                    "label fraction %.3f" % (conf["Ma"], int(labels.numel()),
-                                                             float(labels.float().mean().item())),
+        sensor_info = {"train_set": "%s, %d cells, label fraction %.3f"
+                                    % (train_set, int(labels.numel()), float(labels.float().mean().item())),
                        "train_steps": args.sensor_steps, "batch": 4096, "loss_first": float(hist[:20].mean()),
                        "loss_last": float(hist[-20:].mean()), "threshold": thr,
                        "recall_target": 0.9, "train_s": time.perf_counter() - t0}
@@ -372,7 +591,8 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if head in ("mixed", "learned") else "f64",
-           "data": "synthetic (analytic TGV initial field)", "config": conf,
+           "data": "synthetic (analytic %s initial field)" % ("similarity-profile" if args.workload == "sbli"
+                                                               else "TGV"), "config": conf,
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
            "kernels_ms": {nm: t_ for nm, t_ in prof},
            "variant": {"learned": "mixed precision + learned sensor (headline form)",
@@ -381,7 +601,8 @@ def main():
     if launches_e2e is not None:
         out["gpu_launches_e2e"] = launches_e2e
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.scheme)
+        out["cpu_baseline"] = (cpu_baseline_sbli(args.scheme) if args.workload == "sbli"
+                               else cpu_baseline(args.scheme))
     print(json.dumps(out), flush=True)
     return 0
 

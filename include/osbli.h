@@ -215,6 +215,53 @@ int osbli_fp32_peak(double *tflops);
 /* Message of the last failure on h (or of the last failed osbli_create when h is NULL). */
 const char *osbli_last_error(const osbli_t *h);
 
+/* ---------------------------------------------------------------------------------------------
+ * Ensembles: many independent problems advanced together (the paper's 2D Riemann tubes of
+ * Sec. 5.2 run as a batch).  Every phase of an RK stage is one launch over the blocks of all
+ * members, and a step is one CUDA graph, so the launch count does not grow with the member count
+ * and members of very different sizes share the GPU.  Each member computes exactly what its own
+ * handle would (same kernels and arithmetic).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct osbli_ens osbli_ens_t;
+
+/* params: [nprob] member descriptions (uniform grids, own n, h, dt; inviscid, Re <= 0; WENO5-JS
+ * or TENO5, the same scheme and precision for every member; faces PERIODIC or ZEROGRAD; no
+ * sensor).  cuda_stream: cudaStream_t for all work, or NULL for an ensemble-owned stream.
+ * Errors: EINVAL (with the member index in the message), ENOMEM, ECUDA. */
+int osbli_ensemble_create(int nprob, const osbli_params *params, void *cuda_stream, osbli_ens_t **out);
+
+/* Release the members and tables.  NULL is ignored. */
+void osbli_ensemble_destroy(osbli_ens_t *e);
+
+/* State of member p in / out, [5][nz][ny][nx] FP64, host or device (as osbli_set/get_state). */
+int osbli_ensemble_set_state(osbli_ens_t *e, int p, const double *U);
+int osbli_ensemble_get_state(osbli_ens_t *e, int p, double *U);
+
+/* The handle of member p (owned by the ensemble; for diagnostics / residuals), NULL if out of
+ * range. */
+osbli_t *osbli_ensemble_member(osbli_ens_t *e, int p);
+
+/* nsteps RK3 steps of every member (one graph replay per step), then a synchronising check of
+ * the members' error words.  Errors: ESTATE (a member without state), ENONFINITE (the message
+ * names the lowest member that became non-finite), ECUDA. */
+int osbli_ensemble_step(osbli_ens_t *e, int nsteps);
+
+/* Marching chunk of the line kernels for every member (0: each member's own default, sized to fill
+ * the GPU alone).  Changes launch shapes only: results are bitwise identical. */
+int osbli_ensemble_set_chunk(osbli_ens_t *e, int chunk);
+
+/* Time reps steps for each candidate chunk (0, 8, 16, 32, 64) on the current state, keep the
+ * fastest, restore every member's state.  chunk_out / ms_out (may be NULL): the choice and its
+ * milliseconds per step.  Allocates a copy of the states for the duration of the call. */
+int osbli_ensemble_autotune(osbli_ens_t *e, int reps, int *chunk_out, double *ms_out);
+
+/* Kernel launches of one captured step (0 before the first step), total interior points. */
+int osbli_ensemble_launches_per_step(const osbli_ens_t *e);
+long long osbli_ensemble_points(const osbli_ens_t *e);
+
+/* Message of the last failure on e (or of the last failed osbli_ensemble_create when NULL). */
+const char *osbli_ensemble_last_error(const osbli_ens_t *e);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ static void free_all(osbli *h)
     for (int f = 0; f < 6; f++)
         if (h->B.bd[f]) cudaFree(h->B.bd[f]);
     if (h->B.err) cudaFree(h->B.err);
+    if (h->B.slist) cudaFree(h->B.slist);
     if (h->B.sw) cudaFree(h->B.sw);
     if (h->B.sflag) cudaFree(h->B.sflag);
     if (h->B.gate) cudaFree(h->B.gate);
@@ -220,7 +221,11 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
         CKC(cudaMalloc(&h->B.Rf, NV * fsb));
         CKC(cudaMalloc(&h->B.flag, (size_t)P.vs));
         CKC(cudaMemsetAsync(h->B.flag, 0, (size_t)P.vs, h->stream));
-        CKC(cudaMalloc(&h->B.Dst, NV * fsb));
+        CKC(cudaMalloc(&h->B.Dst, 3 * NV * fsb));
+        // flagged-interface lists: 1/16 of the nodes per direction (a longer list overflows into a
+        // scan of the flag bits)
+        h->B.scap = (int)(P.vs / 16 + 1024);
+        CKC(cudaMalloc(&h->B.slist, (size_t)3 * h->B.scap * sizeof(long long)));
         const long long lefts = (long long)n[1] * n[2] * ((n[0] + 255) / 256);
         CKC(cudaMalloc(&h->B.Dl, (size_t)lefts * NV * sizeof(float)));
         CKC(cudaMemsetAsync(h->B.Rf, 0, NV * fsb, h->stream));
@@ -474,10 +479,11 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     // not captured yet: count the same sequence launch_stage enqueues
     const Dev &P = h->P;
     int per_stage = 1 /*prim*/ + 1 /*update*/;
+    if (P.mixed && !general(P)) per_stage += 1;   // FP64 fix of strong-jump interfaces
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction
-        if (P.mixed && !general(P)) per_stage += (d == 0) ? 2 : 1;   // patch (+ x segment lefts)
+        if (P.mixed && !general(P) && d == 0) per_stage += 1;   // x segment lefts
         for (int s = 0; s < 2; s++) {
             const int bc = P.bc[d][s];
             if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;
@@ -490,6 +496,14 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
 extern "C" const char *osbli_last_error(const osbli_t *h)
 {
     return h ? h->err : g_create_err;
+}
+
+// Device description and buffers of a handle (the ensemble builds its block table from them).
+void osbli_internal_view(osbli_t *h, osb::Dev *P, osb::Bufs *B, bool *state_set)
+{
+    *P = h->P;
+    *B = h->B;
+    *state_set = h->state_set;
 }
 
 // Message slot shared with calls that have no handle (read back by osbli_last_error(NULL)).

@@ -70,6 +70,27 @@ __device__ __forceinline__ double line_eps(const Dev &P, int a, int b)
     return P.rect ? __ldg(P.lesc[DIR] + (long long)b * P.n[DA] + a) : 1.0;
 }
 
+// Strong-jump bookkeeping of the mixed delta path (one stage): per interface m a flag bit per
+// direction, the FP32 flux difference D of flagged interfaces (then their FP64 corrections), and
+// per direction a count and a list of flagged interface indices.
+struct Strong {
+    unsigned char *flag;   // [vs], bit d: interface (m, m + e_d) flagged
+    float *Dst;            // [3][5][vs]
+    int *count;            // [3]
+    long long *list;       // [3][cap]
+    int cap;
+};
+
+// Block coordinates of one problem's launch: the single-problem kernels take them from blockIdx
+// and gridDim, the ensemble kernels from their block table.
+struct Blk {
+    int x, y, z, nx, ny, nz;
+};
+__device__ __forceinline__ Blk self_blk()
+{
+    return {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+}
+
 __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, int j, int k)
 {
     return ((long long)(k + P.g[2]) * P.np[1] + (j + P.g[1])) * P.np[0] + (i + P.g[0]);

@@ -96,7 +96,7 @@ __device__ __forceinline__ long long face_plane_index(const Dev &P, int d, int c
     return (long long)cb * na + ca;
 }
 
-__global__ void k_ghost(Dev P, double *__restrict__ U, int d, const double *__restrict__ bd0,
+__device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *__restrict__ U, int d, const double *__restrict__ bd0,
                         const double *__restrict__ bd1)
 {
     const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
@@ -104,8 +104,8 @@ __global__ void k_ghost(Dev P, double *__restrict__ U, int d, const double *__re
     const long long tot = 2LL * GH * npa * npb;
     const int n = P.n[d];
     const long long plane = (long long)P.n[da] * P.n[db];
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)bk.nx * blockDim.x) {
         const int ia = (int)(t % npa);
         long long q = t / npa;
         const int ib = (int)(q % npb);
@@ -156,6 +156,12 @@ __global__ void k_ghost(Dev P, double *__restrict__ U, int d, const double *__re
     }
 }
 
+__global__ void k_ghost(Dev P, double *__restrict__ U, int d, const double *__restrict__ bd0,
+                        const double *__restrict__ bd1)
+{
+    ghost_body(P, self_blk(), U, d, bd0, bd1);
+}
+
 // After-stage boundary nodes: wall (rho u = 0, rho E = rho_w T_w / (M^2 gamma (gamma-1)),
 // Eq. 41), Dirichlet and inflow nodes.
 __global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const double *__restrict__ bd)
@@ -193,10 +199,10 @@ __global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const doub
 // ------------------------------------------------------------------------------------------
 // Primitives per node (Eqs. 5-7): u, v, w, p, a, sqrt(rho), H, T on every padded node.
 // ------------------------------------------------------------------------------------------
-__global__ void k_prim(Dev P, const double *__restrict__ U, double *__restrict__ W)
+__device__ __forceinline__ void prim_body(const Dev &P, const Blk &bk, const double *__restrict__ U, double *__restrict__ W)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
+         t += (long long)bk.nx * blockDim.x) {
         const double rho = U[0 * P.vs + t];
         const double ir = 1.0 / rho;
         const double u = U[1 * P.vs + t] * ir, v = U[2 * P.vs + t] * ir, w = U[3 * P.vs + t] * ir;
@@ -211,6 +217,11 @@ __global__ void k_prim(Dev P, const double *__restrict__ U, double *__restrict__
         W[W_H * P.vs + t] = (E + p) * ir;
         W[W_T * P.vs + t] = P.gM2 * p * ir;
     }
+}
+
+__global__ void k_prim(Dev P, const double *__restrict__ U, double *__restrict__ W)
+{
+    prim_body(P, self_blk(), U, W);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -447,16 +458,16 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
 // chunk of nodes, carrying the left interface flux in registers; R[node] = -fac (F_{m+1/2} -
 // F_{m-1/2}) (Eq. 10, strong conservation form), first direction writes, later ones add.
 template <int DIR, int SCHEME, bool CURV>
-__global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restrict__ U,
+__device__ __forceinline__ void conv_char_body(const Dev &P, const Blk &bk, const double *__restrict__ U,
                                                    const double *__restrict__ W,
                                                    const double *__restrict__ M,
                                                    double *__restrict__ R, int accumulate, int chunk)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    const int a = bk.x * blockDim.x + threadIdx.x;
+    const int b = bk.y * blockDim.y + threadIdx.y;
     if (a >= P.n[DA] || b >= P.n[DB]) return;
-    const int s0 = blockIdx.z * chunk;
+    const int s0 = bk.z * chunk;
     const int s1 = min(s0 + chunk, P.n[DIR]);
     int ii[3];
     ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
@@ -480,6 +491,15 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
     }
 }
 
+template <int DIR, int SCHEME, bool CURV>
+__global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restrict__ U,
+                                                   const double *__restrict__ W,
+                                                   const double *__restrict__ M,
+                                                   double *__restrict__ R, int accumulate, int chunk)
+{
+    conv_char_body<DIR, SCHEME, CURV>(P, self_blk(), U, W, M, R, accumulate, chunk);
+}
+
 // ------------------------------------------------------------------------------------------
 // Mixed path (precision OSBLI_MIXED): FP32 node copies Uf, Wf; FP32 interface arithmetic and
 // FP32 residual accumulation Rf.  An interface whose stencil contains a strong jump between
@@ -490,13 +510,13 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
 // 5-9 the FP32 rounding of the remainder (U = hi + lo to ~48 bits), so that differences
 // between nearby nodes are formed to FP32 accuracy relative to the difference itself.  Wf holds
 // FP32 primitives (u, v, w, p, a, sqrt(rho), H, T).
-__global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restrict__ Uf,
+__device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, const double *__restrict__ U, float *__restrict__ Uf,
                              float *__restrict__ Wf, int *__restrict__ nstrong)
 {
     // per-direction counts of strong-jump interfaces of this stage start at zero
-    if (blockIdx.x == 0 && threadIdx.x < 3) nstrong[threadIdx.x] = 0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
-         t += (long long)gridDim.x * blockDim.x) {
+    if (bk.x == 0 && threadIdx.x < 3) nstrong[threadIdx.x] = 0;
+    for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
+         t += (long long)bk.nx * blockDim.x) {
         float h[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -518,6 +538,12 @@ __global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restr
         Wf[W_H * P.vs + t] = (E + p) * ir;
         Wf[W_T * P.vs + t] = (float)P.gM2 * p * ir;
     }
+}
+
+__global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restrict__ Uf,
+                             float *__restrict__ Wf, int *__restrict__ nstrong)
+{
+    prim_mixed_body(P, self_blk(), U, Uf, Wf, nstrong);
 }
 
 __device__ __forceinline__ bool strong_jump(const Dev &P, const float *__restrict__ Uf,
@@ -793,15 +819,17 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
 // RT is the storage / arithmetic type of the residual and viscous fluxes (double plain, float
 // mixed); the register update itself is FP64 on both paths.
 template <int MODE, int STAGE, bool VISC, bool CURV, typename RT>
-__global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, double *__restrict__ dU,
+__device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double *__restrict__ U, double *__restrict__ dU,
                                                 const RT *Rin, const RT *__restrict__ V,
                                                 const double *__restrict__ M, double *Rout,
-                                                int *__restrict__ err)
+                                                int *__restrict__ err, Strong sj)
 {
+    // FP64 corrections of strong-jump interfaces (mixed delta path; sj.flag null otherwise)
+    const bool fix = sj.flag && (sj.count[0] | sj.count[1] | sj.count[2]);
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const long long vs = P.vs;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)bk.nx * blockDim.x) {
         const int i = (int)(t % P.n[0]);
         const long long q = t / P.n[0];
         const int j = (int)(q % P.n[1]);
@@ -811,6 +839,24 @@ __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, d
         RT r[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) r[v] = Rin[v * vs + id];
+        if (fix) {
+            const unsigned char f0 = sj.flag[id];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (!P.active[d]) continue;
+                const unsigned char bit = (unsigned char)(1u << d);
+                const long long st = P.st[d];
+                const bool fr = (f0 & bit) != 0, fl = (sj.flag[id - st] & bit) != 0;
+                if (!fr && !fl) continue;
+                const float *Ds = sj.Dst + (long long)d * NV * vs;
+                const RT fac = RT(line_fac(P, d, ijk[d]));
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const RT c = (fr ? RT(Ds[v * vs + id]) : RT(0)) - (fl ? RT(Ds[v * vs + id - st]) : RT(0));
+                    r[v] += -fac * c;
+                }
+            }
+        }
         if (VISC) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
@@ -848,6 +894,15 @@ __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, d
         }
         if (bad) atomicOr(err, 1);
     }
+}
+
+template <int MODE, int STAGE, bool VISC, bool CURV, typename RT>
+__global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, double *__restrict__ dU,
+                                                const RT *Rin, const RT *__restrict__ V,
+                                                const double *__restrict__ M, double *Rout,
+                                                int *__restrict__ err, Strong sj)
+{
+    update_body<MODE, STAGE, VISC, CURV, RT>(P, self_blk(), U, dU, Rin, V, M, Rout, err, sj);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1243,44 +1298,50 @@ __device__ __forceinline__ void central_delta(const Dev &P, const float *__restr
     for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - dF1[v] - fp2[v]) * (1.f / 12.f);
 }
 
-// One interface of the delta-form mixed path.  Interfaces whose stencil holds a strong jump are
-// flagged (flag[m] = 1, m = left node) and their FP32 D kept in Dst; a later per-node pass
-// (k_patch_strong) recomputes them in FP64 and corrects the residual, so the FP32 pass carries
-// no FP64 code (and keeps its register budget).
+// One interface of the delta-form mixed path.  An interface whose stencil holds a strong jump is
+// flagged (bit DIR of flag[m], m = left node), its FP32 D kept in Dst (plane set DIR) and its
+// index appended to the direction's list; after the convective passes k_patch_fix recomputes the
+// listed interfaces in FP64 and leaves the corrections D64 - D32 in Dst, and the update kernel
+// adds them to the two adjacent nodes' residuals (fixed order: deterministic).  The FP32 pass
+// carries no FP64 code and keeps its register budget.  Interfaces computed twice (the carried
+// left interface of a chunk or x segment) are recorded only by their owner (own = true).
 template <int DIR, int SCHEME>
 __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restrict__ Uf,
                                               const float *__restrict__ Wf, long long m, long long st,
-                                              float es, float D[NV], float dF1[NV],
-                                              unsigned char *__restrict__ flag,
-                                              float *__restrict__ Dst, int *__restrict__ nstrong,
-                                              const unsigned char *__restrict__ gate)
+                                              float es, float D[NV], float dF1[NV], const Strong &sj,
+                                              bool own, const unsigned char *__restrict__ gate)
 {
     const bool strong = strong_jump(P, Uf, Wf, m, st);
     if (!gate || strong || gate[m] || gate[m + st]) delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, es, D, dF1);
     else central_delta<DIR>(P, Uf, Wf, m, st, D, dF1);
-    flag[m] = strong ? 1 : 0;
+    if (!own) return;
+    constexpr unsigned char bit = 1u << DIR;
+    const unsigned char f = sj.flag[m];
     if (strong) {
-        atomicAdd(nstrong + DIR, 1);
+        sj.flag[m] = f | bit;
+        const int k = atomicAdd(sj.count + DIR, 1);
+        if (k < sj.cap) sj.list[(long long)DIR * sj.cap + k] = m;
+        float *Ds = sj.Dst + (long long)DIR * NV * P.vs;
 #pragma unroll
-        for (int v = 0; v < NV; v++) Dst[v * P.vs + m] = D[v];
+        for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D[v];
+    } else if (f & bit) {
+        sj.flag[m] = f & (unsigned char)~bit;
     }
 }
 
 // y and z: thread per line of the cross directions (lanes along x, coalesced), marching along DIR.
 template <int DIR, int SCHEME>
-__global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *__restrict__ Uf,
+__device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf,
-                                                         float *__restrict__ Rf,
-                                                         unsigned char *__restrict__ flag,
-                                                         float *__restrict__ Dst, int *__restrict__ nstrong,
+                                                         float *__restrict__ Rf, Strong sj,
                                                          const unsigned char *__restrict__ gate,
                                                          int accumulate, int chunk)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y * blockDim.y + threadIdx.y;
+    const int a = bk.x * blockDim.x + threadIdx.x;
+    const int b = bk.y * blockDim.y + threadIdx.y;
     if (a >= P.n[DA] || b >= P.n[DB]) return;
-    const int s0 = blockIdx.z * chunk;
+    const int s0 = bk.z * chunk;
     const int s1 = min(s0 + chunk, P.n[DIR]);
     int ii[3];
     ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
@@ -1288,11 +1349,11 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
     const long long st = P.st[DIR];
     const float es = (float)line_eps<DIR>(P, a, b);
     float Dm[NV], dF1[NV];
-    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, es, Dm, dF1, flag, Dst, nstrong, gate);
+    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, es, Dm, dF1, sj, s0 == 0, gate);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         float Dp[NV];
-        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, flag, Dst, nstrong, gate);
+        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, sj, true, gate);
         const float fac = (float)line_fac<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -1304,22 +1365,30 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
     }
 }
 
+template <int DIR, int SCHEME>
+__global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *__restrict__ Uf,
+                                                         const float *__restrict__ Wf,
+                                                         float *__restrict__ Rf, Strong sj,
+                                                         const unsigned char *__restrict__ gate,
+                                                         int accumulate, int chunk)
+{
+    conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, accumulate, chunk);
+}
+
 // x: thread per interface along a row segment of up to XSEG nodes (lanes along x, coalesced);
 // the flux difference takes the left neighbour's D from shared memory.  The segment's leftmost
 // interface comes from k_conv_left_x, so every thread forms exactly one interface.
 constexpr int XSEG = 256;
 
 template <int SCHEME>
-__global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restrict__ Uf,
-                                                     const float *__restrict__ Wf,
-                                                     unsigned char *__restrict__ flag,
-                                                     float *__restrict__ Dst, int *__restrict__ nstrong,
+__device__ __forceinline__ void conv_left_x_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
+                                                     const float *__restrict__ Wf, Strong sj,
                                                      const unsigned char *__restrict__ gate,
                                                      float *__restrict__ Dl)
 {
     const int nseg = (P.n[0] + XSEG - 1) / XSEG;
     const long long total = (long long)P.n[1] * P.n[2] * nseg;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = bk.x * (long long)blockDim.x + threadIdx.x;
     if (t >= total) return;
     const int seg = (int)(t % nseg);
     const long long row = t / nseg;
@@ -1327,26 +1396,32 @@ __global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restr
     const long long base = node_index(P, 0, j, k);
     float D[NV], unused[NV];
     const float es = (float)line_eps<0>(P, j, k);
-    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, es, D, unused, flag, Dst, nstrong, gate);
+    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, es, D, unused, sj, seg == 0, gate);
 #pragma unroll
     for (int v = 0; v < NV; v++) Dl[t * NV + v] = D[v];
 }
 
 template <int SCHEME>
-__global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *__restrict__ Uf,
+__global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restrict__ Uf,
+                                                     const float *__restrict__ Wf, Strong sj,
+                                                     const unsigned char *__restrict__ gate,
+                                                     float *__restrict__ Dl)
+{
+    conv_left_x_body<SCHEME>(P, self_blk(), Uf, Wf, sj, gate, Dl);
+}
+
+template <int SCHEME>
+__device__ __forceinline__ void conv_char_delta_x_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
                                                             const float *__restrict__ Wf,
-                                                            float *__restrict__ Rf,
-                                                            unsigned char *__restrict__ flag,
-                                                            float *__restrict__ Dst,
-                                                            int *__restrict__ nstrong,
+                                                            float *__restrict__ Rf, Strong sj,
                                                             const unsigned char *__restrict__ gate,
                                                             const float *__restrict__ Dl, int accumulate)
 {
     __shared__ float sD[NV][XSEG + 1];
-    const int row = blockIdx.x;
-    const int nseg = gridDim.y;
+    const int row = bk.x;
+    const int nseg = bk.ny;
     const int j = row % P.n[1], k = row / P.n[1];
-    const int x0 = blockIdx.y * XSEG;
+    const int x0 = bk.y * XSEG;
     const int t = threadIdx.x;
     const int i = x0 + t;
     const long long base = node_index(P, 0, j, k);
@@ -1354,11 +1429,11 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
     if (i < P.n[0]) {
         float D[NV];
         const float es = (float)line_eps<0>(P, j, k);
-        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, es, D, dF1, flag, Dst, nstrong, gate);
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, es, D, dF1, sj, true, gate);
 #pragma unroll
         for (int v = 0; v < NV; v++) sD[v][t + 1] = D[v];
     }
-    if (t < NV) sD[t][0] = Dl[((long long)row * nseg + blockIdx.y) * NV + t];
+    if (t < NV) sD[t][0] = Dl[((long long)row * nseg + bk.y) * NV + t];
     __syncthreads();
     if (i >= P.n[0]) return;
     const float fac = (float)line_fac<0>(P, i);
@@ -1370,47 +1445,78 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
     }
 }
 
-// FP64 correction of flagged interfaces, one thread per interior node (deterministic):
-// node m's flux difference used D_{m+1/2} - D_{m-1/2}; replace the FP32 D of every flagged one
-// of its two interfaces by the FP64 value.
-template <int DIR, int SCHEME>
-__global__ void __launch_bounds__(128) k_patch_strong(Dev P, const double *__restrict__ U,
-                                                      float *__restrict__ Rf,
-                                                      const unsigned char *__restrict__ flag,
-                                                      const float *__restrict__ Dst,
-                                                      const int *__restrict__ nstrong)
+template <int SCHEME>
+__global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *__restrict__ Uf,
+                                                            const float *__restrict__ Wf,
+                                                            float *__restrict__ Rf, Strong sj,
+                                                            const unsigned char *__restrict__ gate,
+                                                            const float *__restrict__ Dl, int accumulate)
 {
-    if (nstrong[DIR] == 0) return;     // nothing flagged in this direction and stage
+    conv_char_delta_x_body<SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, Dl, accumulate);
+}
+
+// FP64 recomputation of one flagged interface m of direction DIR: Dst (plane set DIR) receives
+// the correction D64 - D32 in place of the FP32 value.
+template <int DIR, int SCHEME>
+__device__ __forceinline__ void fix_interface(const Dev &P, const double *__restrict__ U, float *__restrict__ Dst,
+                                              long long m)
+{
+    constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const long long pa = m % P.np[0], q = m / P.np[0];
+    const int c3[3] = {(int)pa - P.g[0], (int)(q % P.np[1]) - P.g[1], (int)(q / P.np[1]) - P.g[2]};
+    const double es = line_eps<DIR>(P, c3[DA], c3[DB]);
+    float D64[NV], unused[NV];
+    fallback_delta<DIR, SCHEME>(P, U, m, P.st[DIR], es, D64, unused);
+    float *Ds = Dst + (long long)DIR * NV * P.vs;
+#pragma unroll
+    for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D64[v] - Ds[v * P.vs + m];
+}
+
+// All directions' flagged interfaces of the stage, one thread per listed interface.  A direction
+// whose list overflowed (more flagged interfaces than its capacity) is handled by a scan of its
+// flag bits instead: each interior node takes its right interface, the first node of a line
+// also its left one.
+template <int SCHEME>
+__device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, const double *__restrict__ U,
+                                               Strong sj)
+{
+    const int c0 = sj.count[0], c1 = sj.count[1], c2 = sj.count[2];
+    if ((c0 | c1 | c2) == 0) return;
+    const int l0 = c0 <= sj.cap ? c0 : 0, l1 = c1 <= sj.cap ? c1 : 0, l2 = c2 <= sj.cap ? c2 : 0;
+    const long long stride = (long long)bk.nx * blockDim.x;
+    const long long t0 = bk.x * (long long)blockDim.x + threadIdx.x;
+    for (long long t = t0; t < (long long)l0 + l1 + l2; t += stride) {
+        if (t < l0) fix_interface<0, SCHEME>(P, U, sj.Dst, sj.list[t]);
+        else if (t < l0 + l1) fix_interface<1, SCHEME>(P, U, sj.Dst, sj.list[(long long)sj.cap + (t - l0)]);
+        else fix_interface<2, SCHEME>(P, U, sj.Dst, sj.list[2LL * sj.cap + (t - l0 - l1)]);
+    }
+    if (c0 <= sj.cap && c1 <= sj.cap && c2 <= sj.cap) return;
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    const long long st = P.st[DIR];
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = t0; t < N; t += stride) {
         const int i = (int)(t % P.n[0]);
         const long long q = t / P.n[0];
-        const int j = (int)(q % P.n[1]);
-        const int k = (int)(q / P.n[1]);
-        const long long id = node_index(P, i, j, k);
-        const bool fl = flag[id - st] != 0, fr = flag[id] != 0;
-        if (!fl && !fr) continue;
-        constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
-        const int ijk[3] = {i, j, k};
-        const double es = line_eps<DIR>(P, ijk[DA], ijk[DB]);
-        float corr[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float D64[NV], unused[NV];
-        if (fr) {
-            fallback_delta<DIR, SCHEME>(P, U, id, st, es, D64, unused);
-#pragma unroll
-            for (int v = 0; v < NV; v++) corr[v] += D64[v] - Dst[v * P.vs + id];
+        const int ijk[3] = {i, (int)(q % P.n[1]), (int)(q / P.n[1])};
+        const long long id = node_index(P, ijk[0], ijk[1], ijk[2]);
+        const unsigned char f = sj.flag[id];
+        if (c0 > sj.cap) {
+            if (f & 1) fix_interface<0, SCHEME>(P, U, sj.Dst, id);
+            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME>(P, U, sj.Dst, id - P.st[0]);
         }
-        if (fl) {
-            fallback_delta<DIR, SCHEME>(P, U, id - st, st, es, D64, unused);
-#pragma unroll
-            for (int v = 0; v < NV; v++) corr[v] -= D64[v] - Dst[v * P.vs + id - st];
+        if (c1 > sj.cap) {
+            if (f & 2) fix_interface<1, SCHEME>(P, U, sj.Dst, id);
+            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME>(P, U, sj.Dst, id - P.st[1]);
         }
-        const float fac = (float)line_fac<DIR>(P, ijk[DIR]);
-#pragma unroll
-        for (int v = 0; v < NV; v++) Rf[v * P.vs + id] += -fac * corr[v];
+        if (c2 > sj.cap) {
+            if (f & 4) fix_interface<2, SCHEME>(P, U, sj.Dst, id);
+            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME>(P, U, sj.Dst, id - P.st[2]);
+        }
     }
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restrict__ U, Strong sj)
+{
+    patch_fix_body<SCHEME>(P, self_blk(), U, sj);
 }
 
 int conv_chunk(const Dev &P, int d);
@@ -1601,13 +1707,12 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
         if (DIR == 0) {
             const int nseg = (P.n[0] + XSEG - 1) / XSEG;
             const long long lefts = (long long)P.n[1] * P.n[2] * nseg;
-            k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, B.flag, B.Dst,
-                                                                             B.err + 1, gate, B.Dl);
+            k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, strong_of(B), gate,
+                                                                             B.Dl);
             dim3 g(P.n[1] * P.n[2], nseg);
-            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1,
-                                                          gate, B.Dl, acc);
+            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, B.Dl, acc);
         } else {
-            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, B.flag, B.Dst, B.err + 1, gate, acc, chunk);
+            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, acc, chunk);
         }
     } else if (P.mixed) {
         k_conv_char_mixed<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.Uf, B.Wf, B.M, B.Rf, acc, chunk);
@@ -1638,10 +1743,12 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
 template <int MODE, int STAGE, bool VISC, bool CURV>
 static void update_t(const Dev &P, const Bufs &B, int g, cudaStream_t s)
 {
+    const Strong none{nullptr, nullptr, nullptr, nullptr, 0};
     if (P.mixed)
-        k_update<MODE, STAGE, VISC, CURV, float><<<g, 128, 0, s>>>(P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err);
+        k_update<MODE, STAGE, VISC, CURV, float><<<g, 128, 0, s>>>(P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err,
+                                                                    CURV ? none : strong_of(B));
     else
-        k_update<MODE, STAGE, VISC, CURV, double><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.R, B.err);
+        k_update<MODE, STAGE, VISC, CURV, double><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.R, B.err, none);
 }
 
 template <int MODE, int STAGE>
@@ -1658,19 +1765,12 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     }
 }
 
-static void launch_patch(const Dev &P, const Bufs &B, int d, cudaStream_t s)
+static void launch_patch(const Dev &P, const Bufs &B, cudaStream_t s)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const int g = grid_for(N, 128);
-    if (P.scheme == SCH_WENO5JS) {
-        if (d == 0) k_patch_strong<0, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
-        else if (d == 1) k_patch_strong<1, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
-        else k_patch_strong<2, SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
-    } else {
-        if (d == 0) k_patch_strong<0, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
-        else if (d == 1) k_patch_strong<1, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
-        else k_patch_strong<2, SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Rf, B.flag, B.Dst, B.err + 1);
-    }
+    if (P.scheme == SCH_WENO5JS) k_patch_fix<SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, strong_of(B));
+    else k_patch_fix<SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, strong_of(B));
 }
 
 // Optional per-launch event taps (kernel timing): before each launch an event is recorded and
@@ -1711,7 +1811,6 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         launches += launch_sensor_gate(P, B, s);
     }
     int acc = 0;
-    static const char *patch_names[3] = {"patch_x", "patch_y", "patch_z"};
     const bool patch = P.mixed && !general(P) && P.scheme != SCH_CENTRAL4;
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
@@ -1722,11 +1821,11 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         acc = 1;
         launches++;
         if (patch && d == 0) launches++;   // the x segments' left interfaces
-        if (patch) {
-            if (tap) (*tap)(patch_names[d], s);
-            launch_patch(P, B, d, s);
-            launches++;
-        }
+    }
+    if (patch) {   // FP64 recomputation of the stage's strong-jump interfaces (applied by the update)
+        if (tap) (*tap)("patch", s);
+        launch_patch(P, B, s);
+        launches++;
     }
     if (P.viscous) {
         long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -1815,5 +1914,192 @@ void launch_diagnostics(const Dev &P, const Bufs &B, double *part, double *out, 
 }
 
 int diag_partial_size() { return NDIAG * DIAG_BLOCKS; }
+
+// ------------------------------------------------------------------------------------------
+// Ensembles of independent problems: every phase of an RK stage is one launch over the blocks
+// of all problems.  Block b belongs to the problem p with start[p] <= b < start[p + 1] (binary
+// search of the phase's prefix table); the problem's Dev and buffers are staged in shared memory
+// and the single-problem body runs with the block's local coordinates, so each problem computes
+// exactly what its own launches would.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ EnsProb &ens_stage(const EnsProb *__restrict__ tab, const int *__restrict__ start,
+                                              int nprob, int ph, unsigned char *raw, Blk &bk)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int *src = reinterpret_cast<const int *>(tab + lo);
+    int *dst = reinterpret_cast<int *>(raw);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    for (int w = tid; w < (int)(sizeof(EnsProb) / 4); w += blockDim.x * blockDim.y) dst[w] = src[w];
+    __syncthreads();
+    EnsProb &e = *reinterpret_cast<EnsProb *>(raw);
+    const int local = b - start[lo];
+    const int gx = e.g[ph][0], gy = e.g[ph][1], gz = e.g[ph][2];
+    bk = {local % gx, (local / gx) % gy, local / (gx * gy), gx, gy, gz};
+    return e;
+}
+
+#define ENS_PROLOGUE(PH)                                                                           \
+    __shared__ __align__(16) unsigned char raw_[sizeof(EnsProb)];                                  \
+    Blk bk;                                                                                        \
+    EnsProb &e = ens_stage(tab, start, nprob, (PH), raw_, bk);                                     \
+    const Dev &P = e.P;                                                                            \
+    const Bufs &B = e.B;
+
+__global__ void __launch_bounds__(256) k_ens_ghost(const EnsProb *tab, const int *start, int nprob, int d)
+{
+    ENS_PROLOGUE(ENS_G0 + d)
+    ghost_body(P, bk, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
+}
+
+__global__ void __launch_bounds__(256) k_ens_prim(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(ENS_PRIM)
+    if (P.mixed) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1);
+    else prim_body(P, bk, B.U, B.W);
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(128) k_ens_left_x(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(ENS_LX)
+    conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), nullptr, B.Dl);
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(XSEG) k_ens_delta_x(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(ENS_CX)
+    conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, B.Dl, e.acc[0]);
+}
+
+template <int DIR, int SCHEME>
+__global__ void __launch_bounds__(128, 5) k_ens_delta(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(DIR == 1 ? ENS_CY : ENS_CZ)
+    conv_char_delta_body<DIR, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[DIR], e.chunk[DIR]);
+}
+
+template <int DIR, int SCHEME>
+__global__ void __launch_bounds__(128) k_ens_char(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(DIR == 0 ? ENS_CX : DIR == 1 ? ENS_CY : ENS_CZ)
+    conv_char_body<DIR, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[DIR], e.chunk[DIR]);
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(128) k_ens_fix(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(ENS_FIX)
+    patch_fix_body<SCHEME>(P, bk, B.U, strong_of(B));
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(128) k_ens_update(const EnsProb *tab, const int *start, int nprob)
+{
+    ENS_PROLOGUE(ENS_UP)
+    const Strong none{nullptr, nullptr, nullptr, nullptr, 0};
+    if (P.mixed) update_body<0, STAGE, false, false, float>(P, bk, B.U, B.dU, B.Rf, nullptr, B.M, B.R, B.err, strong_of(B));
+    else update_body<0, STAGE, false, false, double>(P, bk, B.U, B.dU, B.R, nullptr, B.M, B.R, B.err, none);
+}
+#undef ENS_PROLOGUE
+
+static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+void ens_phase_grids(const Dev &P, const int chunk[3], int g[ENS_NPH][3])
+{
+    for (int ph = 0; ph < ENS_NPH; ph++) g[ph][0] = g[ph][1] = g[ph][2] = 0;
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    auto one = [&](int ph, int x, int y = 1, int z = 1) { g[ph][0] = x; g[ph][1] = y; g[ph][2] = z; };
+    for (int d = 0; d < 3; d++)
+        if (P.active[d]) one(ENS_G0 + d, ceil_div(2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2], 256));
+    one(ENS_PRIM, ceil_div(P.ntot, 256));
+    const int cph[3] = {ENS_CX, ENS_CY, ENS_CZ};
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+        if (P.mixed && d == 0) {
+            const int nseg = ceil_div(P.n[0], XSEG);
+            one(ENS_LX, ceil_div((long long)P.n[1] * P.n[2] * nseg, 128));
+            one(ENS_CX, P.n[1] * P.n[2], nseg);
+        } else {
+            one(cph[d], ceil_div(P.n[da], 32), ceil_div(P.n[db], 4), ceil_div(P.n[d], chunk[d]));
+        }
+    }
+    if (P.mixed) one(ENS_FIX, ceil_div(N, 128 * 8));   // grid-stride over the flagged interfaces
+    one(ENS_UP, ceil_div(N, 128));
+}
+
+template <int SCHEME>
+static int ens_stage_t(const EnsLaunch &L, int stage, cudaStream_t s)
+{
+    const int np1 = L.nprob + 1;
+    auto st = [&](int ph) { return L.start + ph * np1; };
+    int launches = 0;
+    for (int d = 0; d < 3; d++)
+        if (L.total[ENS_G0 + d]) {
+            k_ens_ghost<<<L.total[ENS_G0 + d], 256, 0, s>>>(L.tab, st(ENS_G0 + d), L.nprob, d);
+            launches++;
+        }
+    k_ens_prim<<<L.total[ENS_PRIM], 256, 0, s>>>(L.tab, st(ENS_PRIM), L.nprob);
+    launches++;
+    const dim3 lb(32, 4);
+    if (L.mixed) {
+        if (L.total[ENS_LX]) {
+            k_ens_left_x<SCHEME><<<L.total[ENS_LX], 128, 0, s>>>(L.tab, st(ENS_LX), L.nprob);
+            k_ens_delta_x<SCHEME><<<L.total[ENS_CX], XSEG, 0, s>>>(L.tab, st(ENS_CX), L.nprob);
+            launches += 2;
+        }
+        if (L.total[ENS_CY]) {
+            k_ens_delta<1, SCHEME><<<L.total[ENS_CY], lb, 0, s>>>(L.tab, st(ENS_CY), L.nprob);
+            launches++;
+        }
+        if (L.total[ENS_CZ]) {
+            k_ens_delta<2, SCHEME><<<L.total[ENS_CZ], lb, 0, s>>>(L.tab, st(ENS_CZ), L.nprob);
+            launches++;
+        }
+        k_ens_fix<SCHEME><<<L.total[ENS_FIX], 128, 0, s>>>(L.tab, st(ENS_FIX), L.nprob);
+        launches++;
+    } else {
+        if (L.total[ENS_CX]) { k_ens_char<0, SCHEME><<<L.total[ENS_CX], lb, 0, s>>>(L.tab, st(ENS_CX), L.nprob); launches++; }
+        if (L.total[ENS_CY]) { k_ens_char<1, SCHEME><<<L.total[ENS_CY], lb, 0, s>>>(L.tab, st(ENS_CY), L.nprob); launches++; }
+        if (L.total[ENS_CZ]) { k_ens_char<2, SCHEME><<<L.total[ENS_CZ], lb, 0, s>>>(L.tab, st(ENS_CZ), L.nprob); launches++; }
+    }
+    if (stage == 0) k_ens_update<0><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
+    else if (stage == 1) k_ens_update<1><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
+    else k_ens_update<2><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
+    return launches + 1;
+}
+
+__global__ void k_ens_errors(const EnsProb *__restrict__ tab, int nprob, int *__restrict__ out)
+{
+    __shared__ int first;
+    if (threadIdx.x == 0) first = 0x7fffffff;
+    __syncthreads();
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+        int *w = tab[p].B.err;
+        if (w[0] & 1) atomicMin(&first, p);
+        w[0] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *out = first == 0x7fffffff ? -1 : first;
+}
+
+void launch_ensemble_errors(const EnsLaunch &L, int *out, cudaStream_t s)
+{
+    k_ens_errors<<<1, 256, 0, s>>>(L.tab, L.nprob, out);
+}
+
+int launch_ensemble_stage(const EnsLaunch &L, int stage, cudaStream_t s)
+{
+    if (L.scheme == SCH_WENO5JS) return ens_stage_t<SCH_WENO5JS>(L, stage, s);
+    return ens_stage_t<SCH_TENO5>(L, stage, s);
+}
+
 
 }  // namespace osb

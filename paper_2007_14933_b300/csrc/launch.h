@@ -15,7 +15,9 @@ struct Bufs {
     float *Uf = nullptr, *Wf = nullptr;                // mixed path: FP32 node copies [2*5] (hi, lo), [NW]
     float *Rf = nullptr, *Vf = nullptr;                // mixed path: FP32 residual [5], viscous [12]
     unsigned char *flag = nullptr;                     // mixed path: strong-jump interface flags [vs]
-    float *Dst = nullptr;                              // mixed path: FP32 flux of flagged interfaces [5]
+    float *Dst = nullptr;                              // mixed path: flagged interfaces' D / corrections [3][5]
+    long long *slist = nullptr;                        // mixed path: flagged interface lists [3][scap]
+    int scap = 0;
     float *Dl = nullptr;                               // mixed path: left interface of each x segment [rows*segs][5]
     void *sw = nullptr;                                // sensor: device weights (BF16 / FP32)
     unsigned char *sflag = nullptr, *gate = nullptr;   // sensor: cell flags, dilated gate [vs]
@@ -48,5 +50,31 @@ int sensor_upload(const float *w, void *d_sw, cudaStream_t s);
 // sensor labels of the current state: ghost fill, per-direction interface labels labd[d] ([vs]
 // bytes each), per-cell OR into out ([N] bytes, compact)
 void launch_labels(const Dev &P, const Bufs &B, unsigned char *labd[3], unsigned char *out, cudaStream_t s);
+
+// ---- ensembles of independent problems (inviscid, uniform or rectilinear grids) ----
+// The phases of one RK stage; each is one launch over the blocks of every problem.
+enum { ENS_G0 = 0, ENS_G1, ENS_G2, ENS_PRIM, ENS_LX, ENS_CX, ENS_CY, ENS_CZ, ENS_FIX, ENS_UP, ENS_NPH };
+__host__ __device__ inline Strong strong_of(const Bufs &B) { return Strong{B.flag, B.Dst, B.err + 1, B.slist, B.scap}; }
+
+struct EnsProb {
+    Dev P;
+    Bufs B;
+    int g[ENS_NPH][3];   // the problem's local grid of each phase (0 blocks: phase skipped)
+    int chunk[3];        // marching chunk of the line kernels per direction
+    int acc[3];          // 1: the direction adds to the residual written by an earlier one
+};
+struct EnsLaunch {
+    const EnsProb *tab = nullptr;      // device, [nprob]
+    const int *start = nullptr;        // device, [ENS_NPH][nprob + 1] block prefix sums
+    int nprob = 0;
+    int total[ENS_NPH] = {};           // blocks of each phase over all problems
+    int mixed = 0, scheme = 0;
+};
+// host side: local grid of every phase of one problem for the given line-kernel chunks
+void ens_phase_grids(const Dev &P, const int chunk[3], int g[ENS_NPH][3]);
+int launch_ensemble_stage(const EnsLaunch &L, int stage, cudaStream_t s);
+// out = lowest member index whose error word has the non-finite bit, else -1; clears the words
+void launch_ensemble_errors(const EnsLaunch &L, int *out, cudaStream_t s);
+int conv_chunk(const Dev &P, int d);
 
 }  // namespace osb

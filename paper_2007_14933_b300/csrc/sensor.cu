@@ -24,7 +24,6 @@ constexpr int SF = 135, SK = 144, SH = 32;
 constexpr int NPARAM = SH * SF + SH + SH * SH + SH + SH + 1;
 constexpr int W1S = 152;   // smem row stride of W1 (bf16): conflict-free fragment loads
 constexpr int W2S = 40;    // smem row stride of W2 and W2^T
-constexpr int FS = 152;    // smem row stride of a feature tile
 
 struct SensorW {
     __nv_bfloat16 W1[SH][SK];

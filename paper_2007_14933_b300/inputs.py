@@ -21,6 +21,10 @@ Workloads (paper sections in brackets):
                    viscous at Ma 0.1 (64^3, 128^3) or TENO5 + viscous at Ma 1.25 (256^3)
     euler_wave()   2D density wave on the sinusoidal curvilinear grid [Sec. 5.3, Eqs. 47-50]
     random_state() seeded smooth/perturbed states for parity tests
+    sbli()         shock / boundary-layer box [Sec. 6]: Mach 2, Re 1e4, similarity inflow,
+                   isothermal wall, 10-degree oblique shock on the top boundary, tanh stretching
+    riemann2d(), riemann_ensemble()
+                   four-quadrant 2D Riemann problems [Sec. 5.2] and seeded ensembles of them
 """
 import math
 
@@ -295,3 +299,46 @@ def sbli(n=(512, 256, 64), Ma=2.0, Re=1e4, Pr=0.72, theta=10.0, stretch=3.0, L=(
     cfg["dt"] = float(cfl / ((np.abs(u) + a).max() / dx + (np.abs(v) + a).max() / dy + a.max() / dz))
     cfg["beta_shock"] = float(np.degrees(b))
     return cfg, U
+
+
+# ---------------------------------------------------------------------------------------------
+# Four-quadrant 2D Riemann problems and seeded ensembles of them.
+# ---------------------------------------------------------------------------------------------
+ENSEMBLE_SIZES = (128, 192, 256, 384, 512, 768, 1024)
+
+
+def riemann2d(N, quad, scheme=TENO5, cfl=0.4, gamma=1.4, ny=None):
+    """Unit square, nodes at cell centres ((i + 1/2)/N), split at (1/2, 1/2); quad[q] = (rho, u, v,
+    p) of quadrant q (0: x > 1/2, y > 1/2; 1: x < 1/2, y > 1/2; 2: x < 1/2, y < 1/2; 3: x > 1/2,
+    y < 1/2), zero-gradient faces, inviscid, dt from the CFL number on the initial state."""
+    nx = int(N)
+    ny = int(ny or N)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    right, top = X > 0.5, Y > 0.5
+    q = np.where(top, np.where(right, 0, 1), np.where(right, 3, 2))
+    Q = np.asarray(quad, dtype=np.float64)
+    rho, u, v, p = (Q[q, c] for c in range(4))
+    U = prim_to_cons(gamma, rho, u, v, np.zeros_like(rho), p)[:, None]
+    cfg = _base((nx, ny, 1), scheme=scheme, gamma=gamma, h=(1.0 / nx, 1.0 / ny, 1.0),
+                bc=[[ZEROGRAD, ZEROGRAD], [ZEROGRAD, ZEROGRAD], [PERIODIC, PERIODIC]])
+    cfg["dt"] = cfl_dt(cfg, U, cfl)
+    return cfg, U
+
+
+def riemann_ensemble(seed, nprob=64, sizes=ENSEMBLE_SIZES, scheme=TENO5, cfl=0.4):
+    """Seeded ensemble: numpy's PCG64 generator seeded with `seed` draws, per problem, N uniformly
+    from `sizes` and then four quadrant states with rho, p ~ U[0.1, 1.5] and u, v ~ U[-1, 1]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nprob):
+        N = int(rng.choice(sizes))
+        quad = np.empty((4, 4))
+        for k in range(4):
+            quad[k, 0] = rng.uniform(0.1, 1.5)
+            quad[k, 1] = rng.uniform(-1.0, 1.0)
+            quad[k, 2] = rng.uniform(-1.0, 1.0)
+            quad[k, 3] = rng.uniform(0.1, 1.5)
+        out.append(riemann2d(N, quad, scheme=scheme, cfl=cfl))
+    return out

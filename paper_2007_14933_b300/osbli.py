@@ -27,7 +27,10 @@ EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_s
             "osbli_profile_name", "osbli_fp64_peak", "osbli_residual_noalloc",
             "osbli_fp32_peak", "osbli_sensor_set_weights", "osbli_sensor_labels",
             "osbli_sensor_features", "osbli_sensor_probs", "osbli_mlp_grad", "osbli_mlp_train",
-            "osbli_mlp_forward"]
+            "osbli_mlp_forward", "osbli_ensemble_create", "osbli_ensemble_destroy",
+            "osbli_ensemble_set_state", "osbli_ensemble_get_state", "osbli_ensemble_member",
+            "osbli_ensemble_step", "osbli_ensemble_set_chunk", "osbli_ensemble_autotune",
+            "osbli_ensemble_launches_per_step", "osbli_ensemble_points", "osbli_ensemble_last_error"]
 SENSOR_NPARAM = 5441
 SENSOR_NFEAT = 144
 
@@ -101,6 +104,26 @@ def load():
         L.osbli_fp32_peak.restype = ctypes.c_int
         L.osbli_last_error.argtypes = [vp]
         L.osbli_last_error.restype = ctypes.c_char_p
+        L.osbli_ensemble_create.argtypes = [ctypes.c_int, ctypes.POINTER(osbli_params), vp, ctypes.POINTER(vp)]
+        L.osbli_ensemble_destroy.argtypes = [vp]
+        L.osbli_ensemble_destroy.restype = None
+        L.osbli_ensemble_set_state.argtypes = [vp, ctypes.c_int, vp]
+        L.osbli_ensemble_get_state.argtypes = [vp, ctypes.c_int, vp]
+        L.osbli_ensemble_member.argtypes = [vp, ctypes.c_int]
+        L.osbli_ensemble_member.restype = vp
+        L.osbli_ensemble_step.argtypes = [vp, ctypes.c_int]
+        L.osbli_ensemble_set_chunk.argtypes = [vp, ctypes.c_int]
+        L.osbli_ensemble_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_double)]
+        L.osbli_ensemble_launches_per_step.argtypes = [vp]
+        L.osbli_ensemble_points.argtypes = [vp]
+        L.osbli_ensemble_points.restype = ctypes.c_longlong
+        L.osbli_ensemble_last_error.argtypes = [vp]
+        L.osbli_ensemble_last_error.restype = ctypes.c_char_p
+        for name in ("osbli_ensemble_create", "osbli_ensemble_set_state", "osbli_ensemble_get_state",
+                     "osbli_ensemble_step", "osbli_ensemble_set_chunk", "osbli_ensemble_autotune",
+                     "osbli_ensemble_launches_per_step"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("osbli_create", "osbli_set_boundary_data", "osbli_set_state", "osbli_get_state",
                      "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
                      "osbli_launches_per_step", "osbli_profile_residual"):
@@ -263,6 +286,102 @@ def osbli_mlp_train(d_feats, d_labels, n, steps, batch, lr, pos_weight, seed, w)
 def osbli_last_error(h):
     m = load().osbli_last_error(h)
     return m.decode() if m else ""
+
+
+def _echeck(e, rc):
+    if rc != OSBLI_OK:
+        msg = load().osbli_ensemble_last_error(e)
+        raise OsbliError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def osbli_ensemble_create(params_list, cuda_stream=None):
+    arr = (osbli_params * len(params_list))(*params_list)
+    e = ctypes.c_void_p()
+    _echeck(None, load().osbli_ensemble_create(len(params_list), arr, ctypes.c_void_p(cuda_stream or 0),
+                                               ctypes.byref(e)))
+    return e
+
+
+def osbli_ensemble_destroy(e):
+    load().osbli_ensemble_destroy(e)
+
+
+def osbli_ensemble_set_state(e, p, U):
+    return _echeck(e, load().osbli_ensemble_set_state(e, int(p), _ptr(U)))
+
+
+def osbli_ensemble_get_state(e, p, U):
+    return _echeck(e, load().osbli_ensemble_get_state(e, int(p), _ptr(U)))
+
+
+def osbli_ensemble_member(e, p):
+    return load().osbli_ensemble_member(e, int(p))
+
+
+def osbli_ensemble_step(e, nsteps):
+    return _echeck(e, load().osbli_ensemble_step(e, int(nsteps)))
+
+
+def osbli_ensemble_set_chunk(e, chunk):
+    return _echeck(e, load().osbli_ensemble_set_chunk(e, int(chunk)))
+
+
+def osbli_ensemble_autotune(e, reps=3):
+    c = ctypes.c_int()
+    ms = ctypes.c_double()
+    _echeck(e, load().osbli_ensemble_autotune(e, int(reps), ctypes.byref(c), ctypes.byref(ms)))
+    return c.value, ms.value
+
+
+def osbli_ensemble_launches_per_step(e):
+    return load().osbli_ensemble_launches_per_step(e)
+
+
+def osbli_ensemble_points(e):
+    return load().osbli_ensemble_points(e)
+
+
+class Ensemble:
+    """Independent problems advanced together; ``cfgs`` are ``inputs`` problem dicts."""
+
+    def __init__(self, cfgs, precision=OSBLI_MIXED, cuda_stream=None):
+        self.e = None
+        self.shapes = [(5, int(c["n"][2]), int(c["n"][1]), int(c["n"][0])) for c in cfgs]
+        self.e = osbli_ensemble_create([make_params(c, precision) for c in cfgs], cuda_stream)
+
+    def close(self):
+        if getattr(self, "e", None):
+            osbli_ensemble_destroy(self.e)
+            self.e = None
+
+    __del__ = close
+
+    def set_state(self, p, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.shapes[p])
+        osbli_ensemble_set_state(self.e, p, U)
+
+    def get_state(self, p, out=None):
+        if out is None:
+            out = np.empty(self.shapes[p])
+        osbli_ensemble_get_state(self.e, p, out)
+        return out
+
+    def step(self, nsteps):
+        osbli_ensemble_step(self.e, nsteps)
+
+    def set_chunk(self, chunk):
+        osbli_ensemble_set_chunk(self.e, chunk)
+
+    def autotune(self, reps=3):
+        return osbli_ensemble_autotune(self.e, reps)
+
+    def launches_per_step(self):
+        return osbli_ensemble_launches_per_step(self.e)
+
+    def points(self):
+        return osbli_ensemble_points(self.e)
 
 
 class Solver:

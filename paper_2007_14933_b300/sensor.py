@@ -56,6 +56,17 @@ def tgv_training_set(N=48, Ma=1.25, nsnap=6, steps_between=12):
     return collect(cfg, U, nsnap, steps_between)
 
 
+SBLI_TRAIN_DESC = ("shock / boundary-layer box 96x48x8 on 60x20x4 (Mach 2, Re 1e4, 10 deg shock from "
+                   "x=10), 5 snapshots every 1200 steps")
+
+
+def sbli_training_set(nsnap=5, steps_between=1200):
+    """TENO5 snapshots of a reduced shock / boundary-layer box while the imposed oblique shock
+    enters the domain and reflects off the boundary layer."""
+    cfg, U = I.sbli(n=(96, 48, 8), L=(60.0, 20.0, 4.0), x_shock=10.0, scheme=I.TENO5)
+    return collect(cfg, U, nsnap, steps_between)
+
+
 def calibrate_threshold(w, feats, labels, recall=0.95):
     """Largest threshold whose recall of the positive labels on (feats, labels) is >= recall."""
     import torch

@@ -50,7 +50,7 @@ def test_sbli_mixed_runs_the_delta_path_and_matches():
     s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
     s.set_state(U)
     names = [nm for nm, _ in s.profile_residual()]
-    assert "patch_y" in names          # Cartesian delta kernels (with FP64 patches) ran
+    assert "patch" in names            # Cartesian delta kernels (with the FP64 fix pass) ran
     s.close()
     Ug, Uo = mixed_vs_oracle(cfg, U, 15)
     assert l2rel(Ug, Uo) <= 1e-5
