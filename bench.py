@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--plain", action="store_true", help="time the plain FP64 form only")
     ap.add_argument("--mixed", action="store_true", help="time the mixed form only")
     ap.add_argument("--no-sensor", action="store_true", help="skip the learned-sensor form")
+    ap.add_argument("--forms", default=None, help="comma list of forms to time (learned, mixed, fp64)")
     ap.add_argument("--sensor-steps", type=int, default=800, help="Adam steps of the sensor training")
     return ap.parse_args()
 
@@ -461,6 +462,8 @@ def main():
         forms = ["mixed"]
     elif args.no_sensor:
         forms = ["mixed", "fp64"]
+    if args.forms:
+        forms = [f for f in args.forms.split(",") if f in ("learned", "mixed", "fp64")]
     head = forms[0]
     prec = {"learned": osbli.OSBLI_MIXED, "mixed": osbli.OSBLI_MIXED, "fp64": osbli.OSBLI_FP64}
     sensor = None

@@ -30,6 +30,7 @@ struct osbli {
     bool sensor_ready = false;
     double *lfac[3] = {nullptr, nullptr, nullptr};   // rectilinear grids: per-line factors
     double *lesc[3] = {nullptr, nullptr, nullptr};   // and per-line epsilon scales
+    float *lfacf[3] = {nullptr, nullptr, nullptr};   // FP32 copies of the factors
     const char *prof_names[32] = {};
     int prof_count = 0;
     char err[512];
@@ -79,6 +80,7 @@ static void free_all(osbli *h)
     for (int d = 0; d < 3; d++) {
         if (h->lfac[d]) cudaFree(h->lfac[d]);
         if (h->lesc[d]) cudaFree(h->lesc[d]);
+        if (h->lfacf[d]) cudaFree(h->lfacf[d]);
     }
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -178,7 +180,10 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
         for (int d = 0; d < 3; d++) hh[d] = P.active[d] ? p->h[d] : 1.0;
         const double Jinv = hh[0] * (hh[1] * hh[2]);
         const double S[3] = {hh[1] * hh[2], hh[2] * hh[0], hh[0] * hh[1]};
-        for (int d = 0; d < 3; d++) P.fac[d] = S[d] / Jinv;
+        for (int d = 0; d < 3; d++) {
+            P.fac[d] = S[d] / Jinv;
+            P.facf[d] = (float)P.fac[d];
+        }
     }
 
     auto fail = [&](int code) {
@@ -274,12 +279,13 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
         // rectilinear detection: per-line factors and a flag raised by any non-rectilinear node
         for (int d = 0; d < 3 && e == cudaSuccess; d++) {
             e = cudaMalloc(&h->lfac[d], (size_t)n[d] * sizeof(double));
+            if (e == cudaSuccess) e = cudaMalloc(&h->lfacf[d], (size_t)n[d] * sizeof(float));
             const size_t lines = (size_t)n[(d == 0) ? 1 : 0] * n[(d == 2) ? 1 : 2];
             if (e == cudaSuccess) e = cudaMalloc(&h->lesc[d], lines * sizeof(double));
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(h->B.err, 0, sizeof(int), h->stream);
         if (e == cudaSuccess) {
-            launch_rect(P, Sraw, smax, h->lfac, h->lesc, h->B.err, h->stream);
+            launch_rect(P, Sraw, smax, h->lfac, h->lesc, h->lfacf, h->B.err, h->stream);
             e = cudaGetLastError();
         }
         unsigned long long hs[3] = {0, 0, 0};
@@ -304,6 +310,7 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
         for (int d = 0; d < 3; d++) {
             P.lfac[d] = P.rect ? h->lfac[d] : nullptr;
             P.lesc[d] = P.rect ? h->lesc[d] : nullptr;
+            P.lfacf[d] = P.rect ? h->lfacf[d] : nullptr;
         }
         if (P.sensor && !P.rect)
             return fail(seterr(h, OSBLI_EINVAL, "the learned sensor needs a Cartesian or rectilinear grid"));

@@ -40,6 +40,8 @@ struct Dev {
     int rect;          // rectilinear grid: Cartesian kernels with per-line factors lfac
     const double *lfac[3];   // rect: S_dd / Jinv of each line position along direction d
     const double *lesc[3];   // rect: 1 / |S~_d|^2 of each line of direction d ([n_DB][n_DA])
+    float facf[3];           // FP32 copies of fac and lfac for the mixed kernels (no double ->
+    const float *lfacf[3];   // float conversion, which runs on the FP64 pipe, in their loops)
 };
 
 // Grids that need the general curvilinear kernels (metric vectors read per node).
@@ -57,6 +59,16 @@ __device__ __forceinline__ double line_fac(const Dev &P, int s)
 __device__ __forceinline__ double line_fac(const Dev &P, int d, int s)
 {
     return P.rect ? __ldg(P.lfac[d] + s) : P.fac[d];
+}
+
+template <int DIR>
+__device__ __forceinline__ float line_facf(const Dev &P, int s)
+{
+    return P.rect ? __ldg(P.lfacf[DIR] + s) : P.facf[DIR];
+}
+__device__ __forceinline__ float line_facf(const Dev &P, int d, int s)
+{
+    return P.rect ? __ldg(P.lfacf[d] + s) : P.facf[d];
 }
 
 // Epsilon scale of the reconstructions along a line of direction DIR through cross indices

@@ -510,21 +510,48 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
 // 5-9 the FP32 rounding of the remainder (U = hi + lo to ~48 bits), so that differences
 // between nearby nodes are formed to FP32 accuracy relative to the difference itself.  Wf holds
 // FP32 primitives (u, v, w, p, a, sqrt(rho), H, T).
-__device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, const double *__restrict__ U, float *__restrict__ Uf,
-                             float *__restrict__ Wf, int *__restrict__ nstrong)
+// FP64 -> FP32 hi/lo pair with integer operations only (double <-> float conversions run on the
+// FP64 pipe, 1/64 of the FP32 rate on this GPU): hi = x rounded to 24 significant bits (half
+// away from zero), lo = x - hi from the dropped 29 mantissa bits as an FP32 value (rounded to
+// 24 bits), so hi + lo = x to ~47 bits and hi is the nearest FP32 value (unbiased, as the
+// primitives built from it need).  Zero and values outside FP32's normal range give
+// hi = lo = 0 (conserved variables never come near them); the remainder's scale 2^(e-1075)
+// underflows to 0 below |x| ~ 1e-22, where lo is negligible against hi.
+__device__ __forceinline__ void split_hi_lo(double x, float &hi, float &lo)
 {
-    // per-direction counts of strong-jump interfaces of this stage start at zero
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int h32 = (unsigned int)(b >> 32), l32 = (unsigned int)b;
+    const unsigned int sign = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7FFu);
+    const int ef = e - 1023 + 127;                     // FP32 biased exponent of hi
+    const unsigned int m23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+    const unsigned int up = (l32 >> 28) & 1u;          // first dropped bit: round the magnitude up
+    const bool ok = ef > 0 && ef < 254;
+    hi = ok ? __uint_as_float(sign | (((unsigned int)ef << 23) + m23 + up)) : 0.f;   // carry into the exponent
+    const int es = e - 1075 + 127;                     // biased exponent of 2^(e - 1075)
+    const float scale = (ok && es > 0) ? __uint_as_float((unsigned int)es << 23) : 0.f;
+    const int rem = (int)(l32 & 0x1FFFFFFFu) - (up ? 0x20000000 : 0);   // x - hi in units of 2^(e-1075)
+    const float r = __int2float_rn(rem) * scale;
+    lo = sign ? -r : r;
+}
+
+__device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, const double *__restrict__ U, float *__restrict__ Uf,
+                             float *__restrict__ Wf, int *__restrict__ nstrong, unsigned char *__restrict__ flag)
+{
+    // per-direction counts of strong-jump interfaces of this stage start at zero, and so do the
+    // interface flags (the convective passes set the bits of their strong-jump interfaces)
     if (bk.x == 0 && threadIdx.x < 3) nstrong[threadIdx.x] = 0;
     for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
          t += (long long)bk.nx * blockDim.x) {
         float h[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            const double x = U[v * P.vs + t];
-            h[v] = (float)x;
+            float lo;
+            split_hi_lo(U[v * P.vs + t], h[v], lo);
             Uf[v * P.vs + t] = h[v];
-            Uf[(NV + v) * P.vs + t] = (float)(x - (double)h[v]);
+            Uf[(NV + v) * P.vs + t] = lo;
         }
+        if (flag) flag[t] = 0;
         const float rho = h[0], mx = h[1], my = h[2], mz = h[3], E = h[4];
         const float ir = 1.0f / rho;
         const float u = mx * ir, v = my * ir, w = mz * ir;
@@ -541,9 +568,9 @@ __device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, con
 }
 
 __global__ void k_prim_mixed(Dev P, const double *__restrict__ U, float *__restrict__ Uf,
-                             float *__restrict__ Wf, int *__restrict__ nstrong)
+                             float *__restrict__ Wf, int *__restrict__ nstrong, unsigned char *__restrict__ flag)
 {
-    prim_mixed_body(P, self_blk(), U, Uf, Wf, nstrong);
+    prim_mixed_body(P, self_blk(), U, Uf, Wf, nstrong, flag);
 }
 
 __device__ __forceinline__ bool strong_jump(const Dev &P, const float *__restrict__ Uf,
@@ -610,7 +637,7 @@ __global__ void __launch_bounds__(128) k_conv_char_mixed(Dev P, const double *__
         const long long id = base + (long long)m * st;
         float Fp[NV];
         mixed_flux<DIR, SCHEME, CURV>(P, qf, U, M, id, st, es, Fp);
-        const float fac = CURV ? (float)(P.shat[DIR] * M[9 * P.vs + id]) : (float)line_fac<DIR>(P, m);
+        const float fac = CURV ? (float)(P.shat[DIR] * M[9 * P.vs + id]) : line_facf<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             const float r = -fac * (Fp[v] - Fm[v]);
@@ -776,7 +803,8 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
 #pragma unroll
             for (int v = 0; v < 4; v++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) gr[v][c] = T(line_fac(P, c, ijk[c])) * dxi[c][v];
+                for (int c = 0; c < 3; c++)
+                    gr[v][c] = (sizeof(T) == 4 ? T(line_facf(P, c, ijk[c])) : T(line_fac(P, c, ijk[c]))) * dxi[c][v];
         }
         const T Tm = T(W[W_T * vs + id]);
         const T mu = viscosity_t<T>(P, Tm);
@@ -849,7 +877,7 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                 const bool fr = (f0 & bit) != 0, fl = (sj.flag[id - st] & bit) != 0;
                 if (!fr && !fl) continue;
                 const float *Ds = sj.Dst + (long long)d * NV * vs;
-                const RT fac = RT(line_fac(P, d, ijk[d]));
+                const RT fac = sizeof(RT) == 4 ? RT(line_facf(P, d, ijk[d])) : RT(line_fac(P, d, ijk[d]));
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
                     const RT c = (fr ? RT(Ds[v * vs + id]) : RT(0)) - (fl ? RT(Ds[v * vs + id - st]) : RT(0));
@@ -864,7 +892,8 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                 const int ie = ijk[d], n = P.n[d];
                 const long long st = P.st[d];
                 const bool per = P.bc[d][0] == BC_PERIODIC;
-                const RT fac = RT(CURV ? P.shat[d] * M[9 * vs + id] : line_fac(P, d, ie));
+                const RT fac = CURV ? RT(P.shat[d] * M[9 * vs + id])
+                                    : (sizeof(RT) == 4 ? RT(line_facf(P, d, ie)) : RT(line_fac(P, d, ie)));
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
                     const RT *f = V + (d * 4 + c) * vs + id;
@@ -1314,19 +1343,15 @@ __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restr
     const bool strong = strong_jump(P, Uf, Wf, m, st);
     if (!gate || strong || gate[m] || gate[m + st]) delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, es, D, dF1);
     else central_delta<DIR>(P, Uf, Wf, m, st, D, dF1);
-    if (!own) return;
-    constexpr unsigned char bit = 1u << DIR;
-    const unsigned char f = sj.flag[m];
-    if (strong) {
-        sj.flag[m] = f | bit;
-        const int k = atomicAdd(sj.count + DIR, 1);
-        if (k < sj.cap) sj.list[(long long)DIR * sj.cap + k] = m;
-        float *Ds = sj.Dst + (long long)DIR * NV * P.vs;
+    if (!own || !strong) return;
+    // the stage's flags were cleared by the primitives pass; one owner per interface, and the
+    // directions run one after another, so this read-modify-write of the byte is unshared
+    sj.flag[m] |= (unsigned char)(1u << DIR);
+    const int k = atomicAdd(sj.count + DIR, 1);
+    if (k < sj.cap) sj.list[(long long)DIR * sj.cap + k] = m;
+    float *Ds = sj.Dst + (long long)DIR * NV * P.vs;
 #pragma unroll
-        for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D[v];
-    } else if (f & bit) {
-        sj.flag[m] = f & (unsigned char)~bit;
-    }
+    for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D[v];
 }
 
 // y and z: thread per line of the cross directions (lanes along x, coalesced), marching along DIR.
@@ -1354,7 +1379,7 @@ __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk
         const long long id = base + (long long)m * st;
         float Dp[NV];
         delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, sj, true, gate);
-        const float fac = (float)line_fac<DIR>(P, m);
+        const float fac = line_facf<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             // F_{m+1/2} - F_{m-1/2} = (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2}
@@ -1436,7 +1461,7 @@ __device__ __forceinline__ void conv_char_delta_x_body(const Dev &P, const Blk &
     if (t < NV) sD[t][0] = Dl[((long long)row * nseg + bk.y) * NV + t];
     __syncthreads();
     if (i >= P.n[0]) return;
-    const float fac = (float)line_fac<0>(P, i);
+    const float fac = line_facf<0>(P, i);
     const long long id = base + i;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -1630,16 +1655,19 @@ void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sr
 // any off-diagonal metric is non-zero or a node's factor differs from its line's by more than
 // 1e-13 (relative).
 __global__ void k_rect_lines(Dev P, const double *__restrict__ Sraw, const unsigned long long *__restrict__ smax,
-                             double *l0, double *l1, double *l2, double *e0, double *e1, double *e2)
+                             double *l0, double *l1, double *l2, double *e0, double *e1, double *e2,
+                             float *f0, float *f1, float *f2)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     double *out[3] = {l0, l1, l2}, *eout[3] = {e0, e1, e2};
+    float *fout[3] = {f0, f1, f2};
     const int d = blockIdx.y;
     const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
     const long long stv[3] = {1, P.n[0], (long long)P.n[0] * P.n[1]};
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n[d]; s += gridDim.x * blockDim.x) {
         const long long o = (long long)s * stv[d];
         out[d][s] = Sraw[(d * 3 + d) * N + o] / Sraw[9 * N + o];
+        fout[d][s] = (float)out[d][s];
     }
     // 1 / |S~_d|^2 of every line of direction d, from its first node
     const double sh = __longlong_as_double((long long)smax[d]);
@@ -1682,10 +1710,11 @@ __global__ void k_rect_check(Dev P, const double *__restrict__ Sraw, const doubl
 }
 
 void launch_rect(const Dev &P, const double *Sraw, const unsigned long long *smax, double *const lfac[3],
-                 double *const lesc[3], int *general_grid, cudaStream_t s)
+                 double *const lesc[3], float *const lfacf[3], int *general_grid, cudaStream_t s)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
-    k_rect_lines<<<dim3(256, 3), 128, 0, s>>>(P, Sraw, smax, lfac[0], lfac[1], lfac[2], lesc[0], lesc[1], lesc[2]);
+    k_rect_lines<<<dim3(256, 3), 128, 0, s>>>(P, Sraw, smax, lfac[0], lfac[1], lfac[2], lesc[0], lesc[1], lesc[2],
+                                              lfacf[0], lfacf[1], lfacf[2]);
     k_rect_check<<<grid_for(N, 256), 256, 0, s>>>(P, Sraw, lfac[0], lfac[1], lfac[2], lesc[0], lesc[1],
                                                   lesc[2], smax, general_grid);
 }
@@ -1803,7 +1832,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         launches++;
     }
     if (tap) (*tap)("prim", s);
-    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1);
+    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
     else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
     if (P.sensor && sensor_now) {
@@ -1894,7 +1923,7 @@ int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent
 
 void launch_prim(const Dev &P, const Bufs &B, cudaStream_t s)
 {
-    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1);
+    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
     else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
 }
 
@@ -1960,7 +1989,7 @@ __global__ void __launch_bounds__(256) k_ens_ghost(const EnsProb *tab, const int
 __global__ void __launch_bounds__(256) k_ens_prim(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(ENS_PRIM)
-    if (P.mixed) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1);
+    if (P.mixed) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
     else prim_body(P, bk, B.U, B.W);
 }
 

@@ -28,7 +28,7 @@ struct Bufs {
 void launch_unpack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s);
 void launch_pack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s);
 void launch_rect(const Dev &P, const double *Sraw, const unsigned long long *smax, double *const lfac[3],
-                 double *const lesc[3], int *general_grid, cudaStream_t s);
+                 double *const lesc[3], float *const lfacf[3], int *general_grid, cudaStream_t s);
 void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sraw,
                     unsigned long long *smax, double *M, cudaStream_t s);
 int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s);

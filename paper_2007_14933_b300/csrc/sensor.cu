@@ -25,8 +25,14 @@ constexpr int NPARAM = SH * SF + SH + SH * SH + SH + SH + 1;
 constexpr int W1S = 152;   // smem row stride of W1 (bf16): conflict-free fragment loads
 constexpr int W2S = 40;    // smem row stride of W2 and W2^T
 
+// Inference layout of W1: columns blocked by quantity q and neighbour row rn (dk, dj), the three
+// x offsets of a row in one group of four (the fourth zero): column (q*9 + rn)*4 + (di + 1).
+constexpr int KR = 192;    // 5 quantities x 9 rows x 4, padded to a multiple of 16
+constexpr int KRS = 200;   // smem row stride (bf16) of that W1: conflict-free fragment loads
+
 struct SensorW {
     __nv_bfloat16 W1[SH][SK];
+    __nv_bfloat16 W1r[SH][KR];
     __nv_bfloat16 W2[SH][SH];
     __nv_bfloat16 W2T[SH][SH];
     float b1[SH], b2[SH], w3[SH], b3;
@@ -215,13 +221,22 @@ __global__ void k_features(Dev P, const double *__restrict__ U, __nv_bfloat16 *_
 // ------------------------------------------------------------------------------------------
 constexpr int INF_WARPS = 4;
 
-// A warp handles 16 consecutive x-cells of one grid row.  The 9 neighbouring rows (dj, dk in
-// {-1,0,1}) of x-positions x0-1 .. x0+16 are staged in shared memory with coalesced loads
-// (rho, u, v, w, p).  Each lane then forms exactly the feature values of its tensor-core A
-// fragments: column c of a cell is (neighbour row, x offset, quantity) from a table, and
-// feature = staged value * scale - offset with per-cell scale/offset (1/rho_c and 1; 1/a_c and
-// u_c/a_c; 1/p_c and 1), so no feature tile is written.
-constexpr int SEG = 16;
+// A warp handles 32 consecutive x-cells of one grid row as two 16-row tensor-core tiles.  The 9
+// neighbouring rows (dj, dk in {-1,0,1}) of x-positions x0-1 .. x0+32 are staged in shared
+// memory with coalesced loads (rho, u, v, w, p).  With the quantity-blocked column order of W1r a
+// lane's A-fragment columns (16 kt + 2t, +1) are the x offsets (-1, 0) of one (q, rn) group for
+// even t and (+1, pad) for odd t, the group being 4 kt + t/2 (+2 for the upper column half): the
+// lane reads the staged row at its cell and scales it, feature = value * M - A with the cell's
+// M, A (1/rho_c and 1; 1/a_c and u_c/a_c; 1/p_c and 1).  The B fragments of W1 serve both tiles.
+constexpr int SEG = 32;
+constexpr int SQS = SEG + 2;
+
+struct InferSmem {
+    __nv_bfloat16 W1[SH][KRS];
+    __nv_bfloat16 W2[SH][W2S];
+    float b1[SH], b2[SH], w3[SH], b3;
+};
+
 __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const float *__restrict__ Uf,
                                                                  const float *__restrict__ Wf,
                                                                  const SensorW *__restrict__ W,
@@ -229,24 +244,26 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
                                                                  unsigned char *__restrict__ flag,
                                                                  float *__restrict__ probs)
 {
-    __shared__ SensorSmem S;
-    __shared__ float sQ[INF_WARPS][9][5][SEG + 2];
-    __shared__ float sM[INF_WARPS][SEG][5], sA[INF_WARPS][SEG][5];
-    __shared__ unsigned short sCol[SK];
-    load_weights(S, W);
-    for (int c = threadIdx.x; c < SK; c += blockDim.x) {
-        unsigned short v = 0xFFFF;
-        if (c < SF) {
-            const int nb = c / 5, q = c % 5;
-            v = (unsigned short)(((nb / 3) << 8) | ((nb % 3) << 4) | q);
-        }
-        sCol[c] = v;
+    __shared__ InferSmem S;
+    __shared__ float sQ[INF_WARPS][9 * 5 * SQS];
+    for (int i = threadIdx.x; i < SH * KR; i += blockDim.x) S.W1[i / KR][i % KR] = W->W1r[i / KR][i % KR];
+    for (int i = threadIdx.x; i < SH * SH; i += blockDim.x) S.W2[i / SH][i % SH] = W->W2[i / SH][i % SH];
+    for (int i = threadIdx.x; i < SH; i += blockDim.x) {
+        S.b1[i] = W->b1[i];
+        S.b2[i] = W->b2[i];
+        S.w3[i] = W->w3[i];
     }
+    if (threadIdx.x == 0) S.b3 = W->b3;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int hb = t >> 1;               // which group of the k-step's column half
+    const bool odd = (t & 1) != 0;       // columns (+1, pad) instead of (-1, 0)
+    const int xo = odd ? 2 : 0;
+    float *Q = sQ[warp];
     const int nseg = (P.n[0] + SEG - 1) / SEG;
     const long long ntiles = (long long)nseg * P.n[1] * P.n[2];
     const long long vs = P.vs;
+    const float gam = (float)P.gamma;
     for (long long tile = blockIdx.x * (long long)INF_WARPS + warp; tile < ntiles;
          tile += (long long)gridDim.x * INF_WARPS) {
         const int seg = (int)(tile % nseg);
@@ -255,56 +272,110 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
         const int x0 = seg * SEG;
         const int ncell = min(SEG, P.n[0] - x0);
         const long long base = node_index(P, x0, j, k);
-        if (lane < SEG + 2) {
-            int dx = lane - 1;
+        for (int pos = lane; pos < SQS; pos += 32) {
+            int dx = pos - 1;
             if (!P.active[0]) dx = 0;
             else if (x0 + dx > P.n[0]) dx = P.n[0] - x0;     // past the first ghost: unused
 #pragma unroll
             for (int r = 0; r < 9; r++) {
                 const int dj = P.active[1] ? r % 3 - 1 : 0, dk = P.active[2] ? r / 3 - 1 : 0;
                 const long long id = base + dx + dj * P.st[1] + dk * P.st[2];
-                sQ[warp][r][0][lane] = Uf[id];
-                sQ[warp][r][1][lane] = Wf[W_U * vs + id];
-                sQ[warp][r][2][lane] = Wf[W_V * vs + id];
-                sQ[warp][r][3][lane] = Wf[W_W * vs + id];
-                sQ[warp][r][4][lane] = Wf[W_P * vs + id];
+                float *q = Q + r * 5 * SQS + pos;
+                q[0 * SQS] = Uf[id];
+                q[1 * SQS] = Wf[W_U * vs + id];
+                q[2 * SQS] = Wf[W_V * vs + id];
+                q[3 * SQS] = Wf[W_W * vs + id];
+                q[4 * SQS] = Wf[W_P * vs + id];
             }
         }
         __syncwarp();
-        if (lane < SEG) {
-            const float r = sQ[warp][4][0][lane + 1], p = sQ[warp][4][4][lane + 1];
-            const float irc = 1.f / r, ipc = 1.f / p;
-            const float iac = rsqrtf((float)P.gamma * p * irc);
-            sM[warp][lane][0] = irc; sA[warp][lane][0] = 1.f;
-            sM[warp][lane][4] = ipc; sA[warp][lane][4] = 1.f;
+        // per-cell scales of the lane's four cells g + 8h (centre row rn = 4)
+        float irc[4], ipc[4], iac[4], ua[4][3];
 #pragma unroll
-            for (int c = 1; c < 4; c++) {
-                sM[warp][lane][c] = iac;
-                sA[warp][lane][c] = sQ[warp][4][c][lane + 1] * iac;
+        for (int h = 0; h < 4; h++) {
+            const float *cq = Q + 4 * 5 * SQS + g + 8 * h + 1;
+            const float r = cq[0], p = cq[4 * SQS];
+            irc[h] = 1.f / r;
+            ipc[h] = 1.f / p;
+            iac[h] = rsqrtf(gam * p * irc[h]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) ua[h][c] = cq[(1 + c) * SQS] * iac[h];
+        }
+        float acc[2][4][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int e = 0; e < 4; e++) acc[mt][nt][e] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < KR / 16; kt++) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int G = 4 * kt + 2 * half + hb;      // (q, rn) group of the lane's columns
+                const int q = G / 9, rn = G - 9 * q;
+                const bool live = G < 45;
+                const float *rowp = Q + (live ? (rn * 5 + q) * SQS : 0) + g + xo;
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const float M = q == 0 ? irc[h] : (q == 4 ? ipc[h] : iac[h]);
+                    const float A = (q == 0 || q == 4) ? 1.f : (q == 1 ? ua[h][0] : (q == 2 ? ua[h][1] : ua[h][2]));
+                    // odd lanes' second column is the zero pad: re-read v0 (stays inside the row)
+                    const float v0 = rowp[8 * h], v1 = rowp[8 * h + (odd ? 0 : 1)];
+                    const float f0 = live ? fmaf(v0, M, -A) : 0.f;
+                    const float f1 = (live && !odd) ? fmaf(v1, M, -A) : 0.f;
+                    a[h >> 1][(h & 1) + 2 * half] = pack2(f0, f1);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const uint32_t b0 = ld32(&S.W1[8 * nt + g][16 * kt + 2 * t]);
+                const uint32_t b1 = ld32(&S.W1[8 * nt + g][16 * kt + 8 + 2 * t]);
+                mma16816(acc[0][nt], a[0], b0, b1);
+                mma16816(acc[1][nt], a[1], b0, b1);
             }
         }
-        __syncwarp();
-        auto feat = [&](int cell, int col) -> float {
-            const unsigned short m = sCol[col];
-            if (m == 0xFFFF || cell >= ncell) return 0.f;
-            const int q = m & 15, di = (m >> 4) & 15, rn = m >> 8;
-            return fmaf(sQ[warp][rn][q][cell + di], sM[warp][cell][q], -sA[warp][cell][q]);
-        };
-        TileOut o;
-        mlp_tile(S, [&](int kt, uint32_t a[4]) {
-            const int c0 = 16 * kt + 2 * t, c1 = c0 + 8;
-            a[0] = pack2(feat(g, c0), feat(g, c0 + 1));
-            a[1] = pack2(feat(g + 8, c0), feat(g + 8, c0 + 1));
-            a[2] = pack2(feat(g, c1), feat(g, c1 + 1));
-            a[3] = pack2(feat(g + 8, c1), feat(g + 8, c1 + 1));
-        }, o);
-        if (t == 0) {
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int ci = g + 8 * h;
-                if (ci < ncell) {
-                    if (flag) flag[base + ci] = o.z[h] > zthresh ? 1 : 0;
-                    if (probs) probs[(row * P.n[0]) + x0 + ci] = 1.f / (1.f + __expf(-o.z[h]));
+        for (int mt = 0; mt < 2; mt++) {
+            float h1[4][4], c2[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    h1[nt][e] = fmaxf(acc[mt][nt][e] + S.b1[8 * nt + 2 * t + (e & 1)], 0.f);
+                    c2[nt][e] = 0.f;
+                }
+#pragma unroll
+            for (int kt = 0; kt < 2; kt++) {
+                const uint32_t a2[4] = {pack2(h1[2 * kt][0], h1[2 * kt][1]), pack2(h1[2 * kt][2], h1[2 * kt][3]),
+                                        pack2(h1[2 * kt + 1][0], h1[2 * kt + 1][1]),
+                                        pack2(h1[2 * kt + 1][2], h1[2 * kt + 1][3])};
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++)
+                    mma16816(c2[nt], a2, ld32(&S.W2[8 * nt + g][16 * kt + 2 * t]),
+                             ld32(&S.W2[8 * nt + g][16 * kt + 8 + 2 * t]));
+            }
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const int col = 8 * nt + 2 * t;
+                s0 += fmaxf(c2[nt][0] + S.b2[col], 0.f) * S.w3[col] + fmaxf(c2[nt][1] + S.b2[col + 1], 0.f) * S.w3[col + 1];
+                s1 += fmaxf(c2[nt][2] + S.b2[col], 0.f) * S.w3[col] + fmaxf(c2[nt][3] + S.b2[col + 1], 0.f) * S.w3[col + 1];
+            }
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+            if (t == 0) {
+                const float z[2] = {s0 + S.b3, s1 + S.b3};
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int ci = 16 * mt + g + 8 * h;
+                    if (ci < ncell) {
+                        if (flag) flag[base + ci] = z[h] > zthresh ? 1 : 0;
+                        if (probs) probs[(row * P.n[0]) + x0 + ci] = 1.f / (1.f + __expf(-z[h]));
+                    }
                 }
             }
         }
@@ -389,7 +460,13 @@ static void pack_weights(const float *w, SensorW &h)
     memset(&h, 0, sizeof(h));
     int o = 0;
     for (int n = 0; n < SH; n++)
-        for (int k = 0; k < SF; k++) h.W1[n][k] = __float2bfloat16_rn(w[o++]);
+        for (int k = 0; k < SF; k++) {
+            // feature k = 5 * (rn * 3 + di + 1) + q  ->  inference column (q * 9 + rn) * 4 + di + 1
+            const int q = k % 5, nb = k / 5, rn = nb / 3, dx = nb % 3;
+            h.W1[n][k] = __float2bfloat16_rn(w[o]);
+            h.W1r[n][(q * 9 + rn) * 4 + dx] = __float2bfloat16_rn(w[o]);
+            o++;
+        }
     for (int n = 0; n < SH; n++) h.b1[n] = w[o++];
     for (int n = 0; n < SH; n++)
         for (int k = 0; k < SH; k++) {
