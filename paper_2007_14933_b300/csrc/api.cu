@@ -490,7 +490,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction
-        if (P.mixed && !general(P) && d == 0) per_stage += 1;   // x segment lefts
+        if (P.mixed && !general(P) && d == 0 && !P.sensor) per_stage += 1;   // x segment lefts
         for (int s = 0; s < 2; s++) {
             const int bc = P.bc[d][s];
             if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;

@@ -1400,10 +1400,278 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
     conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, accumulate, chunk);
 }
 
+// Gated y / z passes (learned sensor on): most interfaces take the central flux, which needs
+// nodes m-1 .. m+2 only.  Each thread keeps those four nodes' FP32 data (hi, lo, u, v, w, p) in
+// registers as it marches, with the pressure and density of m-2 and m+3 for the strong-jump
+// test and the next node prefetched, so every node is loaded once per line instead of once per
+// interface that reads it.  Every interface gets the central D here; an interface that needs the
+// characteristic flux (gate or strong jump) is recorded like a strong jump (flag bit, list, its
+// central D in Dst), and k_patch_fix replaces it (FP32 characteristic flux, or FP64 across a
+// strong jump), the update adding the difference.  The arithmetic of every interface is that of
+// k_conv_char_delta.
+struct NodeW {
+    float h[NV], l[NV], u[3], p;
+};
+
+__device__ __forceinline__ void load_node(const Dev &P, const float *__restrict__ Uf, const float *__restrict__ Wf,
+                                          long long id, NodeW &w)
+{
+    const long long vs = P.vs;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        w.h[v] = Uf[v * vs + id];
+        w.l[v] = Uf[(NV + v) * vs + id];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) w.u[c] = Wf[(W_U + c) * vs + id];
+    w.p = Wf[W_P * vs + id];
+}
+
+// F_k - F_c of node k relative to node c by the product rule (the expressions of node_dflux)
+template <int DIR>
+__device__ __forceinline__ void dflux_w(float gm1, const NodeW &c, const NodeW &k, float dF[NV])
+{
+    float dU[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) dU[v] = (k.h[v] - c.h[v]) + (k.l[v] - c.l[v]);
+    const float irk = __fdividef(1.f, k.h[0]);
+    float du[3], uk[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        du[q] = (dU[1 + q] - c.u[q] * dU[0]) * irk;
+        uk[q] = c.u[q] + du[q];
+    }
+    const float dmu = dU[1] * uk[0] + dU[2] * uk[1] + dU[3] * uk[2] + c.h[1] * du[0] + c.h[2] * du[1] +
+                      c.h[3] * du[2];
+    const float dp = gm1 * (dU[4] - 0.5f * dmu);
+    const float unk = uk[DIR], dun = du[DIR];
+#pragma unroll
+    for (int v = 0; v < NV; v++) dF[v] = unk * dU[v] + dun * c.h[v];
+    dF[1 + DIR] += dp;
+    dF[4] += (c.p + dp) * dun + dp * c.u[DIR];
+}
+
+__device__ __forceinline__ bool jump2(float jump, float p0, float r0, float p1, float r1)
+{
+    return fmaxf(p0, p1) > jump * fminf(p0, p1) || fmaxf(r0, r1) > jump * fminf(r0, r1);
+}
+
+// Tile of the gated y / z passes: 32 lines (lanes along x, coalesced) x TY nodes along DIR, one
+// block of 32 x 8 threads.  The block stages the tile's nodes with a 3-node halo along DIR (FP32
+// hi, lo, u, v, w, p and the gate byte) in shared memory, all loads issued up front; thread
+// (tx, ty) then forms the interfaces of nodes TY/8 * ty .. + TY/8 - 1 of line tx from the staged
+// nodes, and the interface to the left of its first node again (no exchange between threads).
+constexpr int TY = 32;
+constexpr int TYR = TY + 6;         // staged nodes along DIR
+constexpr int TPT = TY / 8;         // nodes per thread
+
+__device__ __forceinline__ void tnode(const float (*sT)[TYR][32], int r, int tx, NodeW &w)
+{
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        w.h[v] = sT[v][r][tx];
+        w.l[v] = sT[NV + v][r][tx];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) w.u[c] = sT[10 + c][r][tx];
+    w.p = sT[13][r][tx];
+}
+
+template <int DIR, int SCHEME>
+__global__ void __launch_bounds__(256, 3) k_conv_delta_tile(Dev P, const float *__restrict__ Uf,
+                                                           const float *__restrict__ Wf, float *__restrict__ Rf,
+                                                           Strong sj, const unsigned char *__restrict__ gate,
+                                                           int accumulate)
+{
+    static_assert(DIR != 0, "x uses k_conv_delta_x_win");
+    constexpr int DB = (DIR == 2) ? 1 : 2;
+    extern __shared__ float smem_tile[];
+    float (*sT)[TYR][32] = reinterpret_cast<float (*)[TYR][32]>(smem_tile);          // [14][TYR][32]
+    unsigned char (*sG)[32] = reinterpret_cast<unsigned char (*)[32]>(smem_tile + 14 * TYR * 32);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = blockIdx.x * 32 + tx;
+    const int b = blockIdx.y;                     // index along DB
+    const int y0 = blockIdx.z * TY;              // first node of the tile along DIR
+    const long long st = P.st[DIR];
+    const long long vs = P.vs;
+    const bool xin = x < P.n[0];
+    int ii[3];
+    ii[0] = xin ? x : 0; ii[DB] = b; ii[DIR] = 0;
+    const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const int n = P.n[DIR];
+    // stage nodes y0 - 3 .. y0 + TY + 2 (clamped to the last ghost n + 2)
+    for (int r = ty; r < TYR; r += 8) {
+        const int y = min(y0 - 3 + r, n + 2);
+        const long long id = base + (long long)y * st;
+        if (xin) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                sT[v][r][tx] = Uf[v * vs + id];
+                sT[NV + v][r][tx] = Uf[(NV + v) * vs + id];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) sT[10 + c][r][tx] = Wf[(W_U + c) * vs + id];
+            sT[13][r][tx] = Wf[W_P * vs + id];
+            sG[r][tx] = gate[id];
+        }
+    }
+    __syncthreads();
+    if (!xin) return;
+    const float gm1 = (float)P.gm1;
+    const float jump = P.jump;
+    const int first = y0 + TPT * ty;             // first node of this thread
+    if (first >= n) return;
+    const int last = min(first + TPT, n);        // one past the last node
+    // staged row of node y is y - (y0 - 3); interface y lies between nodes y and y + 1
+    int r = first - 1 - (y0 - 3);
+    float Dm[NV];
+    for (int y = first - 1; y < last; y++, r++) {
+        bool cha = sG[r][tx] || sG[r + 1][tx];
+#pragma unroll
+        for (int q = -2; q < 3; q++)
+            cha = cha || jump2(jump, sT[13][r + q][tx], sT[0][r + q][tx], sT[13][r + q + 1][tx], sT[0][r + q + 1][tx]);
+        NodeW c, k;
+        tnode(sT, r, tx, c);
+        float D[NV], d1[NV], fp1[NV], fp2[NV];
+        tnode(sT, r - 1, tx, k);
+        dflux_w<DIR>(gm1, c, k, d1);
+        tnode(sT, r + 1, tx, k);
+        dflux_w<DIR>(gm1, c, k, fp1);
+        tnode(sT, r + 2, tx, k);
+        dflux_w<DIR>(gm1, c, k, fp2);
+#pragma unroll
+        for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
+        const long long m = base + (long long)y * st;
+        // the interface left of a thread's first node is recorded by the thread (or tile) owning
+        // the node to its left, except the line's first interface
+        if (cha && (y >= first || y < 0)) {
+            sj.flag[m] |= (unsigned char)(1u << DIR);
+            const int kk = atomicAdd(sj.count + DIR, 1);
+            if (kk < sj.cap) sj.list[(long long)DIR * sj.cap + kk] = m;
+            float *Ds = sj.Dst + (long long)DIR * NV * vs;
+#pragma unroll
+            for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
+        }
+        if (y >= first) {
+            const float fac = line_facf<DIR>(P, y);
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
+                Rf[v * vs + m] = accumulate ? Rf[v * vs + m] + rr : rr;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) Dm[v] = D[v];
+    }
+}
+
+constexpr size_t TILE_SMEM = (size_t)14 * TYR * 32 * sizeof(float) + (size_t)TYR * 32;
+
+// Gated x pass: one block per row segment of XSEG nodes stages the segment's nodes with a
+// 3-node halo (FP32 hi, lo, u, v, w, p) in shared memory with coalesced loads; thread t forms the
+// central D of interface x0 + t (thread 0 also x0 - 1) from the staged nodes and records the
+// interfaces that need the characteristic flux for k_patch_fix, as the gated y / z passes do.
+constexpr int XSEG = 256;   // x segment length of the x passes
+constexpr int XH = 3;
+constexpr int XNS = XSEG + 2 * XH;
+
+__device__ __forceinline__ void snode(const float (*sN)[XNS], int p, NodeW &w)
+{
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        w.h[v] = sN[v][p];
+        w.l[v] = sN[NV + v][p];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) w.u[c] = sN[10 + c][p];
+    w.p = sN[13][p];
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(256) k_conv_delta_x_win(Dev P, const float *__restrict__ Uf,
+                                                         const float *__restrict__ Wf, float *__restrict__ Rf,
+                                                         Strong sj, const unsigned char *__restrict__ gate,
+                                                         int accumulate)
+{
+    static_assert(XSEG == 256, "staging assumes 256-node segments");
+    __shared__ float sN[14][XNS];
+    __shared__ float sD[NV][XSEG + 1];
+    const int row = blockIdx.x;
+    const int j = row % P.n[1], k = row / P.n[1];
+    const int x0 = blockIdx.y * XSEG;
+    const int t = threadIdx.x;
+    const long long base = node_index(P, 0, j, k);
+    const long long vs = P.vs;
+    for (int pos = t; pos < XNS; pos += XSEG) {
+        const int x = x0 - XH + pos;
+        if (x > P.n[0] + 2) continue;               // beyond the row's last ghost: never read
+        const long long id = base + x;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            sN[v][pos] = Uf[v * vs + id];
+            sN[NV + v][pos] = Uf[(NV + v) * vs + id];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) sN[10 + c][pos] = Wf[(W_U + c) * vs + id];
+        sN[13][pos] = Wf[W_P * vs + id];
+    }
+    __syncthreads();
+    const float gm1 = (float)P.gm1;
+    const float jump = P.jump;
+    const int ncell = min(XSEG, P.n[0] - x0);
+    float d1[NV];
+    for (int pass = 0; pass < (t == 0 ? 2 : 1); pass++) {
+        // pass 0: interface x0 + t (between nodes x0 + t and x0 + t + 1); pass 1: x0 - 1
+        const int i = pass == 0 ? x0 + t : x0 - 1;
+        if (pass == 0 && t >= ncell) break;
+        const int p = i - (x0 - XH);
+        NodeW w0, w1, w2, w3;
+        snode(sN, p - 1, w0);
+        snode(sN, p, w1);
+        snode(sN, p + 1, w2);
+        snode(sN, p + 2, w3);
+        const bool cha = jump2(jump, sN[13][p - 2], sN[0][p - 2], w0.p, w0.h[0]) ||
+                         jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                         jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                         jump2(jump, w3.p, w3.h[0], sN[13][p + 3], sN[0][p + 3]) || gate[base + i] ||
+                         gate[base + i + 1];
+        float D[NV], dl[NV], fp1[NV], fp2[NV];
+        dflux_w<0>(gm1, w1, w0, dl);
+        dflux_w<0>(gm1, w1, w2, fp1);
+        dflux_w<0>(gm1, w1, w3, fp2);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            D[v] = (7.f * fp1[v] - dl[v] - fp2[v]) * (1.f / 12.f);
+            sD[v][pass == 0 ? t + 1 : 0] = D[v];
+        }
+        if (pass == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) d1[v] = dl[v];
+        }
+        if (cha && (pass == 0 || x0 == 0)) {        // x0 - 1 belongs to the previous segment
+            const long long m = base + i;
+            sj.flag[m] |= (unsigned char)1u;
+            const int kk = atomicAdd(sj.count, 1);
+            if (kk < sj.cap) sj.list[kk] = m;
+            float *Ds = sj.Dst;
+#pragma unroll
+            for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
+        }
+    }
+    __syncthreads();
+    if (t >= ncell) return;
+    const float fac = line_facf<0>(P, x0 + t);
+    const long long id = base + x0 + t;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        const float r = -fac * ((sD[v][t + 1] - sD[v][t]) - d1[v]);
+        Rf[v * vs + id] = accumulate ? Rf[v * vs + id] + r : r;
+    }
+}
+
 // x: thread per interface along a row segment of up to XSEG nodes (lanes along x, coalesced);
 // the flux difference takes the left neighbour's D from shared memory.  The segment's leftmost
 // interface comes from k_conv_left_x, so every thread forms exactly one interface.
-constexpr int XSEG = 256;
 
 template <int SCHEME>
 __device__ __forceinline__ void conv_left_x_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
@@ -1480,21 +1748,26 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
     conv_char_delta_x_body<SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, Dl, accumulate);
 }
 
-// FP64 recomputation of one flagged interface m of direction DIR: Dst (plane set DIR) receives
-// the correction D64 - D32 in place of the FP32 value.
+// Recomputation of one flagged interface m of direction DIR: across a strong jump the FP64
+// characteristic flux, otherwise (an interface the gated pass gave the central flux) the FP32
+// characteristic flux.  Dst (plane set DIR) receives the correction D_new - D_pass in place of
+// the D the convective pass used.
 template <int DIR, int SCHEME>
-__device__ __forceinline__ void fix_interface(const Dev &P, const double *__restrict__ U, float *__restrict__ Dst,
-                                              long long m)
+__device__ __noinline__ void fix_interface(const Dev &P, const double *__restrict__ U,
+                                           const float *__restrict__ Uf, const float *__restrict__ Wf,
+                                           float *__restrict__ Dst, long long m)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
     const long long pa = m % P.np[0], q = m / P.np[0];
     const int c3[3] = {(int)pa - P.g[0], (int)(q % P.np[1]) - P.g[1], (int)(q / P.np[1]) - P.g[2]};
     const double es = line_eps<DIR>(P, c3[DA], c3[DB]);
-    float D64[NV], unused[NV];
-    fallback_delta<DIR, SCHEME>(P, U, m, P.st[DIR], es, D64, unused);
+    const long long st = P.st[DIR];
+    float Dn[NV], unused[NV];
+    if (strong_jump(P, Uf, Wf, m, st)) fallback_delta<DIR, SCHEME>(P, U, m, st, es, Dn, unused);
+    else delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, (float)es, Dn, unused);
     float *Ds = Dst + (long long)DIR * NV * P.vs;
 #pragma unroll
-    for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D64[v] - Ds[v * P.vs + m];
+    for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = Dn[v] - Ds[v * P.vs + m];
 }
 
 // All directions' flagged interfaces of the stage, one thread per listed interface.  A direction
@@ -1503,6 +1776,7 @@ __device__ __forceinline__ void fix_interface(const Dev &P, const double *__rest
 // also its left one.
 template <int SCHEME>
 __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, const double *__restrict__ U,
+                                               const float *__restrict__ Uf, const float *__restrict__ Wf,
                                                Strong sj)
 {
     const int c0 = sj.count[0], c1 = sj.count[1], c2 = sj.count[2];
@@ -1511,9 +1785,9 @@ __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, cons
     const long long stride = (long long)bk.nx * blockDim.x;
     const long long t0 = bk.x * (long long)blockDim.x + threadIdx.x;
     for (long long t = t0; t < (long long)l0 + l1 + l2; t += stride) {
-        if (t < l0) fix_interface<0, SCHEME>(P, U, sj.Dst, sj.list[t]);
-        else if (t < l0 + l1) fix_interface<1, SCHEME>(P, U, sj.Dst, sj.list[(long long)sj.cap + (t - l0)]);
-        else fix_interface<2, SCHEME>(P, U, sj.Dst, sj.list[2LL * sj.cap + (t - l0 - l1)]);
+        if (t < l0) fix_interface<0, SCHEME>(P, U, Uf, Wf, sj.Dst, sj.list[t]);
+        else if (t < l0 + l1) fix_interface<1, SCHEME>(P, U, Uf, Wf, sj.Dst, sj.list[(long long)sj.cap + (t - l0)]);
+        else fix_interface<2, SCHEME>(P, U, Uf, Wf, sj.Dst, sj.list[2LL * sj.cap + (t - l0 - l1)]);
     }
     if (c0 <= sj.cap && c1 <= sj.cap && c2 <= sj.cap) return;
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -1524,24 +1798,25 @@ __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, cons
         const long long id = node_index(P, ijk[0], ijk[1], ijk[2]);
         const unsigned char f = sj.flag[id];
         if (c0 > sj.cap) {
-            if (f & 1) fix_interface<0, SCHEME>(P, U, sj.Dst, id);
-            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME>(P, U, sj.Dst, id - P.st[0]);
+            if (f & 1) fix_interface<0, SCHEME>(P, U, Uf, Wf, sj.Dst, id);
+            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME>(P, U, Uf, Wf, sj.Dst, id - P.st[0]);
         }
         if (c1 > sj.cap) {
-            if (f & 2) fix_interface<1, SCHEME>(P, U, sj.Dst, id);
-            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME>(P, U, sj.Dst, id - P.st[1]);
+            if (f & 2) fix_interface<1, SCHEME>(P, U, Uf, Wf, sj.Dst, id);
+            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME>(P, U, Uf, Wf, sj.Dst, id - P.st[1]);
         }
         if (c2 > sj.cap) {
-            if (f & 4) fix_interface<2, SCHEME>(P, U, sj.Dst, id);
-            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME>(P, U, sj.Dst, id - P.st[2]);
+            if (f & 4) fix_interface<2, SCHEME>(P, U, Uf, Wf, sj.Dst, id);
+            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME>(P, U, Uf, Wf, sj.Dst, id - P.st[2]);
         }
     }
 }
 
 template <int SCHEME>
-__global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restrict__ U, Strong sj)
+__global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restrict__ U, const float *__restrict__ Uf,
+                                                   const float *__restrict__ Wf, Strong sj)
 {
-    patch_fix_body<SCHEME>(P, self_blk(), U, sj);
+    patch_fix_body<SCHEME>(P, self_blk(), U, Uf, Wf, sj);
 }
 
 int conv_chunk(const Dev &P, int d);
@@ -1733,13 +2008,28 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
 {
     const unsigned char *gate = P.sensor ? B.gate : nullptr;
     if (P.mixed && !CURV) {
-        if (DIR == 0) {
+        if (DIR == 0 && gate) {
+            dim3 g(P.n[1] * P.n[2], (P.n[0] + XSEG - 1) / XSEG);
+            k_conv_delta_x_win<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, acc);
+        } else if (DIR == 0) {
             const int nseg = (P.n[0] + XSEG - 1) / XSEG;
             const long long lefts = (long long)P.n[1] * P.n[2] * nseg;
             k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, strong_of(B), gate,
                                                                              B.Dl);
             dim3 g(P.n[1] * P.n[2], nseg);
             k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, B.Dl, acc);
+        } else if (gate) {
+          if constexpr (DIR != 0) {
+            static bool smem_set = false;   // one attribute call per instantiation
+            if (!smem_set) {
+                cudaFuncSetAttribute(k_conv_delta_tile<DIR, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TILE_SMEM);
+                smem_set = true;
+            }
+            dim3 tg((P.n[0] + 31) / 32, P.n[DIR == 2 ? 1 : 2], (P.n[DIR] + TY - 1) / TY);
+            k_conv_delta_tile<DIR, SCHEME><<<tg, dim3(32, 8), TILE_SMEM, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B),
+                                                                            gate, acc);
+          }
         } else {
             k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, acc, chunk);
         }
@@ -1798,8 +2088,8 @@ static void launch_patch(const Dev &P, const Bufs &B, cudaStream_t s)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const int g = grid_for(N, 128);
-    if (P.scheme == SCH_WENO5JS) k_patch_fix<SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, strong_of(B));
-    else k_patch_fix<SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, strong_of(B));
+    if (P.scheme == SCH_WENO5JS) k_patch_fix<SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    else k_patch_fix<SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
 }
 
 // Optional per-launch event taps (kernel timing): before each launch an event is recorded and
@@ -1849,7 +2139,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         else conv_dir<2>(P, B, acc, s);
         acc = 1;
         launches++;
-        if (patch && d == 0) launches++;   // the x segments' left interfaces
+        if (patch && d == 0 && !P.sensor) launches++;   // the x segments' left interfaces
     }
     if (patch) {   // FP64 recomputation of the stage's strong-jump interfaces (applied by the update)
         if (tap) (*tap)("patch", s);
@@ -2025,7 +2315,7 @@ template <int SCHEME>
 __global__ void __launch_bounds__(128) k_ens_fix(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(ENS_FIX)
-    patch_fix_body<SCHEME>(P, bk, B.U, strong_of(B));
+    patch_fix_body<SCHEME>(P, bk, B.U, B.Uf, B.Wf, strong_of(B));
 }
 
 template <int STAGE>
