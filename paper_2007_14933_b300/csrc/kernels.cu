@@ -1377,6 +1377,10 @@ __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk
     delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, es, Dm, dF1, sj, s0 == 0, gate);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
+        // the residual of the earlier directions, loaded before the interface arithmetic
+        float racc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) racc[v] = accumulate ? Rf[v * P.vs + id] : 0.f;
         float Dp[NV];
         delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, sj, true, gate);
         const float fac = line_facf<DIR>(P, m);
@@ -1384,7 +1388,7 @@ __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk
         for (int v = 0; v < NV; v++) {
             // F_{m+1/2} - F_{m-1/2} = (F_m - F_{m-1}) + D_{m+1/2} - D_{m-1/2}
             const float r = -fac * ((Dp[v] - Dm[v]) - dF1[v]);
-            Rf[v * P.vs + id] = accumulate ? Rf[v * P.vs + id] + r : r;
+            Rf[v * P.vs + id] = accumulate ? racc[v] + r : r;
             Dm[v] = Dp[v];
         }
     }
@@ -1456,6 +1460,18 @@ __device__ __forceinline__ bool jump2(float jump, float p0, float r0, float p1, 
     return fmaxf(p0, p1) > jump * fminf(p0, p1) || fmaxf(r0, r1) > jump * fminf(r0, r1);
 }
 
+// Asynchronous 4-byte global -> shared copy (no register staging, so a thread can have all of
+// its tile's copies in flight at once), and the wait for the thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Tile of the gated y / z passes: 32 lines (lanes along x, coalesced) x TY nodes along DIR, one
 // block of 32 x 8 threads.  The block stages the tile's nodes with a 3-node halo along DIR (FP32
 // hi, lo, u, v, w, p and the gate byte) in shared memory, all loads issued up front; thread
@@ -1505,23 +1521,28 @@ __global__ void __launch_bounds__(256, 3) k_conv_delta_tile(Dev P, const float *
         const long long id = base + (long long)y * st;
         if (xin) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) {
-                sT[v][r][tx] = Uf[v * vs + id];
-                sT[NV + v][r][tx] = Uf[(NV + v) * vs + id];
-            }
+            for (int v = 0; v < 2 * NV; v++) cp_async4(&sT[v][r][tx], Uf + v * vs + id);
 #pragma unroll
-            for (int c = 0; c < 3; c++) sT[10 + c][r][tx] = Wf[(W_U + c) * vs + id];
-            sT[13][r][tx] = Wf[W_P * vs + id];
+            for (int c = 0; c < 4; c++) cp_async4(&sT[10 + c][r][tx], Wf + (W_U + c) * vs + id);
             sG[r][tx] = gate[id];
         }
     }
+    // the residual this pass adds to (earlier directions), for the thread's nodes: loaded now so
+    // that its latency overlaps the staging copies
+    const int first = y0 + TPT * ty;             // first node of this thread
+    const int last = min(first + TPT, n);        // one past the last node
+    float racc[TPT][NV];
+#pragma unroll
+    for (int q = 0; q < TPT; q++)
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+            racc[q][v] = (accumulate && xin && first + q < last) ? Rf[v * vs + base + (long long)(first + q) * st] : 0.f;
+    cp_async_wait_all();
     __syncthreads();
     if (!xin) return;
     const float gm1 = (float)P.gm1;
     const float jump = P.jump;
-    const int first = y0 + TPT * ty;             // first node of this thread
     if (first >= n) return;
-    const int last = min(first + TPT, n);        // one past the last node
     // staged row of node y is y - (y0 - 3); interface y lies between nodes y and y + 1
     int r = first - 1 - (y0 - 3);
     float Dm[NV];
@@ -1554,10 +1575,14 @@ __global__ void __launch_bounds__(256, 3) k_conv_delta_tile(Dev P, const float *
         }
         if (y >= first) {
             const float fac = line_facf<DIR>(P, y);
+            const int q = y - first;
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
-                Rf[v * vs + m] = accumulate ? Rf[v * vs + m] + rr : rr;
+                float acc = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
+                Rf[v * vs + m] = accumulate ? acc + rr : rr;
             }
         }
 #pragma unroll
@@ -1607,14 +1632,11 @@ __global__ void __launch_bounds__(256) k_conv_delta_x_win(Dev P, const float *__
         if (x > P.n[0] + 2) continue;               // beyond the row's last ghost: never read
         const long long id = base + x;
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-            sN[v][pos] = Uf[v * vs + id];
-            sN[NV + v][pos] = Uf[(NV + v) * vs + id];
-        }
+        for (int v = 0; v < 2 * NV; v++) cp_async4(&sN[v][pos], Uf + v * vs + id);
 #pragma unroll
-        for (int c = 0; c < 3; c++) sN[10 + c][pos] = Wf[(W_U + c) * vs + id];
-        sN[13][pos] = Wf[W_P * vs + id];
+        for (int c = 0; c < 4; c++) cp_async4(&sN[10 + c][pos], Wf + (W_U + c) * vs + id);
     }
+    cp_async_wait_all();
     __syncthreads();
     const float gm1 = (float)P.gm1;
     const float jump = P.jump;
