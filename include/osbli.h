@@ -45,7 +45,10 @@ enum {
 };
 
 /* convective scheme (Sec. 2.2-2.6) */
-enum { OSBLI_CENTRAL4 = 0, OSBLI_WENO5JS = 1, OSBLI_TENO5 = 2 };
+enum { OSBLI_CENTRAL4 = 0, OSBLI_WENO5JS = 1, OSBLI_TENO5 = 2, OSBLI_WENO5Z = 3 };
+/* time integrator (Sec. 2.8, Eqs. 36-38): low-storage 2N Runge-Kutta, 3rd order in 3 stages
+ * (Williamson) or 4th order in 5 stages (Carpenter & Kennedy) */
+enum { OSBLI_RK3 = 0, OSBLI_RK4 = 1 };
 
 /* boundary conditions per direction and side (Sec. 3.1.3, Sec. 5-6 set-ups):
  *   PERIODIC   both sides of a direction must be periodic together
@@ -68,16 +71,18 @@ typedef struct {
                                   one >= 3 */
     double gamma, Re, Pr, Ma;  /* Re <= 0: inviscid (no viscous / heat-flux terms) */
     double dt;                 /* fixed time step */
-    int scheme;                /* OSBLI_CENTRAL4 | OSBLI_WENO5JS | OSBLI_TENO5 */
+    int scheme;                /* OSBLI_CENTRAL4 | OSBLI_WENO5JS | OSBLI_TENO5 | OSBLI_WENO5Z (Eq. 22) */
     double teno_ct;            /* TENO cut-off C_T (Eq. 24), e.g. 1e-5 */
     int bc[3][2];              /* bc[direction][side], side 0 = low index */
     double T_wall;             /* isothermal wall temperature (Eq. 41) */
     double sutherland_ratio;   /* T_s/T_ref of Eq. 6; <= 0: constant mu = 1 */
     int precision;             /* OSBLI_FP64 | OSBLI_MIXED */
-    int sensor;                /* 1: learned shock sensor gates TENO vs central fluxes (precision
-                                  OSBLI_MIXED, WENO5-JS/TENO5, uniform grid); 0: off */
+    int sensor;                /* 1: learned shock sensor gates the characteristic vs central
+                                  fluxes (precision OSBLI_MIXED, a WENO/TENO scheme, uniform or
+                                  rectilinear grid); 0: off */
     double h[3];               /* grid spacing per direction when coords == NULL */
     double L[3];               /* period of each periodic direction (coordinate unwrapping) */
+    int rk;                    /* OSBLI_RK3 (3 stages, default) | OSBLI_RK4 (5 stages) */
 } osbli_params;
 
 /* Create a solver for one grid.  coords: NULL (uniform grid, spacing h) or node coordinates of

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "osbli_oracle.c")
 _LIB = os.path.join(_HERE, "libosbli_oracle.so")
 
-CENTRAL4, WENO5JS, TENO5 = 0, 1, 2
+CENTRAL4, WENO5JS, TENO5, WENO5Z = 0, 1, 2, 3
 PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW = 0, 1, 2, 3, 4
 
 
@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("L", ctypes.c_double * 3),
         ("coords", ctypes.c_void_p),
         ("bdata", ctypes.c_void_p * 6),
+        ("rk", ctypes.c_int),
     ]
 
 
@@ -89,6 +90,7 @@ def lib():
         L.orc_char_flux_1d.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_rk3_linear.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int, _D, _D]
+        L.orc_rk_linear.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.c_int, _D, _D]
         L.orc_deriv4.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.orc_deriv4.restype = ctypes.c_double
         L.orc_sutherland.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -142,6 +144,7 @@ class Oracle:
         P.dt = cfg.get("dt", 0.0)
         P.scheme = int(cfg.get("scheme", TENO5))
         P.teno_ct = cfg.get("teno_ct", 1e-5)
+        P.rk = int(cfg.get("rk", 0))
         P.T_wall = cfg.get("T_wall", 1.0)
         P.suth = cfg.get("suth", 0.0)
         self._keep = []
@@ -275,9 +278,13 @@ def char_flux_1d(gamma, scheme, ct, U6, S):
 
 
 def rk3_linear(lam, dt, nsteps, y0=1.0 + 0j):
+    return rk_linear(0, lam, dt, nsteps, y0)
+
+
+def rk_linear(rk, lam, dt, nsteps, y0=1.0 + 0j):
     yr = ctypes.c_double(y0.real)
     yi = ctypes.c_double(y0.imag)
-    lib().orc_rk3_linear(lam.real, lam.imag, dt, int(nsteps), ctypes.byref(yr), ctypes.byref(yi))
+    lib().orc_rk_linear(int(rk), lam.real, lam.imag, dt, int(nsteps), ctypes.byref(yr), ctypes.byref(yi))
     return complex(yr.value, yi.value)
 
 

@@ -39,14 +39,14 @@
 #define NV 5
 #define GH 3
 
-enum { ORC_CENTRAL4 = 0, ORC_WENO5JS = 1, ORC_TENO5 = 2 };
+enum { ORC_CENTRAL4 = 0, ORC_WENO5JS = 1, ORC_TENO5 = 2, ORC_WENO5Z = 3 };
 enum { ORC_PERIODIC = 0, ORC_ZEROGRAD = 1, ORC_WALL = 2, ORC_DIRICHLET = 3, ORC_INFLOW = 4 };
 
 typedef struct {
     int n[3];              /* interior points per direction, 1 = inactive */
     double gamma, Re, Pr, Ma;  /* Re <= 0: inviscid */
     double dt;
-    int scheme;            /* ORC_CENTRAL4 | ORC_WENO5JS | ORC_TENO5 */
+    int scheme;            /* ORC_CENTRAL4 | ORC_WENO5JS | ORC_TENO5 | ORC_WENO5Z */
     double teno_ct;        /* TENO cut-off C_T */
     int bc[3][2];          /* per direction, side */
     double T_wall;         /* isothermal wall temperature */
@@ -55,6 +55,7 @@ typedef struct {
     double L[3];           /* period of each periodic direction for given coords (uniform grid: n*h) */
     const double *coords;  /* [3][nz][ny][nx] physical coordinates or NULL */
     const double *bdata[6];/* face 2*d+s: [5][plane] Dirichlet (rho,u,v,w,p) or inflow (-,u,v,w,T) */
+    int rk;                /* 0: 3-stage RK3, 1: 5-stage RK4 (both low-storage 2N) */
 } orc_params;
 
 typedef struct {
@@ -158,14 +159,27 @@ void orc_smoothness5(const double *f, double *beta)
     beta[2] = (13.0 / 12.0) * a * a + 0.25 * b * b;
 }
 
-/* Nonlinear weights.  WENO-JS: Eqs. 20-21 (p = 2, eps = 1e-6).  TENO5: Eqs. 23-27
+/* Nonlinear weights.  WENO-JS: Eqs. 20-21 (p = 2, eps = 1e-6).  WENO-Z: Eq. 22 with
+ * sigma_r = beta_r, tau = |beta_0 - beta_2|, eps = 1e-16, alpha_r = d_r (1 + (tau / (beta_r +
+ * eps))^2).  TENO5: Eqs. 23-27
  * (C = 1, q = 6, eps = 1e-16, tau_5 = |beta_0 - beta_2|, cut-off C_T).  Returns in *margin the
  * smallest |chi_r - C_T|/C_T (TENO only; used to recognise cut-off decisions that sit on the
  * threshold within rounding). */
 void orc_weights5(const double *beta, int scheme, double ct, double *w, double *margin)
 {
     init_coeffs();
-    if (scheme == ORC_WENO5JS) {
+    if (scheme == ORC_WENO5Z) {
+        const double eps = 1e-16;
+        const double tau = fabs(beta[0] - beta[2]);
+        double a[3], s = 0.0;
+        for (int r = 0; r < 3; r++) {
+            const double x = tau / (beta[r] + eps);
+            a[r] = D3[r] * (1.0 + x * x);
+            s += a[r];
+        }
+        for (int r = 0; r < 3; r++) w[r] = a[r] / s;
+        if (margin) *margin = INFINITY;
+    } else if (scheme == ORC_WENO5JS) {
         const double eps = 1e-6;
         double a[3], s = 0.0;
         for (int r = 0; r < 3; r++) {
@@ -1090,39 +1104,50 @@ void orc_labels(void *h, unsigned char *labels)
 }
 
 /* ------------------------------------------------------------------------------------------
- * Low-storage RK3 (Eqs. 36-38).  The paper does not print A_i, B_i; Williamson's 3-stage 2N
- * scheme is used: A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  dU^(0) = 0 each step.
+ * Low-storage 2N Runge-Kutta (Eqs. 36-38): dU = A_i dU + dt R(U), U = U + B_i dU, dU^(0) = 0
+ * each step.  The paper does not print A_i, B_i.  rk = 0: Williamson's 3-stage 3rd-order
+ * scheme, A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  rk = 1: the 5-stage 4th-order 2N
+ * scheme of Carpenter & Kennedy (1994, the paper's cited reference for its 4th-order
+ * low-storage RK), their published rational coefficients.
  * ------------------------------------------------------------------------------------------ */
-static const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
-static const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+static const int RK_STAGES[2] = {3, 5};
+static const double RK_A[2][5] = {{0.0, -5.0 / 9.0, -153.0 / 128.0, 0.0, 0.0},
+                                  {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0, -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0}};
+static const double RK_B[2][5] = {{1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0, 0.0, 0.0},
+                                  {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0, 1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0, 2277821191437.0 / 14882151754819.0}};
 
 /* one stage of the 2N register update on n values (shared by the solver and the pins) */
-static void rk_stage_update(int stage, double dt, long n, double *U, double *dU, const double *R)
+static void rk_stage_update(int rk, int stage, double dt, long n, double *U, double *dU, const double *R)
 {
     for (long q = 0; q < n; q++) {
-        dU[q] = RK_A[stage] * dU[q] + dt * R[q];
-        U[q] = U[q] + RK_B[stage] * dU[q];
+        dU[q] = RK_A[rk][stage] * dU[q] + dt * R[q];
+        U[q] = U[q] + RK_B[rk][stage] * dU[q];
     }
 }
 
 /* Scalar test equation y' = lambda y, lambda = lr + i li, advanced nsteps with the same stage
  * update as the solver; y stored as the real 2-vector (Re y, Im y). */
-void orc_rk3_linear(double lr, double li, double dt, int nsteps, double *yr, double *yi)
+void orc_rk_linear(int rk, double lr, double li, double dt, int nsteps, double *yr, double *yi)
 {
     double U[2] = {*yr, *yi}, dU[2], R[2];
     for (int n = 0; n < nsteps; n++) {
         dU[0] = 0.0; dU[1] = 0.0;
-        for (int s = 0; s < 3; s++) {
+        for (int s = 0; s < RK_STAGES[rk]; s++) {
             R[0] = lr * U[0] - li * U[1];
             R[1] = li * U[0] + lr * U[1];
-            rk_stage_update(s, dt, 2, U, dU, R);
+            rk_stage_update(rk, s, dt, 2, U, dU, R);
         }
     }
     *yr = U[0];
     *yi = U[1];
 }
 
-/* Advance nsteps RK3 steps.  Returns 0, or -1 when a non-finite value appears. */
+void orc_rk3_linear(double lr, double li, double dt, int nsteps, double *yr, double *yi)
+{
+    orc_rk_linear(0, lr, li, dt, nsteps, yr, yi);
+}
+
+/* Advance nsteps RK steps (P->rk).  Returns 0, or -1 when a non-finite value appears. */
 int orc_step(void *h, int nsteps)
 {
     orc_ctx *c = (orc_ctx *)h;
@@ -1134,10 +1159,11 @@ int orc_step(void *h, int nsteps)
     int rc = 0;
     for (int n = 0; n < nsteps && rc == 0; n++) {
         for (long q = 0; q < NV * plane; q++) dUi[q] = 0.0;
-        for (int s = 0; s < 3; s++) {
+        const int rk = (P->rk == 1) ? 1 : 0;
+        for (int s = 0; s < RK_STAGES[rk]; s++) {
             orc_residual(c, Ri, NULL);
             orc_get_state(c, Ui);
-            rk_stage_update(s, P->dt, NV * plane, Ui, dUi, Ri);
+            rk_stage_update(rk, s, P->dt, NV * plane, Ui, dUi, Ri);
             orc_set_state(c, Ui);
             impose_boundary_nodes(c);
         }

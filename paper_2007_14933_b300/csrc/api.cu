@@ -110,7 +110,7 @@ static int validate(const osbli_params *p, const double *coords)
     }
     if ((long long)n[0] * n[1] * n[2] > (1LL << 31))
         return seterr(nullptr, OSBLI_EINVAL, "grid larger than 2^31 points");
-    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_TENO5)
+    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_WENO5Z)
         return seterr(nullptr, OSBLI_EINVAL, "scheme %d unknown", p->scheme);
     if (!(p->gamma > 1.0) || !(p->Ma > 0.0))
         return seterr(nullptr, OSBLI_EINVAL, "need gamma > 1 and Ma > 0");
@@ -121,8 +121,9 @@ static int validate(const osbli_params *p, const double *coords)
     if (p->precision != OSBLI_FP64 && p->precision != OSBLI_MIXED)
         return seterr(nullptr, OSBLI_EINVAL, "precision %d unknown", p->precision);
     if (p->precision == OSBLI_MIXED && p->scheme == OSBLI_CENTRAL4)
-        return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / TENO5");
+        return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / WENO-Z / TENO5");
     if (p->sensor != 0 && p->sensor != 1) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0 or 1");
+    if (p->rk != OSBLI_RK3 && p->rk != OSBLI_RK4) return seterr(nullptr, OSBLI_EINVAL, "rk %d unknown", p->rk);
     if (p->sensor == 1 && (p->precision != OSBLI_MIXED || p->scheme == OSBLI_CENTRAL4))
         return seterr(nullptr, OSBLI_EINVAL, "the learned sensor gates the mixed-precision WENO/TENO path");
     for (int d = 0; d < 3; d++)
@@ -174,6 +175,8 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     P.dt = p->dt;
     P.mixed = p->precision == OSBLI_MIXED;
     P.sensor = p->sensor == 1;
+    P.rk = p->rk;
+    P.nstage = p->rk == OSBLI_RK4 ? 5 : 3;
     P.jump = 1.5f;
     if (!P.curv) {
         double hh[3];
@@ -386,7 +389,7 @@ extern "C" int osbli_rk_step(osbli_t *h, int nsteps)
         cudaGraph_t g = nullptr;
         CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         int launches = 0;
-        for (int s = 0; s < 3; s++) launches += launch_stage(h->P, h->B, s, h->stream);
+        for (int s = 0; s < h->P.nstage; s++) launches += launch_stage(h->P, h->B, s, h->stream);
         cudaError_t le = cudaGetLastError();
         cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -497,7 +500,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
         }
     }
     if (P.viscous) per_stage++;
-    return 3 * per_stage;
+    return P.nstage * per_stage + (P.sensor ? 2 : 0);
 }
 
 extern "C" const char *osbli_last_error(const osbli_t *h)

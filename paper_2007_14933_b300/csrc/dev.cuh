@@ -18,7 +18,7 @@ constexpr int NV = 5;
 constexpr int GH = 3;   // ghost width: WENO5/TENO5 stencil i-2..i+3 (Sec. 2.3-2.5)
 
 enum { W_U = 0, W_V, W_W, W_P, W_A, W_SR, W_H, W_T, NW };
-enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2 };
+enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2, SCH_WENO5Z = 3 };
 enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4 };
 
 struct Dev {
@@ -37,6 +37,7 @@ struct Dev {
     int mixed;         // OSBLI_MIXED: FP32 reconstruction arithmetic
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
     int sensor;        // learned gate active (mixed path, Cartesian or rectilinear grids)
+    int rk, nstage;    // time integrator: 0 RK3 (3 stages), 1 RK4 (5 stages), low-storage 2N
     int rect;          // rectilinear grid: Cartesian kernels with per-line factors lfac
     const double *lfac[3];   // rect: S_dd / Jinv of each line position along direction d
     const double *lesc[3];   // rect: 1 / |S~_d|^2 of each line of direction d ([n_DB][n_DA])
@@ -133,6 +134,8 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // Candidates (Eq. 14, k = 3; the ENO coefficients of the cited Shu 1997 notes), Jiang-Shu
 // smoothness indicators (Eqs. 17-19, as printed), and
 //   WENO-JS weights (Eqs. 20-21, p = 2, eps = 1e-6), linear weights d = (3/10, 3/5, 1/10);
+//   WENO-Z (Eq. 22): alpha_r = d_r (1 + (tau5/(beta_r + eps))^2), tau5 = |beta_0 - beta_2|,
+//   eps = 1e-16 (FP64; FP32: the TENO rescaling below);
 //   TENO5 (Eqs. 23-27): gamma_r = (1 + tau5/(beta_r + eps))^6, tau5 = |beta_0 - beta_2|,
 //   stencil r kept when gamma_r / sum(gamma) >= C_T, omega_r = d_r delta_r / sum d delta.
 // FP64: eps = 1e-16; the three reciprocals 1/(beta_r + eps) come from one division of their
@@ -164,7 +167,25 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, T es, bo
     const T q1 = -T(1.0 / 6.0) * f1 + T(5.0 / 6.0) * f2 + T(1.0 / 3.0) * f3;
     const T q2 = T(1.0 / 3.0) * f0 - T(7.0 / 6.0) * f1 + T(11.0 / 6.0) * f2;
 
-    if (SCHEME == SCH_TENO5) {
+    if (SCHEME == SCH_WENO5Z) {
+        const T tau = fabs(b0 - b2);
+        T x0, x1, x2;
+        if (F32) {
+            const T eps = T(1e-12) * T(0.2) * (f0 * f0 + f1 * f1 + f2 * f2 + f3 * f3 + f4 * f4) + T(1e-30);
+            x0 = fdiv(tau, b0 + eps);
+            x1 = fdiv(tau, b1 + eps);
+            x2 = fdiv(tau, b2 + eps);
+        } else {
+            const T eps = T(1e-16) * es;
+            const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+            const T ip = T(1) / (e0 * e1 * e2);
+            x0 = tau * (ip * e1 * e2);
+            x1 = tau * (ip * e0 * e2);
+            x2 = tau * (ip * e0 * e1);
+        }
+        const T a0 = T(0.3) * (T(1) + x0 * x0), a1 = T(0.6) * (T(1) + x1 * x1), a2 = T(0.1) * (T(1) + x2 * x2);
+        return fdiv(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+    } else if (SCHEME == SCH_TENO5) {
         const T tau = fabs(b0 - b2);
         T x0, x1, x2;
         if (F32) {

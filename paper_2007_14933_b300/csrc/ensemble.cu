@@ -122,10 +122,10 @@ extern "C" int osbli_ensemble_create(int nprob, const osbli_params *params, void
         const osbli_params &q = params[p];
         if (q.Re > 0.0) return eseterr(nullptr, OSBLI_EINVAL, "member %d: ensembles are inviscid (Re <= 0)", p);
         if (q.sensor != 0) return eseterr(nullptr, OSBLI_EINVAL, "member %d: no learned sensor in ensembles", p);
-        if (q.scheme != OSBLI_WENO5JS && q.scheme != OSBLI_TENO5)
-            return eseterr(nullptr, OSBLI_EINVAL, "member %d: ensembles run WENO5-JS or TENO5", p);
-        if (q.scheme != params[0].scheme || q.precision != params[0].precision)
-            return eseterr(nullptr, OSBLI_EINVAL, "member %d: scheme and precision must match member 0", p);
+        if (q.scheme == OSBLI_CENTRAL4)
+            return eseterr(nullptr, OSBLI_EINVAL, "member %d: ensembles run WENO5-JS, WENO-Z or TENO5", p);
+        if (q.scheme != params[0].scheme || q.precision != params[0].precision || q.rk != params[0].rk)
+            return eseterr(nullptr, OSBLI_EINVAL, "member %d: scheme, precision and rk must match member 0", p);
         const int n[3] = {q.nx, q.ny, q.nz};
         for (int d = 0; d < 3; d++)
             for (int s = 0; s < 2; s++)
@@ -166,6 +166,7 @@ extern "C" int osbli_ensemble_create(int nprob, const osbli_params *params, void
     e->L.nprob = nprob;
     e->L.mixed = params[0].precision == OSBLI_MIXED;
     e->L.scheme = params[0].scheme;
+    e->L.nstage = params[0].rk == OSBLI_RK4 ? 5 : 3;
     int rc = build_tables(e);
     if (rc != OSBLI_OK) return fail(rc);
     *out = e;
@@ -208,7 +209,7 @@ static int capture(osbli_ens *e)
     cudaGraph_t g = nullptr;
     ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
-    for (int s = 0; s < 3; s++) launches += launch_ensemble_stage(e->L, s, e->stream);
+    for (int s = 0; s < e->L.nstage; s++) launches += launch_ensemble_stage(e->L, s, e->stream);
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {

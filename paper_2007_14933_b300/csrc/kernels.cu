@@ -11,8 +11,14 @@
 namespace osb {
 
 // 2N-storage RK3 of Williamson (the paper's Eqs. 36-38 leave A_i, B_i to the cited scheme).
-__constant__ double c_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
-__constant__ double c_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+// Low-storage 2N Runge-Kutta coefficients (Eqs. 36-38; the paper prints none): row 0 Williamson's
+// 3-stage 3rd-order scheme, row 1 the 5-stage 4th-order scheme of Carpenter & Kennedy (1994).
+__constant__ double c_rkA[2][5] = {{0.0, -5.0 / 9.0, -153.0 / 128.0, 0.0, 0.0},
+                                   {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+     -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0}};
+__constant__ double c_rkB[2][5] = {{1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0, 0.0, 0.0},
+                                   {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0, 1720146321549.0 / 2090206949498.0,
+     3134564353537.0 / 4481467310338.0, 2277821191437.0 / 14882151754819.0}};
 
 static int g_num_sms = 0;
 static int grid_for(long long work, int threads)
@@ -915,9 +921,9 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             double du = P.dt * (double)r[v];
-            if (STAGE > 0) du = c_rkA[STAGE] * dU[v * vs + id] + du;
+            if (STAGE > 0) du = c_rkA[P.rk][STAGE] * dU[v * vs + id] + du;
             dU[v * vs + id] = du;
-            const double un = U[v * vs + id] + c_rkB[STAGE] * du;
+            const double un = U[v * vs + id] + c_rkB[P.rk][STAGE] * du;
             U[v * vs + id] = un;
             bad |= !isfinite(un);
         }
@@ -2075,6 +2081,9 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
     } else if (P.scheme == SCH_WENO5JS) {
         if (general(P)) conv_char_launch<DIR, SCH_WENO5JS, true>(P, B, acc, chunk, grd, blk, s);
         else conv_char_launch<DIR, SCH_WENO5JS, false>(P, B, acc, chunk, grd, blk, s);
+    } else if (P.scheme == SCH_WENO5Z) {
+        if (general(P)) conv_char_launch<DIR, SCH_WENO5Z, true>(P, B, acc, chunk, grd, blk, s);
+        else conv_char_launch<DIR, SCH_WENO5Z, false>(P, B, acc, chunk, grd, blk, s);
     } else {
         if (general(P)) conv_char_launch<DIR, SCH_TENO5, true>(P, B, acc, chunk, grd, blk, s);
         else conv_char_launch<DIR, SCH_TENO5, false>(P, B, acc, chunk, grd, blk, s);
@@ -2111,6 +2120,7 @@ static void launch_patch(const Dev &P, const Bufs &B, cudaStream_t s)
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const int g = grid_for(N, 128);
     if (P.scheme == SCH_WENO5JS) k_patch_fix<SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    else if (P.scheme == SCH_WENO5Z) k_patch_fix<SCH_WENO5Z><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
     else k_patch_fix<SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
 }
 
@@ -2206,7 +2216,9 @@ int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
     int launches = residual_front(P, B, s, nullptr, stage == 0);
     if (stage == 0) update<0, 0>(P, B, s);
     else if (stage == 1) update<0, 1>(P, B, s);
-    else update<0, 2>(P, B, s);
+    else if (stage == 2) update<0, 2>(P, B, s);
+    else if (stage == 3) update<0, 3>(P, B, s);
+    else update<0, 4>(P, B, s);
     launches++;
     launches += boundary_nodes(P, B, s);
     return launches;
@@ -2413,7 +2425,9 @@ static int ens_stage_t(const EnsLaunch &L, int stage, cudaStream_t s)
     }
     if (stage == 0) k_ens_update<0><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
     else if (stage == 1) k_ens_update<1><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
-    else k_ens_update<2><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
+    else if (stage == 2) k_ens_update<2><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
+    else if (stage == 3) k_ens_update<3><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
+    else k_ens_update<4><<<L.total[ENS_UP], 128, 0, s>>>(L.tab, st(ENS_UP), L.nprob);
     return launches + 1;
 }
 
@@ -2439,6 +2453,7 @@ void launch_ensemble_errors(const EnsLaunch &L, int *out, cudaStream_t s)
 int launch_ensemble_stage(const EnsLaunch &L, int stage, cudaStream_t s)
 {
     if (L.scheme == SCH_WENO5JS) return ens_stage_t<SCH_WENO5JS>(L, stage, s);
+    if (L.scheme == SCH_WENO5Z) return ens_stage_t<SCH_WENO5Z>(L, stage, s);
     return ens_stage_t<SCH_TENO5>(L, stage, s);
 }
 

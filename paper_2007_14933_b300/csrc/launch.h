@@ -68,7 +68,7 @@ struct EnsLaunch {
     const int *start = nullptr;        // device, [ENS_NPH][nprob + 1] block prefix sums
     int nprob = 0;
     int total[ENS_NPH] = {};           // blocks of each phase over all problems
-    int mixed = 0, scheme = 0;
+    int mixed = 0, scheme = 0, nstage = 3;
 };
 // host side: local grid of every phase of one problem for the given line-kernel chunks
 void ens_phase_grids(const Dev &P, const int chunk[3], int g[ENS_NPH][3]);

@@ -91,7 +91,7 @@ extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, 
         if (n[d] < (per ? 3 : 5)) return fail(OSBLI_EINVAL, "direction %lld too short (%lld points)", d, n[d]);
         if (!(p->h[d] > 0.0)) return fail(OSBLI_EINVAL, "h[%lld] must be > 0", d);
     }
-    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_TENO5) return fail(OSBLI_EINVAL, "unknown scheme");
+    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_WENO5Z) return fail(OSBLI_EINVAL, "unknown scheme");
     if (!(p->gamma > 1.0) || !(p->Ma > 0.0)) return fail(OSBLI_EINVAL, "need gamma > 1 and Ma > 0");
     if (p->Re > 0.0 && !(p->Pr > 0.0)) return fail(OSBLI_EINVAL, "viscous run needs Pr > 0");
     if (p->scheme == OSBLI_TENO5 && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))

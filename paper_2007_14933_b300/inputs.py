@@ -7,7 +7,7 @@ plain dict:
     n        interior points (nx, ny, nz); 1 marks an inactive direction
     gamma, Re, Pr, Ma   (Re <= 0: inviscid)
     dt       fixed time step
-    scheme   0 central 4th order, 1 WENO5-JS, 2 TENO5 (characteristic, Roe average)
+    scheme   0 central 4th order, 1 WENO5-JS, 2 TENO5, 3 WENO-Z (characteristic, Roe average)
     teno_ct  TENO cut-off C_T
     bc       bc[d][s]: 0 periodic, 1 zero-gradient, 2 isothermal wall, 3 Dirichlet, 4 inflow
     T_wall, suth (T_s/T_ref of Sutherland's law, <= 0: mu = 1)
@@ -30,7 +30,7 @@ import math
 
 import numpy as np
 
-CENTRAL4, WENO5JS, TENO5 = 0, 1, 2
+CENTRAL4, WENO5JS, TENO5, WENO5Z = 0, 1, 2, 3
 PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW = 0, 1, 2, 3, 4
 
 
@@ -342,3 +342,23 @@ def riemann_ensemble(seed, nprob=64, sizes=ENSEMBLE_SIZES, scheme=TENO5, cfl=0.4
             quad[k, 3] = rng.uniform(0.1, 1.5)
         out.append(riemann2d(N, quad, scheme=scheme, cfl=cfl))
     return out
+
+
+def shu_osher(N=320, scheme=WENO5Z, dt=2e-4):
+    """Shu-Osher shock / density-wave interaction [Sec. 5.2]: x in [-5, 5], nodes at cell centres,
+    (rho, u, p) = (3.857143, 2.629369, 10.33333) for x < -4, else (1 + 0.2 sin 5x, 0, 1) (the
+    printed right state lists u and p as (1.0, 0.0); the textbook problem has u = 0, p = 1),
+    Dirichlet faces holding the initial end states, dt = 2e-4 (t = 1.8 after 9000 steps)."""
+    x = -5.0 + (np.arange(N) + 0.5) * 10.0 / N
+    left = x < -4.0
+    rho = np.where(left, 3.857143, 1.0 + 0.2 * np.sin(5.0 * x))
+    u = np.where(left, 2.629369, 0.0)
+    p = np.where(left, 10.33333, 1.0)
+    z = np.zeros(N)
+    cfg = _base((N, 1, 1), scheme=scheme, dt=dt, h=(10.0 / N, 1.0, 1.0),
+                bc=[[DIRICHLET, DIRICHLET], [PERIODIC, PERIODIC], [PERIODIC, PERIODIC]])
+    lo = np.array([3.857143, 2.629369, 0.0, 0.0, 10.33333]).reshape(5, 1)
+    hi = np.array([1.0 + 0.2 * np.sin(5.0 * 5.0), 0.0, 0.0, 0.0, 1.0]).reshape(5, 1)
+    cfg["bdata"] = {(0, 0): lo, (0, 1): hi}
+    U = prim_to_cons(cfg["gamma"], rho, u, z, z, p).reshape(5, 1, 1, N)
+    return cfg, U, x

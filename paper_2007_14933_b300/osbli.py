@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(HERE, "libosbli.so")
 
 OSBLI_OK, OSBLI_EINVAL, OSBLI_ENOMEM, OSBLI_ECUDA, OSBLI_ENONFINITE, OSBLI_ETIMEOUT, OSBLI_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5 = 0, 1, 2
+OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5, OSBLI_WENO5Z = 0, 1, 2, 3
 OSBLI_PERIODIC, OSBLI_ZEROGRAD, OSBLI_WALL, OSBLI_DIRICHLET, OSBLI_INFLOW = 0, 1, 2, 3, 4
 OSBLI_FP64, OSBLI_MIXED = 0, 1
+OSBLI_RK3, OSBLI_RK4 = 0, 1
 
 EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_set_state",
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
@@ -50,6 +51,7 @@ class osbli_params(ctypes.Structure):
         ("sensor", ctypes.c_int),
         ("h", ctypes.c_double * 3),
         ("L", ctypes.c_double * 3),
+        ("rk", ctypes.c_int),
     ]
 
 
@@ -171,6 +173,7 @@ def make_params(cfg, precision=OSBLI_FP64):
     p.sutherland_ratio = cfg.get("suth", 0.0)
     p.precision = int(precision)
     p.sensor = int(cfg.get("sensor", 0))
+    p.rk = int(cfg.get("rk", 0))
     return p
 
 

@@ -46,7 +46,7 @@ def mixed_vs_oracle(cfg, U, steps):
     return Ug, o.get_state()
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z])
 def test_mixed_tgv_smooth_phase_l2(scheme):
     # 40 steps reach t ~ 1.1, before the Ma 1.25 TGV forms shocklets (smooth flow)
     cfg, U = I.tgv(n=(32, 28, 24), Ma=1.25, scheme=scheme)

@@ -1,5 +1,9 @@
 """GPU (libosbli, through the C ABI) against the CPU oracle, element by element.
 
+Points where the oracle itself is ill-conditioned (its residual moves by more than 1e-11 under a
+1e-15 relative perturbation of the state; found with WENO-Z on exactly symmetric TGV data) are
+likewise checked with the loose bound only.
+
 Tolerance (plain FP64 path): max over variables v and points of |X_gpu - X_oracle| divided by
 max over points |X_oracle,v| must be <= 1e-11 (the three momentum components share one scale,
 the largest of their maxima, so that a component that vanishes in exact arithmetic -- spanwise
@@ -55,9 +59,25 @@ def residual_pair(cfg, U):
     return Rg, Ro, margin
 
 
+def sensitive_points(cfg, U, Ro):
+    """Points whose oracle residual moves by more than 1e-11 (relative) when the state is perturbed
+    by one part in 1e15: two correct FP64 evaluations may legitimately differ there.  WENO-Z's
+    weights (Eq. 22, eps = 1e-16) are ill-conditioned at such points of exactly symmetric data."""
+    rng = np.random.default_rng(0)
+    o = O.Oracle(cfg)
+    o.set_state(U * (1 + 1e-15 * rng.standard_normal(U.shape)))
+    R1 = o.residual()
+    d = np.abs(R1 - Ro).reshape(5, -1)
+    scale = np.abs(Ro).reshape(5, -1).max(axis=1)
+    scale[1:4] = scale[1:4].max()
+    return (d / scale[:, None]).max(axis=0).reshape(Ro.shape[1:]) > 1e-11
+
+
 def check_residual(cfg, U):
     Rg, Ro, margin = residual_pair(cfg, U)
     safe = margin > 1e-9
+    if cfg.get("scheme") == I.WENO5Z:
+        safe &= ~sensitive_points(cfg, U, Ro)
     assert relerr(Rg, Ro, safe) <= TOL
     if (~safe).any():   # ambiguous TENO cut-offs: still bounded
         assert relerr(Rg, Ro) < 1e-3
@@ -113,13 +133,13 @@ def test_residual_tgv_central_viscous():
     check_residual(cfg, U)
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z])
 def test_residual_tgv_characteristic_viscous_ragged(scheme):
     cfg, U = I.tgv(n=(20, 12, 9), Ma=1.25, scheme=scheme)
     check_residual(cfg, U)
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z])
 def test_residual_shocky_random_state(scheme):
     n = (13, 9, 7)
     U = I.random_state(n, seed=3, shocky=True)
@@ -133,7 +153,7 @@ def test_residual_sod():
     check_residual(cfg, U)
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.CENTRAL4])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.CENTRAL4, I.WENO5Z])
 def test_residual_curvilinear_euler_wave(scheme):
     cfg, U = I.euler_wave(24, scheme=scheme)
     check_residual(cfg, U)
@@ -282,3 +302,12 @@ def test_torch_device_buffers_roundtrip():
     osbli.osbli_get_state(s.h, out)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), U)
+
+
+@pytest.mark.parametrize("scheme", [I.TENO5, I.CENTRAL4])
+def test_rk4_five_stage_steps(scheme):
+    """The 5-stage 4th-order low-storage integrator (rk = 1) against the oracle's."""
+    cfg, U = I.tgv(12, Ma=1.25 if scheme != I.CENTRAL4 else 0.1, scheme=scheme)
+    cfg = dict(cfg, rk=1)
+    Ug, Uo = run_pair(cfg, U, 30)
+    assert relerr(Ug, Uo) <= TOL

@@ -85,7 +85,7 @@ def test_smoothness_indicators_match_integral_definition():
 
 
 # ---------------------------------------------------------------- Eqs. 20-27: weights
-@pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5])
+@pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5, O.WENO5Z])
 def test_linear_data_gives_optimal_weights(scheme):
     d = O.linear_weights()
     for a, b in [(0.3, 1.7), (-2.0, 0.01), (5.0, -3.0)]:
@@ -102,6 +102,9 @@ def test_teno_cuts_discontinuous_stencils():
     assert v == 0.0
     v2, w2 = O.recon5([0.0, 0.0, 0.0, 1.0, 1.0], O.WENO5JS)
     assert w2[2] > 0.99 and abs(v2) < 0.01
+    # WENO-Z (Eq. 22): tau = beta_0 >> eps puts all weight on the smooth stencil
+    v3, w3 = O.recon5([0.0, 0.0, 0.0, 1.0, 1.0], O.WENO5Z)
+    assert w3[2] > 1 - 1e-12 and abs(v3) < 1e-12
 
 
 def test_teno_cutoff_threshold():
@@ -204,6 +207,20 @@ def test_rk3_amplification_polynomial(z):
     assert abs(y - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
 
 
+def test_rk4_amplification_polynomial_and_order():
+    """The 5-stage 2N scheme (rk = 1): its amplification factor is a degree-5 polynomial whose
+    first five coefficients are those of exp(z) (4th order), recovered exactly from six
+    samples; and the global error on y' = lambda y falls as dt^4."""
+    zs = np.array([-1.0, -0.5, 0.25, 0.5, 1.0, 1.5])
+    vals = np.array([O.rk_linear(1, complex(z), 1.0, 1).real for z in zs])
+    coef = np.linalg.solve(np.vander(zs, 6, increasing=True), vals)
+    np.testing.assert_allclose(coef[:5], [1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0], atol=1e-12)
+    assert abs(coef[5]) > 1e-4          # not exp(z) to 5th order: a genuine 4th-order scheme
+    lam = complex(-0.7, 2.0)
+    errs = [abs(O.rk_linear(1, lam, 1.0 / n, n) - np.exp(lam)) for n in (20, 40)]
+    assert 3.8 < math.log2(errs[0] / errs[1]) < 4.3
+
+
 def test_rk3_third_order_in_time():
     lam = -1.0 + 2.0j
     errs = [abs(O.rk3_linear(lam, 1.0 / n, n) - np.exp(lam)) for n in (20, 40)]
@@ -260,6 +277,21 @@ def test_sod_weno5js_against_exact_solution():
     xs_num = x[np.where((rho[:-1] >= mid) & (rho[1:] < mid))[0][-1]]
     xs_ex = x[np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]]
     assert abs(xs_num - xs_ex) <= 1.0 / 400 + 1e-12
+
+
+def test_sod_wenoz_less_dissipative_than_wenojs():
+    """Sec. 2.4: WENO-Z lowers the dissipation of WENO-JS -- on Sod (N = 400, t = 0.2) its L1
+    density error against the exact solution is the smaller one, shock still within a cell."""
+    errs = {}
+    for scheme in (O.WENO5JS, O.WENO5Z):
+        cfg, U, x = I.sod(scheme=scheme)
+        o = O.Oracle(cfg)
+        o.set_state(U)
+        o.step(800)
+        rho = o.get_state()[0, 0, 0]
+        r, _, _ = O.riemann_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+        errs[scheme] = np.abs(rho - r).mean()
+    assert errs[O.WENO5Z] < errs[O.WENO5JS] < 4e-3
 
 
 # ---------------------------------------------------------------- Eqs. 2-5: viscous terms
@@ -374,13 +406,15 @@ def test_metrics_of_sinusoidal_grid():
     np.testing.assert_allclose(S[1, 0, 0] * sh[1], -y_i, atol=2e-3 * d)
 
 
+@pytest.mark.parametrize("scheme", [O.TENO5, O.WENO5Z])
 @pytest.mark.parametrize("A,order", [(0.0, 5.0), (0.04, 4.0)])
-def test_euler_wave_order_of_convergence(A, order):
-    """Eq. 47 on the grid of Eqs. 48-49: L1 and Linf rates within 10 % of the formal order.
-    The metrics are 4th-order central (Sec. 2.7), which bounds the curvilinear order at 4."""
+def test_euler_wave_order_of_convergence(A, order, scheme):
+    """Eq. 47 on the grid of Eqs. 48-49: L1 and Linf rates within 10 % of the formal order (the
+    paper's Sec. 5.3 check of its WENO-Z schemes).  The metrics are 4th-order central (Sec. 2.7),
+    which bounds the curvilinear order at 4."""
     errs = []
     for N in (32, 64):
-        cfg, U = I.euler_wave(N, scheme=O.TENO5, dt=1e-3 * 32 / N, A=A)
+        cfg, U = I.euler_wave(N, scheme=scheme, dt=1e-3 * 32 / N, A=A)
         o = O.Oracle(cfg)
         o.set_state(U)
         ns = int(round(0.25 / cfg["dt"]))
