@@ -221,21 +221,65 @@ __global__ void k_features(Dev P, const double *__restrict__ U, __nv_bfloat16 *_
 // ------------------------------------------------------------------------------------------
 constexpr int INF_WARPS = 4;
 
-// A warp handles 32 consecutive x-cells of one grid row as two 16-row tensor-core tiles.  The 9
-// neighbouring rows (dj, dk in {-1,0,1}) of x-positions x0-1 .. x0+32 are staged in shared
-// memory with coalesced loads (rho, u, v, w, p).  With the quantity-blocked column order of W1r a
-// lane's A-fragment columns (16 kt + 2t, +1) are the x offsets (-1, 0) of one (q, rn) group for
-// even t and (+1, pad) for odd t, the group being 4 kt + t/2 (+2 for the upper column half): the
-// lane reads the staged row at its cell and scales it, feature = value * M - A with the cell's
-// M, A (1/rho_c and 1; 1/a_c and u_c/a_c; 1/p_c and 1).  The B fragments of W1 serve both tiles.
+// A warp owns a column of tiles: 32 consecutive x-cells (two 16-row tensor-core tiles) at one
+// z index, marching along y.  The three z-rows (dk = -1, 0, 1) of each y-plane over x-positions
+// x0-1 .. x0+32 (rho, u, v, w, p) are staged in shared memory by asynchronous copies into a ring
+// of four y-planes: while tile j is computed from planes j-1, j, j+1, plane j+2 is in flight, and
+// every node's values are fetched once per column instead of once per tile that reads them.
+// With the quantity-blocked column order of W1r a lane's A-fragment columns (16 kt + 2t, +1) are
+// the x offsets (-1, 0) of one (q, rn) group for even t and (+1, pad) for odd t, the group being
+// 4 kt + t/2 (+2 for the upper column half): the lane reads the staged row at its cell and
+// scales it, feature = value * M - A with the cell's M, A (1/rho_c and 1; 1/a_c and u_c/a_c;
+// 1/p_c and 1).  B fragments come from shared memory by ldmatrix and serve both tiles.
 constexpr int SEG = 32;
 constexpr int SQS = SEG + 2;
+constexpr int NSLOT = 4;
+constexpr int PLANE = 3 * 5 * SQS;        // floats of one staged y-plane
 
 struct InferSmem {
     __nv_bfloat16 W1[SH][KRS];
     __nv_bfloat16 W2[SH][W2S];
     float b1[SH], b2[SH], w3[SH], b3;
 };
+constexpr size_t INFER_SMEM = sizeof(InferSmem) + (size_t)INF_WARPS * NSLOT * PLANE * sizeof(float);
+
+__device__ __forceinline__ void ldsm_x4(const void *p, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void cpa4(float *smem, const float *gmem)
+{
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// stage y-plane jy (clamped to 0 when y is inactive) of the column (x0, k) into ring slot `slot`
+__device__ __forceinline__ void stage_plane(const Dev &P, const float *__restrict__ Uf, const float *__restrict__ Wf,
+                                            float *ring, int slot, int x0, int jy, int k, int lane)
+{
+    if (!P.active[1]) jy = 0;
+    float *dst = ring + slot * PLANE;
+    for (int pos = lane; pos < SQS; pos += 32) {
+        int dx = pos - 1;
+        if (!P.active[0]) dx = 0;
+        else if (x0 + dx > P.n[0]) dx = P.n[0] - x0;     // past the first ghost: unused
+#pragma unroll
+        for (int dkr = 0; dkr < 3; dkr++) {
+            const int dk = P.active[2] ? dkr - 1 : 0;
+            const long long id = node_index(P, x0 + dx, jy, k + dk);
+            float *q = dst + dkr * 5 * SQS + pos;
+            cpa4(q + 0 * SQS, Uf + id);
+            cpa4(q + 1 * SQS, Wf + W_U * P.vs + id);
+            cpa4(q + 2 * SQS, Wf + W_V * P.vs + id);
+            cpa4(q + 3 * SQS, Wf + W_W * P.vs + id);
+            cpa4(q + 4 * SQS, Wf + W_P * P.vs + id);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const float *__restrict__ Uf,
                                                                  const float *__restrict__ Wf,
@@ -244,8 +288,9 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
                                                                  unsigned char *__restrict__ flag,
                                                                  float *__restrict__ probs)
 {
-    __shared__ InferSmem S;
-    __shared__ float sQ[INF_WARPS][9 * 5 * SQS];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
+    float *rings = reinterpret_cast<float *>(smem_raw + sizeof(InferSmem));
     for (int i = threadIdx.x; i < SH * KR; i += blockDim.x) S.W1[i / KR][i % KR] = W->W1r[i / KR][i % KR];
     for (int i = threadIdx.x; i < SH * SH; i += blockDim.x) S.W2[i / SH][i % SH] = W->W2[i / SH][i % SH];
     for (int i = threadIdx.x; i < SH; i += blockDim.x) {
@@ -259,126 +304,141 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
     const int hb = t >> 1;               // which group of the k-step's column half
     const bool odd = (t & 1) != 0;       // columns (+1, pad) instead of (-1, 0)
     const int xo = odd ? 2 : 0;
-    float *Q = sQ[warp];
+    float *ring = rings + warp * NSLOT * PLANE;
+    // ldmatrix row addresses: lanes 8i..8i+7 give the rows of matrix i of an x4 load
+    const int lm = lane >> 3, lr = lane & 7;
     const int nseg = (P.n[0] + SEG - 1) / SEG;
-    const long long ntiles = (long long)nseg * P.n[1] * P.n[2];
-    const long long vs = P.vs;
+    const long long ncol = (long long)nseg * P.n[2];
     const float gam = (float)P.gamma;
-    for (long long tile = blockIdx.x * (long long)INF_WARPS + warp; tile < ntiles;
-         tile += (long long)gridDim.x * INF_WARPS) {
-        const int seg = (int)(tile % nseg);
-        const long long row = tile / nseg;
-        const int j = (int)(row % P.n[1]), k = (int)(row / P.n[1]);
+    const int ny = P.n[1];
+    for (long long col = blockIdx.x * (long long)INF_WARPS + warp; col < ncol;
+         col += (long long)gridDim.x * INF_WARPS) {
+        const int seg = (int)(col % nseg);
+        const int k = (int)(col / nseg);
         const int x0 = seg * SEG;
         const int ncell = min(SEG, P.n[0] - x0);
-        const long long base = node_index(P, x0, j, k);
-        for (int pos = lane; pos < SQS; pos += 32) {
-            int dx = pos - 1;
-            if (!P.active[0]) dx = 0;
-            else if (x0 + dx > P.n[0]) dx = P.n[0] - x0;     // past the first ghost: unused
+        // ring slot of y-plane jy: (jy + 1) & 3
+        stage_plane(P, Uf, Wf, ring, 0, x0, -1, k, lane);
+        stage_plane(P, Uf, Wf, ring, 1, x0, 0, k, lane);
+        stage_plane(P, Uf, Wf, ring, 2, x0, 1, k, lane);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        for (int j = 0; j < ny; j++) {
+            if (j + 2 <= ny) stage_plane(P, Uf, Wf, ring, (j + 3) & 3, x0, j + 2, k, lane);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            __syncwarp();
+            // per-cell scales of the lane's four cells g + 8h (centre plane j, centre z-row)
+            const float *cen = ring + ((j + 1) & 3) * PLANE + 1 * 5 * SQS;
+            float irc[4], ipc[4], iac[4], ua[4][3];
 #pragma unroll
-            for (int r = 0; r < 9; r++) {
-                const int dj = P.active[1] ? r % 3 - 1 : 0, dk = P.active[2] ? r / 3 - 1 : 0;
-                const long long id = base + dx + dj * P.st[1] + dk * P.st[2];
-                float *q = Q + r * 5 * SQS + pos;
-                q[0 * SQS] = Uf[id];
-                q[1 * SQS] = Wf[W_U * vs + id];
-                q[2 * SQS] = Wf[W_V * vs + id];
-                q[3 * SQS] = Wf[W_W * vs + id];
-                q[4 * SQS] = Wf[W_P * vs + id];
+            for (int h = 0; h < 4; h++) {
+                const float *cq = cen + g + 8 * h + 1;
+                const float r = cq[0], p = cq[4 * SQS];
+                irc[h] = 1.f / r;
+                ipc[h] = 1.f / p;
+                iac[h] = rsqrtf(gam * p * irc[h]);
+#pragma unroll
+                for (int c = 0; c < 3; c++) ua[h][c] = cq[(1 + c) * SQS] * iac[h];
             }
-        }
-        __syncwarp();
-        // per-cell scales of the lane's four cells g + 8h (centre row rn = 4)
-        float irc[4], ipc[4], iac[4], ua[4][3];
+            float acc[2][4][4];
 #pragma unroll
-        for (int h = 0; h < 4; h++) {
-            const float *cq = Q + 4 * 5 * SQS + g + 8 * h + 1;
-            const float r = cq[0], p = cq[4 * SQS];
-            irc[h] = 1.f / r;
-            ipc[h] = 1.f / p;
-            iac[h] = rsqrtf(gam * p * irc[h]);
-#pragma unroll
-            for (int c = 0; c < 3; c++) ua[h][c] = cq[(1 + c) * SQS] * iac[h];
-        }
-        float acc[2][4][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                for (int e = 0; e < 4; e++) acc[mt][nt][e] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < KR / 16; kt++) {
-            uint32_t a[2][4];
-#pragma unroll
-            for (int half = 0; half < 2; half++) {
-                const int G = 4 * kt + 2 * half + hb;      // (q, rn) group of the lane's columns
-                const int q = G / 9, rn = G - 9 * q;
-                const bool live = G < 45;
-                const float *rowp = Q + (live ? (rn * 5 + q) * SQS : 0) + g + xo;
-#pragma unroll
-                for (int h = 0; h < 4; h++) {
-                    const float M = q == 0 ? irc[h] : (q == 4 ? ipc[h] : iac[h]);
-                    const float A = (q == 0 || q == 4) ? 1.f : (q == 1 ? ua[h][0] : (q == 2 ? ua[h][1] : ua[h][2]));
-                    // odd lanes' second column is the zero pad: re-read v0 (stays inside the row)
-                    const float v0 = rowp[8 * h], v1 = rowp[8 * h + (odd ? 0 : 1)];
-                    const float f0 = live ? fmaf(v0, M, -A) : 0.f;
-                    const float f1 = (live && !odd) ? fmaf(v1, M, -A) : 0.f;
-                    a[h >> 1][(h & 1) + 2 * half] = pack2(f0, f1);
-                }
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++) {
-                const uint32_t b0 = ld32(&S.W1[8 * nt + g][16 * kt + 2 * t]);
-                const uint32_t b1 = ld32(&S.W1[8 * nt + g][16 * kt + 8 + 2 * t]);
-                mma16816(acc[0][nt], a[0], b0, b1);
-                mma16816(acc[1][nt], a[1], b0, b1);
-            }
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; mt++) {
-            float h1[4][4], c2[4][4];
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    h1[nt][e] = fmaxf(acc[mt][nt][e] + S.b1[8 * nt + 2 * t + (e & 1)], 0.f);
-                    c2[nt][e] = 0.f;
-                }
-#pragma unroll
-            for (int kt = 0; kt < 2; kt++) {
-                const uint32_t a2[4] = {pack2(h1[2 * kt][0], h1[2 * kt][1]), pack2(h1[2 * kt][2], h1[2 * kt][3]),
-                                        pack2(h1[2 * kt + 1][0], h1[2 * kt + 1][1]),
-                                        pack2(h1[2 * kt + 1][2], h1[2 * kt + 1][3])};
+            for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++)
-                    mma16816(c2[nt], a2, ld32(&S.W2[8 * nt + g][16 * kt + 2 * t]),
-                             ld32(&S.W2[8 * nt + g][16 * kt + 8 + 2 * t]));
-            }
-            float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-            for (int nt = 0; nt < 4; nt++) {
-                const int col = 8 * nt + 2 * t;
-                s0 += fmaxf(c2[nt][0] + S.b2[col], 0.f) * S.w3[col] + fmaxf(c2[nt][1] + S.b2[col + 1], 0.f) * S.w3[col + 1];
-                s1 += fmaxf(c2[nt][2] + S.b2[col], 0.f) * S.w3[col] + fmaxf(c2[nt][3] + S.b2[col + 1], 0.f) * S.w3[col + 1];
-            }
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-            if (t == 0) {
-                const float z[2] = {s0 + S.b3, s1 + S.b3};
+                    for (int e = 0; e < 4; e++) acc[mt][nt][e] = 0.f;
+            // the three y-planes of the tile's neighbourhood (dj = -1, 0, 1)
+            const float *pb[3] = {ring + (j & 3) * PLANE, ring + ((j + 1) & 3) * PLANE, ring + ((j + 2) & 3) * PLANE};
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int ci = 16 * mt + g + 8 * h;
-                    if (ci < ncell) {
-                        if (flag) flag[base + ci] = z[h] > zthresh ? 1 : 0;
-                        if (probs) probs[(row * P.n[0]) + x0 + ci] = 1.f / (1.f + __expf(-z[h]));
+            for (int kt = 0; kt < KR / 16; kt++) {
+                uint32_t a[2][4];
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    // the lane's group is C + hb: both candidates are compile-time after unrolling,
+                    // so quantity, plane and row resolve to constants and one select on hb
+                    const int C = 4 * kt + 2 * half;
+                    const int q0 = C / 9, q1 = (C + 1) / 9;
+                    const int rn0 = C - 9 * q0, rn1 = C + 1 - 9 * q1;
+                    const bool live0 = C < 45, live1 = C + 1 < 45;
+                    const float *r0 = live0 ? pb[rn0 % 3] + ((rn0 / 3) * 5 + q0) * SQS : ring;
+                    const float *r1 = live1 ? pb[rn1 % 3] + ((rn1 / 3) * 5 + q1) * SQS : ring;
+                    const float *rowp = (hb ? r1 : r0) + g + xo;
+                    const bool live = hb ? live1 : live0;
+#pragma unroll
+                    for (int h = 0; h < 4; h++) {
+                        auto Mq = [&](int q) { return q == 0 ? irc[h] : (q == 4 ? ipc[h] : iac[h]); };
+                        auto Aq = [&](int q) {
+                            return (q == 0 || q == 4) ? 1.f : (q == 1 ? ua[h][0] : (q == 2 ? ua[h][1] : ua[h][2]));
+                        };
+                        const float M = (q0 == q1) ? Mq(q0) : (hb ? Mq(q1) : Mq(q0));
+                        const float A = (q0 == q1) ? Aq(q0) : (hb ? Aq(q1) : Aq(q0));
+                        // odd lanes' second column is the zero pad: re-read v0 (stays inside the row)
+                        const float v0 = rowp[8 * h], v1 = rowp[8 * h + (odd ? 0 : 1)];
+                        const float f0 = live ? fmaf(v0, M, -A) : 0.f;
+                        const float f1 = (live && !odd) ? fmaf(v1, M, -A) : 0.f;
+                        a[h >> 1][(h & 1) + 2 * half] = pack2(f0, f1);
+                    }
+                }
+#pragma unroll
+                for (int np = 0; np < 2; np++) {
+                    // matrices: (n-tile 2np, k lo), (2np, k hi), (2np+1, k lo), (2np+1, k hi)
+                    uint32_t b00, b01, b10, b11;
+                    ldsm_x4(&S.W1[8 * (2 * np + (lm >> 1)) + lr][16 * kt + 8 * (lm & 1)], b00, b01, b10, b11);
+                    mma16816(acc[0][2 * np], a[0], b00, b01);
+                    mma16816(acc[1][2 * np], a[1], b00, b01);
+                    mma16816(acc[0][2 * np + 1], a[0], b10, b11);
+                    mma16816(acc[1][2 * np + 1], a[1], b10, b11);
+                }
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) {
+                float h1[4][4], c2[4][4];
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        h1[nt][e] = fmaxf(acc[mt][nt][e] + S.b1[8 * nt + 2 * t + (e & 1)], 0.f);
+                        c2[nt][e] = 0.f;
+                    }
+#pragma unroll
+                for (int kt = 0; kt < 2; kt++) {
+                    const uint32_t a2[4] = {pack2(h1[2 * kt][0], h1[2 * kt][1]), pack2(h1[2 * kt][2], h1[2 * kt][3]),
+                                            pack2(h1[2 * kt + 1][0], h1[2 * kt + 1][1]),
+                                            pack2(h1[2 * kt + 1][2], h1[2 * kt + 1][3])};
+#pragma unroll
+                    for (int np = 0; np < 2; np++) {
+                        uint32_t b00, b01, b10, b11;
+                        ldsm_x4(&S.W2[8 * (2 * np + (lm >> 1)) + lr][16 * kt + 8 * (lm & 1)], b00, b01, b10, b11);
+                        mma16816(c2[2 * np], a2, b00, b01);
+                        mma16816(c2[2 * np + 1], a2, b10, b11);
+                    }
+                }
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++) {
+                    const int colw = 8 * nt + 2 * t;
+                    s0 += fmaxf(c2[nt][0] + S.b2[colw], 0.f) * S.w3[colw] + fmaxf(c2[nt][1] + S.b2[colw + 1], 0.f) * S.w3[colw + 1];
+                    s1 += fmaxf(c2[nt][2] + S.b2[colw], 0.f) * S.w3[colw] + fmaxf(c2[nt][3] + S.b2[colw + 1], 0.f) * S.w3[colw + 1];
+                }
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+                if (t == 0) {
+                    const float z[2] = {s0 + S.b3, s1 + S.b3};
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int ci = 16 * mt + g + 8 * h;
+                        if (ci < ncell) {
+                            if (flag) flag[node_index(P, x0 + ci, j, k)] = z[h] > zthresh ? 1 : 0;
+                            if (probs) probs[((long long)k * ny + j) * P.n[0] + x0 + ci] = 1.f / (1.f + __expf(-z[h]));
+                        }
                     }
                 }
             }
+            __syncwarp();    // every lane is done with plane j - 1 before its slot is refilled
         }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncwarp();
     }
 }
@@ -425,12 +485,23 @@ static int sm_count()
     return n > 0 ? n : 148;
 }
 
+static int infer_blocks(const Dev &P)
+{
+    static bool attr = false;   // dynamic shared memory above the 48 KB default, set once
+    if (!attr) {
+        cudaFuncSetAttribute(k_sensor_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
+        attr = true;
+    }
+    const long long cols = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[2];
+    long long blocks = (cols + INF_WARPS - 1) / INF_WARPS;
+    if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
+    return (int)blocks;
+}
+
 int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s)
 {
-    const long long tiles = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[1] * P.n[2];
-    long long blocks = (tiles + INF_WARPS - 1) / INF_WARPS;
-    if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
-    k_sensor_infer<<<(int)blocks, 32 * INF_WARPS, 0, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw, B.zthresh, B.sflag, nullptr);
+    k_sensor_infer<<<infer_blocks(P), 32 * INF_WARPS, INFER_SMEM, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw,
+                                                                       B.zthresh, B.sflag, nullptr);
     long long db = (P.ntot + 255) / 256;
     if (db > (long long)sm_count() * 16) db = (long long)sm_count() * 16;
     k_dilate<<<(int)db, 256, 0, s>>>(P, B.sflag, B.gate, 0);
@@ -440,10 +511,8 @@ int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s)
 void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s)
 {
     launch_prim(P, B, s);
-    const long long tiles = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[1] * P.n[2];
-    long long blocks = (tiles + INF_WARPS - 1) / INF_WARPS;
-    if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
-    k_sensor_infer<<<(int)blocks, 32 * INF_WARPS, 0, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw, B.zthresh, nullptr, probs);
+    k_sensor_infer<<<infer_blocks(P), 32 * INF_WARPS, INFER_SMEM, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw,
+                                                                       B.zthresh, nullptr, probs);
 }
 
 void launch_features(const Dev &P, const Bufs &B, void *X, cudaStream_t s)
