@@ -222,7 +222,7 @@ __global__ void k_features(Dev P, const double *__restrict__ U, __nv_bfloat16 *_
 constexpr int INF_WARPS = 4;
 
 // A warp owns a column of tiles: 32 consecutive x-cells (two 16-row tensor-core tiles) at one
-// z index, marching along y.  The three z-rows (dk = -1, 0, 1) of each y-plane over x-positions
+// z index, marching along y over up to YCH tiles.  The three z-rows (dk = -1, 0, 1) of each y-plane over x-positions
 // x0-1 .. x0+32 (rho, u, v, w, p) are staged in shared memory by asynchronous copies into a ring
 // of four y-planes: while tile j is computed from planes j-1, j, j+1, plane j+2 is in flight, and
 // every node's values are fetched once per column instead of once per tile that reads them.
@@ -234,6 +234,7 @@ constexpr int INF_WARPS = 4;
 constexpr int SEG = 32;
 constexpr int SQS = SEG + 2;
 constexpr int NSLOT = 4;
+constexpr int YCH = 32;                   // y extent of one warp's march
 constexpr int PLANE = 3 * 5 * SQS;        // floats of one staged y-plane
 
 struct InferSmem {
@@ -308,22 +309,25 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
     // ldmatrix row addresses: lanes 8i..8i+7 give the rows of matrix i of an x4 load
     const int lm = lane >> 3, lr = lane & 7;
     const int nseg = (P.n[0] + SEG - 1) / SEG;
-    const long long ncol = (long long)nseg * P.n[2];
-    const float gam = (float)P.gamma;
     const int ny = P.n[1];
-    for (long long col = blockIdx.x * (long long)INF_WARPS + warp; col < ncol;
-         col += (long long)gridDim.x * INF_WARPS) {
-        const int seg = (int)(col % nseg);
-        const int k = (int)(col / nseg);
+    const int nyc = (ny + YCH - 1) / YCH;
+    const long long nitem = (long long)nseg * P.n[2] * nyc;
+    const float gam = (float)P.gamma;
+    for (long long it = blockIdx.x * (long long)INF_WARPS + warp; it < nitem;
+         it += (long long)gridDim.x * INF_WARPS) {
+        const int seg = (int)(it % nseg);
+        const long long rest = it / nseg;
+        const int k = (int)(rest % P.n[2]);
+        const int j0 = (int)(rest / P.n[2]) * YCH, j1 = min(j0 + YCH, ny);
         const int x0 = seg * SEG;
         const int ncell = min(SEG, P.n[0] - x0);
         // ring slot of y-plane jy: (jy + 1) & 3
-        stage_plane(P, Uf, Wf, ring, 0, x0, -1, k, lane);
-        stage_plane(P, Uf, Wf, ring, 1, x0, 0, k, lane);
-        stage_plane(P, Uf, Wf, ring, 2, x0, 1, k, lane);
+        stage_plane(P, Uf, Wf, ring, j0 & 3, x0, j0 - 1, k, lane);
+        stage_plane(P, Uf, Wf, ring, (j0 + 1) & 3, x0, j0, k, lane);
+        stage_plane(P, Uf, Wf, ring, (j0 + 2) & 3, x0, j0 + 1, k, lane);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
-        for (int j = 0; j < ny; j++) {
-            if (j + 2 <= ny) stage_plane(P, Uf, Wf, ring, (j + 3) & 3, x0, j + 2, k, lane);
+        for (int j = j0; j < j1; j++) {
+            if (j + 2 <= j1) stage_plane(P, Uf, Wf, ring, (j + 3) & 3, x0, j + 2, k, lane);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             __syncwarp();
@@ -492,7 +496,7 @@ static int infer_blocks(const Dev &P)
         cudaFuncSetAttribute(k_sensor_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
         attr = true;
     }
-    const long long cols = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[2];
+    const long long cols = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[2] * ((P.n[1] + YCH - 1) / YCH);
     long long blocks = (cols + INF_WARPS - 1) / INF_WARPS;
     if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
     return (int)blocks;
