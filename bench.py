@@ -69,6 +69,13 @@ def _measured_hbm():
 
 HBM_GBS = _measured_hbm()
 
+# dram__bytes_read.sum + dram__bytes_write.sum per interior point of one launch, from ncu captures
+# of the same kernel on a smaller grid (traffic grows with the points processed)
+DRAM_BYTES_PER_POINT = {
+    "k_conv_delta_tile": (101.6, "ncu capture of k_conv_delta_tile<2,2> on TGV 160^3 (349.3 MB read + "
+                                 "66.6 MB written over 4.096 M points), scaled to this grid"),
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -531,7 +538,10 @@ def main():
         flops = (f_int * FLOPS_CONV_POINT_DIR[args.scheme] + (1.0 - f_int) * FLOPS_CENTRAL_DELTA) * npts
     if head in ("mixed", "learned"):
         peak, pdt = osbli.osbli_fp32_peak(), "fp32"
-        kern = "k_conv_char_delta" if dom_name != "conv_x" else "k_conv_char_delta_x"
+        if head == "learned":
+            kern = "k_conv_delta_tile" if dom_name != "conv_x" else "k_conv_delta_x_win"
+        else:
+            kern = "k_conv_char_delta" if dom_name != "conv_x" else "k_conv_char_delta_x"
         src = "FP32 FMA throughput measured in this run (osbli_fp32_peak)"
     else:
         peak, pdt, kern = osbli.osbli_fp64_peak(), "fp64", "k_conv_char"
@@ -554,6 +564,10 @@ def main():
         hbm = {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS, "unit": "GB/s", "frac": gbs / HBM_GBS,
                "traffic": None, "kernel": "%s (%s)" % (kern, dom_name),
                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "bytes_per_launch": hbm_bytes}
+        if kern in DRAM_BYTES_PER_POINT:
+            # DRAM traffic of the kernel per point from its ncu capture, scaled to this launch
+            hbm["traffic"] = DRAM_BYTES_PER_POINT[kern][0] * npts
+            hbm["traffic_source"] = DRAM_BYTES_PER_POINT[kern][1]
         # the binding roofline is the one the launch comes closest to
         roofline = dict(hbm if hbm["frac"] > alu["frac"] else alu)
         roofline["other"] = alu if roofline["bound"] == "hbm" else hbm
