@@ -1500,7 +1500,7 @@ __device__ __forceinline__ void tnode(const float (*sT)[TYR][32], int r, int tx,
 }
 
 template <int DIR, int SCHEME>
-__global__ void __launch_bounds__(256, 3) k_conv_delta_tile(Dev P, const float *__restrict__ Uf,
+__global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *__restrict__ Uf,
                                                            const float *__restrict__ Wf, float *__restrict__ Rf,
                                                            Strong sj, const unsigned char *__restrict__ gate,
                                                            int accumulate)
@@ -1549,23 +1549,25 @@ __global__ void __launch_bounds__(256, 3) k_conv_delta_tile(Dev P, const float *
     const float gm1 = (float)P.gm1;
     const float jump = P.jump;
     if (first >= n) return;
-    // staged row of node y is y - (y0 - 3); interface y lies between nodes y and y + 1
+    // staged row of node y is y - (y0 - 3); interface y lies between nodes y and y + 1.  The four
+    // nodes of an interface's central flux are kept in registers and shifted by one per node.
     int r = first - 1 - (y0 - 3);
+    NodeW w0, w1, w2, w3;
+    tnode(sT, r - 1, tx, w0);
+    tnode(sT, r, tx, w1);
+    tnode(sT, r + 1, tx, w2);
+    tnode(sT, r + 2, tx, w3);
     float Dm[NV];
+#pragma unroll 1
     for (int y = first - 1; y < last; y++, r++) {
-        bool cha = sG[r][tx] || sG[r + 1][tx];
-#pragma unroll
-        for (int q = -2; q < 3; q++)
-            cha = cha || jump2(jump, sT[13][r + q][tx], sT[0][r + q][tx], sT[13][r + q + 1][tx], sT[0][r + q + 1][tx]);
-        NodeW c, k;
-        tnode(sT, r, tx, c);
+        bool cha = sG[r][tx] || sG[r + 1][tx] || jump2(jump, sT[13][r - 2][tx], sT[0][r - 2][tx], w0.p, w0.h[0]) ||
+                   jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                   jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                   jump2(jump, w3.p, w3.h[0], sT[13][r + 3][tx], sT[0][r + 3][tx]);
         float D[NV], d1[NV], fp1[NV], fp2[NV];
-        tnode(sT, r - 1, tx, k);
-        dflux_w<DIR>(gm1, c, k, d1);
-        tnode(sT, r + 1, tx, k);
-        dflux_w<DIR>(gm1, c, k, fp1);
-        tnode(sT, r + 2, tx, k);
-        dflux_w<DIR>(gm1, c, k, fp2);
+        dflux_w<DIR>(gm1, w1, w0, d1);
+        dflux_w<DIR>(gm1, w1, w2, fp1);
+        dflux_w<DIR>(gm1, w1, w3, fp2);
 #pragma unroll
         for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
         const long long m = base + (long long)y * st;
@@ -1593,6 +1595,10 @@ __global__ void __launch_bounds__(256, 3) k_conv_delta_tile(Dev P, const float *
         }
 #pragma unroll
         for (int v = 0; v < NV; v++) Dm[v] = D[v];
+        if (y + 1 < last) {
+            w0 = w1; w1 = w2; w2 = w3;
+            tnode(sT, r + 3, tx, w3);
+        }
     }
 }
 
