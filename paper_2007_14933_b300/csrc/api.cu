@@ -173,6 +173,8 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     P.gM2 = p->gamma * p->Ma * p->Ma;
     P.kq = P.viscous ? 1.0 / ((p->gamma - 1.0) * p->Ma * p->Ma * p->Pr * p->Re) : 0.0;
     P.dt = p->dt;
+    P.dthi = (float)p->dt;
+    P.dtlo = (float)(p->dt - (double)P.dthi);
     P.mixed = p->precision == OSBLI_MIXED;
     P.sensor = p->sensor == 1;
     P.rk = p->rk;

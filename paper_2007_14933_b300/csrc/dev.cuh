@@ -34,6 +34,7 @@ struct Dev {
     double fac[3];     // uniform grid: s_d / Jinv = 1/h_d
     double shat[3];    // curvilinear grid: s_d = max |S_d|
     double dt;
+    float dthi, dtlo;  // dt = dthi + dtlo (FP32 parts, mixed path register update)
     int mixed;         // OSBLI_MIXED: FP32 reconstruction arithmetic
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
     int sensor;        // learned gate active (mixed path, Cartesian or rectilinear grids)

@@ -516,6 +516,19 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
 // 5-9 the FP32 rounding of the remainder (U = hi + lo to ~48 bits), so that differences
 // between nearby nodes are formed to FP32 accuracy relative to the difference itself.  Wf holds
 // FP32 primitives (u, v, w, p, a, sqrt(rho), H, T).
+// FP32 -> FP64 widening by integer operations (exact for normal values, infinities and NaN;
+// FP32 subnormals flush to zero), since double <-> float conversions run on the FP64 pipe.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long ex = (unsigned long long)(e == 0xFFu ? 0x7FFu : e + 896u) << 52;
+    const unsigned long long man = (unsigned long long)(b & 0x7FFFFFu) << 29;
+    return __longlong_as_double((long long)(sign | ex | man));
+}
+
 // FP64 -> FP32 hi/lo pair with integer operations only (double <-> float conversions run on the
 // FP64 pipe, 1/64 of the FP32 rate on this GPU): hi = x rounded to 24 significant bits (half
 // away from zero), lo = x - hi from the dropped 29 mantissa bits as an FP32 value (rounded to
@@ -920,7 +933,15 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
         bool bad = false;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            double du = P.dt * (double)r[v];
+            double du;
+            if (sizeof(RT) == 4) {
+                // mixed path: dt r formed in FP32 with dt split into two FP32 parts (the error is
+                // that of r's own FP32 rounding) and widened to FP64 by integer operations, so the
+                // register update costs two FP64 operations (the FP64 pipe runs at 1/64 rate)
+                du = f2d_bits(fmaf(P.dthi, (float)r[v], P.dtlo * (float)r[v]));
+            } else {
+                du = P.dt * (double)r[v];
+            }
             if (STAGE > 0) du = c_rkA[P.rk][STAGE] * dU[v * vs + id] + du;
             dU[v * vs + id] = du;
             const double un = U[v * vs + id] + c_rkB[P.rk][STAGE] * du;
