@@ -56,9 +56,12 @@ enum { OSBLI_RK3 = 0, OSBLI_RK4 = 1 };
  *   WALL       isothermal no-slip wall on the boundary node (Eqs. 40-46), temperature T_wall
  *   DIRICHLET  ghosts and boundary node from osbli_set_boundary_data (rho, u, v, w, p)
  *   INFLOW     ghosts and boundary node: u, v, w, T from osbli_set_boundary_data (slot 0 unused),
- *              pressure extrapolated from the first interior node, rho = gamma Ma^2 p / T */
+ *              pressure extrapolated from the first interior node, rho = gamma Ma^2 p / T
+ *   ADIABATIC  no-slip wall with zero heat flux (the laminar channel of Sec. 5.4): ghost
+ *              temperatures mirror the interior; after each stage the wall node's temperature
+ *              makes the one-sided 4th-order derivative vanish, (48T1 - 36T2 + 16T3 - 3T4)/25 */
 enum { OSBLI_PERIODIC = 0, OSBLI_ZEROGRAD = 1, OSBLI_WALL = 2, OSBLI_DIRICHLET = 3,
-       OSBLI_INFLOW = 4 };
+       OSBLI_INFLOW = 4, OSBLI_ADIABATIC = 5 };
 
 /* arithmetic of the reconstruction (Sec. 2.2-2.5) */
 enum { OSBLI_FP64 = 0, OSBLI_MIXED = 1 };
@@ -83,6 +86,8 @@ typedef struct {
     double h[3];               /* grid spacing per direction when coords == NULL */
     double L[3];               /* period of each periodic direction (coordinate unwrapping) */
     int rk;                    /* OSBLI_RK3 (3 stages, default) | OSBLI_RK4 (5 stages) */
+    double force[3];           /* body force per unit volume on the momentum; its work f.u enters
+                                  the energy equation (0, 0, 0: none) */
 } osbli_params;
 
 /* Create a solver for one grid.  coords: NULL (uniform grid, spacing h) or node coordinates of

@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "osbli_oracle.c")
 _LIB = os.path.join(_HERE, "libosbli_oracle.so")
 
 CENTRAL4, WENO5JS, TENO5, WENO5Z = 0, 1, 2, 3
-PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW = 0, 1, 2, 3, 4
+PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW, ADIABATIC = 0, 1, 2, 3, 4, 5
 
 
 def build(force=False):
@@ -52,6 +52,7 @@ class Params(ctypes.Structure):
         ("coords", ctypes.c_void_p),
         ("bdata", ctypes.c_void_p * 6),
         ("rk", ctypes.c_int),
+        ("force", ctypes.c_double * 3),
     ]
 
 
@@ -145,6 +146,8 @@ class Oracle:
         P.scheme = int(cfg.get("scheme", TENO5))
         P.teno_ct = cfg.get("teno_ct", 1e-5)
         P.rk = int(cfg.get("rk", 0))
+        for q, f in enumerate(cfg.get("force", (0.0, 0.0, 0.0))):
+            P.force[q] = float(f)
         P.T_wall = cfg.get("T_wall", 1.0)
         P.suth = cfg.get("suth", 0.0)
         self._keep = []

@@ -40,7 +40,7 @@
 #define GH 3
 
 enum { ORC_CENTRAL4 = 0, ORC_WENO5JS = 1, ORC_TENO5 = 2, ORC_WENO5Z = 3 };
-enum { ORC_PERIODIC = 0, ORC_ZEROGRAD = 1, ORC_WALL = 2, ORC_DIRICHLET = 3, ORC_INFLOW = 4 };
+enum { ORC_PERIODIC = 0, ORC_ZEROGRAD = 1, ORC_WALL = 2, ORC_DIRICHLET = 3, ORC_INFLOW = 4, ORC_ADIABATIC = 5 };
 
 typedef struct {
     int n[3];              /* interior points per direction, 1 = inactive */
@@ -56,6 +56,7 @@ typedef struct {
     const double *coords;  /* [3][nz][ny][nx] physical coordinates or NULL */
     const double *bdata[6];/* face 2*d+s: [5][plane] Dirichlet (rho,u,v,w,p) or inflow (-,u,v,w,T) */
     int rk;                /* 0: 3-stage RK3, 1: 5-stage RK4 (both low-storage 2N) */
+    double force[3];       /* body force per unit volume (momentum) and its work f.u (energy) */
 } orc_params;
 
 typedef struct {
@@ -564,6 +565,11 @@ static void compute_metrics(orc_ctx *c)
  *   DIRICHLET  ghosts and boundary node = the given primitive plane (rho,u,v,w,p).
  *   INFLOW     velocity and temperature from the given plane, pressure extrapolated from the
  *              first interior node (zero order), rho = gamma M^2 p / T; ghosts and node.
+ *   ADIABATIC  no-slip wall with zero heat flux (the laminar channel of Sec. 5.4; the paper
+ *              prints no discretisation): as WALL but the ghost temperature mirrors the interior,
+ *              T_{-i} = T_i; after each stage the wall node gets rho u_i = 0 and the temperature
+ *              that makes the one-sided 4th-order derivative (Eq. 30) vanish,
+ *              T_w = (48 T_1 - 36 T_2 + 16 T_3 - 3 T_4) / 25, rho E = rho_w T_w / (M^2 gamma (gamma-1)).
  * The plane of a face lists the interior nodes of the two other directions (lower first
  * direction fastest); ghost lines of those directions clamp to the nearest interior line.
  * ------------------------------------------------------------------------------------------ */
@@ -641,7 +647,7 @@ static void ghost_fill(orc_ctx *c)
                             for (int v = 0; v < NV; v++) U[v * nt + idg] = U[v * nt + src];
                         } else if (bc == ORC_ZEROGRAD) {
                             for (int v = 0; v < NV; v++) U[v * nt + idg] = ub[v];
-                        } else if (bc == ORC_WALL) {
+                        } else if (bc == ORC_WALL || bc == ORC_ADIABATIC) {
                             primitives(P, ub, &wb);
                             primitives(P, u1, &w1);
                             int mi = s == 0 ? gi : n - 1 - gi;   /* mirrored interior node */
@@ -651,7 +657,7 @@ static void ghost_fill(orc_ctx *c)
                             prim_t wm;
                             load_state(U, idm, nt, um);
                             primitives(P, um, &wm);
-                            double Tg = (gi + 1) * P->T_wall - gi * w1.T;
+                            double Tg = bc == ORC_ADIABATIC ? wm.T : (gi + 1) * P->T_wall - gi * w1.T;
                             double rg = P->Ma * P->Ma * P->gamma * wb.p / Tg;
                             double ug[3] = {-wm.u[0], -wm.u[1], -wm.u[2]};
                             set_from_prim(P, U, idg, nt, rg, ug, wb.p);
@@ -684,7 +690,7 @@ static void impose_boundary_nodes(orc_ctx *c)
         int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
         for (int s = 0; s < 2; s++) {
             int bc = P->bc[d][s];
-            if (bc != ORC_WALL && bc != ORC_DIRICHLET && bc != ORC_INFLOW) continue;
+            if (bc != ORC_WALL && bc != ORC_DIRICHLET && bc != ORC_INFLOW && bc != ORC_ADIABATIC) continue;
             for (int ib = 0; ib < P->n[db]; ib++)
                 for (int ia = 0; ia < P->n[da]; ia++) {
                     int ii[3];
@@ -693,7 +699,23 @@ static void impose_boundary_nodes(orc_ctx *c)
                     long idb = IDX(c, ii[0], ii[1], ii[2]);
                     ii[d] = s == 0 ? 1 : n - 2;
                     long id1 = IDX(c, ii[0], ii[1], ii[2]);
-                    if (bc == ORC_WALL) {
+                    if (bc == ORC_ADIABATIC) {
+                        double Tn[5];
+                        for (int q = 1; q <= 4; q++) {
+                            ii[d] = s == 0 ? q : n - 1 - q;
+                            double uq[5];
+                            prim_t wq;
+                            load_state(U, IDX(c, ii[0], ii[1], ii[2]), nt, uq);
+                            primitives(P, uq, &wq);
+                            Tn[q] = wq.T;
+                        }
+                        double Tw = (48.0 * Tn[1] - 36.0 * Tn[2] + 16.0 * Tn[3] - 3.0 * Tn[4]) / 25.0;
+                        double rw = U[0 * nt + idb];
+                        U[1 * nt + idb] = 0.0;
+                        U[2 * nt + idb] = 0.0;
+                        U[3 * nt + idb] = 0.0;
+                        U[4 * nt + idb] = rw * Tw / (P->Ma * P->Ma * P->gamma * (P->gamma - 1.0));
+                    } else if (bc == ORC_WALL) {
                         double rw = U[0 * nt + idb];
                         U[1 * nt + idb] = 0.0;
                         U[2 * nt + idb] = 0.0;
@@ -979,6 +1001,17 @@ static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double
                 double D = deriv4(vflux_fetch, &ud, ii[d], P->n[d], P->bc[d][0] == ORC_PERIODIC);
                 R[1 + comp] += fac * D;
             }
+        }
+    }
+    /* body force per unit volume and its work (the laminar channel's driving force) */
+    if (P->force[0] != 0.0 || P->force[1] != 0.0 || P->force[2] != 0.0) {
+        double u5[5];
+        prim_t w;
+        load_state(c->U, id, c->ntot, u5);
+        primitives(P, u5, &w);
+        for (int q = 0; q < 3; q++) {
+            R[1 + q] += P->force[q];
+            R[4] += P->force[q] * w.u[q];
         }
     }
 }

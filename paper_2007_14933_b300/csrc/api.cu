@@ -93,7 +93,7 @@ static int validate(const osbli_params *p, const double *coords)
     for (int d = 0; d < 3; d++) {
         if (n[d] < 1) return seterr(nullptr, OSBLI_EINVAL, "n[%d] = %d < 1", d, n[d]);
         for (int s = 0; s < 2; s++)
-            if (p->bc[d][s] < OSBLI_PERIODIC || p->bc[d][s] > OSBLI_INFLOW)
+            if (p->bc[d][s] < OSBLI_PERIODIC || p->bc[d][s] > OSBLI_ADIABATIC)
                 return seterr(nullptr, OSBLI_EINVAL, "bc[%d][%d] = %d unknown", d, s, p->bc[d][s]);
         if (n[d] == 1) continue;
         const bool per0 = p->bc[d][0] == OSBLI_PERIODIC, per1 = p->bc[d][1] == OSBLI_PERIODIC;
@@ -178,6 +178,8 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     P.mixed = p->precision == OSBLI_MIXED;
     P.sensor = p->sensor == 1;
     P.rk = p->rk;
+    for (int d = 0; d < 3; d++) P.force[d] = p->force[d];
+    P.forced = p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0;
     P.nstage = p->rk == OSBLI_RK4 ? 5 : 3;
     P.jump = 1.5f;
     if (!P.curv) {
@@ -498,7 +500,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
         if (P.mixed && !general(P) && d == 0 && !P.sensor) per_stage += 1;   // x segment lefts
         for (int s = 0; s < 2; s++) {
             const int bc = P.bc[d][s];
-            if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW) per_stage++;
+            if (bc == OSBLI_WALL || bc == OSBLI_DIRICHLET || bc == OSBLI_INFLOW || bc == OSBLI_ADIABATIC) per_stage++;
         }
     }
     if (P.viscous) per_stage++;

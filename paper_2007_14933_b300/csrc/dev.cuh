@@ -19,7 +19,7 @@ constexpr int GH = 3;   // ghost width: WENO5/TENO5 stencil i-2..i+3 (Sec. 2.3-2
 
 enum { W_U = 0, W_V, W_W, W_P, W_A, W_SR, W_H, W_T, NW };
 enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2, SCH_WENO5Z = 3 };
-enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4, BC_ADIABATIC = 5 };
 
 struct Dev {
     int n[3], g[3], np[3];
@@ -39,6 +39,8 @@ struct Dev {
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
     int sensor;        // learned gate active (mixed path, Cartesian or rectilinear grids)
     int rk, nstage;    // time integrator: 0 RK3 (3 stages), 1 RK4 (5 stages), low-storage 2N
+    double force[3];   // body force per unit volume; its work f.u enters the energy equation
+    int forced;
     int rect;          // rectilinear grid: Cartesian kernels with per-line factors lfac
     const double *lfac[3];   // rect: S_dd / Jinv of each line position along direction d
     const double *lesc[3];   // rect: 1 / |S~_d|^2 of each line of direction d ([n_DB][n_DA])

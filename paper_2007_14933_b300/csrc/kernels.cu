@@ -130,9 +130,10 @@ __device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *
             const long long src = node_index(P, ii[0], ii[1], ii[2]);
 #pragma unroll
             for (int v = 0; v < NV; v++) U[v * P.vs + idg] = U[v * P.vs + src];
-        } else if (bc == BC_WALL) {
+        } else if (bc == BC_WALL || bc == BC_ADIABATIC) {
             // Eqs. 43-46: T_{-i} = (i+1) T_w - i T_1, rho_{-i} = M^2 gamma p_w / T_{-i},
-            // velocity reflected from interior node i, pressure = wall pressure p_w.
+            // velocity reflected from interior node i, pressure = wall pressure p_w.  Adiabatic
+            // wall: the ghost temperature mirrors the interior, T_{-i} = T_i (zero heat flux).
             double r0, u0, v0, w0, pw, r1, u1, v1, w1, p1, rm, um, vm, wm, pm;
             ii[d] = (s == 0) ? 0 : n - 1;
             cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), r0, u0, v0, w0, pw);
@@ -141,7 +142,7 @@ __device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *
             ii[d] = (s == 0) ? gi : n - 1 - gi;
             cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), rm, um, vm, wm, pm);
             const double T1 = P.gM2 * p1 / r1;
-            const double Tg = (gi + 1) * P.Tw - gi * T1;
+            const double Tg = bc == BC_ADIABATIC ? P.gM2 * pm / rm : (gi + 1) * P.Tw - gi * T1;
             const double rg = P.Ma * P.Ma * P.gamma * pw / Tg;
             set_prim(P, U, idg, rg, -um, -vm, -wm, pw);
         } else if (bc == BC_DIRICHLET) {
@@ -183,7 +184,23 @@ __global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const doub
         ii[db] = (int)(t / P.n[da]);
         ii[d] = (s == 0) ? 0 : n - 1;
         const long long idb = node_index(P, ii[0], ii[1], ii[2]);
-        if (bc == BC_WALL) {
+        if (bc == BC_ADIABATIC) {
+            // wall temperature from the one-sided 4th-order zero-gradient condition (Eq. 30)
+            double Tn[5];
+#pragma unroll
+            for (int q = 1; q <= 4; q++) {
+                ii[d] = (s == 0) ? q : n - 1 - q;
+                double rq, uq, vq, wq, pq;
+                cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), rq, uq, vq, wq, pq);
+                Tn[q] = P.gM2 * pq / rq;
+            }
+            const double Tw = (48.0 * Tn[1] - 36.0 * Tn[2] + 16.0 * Tn[3] - 3.0 * Tn[4]) / 25.0;
+            const double rw = U[idb];
+            U[1 * P.vs + idb] = 0.0;
+            U[2 * P.vs + idb] = 0.0;
+            U[3 * P.vs + idb] = 0.0;
+            U[4 * P.vs + idb] = rw * Tw / (P.Ma * P.Ma * P.gamma * P.gm1);
+        } else if (bc == BC_WALL) {
             const double rw = U[idb];
             U[1 * P.vs + idb] = 0.0;
             U[2 * P.vs + idb] = 0.0;
@@ -903,6 +920,17 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                     r[v] += -fac * c;
                 }
             }
+        }
+        if (P.forced) {
+            // body force per unit volume and its work (u from the node's FP64 state)
+            const double ir = 1.0 / U[id];
+            double work = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                r[1 + c] += RT(P.force[c]);
+                work += P.force[c] * U[(1 + c) * vs + id] * ir;
+            }
+            r[4] += RT(work);
         }
         if (VISC) {
 #pragma unroll
@@ -2228,7 +2256,7 @@ static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s)
         if (!P.active[d]) continue;
         for (int sd = 0; sd < 2; sd++) {
             int bc = P.bc[d][sd];
-            if (bc != BC_WALL && bc != BC_DIRICHLET && bc != BC_INFLOW) continue;
+            if (bc != BC_WALL && bc != BC_DIRICHLET && bc != BC_INFLOW && bc != BC_ADIABATIC) continue;
             long long plane = (long long)P.n[(d == 0) ? 1 : 0] * P.n[(d == 2) ? 1 : 2];
             k_bnodes<<<grid_for(plane, 256), 256, 0, s>>>(P, B.U, d, sd, B.bd[2 * d + sd]);
             launches++;

@@ -9,7 +9,10 @@ plain dict:
     dt       fixed time step
     scheme   0 central 4th order, 1 WENO5-JS, 2 TENO5, 3 WENO-Z (characteristic, Roe average)
     teno_ct  TENO cut-off C_T
-    bc       bc[d][s]: 0 periodic, 1 zero-gradient, 2 isothermal wall, 3 Dirichlet, 4 inflow
+    bc       bc[d][s]: 0 periodic, 1 zero-gradient, 2 isothermal wall, 3 Dirichlet, 4 inflow,
+             5 adiabatic wall
+    force    optional body force per unit volume (its work enters the energy equation)
+    rk       0: 3-stage RK3 (default), 1: 5-stage RK4
     T_wall, suth (T_s/T_ref of Sutherland's law, <= 0: mu = 1)
     h, L     uniform spacings / periods
     coords   optional [3][nz][ny][nx] node coordinates (curvilinear grids)
@@ -23,6 +26,8 @@ Workloads (paper sections in brackets):
     random_state() seeded smooth/perturbed states for parity tests
     sbli()         shock / boundary-layer box [Sec. 6]: Mach 2, Re 1e4, similarity inflow,
                    isothermal wall, 10-degree oblique shock on the top boundary, tanh stretching
+    laminar_channel() mixed isothermal / adiabatic-wall channel [Sec. 5.4] at its analytic state
+    shu_osher()    Shu-Osher shock / density-wave interaction [Sec. 5.2]
     riemann2d(), riemann_ensemble()
                    four-quadrant 2D Riemann problems [Sec. 5.2] and seeded ensembles of them
 """
@@ -31,7 +36,7 @@ import math
 import numpy as np
 
 CENTRAL4, WENO5JS, TENO5, WENO5Z = 0, 1, 2, 3
-PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW = 0, 1, 2, 3, 4
+PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW, ADIABATIC = 0, 1, 2, 3, 4, 5
 
 
 def prim_to_cons(gamma, rho, u, v, w, p):
@@ -362,3 +367,33 @@ def shu_osher(N=320, scheme=WENO5Z, dt=2e-4):
     cfg["bdata"] = {(0, 0): lo, (0, 1): hi}
     U = prim_to_cons(cfg["gamma"], rho, u, z, z, p).reshape(5, 1, 1, N)
     return cfg, U, x
+
+
+def laminar_channel_exact(y, Re=90.0, Pr=0.72, Ma=0.01, gamma=1.4):
+    """Analytic laminar channel [Sec. 5.4]: isothermal wall (T = 1) at y = -1, adiabatic wall at
+    y = 1, constant viscosity: u = Re (1 - y^2) / 2, T = 1 - Re^2 Ma^2 Pr (gamma-1) (y^4 - 4y - 5)/12."""
+    u = Re * (1.0 - y ** 2) / 2.0
+    T = 1.0 - Re ** 2 * Ma ** 2 * Pr * (gamma - 1.0) * (y ** 4 - 4.0 * y - 5.0) / 12.0
+    return u, T
+
+
+def laminar_channel(Nx=32, Ny=64, Re=90.0, Pr=0.72, Ma=0.01, scheme=CENTRAL4, dt=1e-4):
+    """The channel of Sec. 5.4 on Lx = 2 pi (periodic), y in [-1, 1] with wall nodes at both ends,
+    at its analytic steady state: unit body force along x (its work u in the energy equation),
+    uniform pressure 1/(gamma Ma^2), rho = 1/T, constant viscosity."""
+    g = 1.4
+    x = np.arange(Nx) * 2.0 * np.pi / Nx
+    y = np.linspace(-1.0, 1.0, Ny)
+    u1, T1 = laminar_channel_exact(y, Re, Pr, Ma, g)
+    shape = (1, Ny, Nx)
+    u = np.broadcast_to(u1[None, :, None], shape)
+    T = np.broadcast_to(T1[None, :, None], shape)
+    p = np.full(shape, 1.0 / (g * Ma * Ma))
+    rho = 1.0 / T
+    z = np.zeros(shape)
+    U = prim_to_cons(g, rho, u, z, z, p)
+    cfg = _base((Nx, Ny, 1), scheme=scheme, Re=Re, Pr=Pr, Ma=Ma, dt=dt, T_wall=1.0,
+                h=(2.0 * np.pi / Nx, 2.0 / (Ny - 1), 1.0),
+                bc=[[PERIODIC, PERIODIC], [WALL, ADIABATIC], [PERIODIC, PERIODIC]])
+    cfg["force"] = (1.0, 0.0, 0.0)
+    return cfg, U, y

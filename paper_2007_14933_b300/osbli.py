@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libosbli.so")
 OSBLI_OK, OSBLI_EINVAL, OSBLI_ENOMEM, OSBLI_ECUDA, OSBLI_ENONFINITE, OSBLI_ETIMEOUT, OSBLI_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
 OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5, OSBLI_WENO5Z = 0, 1, 2, 3
-OSBLI_PERIODIC, OSBLI_ZEROGRAD, OSBLI_WALL, OSBLI_DIRICHLET, OSBLI_INFLOW = 0, 1, 2, 3, 4
+OSBLI_PERIODIC, OSBLI_ZEROGRAD, OSBLI_WALL, OSBLI_DIRICHLET, OSBLI_INFLOW, OSBLI_ADIABATIC = 0, 1, 2, 3, 4, 5
 OSBLI_FP64, OSBLI_MIXED = 0, 1
 OSBLI_RK3, OSBLI_RK4 = 0, 1
 
@@ -52,6 +52,7 @@ class osbli_params(ctypes.Structure):
         ("h", ctypes.c_double * 3),
         ("L", ctypes.c_double * 3),
         ("rk", ctypes.c_int),
+        ("force", ctypes.c_double * 3),
     ]
 
 
@@ -174,6 +175,8 @@ def make_params(cfg, precision=OSBLI_FP64):
     p.precision = int(precision)
     p.sensor = int(cfg.get("sensor", 0))
     p.rk = int(cfg.get("rk", 0))
+    for q, f in enumerate(cfg.get("force", (0.0, 0.0, 0.0))):
+        p.force[q] = float(f)
     return p
 
 

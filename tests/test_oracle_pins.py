@@ -454,3 +454,37 @@ def test_isothermal_wall_ghosts_continue_linear_temperature():
         np.testing.assert_allclose(pg, pw, rtol=1e-13)
         np.testing.assert_allclose(ug, -0.1 * gi, rtol=1e-13)
         np.testing.assert_allclose(vg, -0.02 * gi, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- Sec. 5.4: laminar channel
+def test_laminar_channel_analytic_state_is_discrete_steady_state():
+    """Sec. 5.4: isothermal wall (T = 1) at y = -1, adiabatic wall at y = 1, unit body force, constant
+    viscosity.  The analytic profiles are a quadratic (u) and a quartic (T), on which the 4th-order
+    operators and their one-sided closures are exact, so the oracle's residual of the analytic state
+    vanishes to rounding at every node, walls included, and the state does not drift; the paper's
+    adiabatic-wall temperature T_aw = 1.155520 follows from the profile."""
+    cfg, U, y = I.laminar_channel()
+    _, Taw = I.laminar_channel_exact(np.array([1.0]))
+    assert abs(Taw[0] - 1.155520) < 5e-7
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    R = o.residual()
+    # the balancing terms are O(1) (momentum: the unit force) and O(Re) (energy)
+    assert np.abs(R[1]).max() < 1e-10 and np.abs(R[4]).max() < 1e-8 and np.abs(R[0]).max() < 1e-12
+    o.step(100)
+    V = o.get_state()
+    for v in (0, 1, 4):
+        assert np.abs(V[v] - U[v]).max() <= 1e-13 * np.abs(U[v]).max()
+
+
+def test_laminar_channel_wall_conditions_matter():
+    """The same state with the adiabatic wall replaced by an isothermal one at T = 1, or without the
+    body force's work, is no longer steady: the pin above sees each ingredient."""
+    cfg, U, y = I.laminar_channel()
+    o = O.Oracle(dict(cfg, bc=[[I.PERIODIC, I.PERIODIC], [I.WALL, I.WALL], [I.PERIODIC, I.PERIODIC]]))
+    o.set_state(U)
+    o.step(1)
+    assert np.abs(o.get_state()[4] - U[4]).max() > 1e-6 * np.abs(U[4]).max()
+    o = O.Oracle(dict(cfg, force=(0.0, 0.0, 0.0)))
+    o.set_state(U)
+    assert np.abs(o.residual()[1]).max() > 0.5
