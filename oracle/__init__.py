@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the CP
 ``bench.py`` are the only callers.  The oracle is plain C (``osbli_oracle.c``) built with gcc and
 loaded through ctypes; it shares no code with the CUDA path and never calls it.
 
-Parity pins (see ``tests/test_oracle_pins.py``): ENO coefficients and optimal weights against the
-polynomial-exactness definition, the printed smoothness indicators against their integral definition
+Parity pins (see ``tests/test_oracle_pins.py``): ENO coefficients and optimal weights (5th order and
+TENO6) against the polynomial-exactness definition, the printed smoothness indicators against their integral definition
 (Eq. 16), WENO/TENO weights on linear and discontinuous data, eigensystem identities, the RK3
 amplification polynomial, the exact Riemann solution for Sod, the closed-form viscous and heat-flux
 residuals, TGV kinetic-energy pins, discrete conservation and the curvilinear order of convergence.
@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "osbli_oracle.c")
 _LIB = os.path.join(_HERE, "libosbli_oracle.so")
 
-CENTRAL4, WENO5JS, TENO5, WENO5Z = 0, 1, 2, 3
+CENTRAL4, WENO5JS, TENO5, WENO5Z, TENO6 = 0, 1, 2, 3, 4
 PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW, ADIABATIC = 0, 1, 2, 3, 4, 5
 
 
@@ -86,6 +86,12 @@ def lib():
         L.orc_recon5.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                  ctypes.c_void_p]
         L.orc_recon5.restype = ctypes.c_double
+        L.orc_teno6_linear_weights.argtypes = [ctypes.c_void_p]
+        L.orc_smoothness_cubic.argtypes = [ctypes.c_void_p]
+        L.orc_smoothness_cubic.restype = ctypes.c_double
+        L.orc_weights6.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_recon6.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_recon6.restype = ctypes.c_double
         L.orc_flux.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_eigensystem.argtypes = [ctypes.c_double] + [ctypes.c_void_p] * 6
         L.orc_char_flux_1d.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double,
@@ -252,6 +258,32 @@ def recon5(f, scheme, ct=1e-5):
     w = np.empty(3)
     m = np.empty(1)
     v = lib().orc_recon5(_p(f), int(scheme), float(ct), _p(w), _p(m))
+    return v, w
+
+
+def teno6_linear_weights():
+    d = np.empty(4)
+    lib().orc_teno6_linear_weights(_p(d))
+    return d
+
+
+def smoothness_cubic(g):
+    return lib().orc_smoothness_cubic(_p(_f64(g)))
+
+
+def weights6(beta, ct=1e-5):
+    beta = _f64(beta)
+    w = np.empty(4)
+    m = np.empty(1)
+    lib().orc_weights6(_p(beta), float(ct), _p(w), _p(m))
+    return w, float(m[0])
+
+
+def recon6(f, ct=1e-5):
+    f = _f64(f)
+    w = np.empty(4)
+    m = np.empty(1)
+    v = lib().orc_recon6(_p(f), float(ct), _p(w), _p(m))
     return v, w
 
 

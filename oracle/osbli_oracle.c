@@ -23,7 +23,7 @@
  *     with S_d = Jinv grad(xi_d) (cross products of the coordinate derivatives) and
  *     Jinv = det(dx/dxi).  S_d is normalised by s_d = max over the interior of |S_d|, so that
  *     on a uniform Cartesian grid the reconstructed flux is the physical flux itself.
- *   - Ghost width 3 (the WENO5/TENO5 stencil i-2..i+3 of Sec. 2.2-2.5).
+ *   - Ghost width 3 (the WENO5/TENO5/TENO6 stencil i-2..i+3 of Sec. 2.2-2.5).
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no contraction: every product and
  * sum is rounded as written).
@@ -39,14 +39,14 @@
 #define NV 5
 #define GH 3
 
-enum { ORC_CENTRAL4 = 0, ORC_WENO5JS = 1, ORC_TENO5 = 2, ORC_WENO5Z = 3 };
+enum { ORC_CENTRAL4 = 0, ORC_WENO5JS = 1, ORC_TENO5 = 2, ORC_WENO5Z = 3, ORC_TENO6 = 4 };
 enum { ORC_PERIODIC = 0, ORC_ZEROGRAD = 1, ORC_WALL = 2, ORC_DIRICHLET = 3, ORC_INFLOW = 4, ORC_ADIABATIC = 5 };
 
 typedef struct {
     int n[3];              /* interior points per direction, 1 = inactive */
     double gamma, Re, Pr, Ma;  /* Re <= 0: inviscid */
     double dt;
-    int scheme;            /* ORC_CENTRAL4 | ORC_WENO5JS | ORC_TENO5 | ORC_WENO5Z */
+    int scheme;            /* ORC_CENTRAL4 | ORC_WENO5JS | ORC_TENO5 | ORC_WENO5Z | ORC_TENO6 */
     double teno_ct;        /* TENO cut-off C_T */
     int bc[3][2];          /* per direction, side */
     double T_wall;         /* isothermal wall temperature */
@@ -132,14 +132,38 @@ void orc_linear_weights(double d[3])
     d[1] = 1.0 - d[0] - d[2];
 }
 
+static double C4[4];      /* TENO6 fourth candidate: reconstruction at x_{i+1/2} from f_{i..i+3} */
+static double D6[4];      /* d_r, TENO6 */
+
+/* TENO6 linear weights (Sec. 2.5; the values are not printed).  Reading: the unique d_r with
+ * sum_r d_r f^(r) equal to the 6-point reconstruction on {i-2..i+3}, the candidates being the
+ * three 3-point stencils of the 5th-order schemes (r = 0: {i..i+2}, 1: {i-1..i+1}, 2:
+ * {i-2..i}) and the 4-point stencil r = 3: {i..i+3}.  Solved coefficient by coefficient:
+ * f_{i-2} only in r = 2, f_{i+3} only in r = 3, f_{i-1} in r = 1 and 2, then sum d_r = 1. */
+void orc_teno6_linear_weights(double d[4])
+{
+    double c6[36], c3[9], c4[16];
+    orc_eno_coeffs(6, c6);
+    orc_eno_coeffs(3, c3);
+    orc_eno_coeffs(4, c4);
+    const double *big = &c6[2 * 6];      /* coefficient of f_{i-2+j}, j = 0..5 */
+    d[2] = big[0] / c3[2 * 3 + 0];
+    d[3] = big[5] / c4[0 * 4 + 3];
+    d[1] = (big[1] - d[2] * c3[2 * 3 + 1]) / c3[1 * 3 + 0];
+    d[0] = 1.0 - d[1] - d[2] - d[3];
+}
+
 static void init_coeffs(void)
 {
     if (coeffs_ready) return;
-    double c[9];
+    double c[9], c4[16];
     orc_eno_coeffs(3, c);
     for (int r = 0; r < 3; r++)
         for (int j = 0; j < 3; j++) C3[r][j] = c[r * 3 + j];
     orc_linear_weights(D3);
+    orc_eno_coeffs(4, c4);
+    for (int j = 0; j < 4; j++) C4[j] = c4[j];
+    orc_teno6_linear_weights(D6);
     coeffs_ready = 1;
 }
 
@@ -212,6 +236,66 @@ void orc_weights5(const double *beta, int scheme, double ct, double *w, double *
         for (int r = 0; r < 3; r++) w[r] = dl[r] / dsum;
         if (margin) *margin = mg;
     }
+}
+
+/* Smoothness indicator of the 4-point TENO6 stencil {i..i+3} (g[0..3] = f_{i..i+3}): the
+ * Jiang-Shu measure of Eq. 16 for k = 4 (sum over l = 1..3 of dx^(2l-1) times the integral over
+ * cell i of the squared l-th derivative of the cubic whose cell averages are g), written out. */
+double orc_smoothness_cubic(const double *g)
+{
+    const double a = -11.0 * g[0] + 18.0 * g[1] - 9.0 * g[2] + 2.0 * g[3];
+    const double b = 2.0 * g[0] - 5.0 * g[1] + 4.0 * g[2] - g[3];
+    const double c = -g[0] + 3.0 * g[1] - 3.0 * g[2] + g[3];
+    return a * a / 36.0 + (13.0 / 12.0) * b * b + (781.0 / 720.0) * c * c;
+}
+
+/* TENO6 weights (Eqs. 23-27 with K = 6): gamma_r = (1 + tau_6 / (beta_r + eps))^6, r = 0..3,
+ * tau_6 = |beta_3 - (beta_0 + beta_2 + 4 beta_1) / 6| as printed, eps = 1e-16, chi_r =
+ * gamma_r / sum gamma, delta_r = [chi_r >= C_T], omega_r = d_r delta_r / sum d delta.  *margin
+ * as for TENO5. */
+void orc_weights6(const double *beta, double ct, double *w, double *margin)
+{
+    init_coeffs();
+    const double eps = 1e-16;
+    const double tau = fabs(beta[3] - (beta[0] + beta[2] + 4.0 * beta[1]) / 6.0);
+    double gam[4], sg = 0.0;
+    for (int r = 0; r < 4; r++) {
+        double t = 1.0 + tau / (beta[r] + eps);
+        double t2 = t * t;
+        gam[r] = t2 * t2 * t2;
+        sg += gam[r];
+    }
+    double dsum = 0.0, dl[4], mg = INFINITY;
+    for (int r = 0; r < 4; r++) {
+        double chi = gam[r] / sg;
+        int delta = (chi < ct) ? 0 : 1;
+        double m = fabs(chi - ct) / ct;
+        if (m < mg) mg = m;
+        dl[r] = D6[r] * (double)delta;
+        dsum += dl[r];
+    }
+    for (int r = 0; r < 4; r++) w[r] = dl[r] / dsum;
+    if (margin) *margin = mg;
+}
+
+/* TENO6 reconstruction of the value at x_{i+1/2} from f[0..5] = f_{i-2..i+3}. */
+double orc_recon6(const double *f, double ct, double *wout, double *margin)
+{
+    init_coeffs();
+    double beta[4], w[4], fr[4];
+    orc_smoothness5(f, beta);
+    beta[3] = orc_smoothness_cubic(f + 2);
+    orc_weights6(beta, ct, w, margin);
+    for (int r = 0; r < 3; r++) {
+        double s = 0.0;
+        for (int j = 0; j < 3; j++) s += C3[r][j] * f[2 - r + j];
+        fr[r] = s;
+    }
+    fr[3] = 0.0;
+    for (int j = 0; j < 4; j++) fr[3] += C4[j] * f[2 + j];
+    if (wout)
+        for (int r = 0; r < 4; r++) wout[r] = w[r];
+    return w[0] * fr[0] + w[1] * fr[1] + w[2] * fr[2] + w[3] * fr[3];
 }
 
 /* Reconstruction of the value at x_{i+1/2} from f[0..4] = f_{i-2..i+2} (Eqs. 14-15). */
@@ -822,11 +906,17 @@ static void interface_flux(const orc_ctx *c, int d, long m, double *Fh, double *
             gp[s] = 0.5 * (gg + alpha * V);
             gm[s] = 0.5 * (gg - alpha * V);
         }
-        /* (e) reconstruct g+ from nodes m-2..m+2 and g- mirrored from m+3..m-1 */
-        double fm[5] = {gm[5], gm[4], gm[3], gm[2], gm[1]};
-        double m1 = INFINITY, m2 = INFINITY, w1[3], w2[3];
-        double hp = orc_recon5(gp, P->scheme, P->teno_ct, w1, &m1);
-        double hm = orc_recon5(fm, P->scheme, P->teno_ct, w2, &m2);
+        /* (e) reconstruct g+ from nodes m-2..m+2 and g- mirrored from m+3..m-1 (TENO6: g+ from
+         * m-2..m+3 and g- mirrored from m+3..m-2) */
+        double fm[6] = {gm[5], gm[4], gm[3], gm[2], gm[1], gm[0]};
+        double m1 = INFINITY, m2 = INFINITY, w1[4], w2[4], hp, hm;
+        if (P->scheme == ORC_TENO6) {
+            hp = orc_recon6(gp, P->teno_ct, w1, &m1);
+            hm = orc_recon6(fm, P->teno_ct, w2, &m2);
+        } else {
+            hp = orc_recon5(gp, P->scheme, P->teno_ct, w1, &m1);
+            hm = orc_recon5(fm, P->scheme, P->teno_ct, w2, &m2);
+        }
         if (cut && P->scheme == ORC_TENO5) {
             if (cut_matters(gp, hp, w1, floor_) || cut_matters(fm, hm, w2, floor_)) *cut = 1;
         }

@@ -7,7 +7,8 @@ plain dict:
     n        interior points (nx, ny, nz); 1 marks an inactive direction
     gamma, Re, Pr, Ma   (Re <= 0: inviscid)
     dt       fixed time step
-    scheme   0 central 4th order, 1 WENO5-JS, 2 TENO5, 3 WENO-Z (characteristic, Roe average)
+    scheme   0 central 4th order, 1 WENO5-JS, 2 TENO5, 3 WENO-Z, 4 TENO6 (characteristic, Roe
+             average)
     teno_ct  TENO cut-off C_T
     bc       bc[d][s]: 0 periodic, 1 zero-gradient, 2 isothermal wall, 3 Dirichlet, 4 inflow,
              5 adiabatic wall
@@ -35,7 +36,7 @@ import math
 
 import numpy as np
 
-CENTRAL4, WENO5JS, TENO5, WENO5Z = 0, 1, 2, 3
+CENTRAL4, WENO5JS, TENO5, WENO5Z, TENO6 = 0, 1, 2, 3, 4
 PERIODIC, ZEROGRAD, WALL, DIRICHLET, INFLOW, ADIABATIC = 0, 1, 2, 3, 4, 5
 
 

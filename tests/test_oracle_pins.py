@@ -84,6 +84,78 @@ def test_smoothness_indicators_match_integral_definition():
                                    atol=1e-13)
 
 
+# ---------------------------------------------------------------- TENO6 (Sec. 2.5, K = 6)
+def test_teno6_linear_weights_reproduce_sixth_order_reconstruction():
+    """The paper prints no TENO6 d_r; the reading is the unique set whose linear combination of
+    the candidates {i..i+2}, {i-1..i+1}, {i-2..i}, {i..i+3} is the 6-point reconstruction on
+    {i-2..i+3}: the textbook (1, -8, 37, 37, -8, 1)/60 stencil, exact for quintics.  Solving the
+    six coefficient equations by hand gives d = (3/10, 9/20, 1/20, 1/5)."""
+    d = O.teno6_linear_weights()
+    np.testing.assert_allclose(d, [0.3, 0.45, 0.05, 0.2], atol=1e-14)
+    c3, c4 = O.eno_coeffs(3), O.eno_coeffs(4)
+    np.testing.assert_allclose(c4[0], np.array([3, 13, -5, 1]) / 12.0, atol=1e-14)
+    comb = np.zeros(6)
+    for r in range(3):
+        for j in range(3):
+            comb[2 - r + j] += d[r] * c3[r, j]
+    comb[2:6] += d[3] * c4[0]
+    np.testing.assert_allclose(comb, np.array([1, -8, 37, 37, -8, 1]) / 60.0, atol=1e-14)
+    for m in range(6):
+        f = [_cell_avg_monomial(m, j) for j in range(-2, 4)]
+        assert abs(np.dot(comb, f) - 0.5 ** m) < 1e-12
+        v, _ = O.recon6(f)
+        if m <= 1:      # linear data keeps every stencil (all beta equal, tau_6 = 0)
+            assert abs(v - 0.5 ** m) < 1e-12
+
+
+def _beta_cubic_from_definition(g):
+    """Eq. 16 for k = 4: sum over l = 1..3 of the integral over cell i of (q^(l))^2, q the cubic
+    whose averages over cells i..i+3 are g (unit spacing)."""
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    xs, ws = 0.5 * xg, 0.5 * wg
+    A = np.array([[_cell_avg_monomial(m, j) for m in range(4)] for j in range(4)])
+    c = np.linalg.solve(A, np.asarray(g, dtype=float))
+    q1 = c[1] + 2 * c[2] * xs + 3 * c[3] * xs ** 2
+    q2 = 2 * c[2] + 6 * c[3] * xs
+    q3 = 6 * c[3] * np.ones_like(xs)
+    return float(np.sum(ws * (q1 ** 2 + q2 ** 2 + q3 ** 2)))
+
+
+def test_cubic_smoothness_indicator_matches_integral_definition():
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        g = rng.normal(size=4)
+        assert O.smoothness_cubic(g) == pytest.approx(_beta_cubic_from_definition(g), rel=1e-12,
+                                                      abs=1e-13)
+    # a cubic's derivatives vanish only for constants
+    assert O.smoothness_cubic([2.0, 2.0, 2.0, 2.0]) == 0.0
+
+
+def test_teno6_weights_tau6_and_cutoff():
+    """Eq. 27's tau_6 = |beta_3 - (beta_0 + beta_2 + 4 beta_1)/6| and the cut-off of Eq. 24."""
+    beta = np.array([1e-10, 2e-10, 3.0, 1e-12])
+    w, margin = O.weights6(beta, 1e-5)
+    tau = abs(beta[3] - (beta[0] + beta[2] + 4 * beta[1]) / 6)
+    gam = (1 + tau / (beta + 1e-16)) ** 6
+    chi = gam / gam.sum()
+    keep = chi >= 1e-5
+    d = np.array([0.3, 0.45, 0.05, 0.2])
+    np.testing.assert_allclose(w, d * keep / (d * keep).sum(), rtol=1e-14)
+    assert w[2] == 0.0 and w[3] > 0.0
+    assert margin == pytest.approx(np.min(np.abs(chi - 1e-5) / 1e-5), rel=1e-12)
+
+
+def test_teno6_cuts_discontinuous_stencils():
+    # step between i and i+1: only {i-2, i-1, i} is smooth
+    v, w = O.recon6([0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    np.testing.assert_array_equal(w, [0.0, 0.0, 1.0, 0.0])
+    assert v == 0.0
+    # step between i-1 and i: {i..i+2} and {i..i+3} survive, in the ratio d_0 : d_3
+    v, w = O.recon6([0.0, 0.0, 1.0, 1.0, 1.0, 1.0])
+    np.testing.assert_allclose(w, [0.6, 0.0, 0.0, 0.4], atol=1e-15)
+    assert v == pytest.approx(1.0, abs=1e-15)
+
+
 # ---------------------------------------------------------------- Eqs. 20-27: weights
 @pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5, O.WENO5Z])
 def test_linear_data_gives_optimal_weights(scheme):
@@ -160,7 +232,7 @@ def test_roe_average_satisfies_property_u():
         np.testing.assert_allclose(A @ (UR - UL), O.flux(g, UR, n) - O.flux(g, UL, n), atol=1e-12)
 
 
-@pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5])
+@pytest.mark.parametrize("scheme", [O.WENO5JS, O.TENO5, O.TENO6])
 def test_char_flux_consistency_and_order(scheme):
     g = 1.4
     # uniform data: the interface flux is the physical flux
@@ -294,6 +366,28 @@ def test_sod_wenoz_less_dissipative_than_wenojs():
     assert errs[O.WENO5Z] < errs[O.WENO5JS] < 4e-3
 
 
+def test_sod_teno6_against_exact_solution():
+    """Sec. 2.5: TENO6 on Sod (N = 400, t = 0.2) stays within the bounds of the initial data
+    (no overshoot beyond rounding), its shock within one cell of the exact one, and its L1
+    density error below the 5th-order TENO5's (the higher-order, lower-dissipation scheme)."""
+    errs = {}
+    for scheme in (O.TENO5, O.TENO6):
+        cfg, U, x = I.sod(scheme=scheme)
+        o = O.Oracle(cfg)
+        o.set_state(U)
+        o.step(800)
+        rho = o.get_state()[0, 0, 0]
+        r, _, _ = O.riemann_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+        errs[scheme] = np.abs(rho - r).mean()
+    assert rho.max() < 1.0 + 1e-6 and rho.min() > 0.125 - 1e-6
+    rr_star = float(_golden_rows("sod_star.txt")[0][3])
+    mid = 0.5 * (rr_star + 0.125)
+    xs_num = x[np.where((rho[:-1] >= mid) & (rho[1:] < mid))[0][-1]]
+    xs_ex = x[np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]]
+    assert abs(xs_num - xs_ex) <= 1.0 / 400 + 1e-12
+    assert errs[O.TENO6] < errs[O.TENO5] < 4e-3
+
+
 # ---------------------------------------------------------------- Eqs. 2-5: viscous terms
 def _line_cfg(N, Re, stretch=0.0):
     L = 2 * math.pi
@@ -359,7 +453,7 @@ def test_tgv_initial_kinetic_energy_and_dissipation():
     assert dke == pytest.approx(-0.75 / cfg["Re"], rel=0.01)
 
 
-@pytest.mark.parametrize("scheme", [O.CENTRAL4, O.TENO5, O.WENO5JS])
+@pytest.mark.parametrize("scheme", [O.CENTRAL4, O.TENO5, O.WENO5JS, O.TENO6])
 def test_discrete_conservation_periodic(scheme):
     if scheme == O.CENTRAL4:
         cfg, U = I.tgv(12, Ma=0.1, scheme=scheme)
@@ -406,12 +500,14 @@ def test_metrics_of_sinusoidal_grid():
     np.testing.assert_allclose(S[1, 0, 0] * sh[1], -y_i, atol=2e-3 * d)
 
 
-@pytest.mark.parametrize("scheme", [O.TENO5, O.WENO5Z])
-@pytest.mark.parametrize("A,order", [(0.0, 5.0), (0.04, 4.0)])
-def test_euler_wave_order_of_convergence(A, order, scheme):
+@pytest.mark.parametrize("scheme,A,order", [(O.TENO5, 0.0, 5.0), (O.TENO5, 0.04, 4.0),
+                                             (O.WENO5Z, 0.0, 5.0), (O.WENO5Z, 0.04, 4.0),
+                                             (O.TENO6, 0.0, 6.0)])
+def test_euler_wave_order_of_convergence(scheme, A, order):
     """Eq. 47 on the grid of Eqs. 48-49: L1 and Linf rates within 10 % of the formal order (the
     paper's Sec. 5.3 check of its WENO-Z schemes).  The metrics are 4th-order central (Sec. 2.7),
-    which bounds the curvilinear order at 4."""
+    which bounds the curvilinear order at 4.  TENO6 on the Cartesian grid: 6th order (its linear
+    scheme is the 6-point reconstruction)."""
     errs = []
     for N in (32, 64):
         cfg, U = I.euler_wave(N, scheme=scheme, dt=1e-3 * 32 / N, A=A)
