@@ -6,8 +6,8 @@
  *   - compressible Navier-Stokes residual (Sec. 2.1, Eqs. 1-7) on a structured grid, curvilinear
  *     through metric terms evaluated once with the 4th-order central / one-sided schemes
  *     (Sec. 2.6-2.7, Eqs. 28-33);
- *   - convective terms by characteristic-space WENO5-JS or TENO5 reconstruction with a
- *     Roe-averaged eigensystem and local Lax-Friedrichs splitting (Sec. 2.2 algorithm,
+ *   - convective terms by characteristic-space WENO5-JS, WENO-Z, TENO5 or TENO6 reconstruction
+ *     with a Roe-averaged eigensystem and local Lax-Friedrichs splitting (Sec. 2.2 algorithm,
  *     Eqs. 9-27), or 4th-order central differences (Sec. 2.6);
  *   - viscous and heat-flux terms by 4th-order central differences (Eqs. 4-5, 28-33);
  *   - the low-storage 3-stage RK update dU = A dU + dt R, U = U + B dU (Sec. 2.8, Eqs. 36-38);
@@ -45,7 +45,7 @@ enum {
 };
 
 /* convective scheme (Sec. 2.2-2.6) */
-enum { OSBLI_CENTRAL4 = 0, OSBLI_WENO5JS = 1, OSBLI_TENO5 = 2, OSBLI_WENO5Z = 3 };
+enum { OSBLI_CENTRAL4 = 0, OSBLI_WENO5JS = 1, OSBLI_TENO5 = 2, OSBLI_WENO5Z = 3, OSBLI_TENO6 = 4 };
 /* time integrator (Sec. 2.8, Eqs. 36-38): low-storage 2N Runge-Kutta, 3rd order in 3 stages
  * (Williamson) or 4th order in 5 stages (Carpenter & Kennedy) */
 enum { OSBLI_RK3 = 0, OSBLI_RK4 = 1 };
@@ -74,8 +74,11 @@ typedef struct {
                                   one >= 3 */
     double gamma, Re, Pr, Ma;  /* Re <= 0: inviscid (no viscous / heat-flux terms) */
     double dt;                 /* fixed time step */
-    int scheme;                /* OSBLI_CENTRAL4 | OSBLI_WENO5JS | OSBLI_TENO5 | OSBLI_WENO5Z (Eq. 22) */
-    double teno_ct;            /* TENO cut-off C_T (Eq. 24), e.g. 1e-5 */
+    int scheme;                /* OSBLI_CENTRAL4 | OSBLI_WENO5JS | OSBLI_TENO5 | OSBLI_WENO5Z (Eq. 22) |
+                                  OSBLI_TENO6 (K = 6: Eq. 27's tau_6, the 4-point candidate on
+                                  i..i+3, linear weights of the 6-point reconstruction; same
+                                  i-2..i+3 stencil and ghost width) */
+    double teno_ct;            /* TENO cut-off C_T (Eq. 24), e.g. 1e-5 (TENO5 and TENO6) */
     int bc[3][2];              /* bc[direction][side], side 0 = low index */
     double T_wall;             /* isothermal wall temperature (Eq. 41) */
     double sutherland_ratio;   /* T_s/T_ref of Eq. 6; <= 0: constant mu = 1 */
@@ -234,8 +237,8 @@ const char *osbli_last_error(const osbli_t *h);
  * ------------------------------------------------------------------------------------------- */
 typedef struct osbli_ens osbli_ens_t;
 
-/* params: [nprob] member descriptions (uniform grids, own n, h, dt; inviscid, Re <= 0; WENO5-JS
- * or TENO5, the same scheme and precision for every member; faces PERIODIC or ZEROGRAD; no
+/* params: [nprob] member descriptions (uniform grids, own n, h, dt; inviscid, Re <= 0; WENO5-JS,
+ * WENO-Z, TENO5 or TENO6, the same scheme and precision for every member; faces PERIODIC or ZEROGRAD; no
  * sensor).  cuda_stream: cudaStream_t for all work, or NULL for an ensemble-owned stream.
  * Errors: EINVAL (with the member index in the message), ENOMEM, ECUDA. */
 int osbli_ensemble_create(int nprob, const osbli_params *params, void *cuda_stream, osbli_ens_t **out);

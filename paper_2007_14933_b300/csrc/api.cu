@@ -110,18 +110,18 @@ static int validate(const osbli_params *p, const double *coords)
     }
     if ((long long)n[0] * n[1] * n[2] > (1LL << 31))
         return seterr(nullptr, OSBLI_EINVAL, "grid larger than 2^31 points");
-    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_WENO5Z)
+    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_TENO6)
         return seterr(nullptr, OSBLI_EINVAL, "scheme %d unknown", p->scheme);
     if (!(p->gamma > 1.0) || !(p->Ma > 0.0))
         return seterr(nullptr, OSBLI_EINVAL, "need gamma > 1 and Ma > 0");
     if (p->Re > 0.0 && !(p->Pr > 0.0)) return seterr(nullptr, OSBLI_EINVAL, "viscous run needs Pr > 0");
     if (!isfinite(p->dt) || p->dt < 0.0) return seterr(nullptr, OSBLI_EINVAL, "dt must be finite and >= 0");
-    if (p->scheme == OSBLI_TENO5 && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))
+    if ((p->scheme == OSBLI_TENO5 || p->scheme == OSBLI_TENO6) && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))
         return seterr(nullptr, OSBLI_EINVAL, "teno_ct must lie in (0, 1)");
     if (p->precision != OSBLI_FP64 && p->precision != OSBLI_MIXED)
         return seterr(nullptr, OSBLI_EINVAL, "precision %d unknown", p->precision);
     if (p->precision == OSBLI_MIXED && p->scheme == OSBLI_CENTRAL4)
-        return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / WENO-Z / TENO5");
+        return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / WENO-Z / TENO5 / TENO6");
     if (p->sensor != 0 && p->sensor != 1) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0 or 1");
     if (p->rk != OSBLI_RK3 && p->rk != OSBLI_RK4) return seterr(nullptr, OSBLI_EINVAL, "rk %d unknown", p->rk);
     if (p->sensor == 1 && (p->precision != OSBLI_MIXED || p->scheme == OSBLI_CENTRAL4))

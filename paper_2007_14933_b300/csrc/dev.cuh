@@ -18,7 +18,7 @@ constexpr int NV = 5;
 constexpr int GH = 3;   // ghost width: WENO5/TENO5 stencil i-2..i+3 (Sec. 2.3-2.5)
 
 enum { W_U = 0, W_V, W_W, W_P, W_A, W_SR, W_H, W_T, NW };
-enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2, SCH_WENO5Z = 3 };
+enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2, SCH_WENO5Z = 3, SCH_TENO6 = 4 };
 enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4, BC_ADIABATIC = 5 };
 
 struct Dev {
@@ -230,6 +230,90 @@ __device__ __forceinline__ T recon5(T f0, T f1, T f2, T f3, T f4, T ct, T es, bo
         }
         return fdiv(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// TENO6 (Sec. 2.5 with K = 6) at x_{i+1/2} from f0..f5 = f_{i-2..i+3}: the candidates and
+// indicators of recon5 plus the 4-point candidate on {i..i+3},
+//   q3 = (3 f_i + 13 f_{i+1} - 5 f_{i+2} + f_{i+3}) / 12,
+//   beta_3 = (-11 f_i + 18 f_{i+1} - 9 f_{i+2} + 2 f_{i+3})^2 / 36
+//          + 13/12 (2 f_i - 5 f_{i+1} + 4 f_{i+2} - f_{i+3})^2 + 781/720 (-f_i + 3 f_{i+1} - 3 f_{i+2} + f_{i+3})^2
+// (Eq. 16 worked out for the cubic), tau_6 = |beta_3 - (beta_0 + beta_2 + 4 beta_1)/6| (Eq. 27),
+// gamma_r = (1 + tau_6/(beta_r + eps))^6, the cut-off of TENO5, and linear weights
+// d = (3/10, 9/20, 1/20, 1/5) for (q0, q1, q2, q3): the only set whose combination is the 6-point
+// reconstruction (1, -8, 37, 37, -8, 1)/60.  Epsilon and the FP32 normalisation as in recon5.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T recon6(T f0, T f1, T f2, T f3, T f4, T f5, T ct, T es, bool *allkept = nullptr)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    const T c13_12 = T(13.0 / 12.0), q = T(0.25);
+    T a, b, c;
+    a = f2 - T(2) * f3 + f4;
+    b = T(3) * f2 - T(4) * f3 + f4;
+    const T b0 = c13_12 * a * a + q * b * b;
+    a = f1 - T(2) * f2 + f3;
+    b = f1 - f3;
+    const T b1 = c13_12 * a * a + q * b * b;
+    a = f0 - T(2) * f1 + f2;
+    b = f0 - T(4) * f1 + T(3) * f2;
+    const T b2 = c13_12 * a * a + q * b * b;
+    a = T(-11) * f2 + T(18) * f3 - T(9) * f4 + T(2) * f5;
+    b = T(2) * f2 - T(5) * f3 + T(4) * f4 - f5;
+    c = (f3 - f4) * T(3) + (f5 - f2);
+    const T b3 = T(1.0 / 36.0) * a * a + c13_12 * b * b + T(781.0 / 720.0) * c * c;
+
+    const T q0 = T(1.0 / 3.0) * f2 + T(5.0 / 6.0) * f3 - T(1.0 / 6.0) * f4;
+    const T q1 = -T(1.0 / 6.0) * f1 + T(5.0 / 6.0) * f2 + T(1.0 / 3.0) * f3;
+    const T q2 = T(1.0 / 3.0) * f0 - T(7.0 / 6.0) * f1 + T(11.0 / 6.0) * f2;
+    const T q3 = T(0.25) * f2 + T(13.0 / 12.0) * f3 - T(5.0 / 12.0) * f4 + T(1.0 / 12.0) * f5;
+
+    const T tau = fabs(b3 - T(1.0 / 6.0) * (b0 + b2 + T(4) * b1));
+    T x0, x1, x2, x3;
+    if (F32) {
+        const T eps = T(1e-12) * T(1.0 / 6.0) * (f0 * f0 + f1 * f1 + f2 * f2 + f3 * f3 + f4 * f4 + f5 * f5) + T(1e-30);
+        x0 = T(1) + fdiv(tau, b0 + eps);
+        x1 = T(1) + fdiv(tau, b1 + eps);
+        x2 = T(1) + fdiv(tau, b2 + eps);
+        x3 = T(1) + fdiv(tau, b3 + eps);
+        const T r = fdiv(T(1), fmax(fmax(x0, x1), fmax(x2, x3)));
+        x0 *= r; x1 *= r; x2 *= r; x3 *= r;
+    } else {
+        const T eps = T(1e-16) * es;
+        const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps, e3 = b3 + eps;
+        const T e01 = e0 * e1, e23 = e2 * e3;
+        const T ip = T(1) / (e01 * e23);
+        x0 = T(1) + tau * (ip * e1 * e23);
+        x1 = T(1) + tau * (ip * e0 * e23);
+        x2 = T(1) + tau * (ip * e01 * e3);
+        x3 = T(1) + tau * (ip * e01 * e2);
+    }
+    x0 = x0 * x0; x1 = x1 * x1; x2 = x2 * x2; x3 = x3 * x3;
+    const T g0 = x0 * x0 * x0, g1 = x1 * x1 * x1, g2 = x2 * x2 * x2, g3 = x3 * x3 * x3;
+    const T th = ct * ((g0 + g1) + (g2 + g3));
+    const bool k0 = g0 >= th, k1 = g1 >= th, k2 = g2 >= th, k3 = g3 >= th;
+    if (allkept) *allkept = k0 && k1 && k2 && k3;
+    const T w0 = k0 ? T(0.3) : T(0), w1 = k1 ? T(0.45) : T(0), w2 = k2 ? T(0.05) : T(0),
+            w3 = k3 ? T(0.2) : T(0);
+    const T r = w0 * q0 + w1 * q1 + w2 * q2 + w3 * q3;
+    if (k0 && k1 && k2 && k3) return r;
+    return r / ((w0 + w1) + (w2 + w3));
+}
+
+// Nodes a reconstruction reads on each side of the interface: i-2..i+2 for the 5th-order
+// schemes, i-2..i+3 for TENO6 (g+ from the left, g- mirrored from the right).
+template <int SCHEME> struct Stencil { static constexpr int NS = SCHEME == SCH_TENO6 ? 6 : 5; };
+
+// g+ reconstructed from gp[0..NS-1] (nodes i-2..), g- from gm mirrored (gm[k]: node i+3-(NS-1)+k).
+template <int SCHEME, typename T, int NS>
+__device__ __forceinline__ T recon_pair(const T (&gp)[NS], const T (&gm)[NS], T ct, T es)
+{
+    if constexpr (SCHEME == SCH_TENO6)
+        return recon6<T>(gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], ct, es) +
+               recon6<T>(gm[5], gm[4], gm[3], gm[2], gm[1], gm[0], ct, es);
+    else
+        return recon5<SCHEME, T>(gp[0], gp[1], gp[2], gp[3], gp[4], ct, es) +
+               recon5<SCHEME, T>(gm[4], gm[3], gm[2], gm[1], gm[0], ct, es);
 }
 
 // Sensor label of one TENO reconstruction (an addition to the method; the paper has none): the

@@ -123,7 +123,7 @@ extern "C" int osbli_ensemble_create(int nprob, const osbli_params *params, void
         if (q.Re > 0.0) return eseterr(nullptr, OSBLI_EINVAL, "member %d: ensembles are inviscid (Re <= 0)", p);
         if (q.sensor != 0) return eseterr(nullptr, OSBLI_EINVAL, "member %d: no learned sensor in ensembles", p);
         if (q.scheme == OSBLI_CENTRAL4)
-            return eseterr(nullptr, OSBLI_EINVAL, "member %d: ensembles run WENO5-JS, WENO-Z or TENO5", p);
+            return eseterr(nullptr, OSBLI_EINVAL, "member %d: ensembles run WENO5-JS, WENO-Z, TENO5 or TENO6", p);
         if (q.scheme != params[0].scheme || q.precision != params[0].precision || q.rk != params[0].rk)
             return eseterr(nullptr, OSBLI_EINVAL, "member %d: scheme, precision and rk must match member 0", p);
         const int n[3] = {q.nx, q.ny, q.nz};

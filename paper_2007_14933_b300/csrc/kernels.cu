@@ -385,7 +385,8 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
     const T h0 = T(0.5) * al0, h1 = T(0.5) * al1, h4 = T(0.5) * al4;
 
     // (c) projection and (d) splitting
-    T gp[NV][5], gm[NV][5];
+    constexpr int NS = Stencil<SCHEME>::NS;
+    T gp[NV][NS], gm[NV][NS];
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const long long id = m + (s - 2) * st;
@@ -435,8 +436,8 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
         const T hh[NV] = {h0, h1, h1, h1, h4};
 #pragma unroll
         for (int j = 0; j < NV; j++) {
-            if (s < 5) gp[j][s] = fma(hh[j], Vc[j], T(0.5) * Gc[j]);
-            if (s > 0) gm[j][s - 1] = fma(-hh[j], Vc[j], T(0.5) * Gc[j]);
+            if (s < NS) gp[j][s] = fma(hh[j], Vc[j], T(0.5) * Gc[j]);
+            if (s >= 6 - NS) gm[j][s - (6 - NS)] = fma(-hh[j], Vc[j], T(0.5) * Gc[j]);
         }
     }
     // (e) reconstruction
@@ -445,7 +446,8 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
     const double floor_ = LABEL ? 1e-5 * 0.5 * (q.rho(m) + q.rho(mr)) * fmax(al0, al4) : 0.0;
 #pragma unroll
     for (int j = 0; j < NV; j++) {
-        if (LABEL) {
+        if constexpr (LABEL) {
+            static_assert(NS == 5, "labels are TENO5 decisions");
             bool kp = true, km = true;
             const T vp = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, es, &kp);
             const T vm = recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, es, &km);
@@ -453,8 +455,7 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
             *label = *label || cut_matters(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], vp, kp, floor_) ||
                      cut_matters(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], vm, km, floor_);
         } else {
-            g[j] = recon5<SCHEME, T>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, es) +
-                   recon5<SCHEME, T>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, es);
+            g[j] = recon_pair<SCHEME, T, NS>(gp[j], gm[j], ct, es);
         }
     }
     // (f) back-projection F = R g
@@ -1255,7 +1256,8 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
     for (int c = 0; c < 3; c++) uc[c] = Wf[(W_U + c) * vs + m];
     const float pc = Wf[W_P * vs + m];
 
-    float gp[NV][5], gm[NV][5];
+    constexpr int NS = Stencil<SCHEME>::NS;
+    float gp[NV][NS], gm[NV][NS];
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         float Vc[NV], Gc[NV];
@@ -1313,16 +1315,14 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
         }
 #pragma unroll
         for (int j = 0; j < NV; j++) {
-            if (s < 5) gp[j][s] = fmaf(hh[j], Vc[j], 0.5f * Gc[j]);
-            if (s > 0) gm[j][s - 1] = fmaf(-hh[j], Vc[j], 0.5f * Gc[j]);
+            if (s < NS) gp[j][s] = fmaf(hh[j], Vc[j], 0.5f * Gc[j]);
+            if (s >= 6 - NS) gm[j][s - (6 - NS)] = fmaf(-hh[j], Vc[j], 0.5f * Gc[j]);
         }
     }
     float g[NV];
     const float ct = (float)P.ct;
 #pragma unroll
-    for (int j = 0; j < NV; j++)
-        g[j] = recon5<SCHEME, float>(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], ct, es) +
-               recon5<SCHEME, float>(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], ct, es);
+    for (int j = 0; j < NV; j++) g[j] = recon_pair<SCHEME, float, NS>(gp[j], gm[j], ct, es);
     const float s04 = g[0] + g[4], d40 = g[4] - g[0];
     const float sm = s04 + g[1];
     D[0] = sm;
@@ -2139,6 +2139,9 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
     } else if (P.scheme == SCH_WENO5Z) {
         if (general(P)) conv_char_launch<DIR, SCH_WENO5Z, true>(P, B, acc, chunk, grd, blk, s);
         else conv_char_launch<DIR, SCH_WENO5Z, false>(P, B, acc, chunk, grd, blk, s);
+    } else if (P.scheme == SCH_TENO6) {
+        if (general(P)) conv_char_launch<DIR, SCH_TENO6, true>(P, B, acc, chunk, grd, blk, s);
+        else conv_char_launch<DIR, SCH_TENO6, false>(P, B, acc, chunk, grd, blk, s);
     } else {
         if (general(P)) conv_char_launch<DIR, SCH_TENO5, true>(P, B, acc, chunk, grd, blk, s);
         else conv_char_launch<DIR, SCH_TENO5, false>(P, B, acc, chunk, grd, blk, s);
@@ -2176,6 +2179,7 @@ static void launch_patch(const Dev &P, const Bufs &B, cudaStream_t s)
     const int g = grid_for(N, 128);
     if (P.scheme == SCH_WENO5JS) k_patch_fix<SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
     else if (P.scheme == SCH_WENO5Z) k_patch_fix<SCH_WENO5Z><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    else if (P.scheme == SCH_TENO6) k_patch_fix<SCH_TENO6><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
     else k_patch_fix<SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
 }
 
@@ -2509,6 +2513,7 @@ int launch_ensemble_stage(const EnsLaunch &L, int stage, cudaStream_t s)
 {
     if (L.scheme == SCH_WENO5JS) return ens_stage_t<SCH_WENO5JS>(L, stage, s);
     if (L.scheme == SCH_WENO5Z) return ens_stage_t<SCH_WENO5Z>(L, stage, s);
+    if (L.scheme == SCH_TENO6) return ens_stage_t<SCH_TENO6>(L, stage, s);
     return ens_stage_t<SCH_TENO5>(L, stage, s);
 }
 

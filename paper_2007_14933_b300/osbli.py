@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libosbli.so")
 
 OSBLI_OK, OSBLI_EINVAL, OSBLI_ENOMEM, OSBLI_ECUDA, OSBLI_ENONFINITE, OSBLI_ETIMEOUT, OSBLI_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5, OSBLI_WENO5Z = 0, 1, 2, 3
+OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5, OSBLI_WENO5Z, OSBLI_TENO6 = 0, 1, 2, 3, 4
 OSBLI_PERIODIC, OSBLI_ZEROGRAD, OSBLI_WALL, OSBLI_DIRICHLET, OSBLI_INFLOW, OSBLI_ADIABATIC = 0, 1, 2, 3, 4, 5
 OSBLI_FP64, OSBLI_MIXED = 0, 1
 OSBLI_RK3, OSBLI_RK4 = 0, 1

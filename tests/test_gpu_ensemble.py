@@ -41,7 +41,7 @@ def small_members(scheme=I.TENO5, seed=7):
     return out
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.TENO6])
 def test_ensemble_fp64_members_match_oracle(scheme):
     mem = small_members(scheme)
     ens = osbli.Ensemble([c for c, _ in mem], precision=osbli.OSBLI_FP64)

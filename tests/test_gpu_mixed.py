@@ -46,7 +46,7 @@ def mixed_vs_oracle(cfg, U, steps):
     return Ug, o.get_state()
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z, I.TENO6])
 def test_mixed_tgv_smooth_phase_l2(scheme):
     # 40 steps reach t ~ 1.1, before the Ma 1.25 TGV forms shocklets (smooth flow)
     cfg, U = I.tgv(n=(32, 28, 24), Ma=1.25, scheme=scheme)
@@ -60,8 +60,14 @@ def test_mixed_curvilinear_euler_wave_l2():
     assert l2rel(Ug, Uo) <= L2_TOL
 
 
-def test_mixed_sod_shock_position_within_one_cell():
-    cfg, U, x = I.sod()
+@pytest.mark.parametrize("scheme,l2_bound", [(I.WENO5JS, 1e-4), (I.TENO6, 1e-3)])
+def test_mixed_sod_shock_position_within_one_cell(scheme, l2_bound):
+    """The bar on discontinuous flow is the shock position; the L2 difference is recorded with a
+    looser bound.  TENO6's linear scheme (all four stencils kept) is the non-dissipative 6-point
+    central reconstruction, so in the rarefaction, where FP32 and FP64 take a few cut-off
+    decisions differently, nothing damps the difference: it reaches ~2e-3 in density over the
+    rarefaction fan (L2 2.6e-4) where WENO5-JS stays near 1e-7."""
+    cfg, U, x = I.sod(scheme=scheme)
     Ug, Uo = mixed_vs_oracle(cfg, U, 800)
     rg, ro = Ug[0, 0, 0], Uo[0, 0, 0]
     mid = 0.5 * (0.26557 + 0.125)
@@ -69,7 +75,7 @@ def test_mixed_sod_shock_position_within_one_cell():
     def shock(r):
         return x[np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]]
     assert abs(shock(rg) - shock(ro)) <= 1.0 / 400 + 1e-12
-    assert l2rel(Ug, Uo) <= 1e-4          # discontinuous solution: recorded, looser
+    assert l2rel(Ug, Uo) <= l2_bound      # discontinuous solution: recorded, looser
 
 
 def test_mixed_residual_on_jumps_and_walls():

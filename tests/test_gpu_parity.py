@@ -8,7 +8,7 @@ Tolerance (plain FP64 path): max over variables v and points of |X_gpu - X_oracl
 max over points |X_oracle,v| must be <= 1e-11 (the three momentum components share one scale,
 the largest of their maxima, so that a component that vanishes in exact arithmetic -- spanwise
 momentum of a 2D flow -- is judged against the momentum, not against its own rounding noise), for single residual evaluations and after
-multi-step runs.  For TENO5 a stencil cut-off decision delta_r = [chi_r >= C_T] whose chi_r
+multi-step runs.  For TENO5 and TENO6 a stencil cut-off decision delta_r = [chi_r >= C_T] whose chi_r
 lies within rounding of C_T may legitimately differ between two correct FP64 evaluations; points
 whose oracle margin |chi - C_T|/C_T is below 1e-9 are checked separately (bounded deviation)
 instead of at 1e-11.
@@ -133,13 +133,13 @@ def test_residual_tgv_central_viscous():
     check_residual(cfg, U)
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z, I.TENO6])
 def test_residual_tgv_characteristic_viscous_ragged(scheme):
     cfg, U = I.tgv(n=(20, 12, 9), Ma=1.25, scheme=scheme)
     check_residual(cfg, U)
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.WENO5Z, I.TENO6])
 def test_residual_shocky_random_state(scheme):
     n = (13, 9, 7)
     U = I.random_state(n, seed=3, shocky=True)
@@ -153,14 +153,14 @@ def test_residual_sod():
     check_residual(cfg, U)
 
 
-@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.CENTRAL4, I.WENO5Z])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS, I.CENTRAL4, I.WENO5Z, I.TENO6])
 def test_residual_curvilinear_euler_wave(scheme):
     cfg, U = I.euler_wave(24, scheme=scheme)
     check_residual(cfg, U)
 
 
 @pytest.mark.parametrize("skew", [0.0, 0.4])
-@pytest.mark.parametrize("scheme", [I.TENO5, I.CENTRAL4])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.CENTRAL4, I.TENO6])
 def test_residual_walls_inflow_dirichlet(scheme, skew):
     cfg, U = wall_box(scheme=scheme, skew=skew)
     check_residual(cfg, U)
@@ -196,6 +196,20 @@ def test_tgv_teno_100_steps():
     cfg, U = I.tgv(12, Ma=1.25, scheme=I.TENO5)
     Ug, Uo = run_pair(cfg, U, 100)
     assert relerr(Ug, Uo) <= TOL
+
+
+def test_tgv_teno6_100_steps():
+    cfg, U = I.tgv(12, Ma=1.25, scheme=I.TENO6)
+    Ug, Uo = run_pair(cfg, U, 100)
+    assert relerr(Ug, Uo) <= TOL
+
+
+def test_sod_teno6_800_steps_matches_oracle_and_exact():
+    cfg, U, x = I.sod(scheme=I.TENO6)
+    Ug, Uo = run_pair(cfg, U, 800)
+    assert relerr(Ug, Uo) <= TOL
+    r, _, _ = O.riemann_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], 0.5, 0.2, x)
+    assert np.abs(Ug[0, 0, 0] - r).mean() < 4e-3
 
 
 def test_euler_wave_teno_100_steps():
