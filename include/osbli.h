@@ -47,8 +47,11 @@ enum {
 /* convective scheme (Sec. 2.2-2.6) */
 enum { OSBLI_CENTRAL4 = 0, OSBLI_WENO5JS = 1, OSBLI_TENO5 = 2, OSBLI_WENO5Z = 3, OSBLI_TENO6 = 4 };
 /* time integrator (Sec. 2.8, Eqs. 36-38): low-storage 2N Runge-Kutta, 3rd order in 3 stages
- * (Williamson) or 4th order in 5 stages (Carpenter & Kennedy) */
-enum { OSBLI_RK3 = 0, OSBLI_RK4 = 1 };
+ * (Williamson) or 4th order in 5 stages (Carpenter & Kennedy); or the 3rd-order
+ * strong-stability-preserving scheme of Gottlieb & Shu (1998) in its convex form
+ * (U1 = U^n + dt R(U^n), U2 = 3/4 U^n + 1/4 (U1 + dt R(U1)), U^{n+1} = 1/3 U^n + 2/3 (U2 + dt
+ * R(U2)); the second register holds U^n, so the storage is the same two arrays) */
+enum { OSBLI_RK3 = 0, OSBLI_RK4 = 1, OSBLI_SSPRK3 = 2 };
 
 /* boundary conditions per direction and side (Sec. 3.1.3, Sec. 5-6 set-ups):
  *   PERIODIC   both sides of a direction must be periodic together
@@ -88,7 +91,8 @@ typedef struct {
                                   rectilinear grid); 0: off */
     double h[3];               /* grid spacing per direction when coords == NULL */
     double L[3];               /* period of each periodic direction (coordinate unwrapping) */
-    int rk;                    /* OSBLI_RK3 (3 stages, default) | OSBLI_RK4 (5 stages) */
+    int rk;                    /* OSBLI_RK3 (3 stages, default) | OSBLI_RK4 (5 stages) |
+                                  OSBLI_SSPRK3 (3 stages) */
     double force[3];           /* body force per unit volume on the momentum; its work f.u enters
                                   the energy equation (0, 0, 0: none) */
 } osbli_params;

@@ -1232,8 +1232,16 @@ void orc_labels(void *h, unsigned char *labels)
  * scheme, A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  rk = 1: the 5-stage 4th-order 2N
  * scheme of Carpenter & Kennedy (1994, the paper's cited reference for its 4th-order
  * low-storage RK), their published rational coefficients.
+ * rk = 2: the 3rd-order strong-stability-preserving scheme the paper takes from Gottlieb & Shu
+ * (1998), whose coefficients it does not print either.  Reading: their optimal 3-stage SSP
+ * scheme in its convex form -- each stage a convex combination of U^n and one forward-Euler
+ * step of the previous stage,
+ *     U1 = U^n + dt R(U^n),  U2 = 3/4 U^n + 1/4 (U1 + dt R(U1)),
+ *     U^{n+1} = 1/3 U^n + 2/3 (U2 + dt R(U2)),
+ * with the second register holding U^n (the same two arrays per equation as the 2N form).
  * ------------------------------------------------------------------------------------------ */
-static const int RK_STAGES[2] = {3, 5};
+static const int RK_STAGES[3] = {3, 5, 3};
+static const double SSP_ALPHA[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};   /* weight of U^n per stage */
 static const double RK_A[2][5] = {{0.0, -5.0 / 9.0, -153.0 / 128.0, 0.0, 0.0},
                                   {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0, -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0}};
 static const double RK_B[2][5] = {{1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0, 0.0, 0.0},
@@ -1242,6 +1250,14 @@ static const double RK_B[2][5] = {{1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0, 0.0, 0.0}
 /* one stage of the 2N register update on n values (shared by the solver and the pins) */
 static void rk_stage_update(int rk, int stage, double dt, long n, double *U, double *dU, const double *R)
 {
+    if (rk == 2) {
+        const double a = SSP_ALPHA[stage];
+        for (long q = 0; q < n; q++) {
+            if (stage == 0) dU[q] = U[q];
+            U[q] = a * dU[q] + (1.0 - a) * (U[q] + dt * R[q]);
+        }
+        return;
+    }
     for (long q = 0; q < n; q++) {
         dU[q] = RK_A[rk][stage] * dU[q] + dt * R[q];
         U[q] = U[q] + RK_B[rk][stage] * dU[q];
@@ -1282,7 +1298,7 @@ int orc_step(void *h, int nsteps)
     int rc = 0;
     for (int n = 0; n < nsteps && rc == 0; n++) {
         for (long q = 0; q < NV * plane; q++) dUi[q] = 0.0;
-        const int rk = (P->rk == 1) ? 1 : 0;
+        const int rk = (P->rk == 1 || P->rk == 2) ? P->rk : 0;
         for (int s = 0; s < RK_STAGES[rk]; s++) {
             orc_residual(c, Ri, NULL);
             orc_get_state(c, Ui);

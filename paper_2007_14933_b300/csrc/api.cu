@@ -123,7 +123,8 @@ static int validate(const osbli_params *p, const double *coords)
     if (p->precision == OSBLI_MIXED && p->scheme == OSBLI_CENTRAL4)
         return seterr(nullptr, OSBLI_EINVAL, "the mixed precision path applies to WENO5-JS / WENO-Z / TENO5 / TENO6");
     if (p->sensor != 0 && p->sensor != 1) return seterr(nullptr, OSBLI_EINVAL, "sensor must be 0 or 1");
-    if (p->rk != OSBLI_RK3 && p->rk != OSBLI_RK4) return seterr(nullptr, OSBLI_EINVAL, "rk %d unknown", p->rk);
+    if (p->rk != OSBLI_RK3 && p->rk != OSBLI_RK4 && p->rk != OSBLI_SSPRK3)
+        return seterr(nullptr, OSBLI_EINVAL, "rk %d unknown", p->rk);
     if (p->sensor == 1 && (p->precision != OSBLI_MIXED || p->scheme == OSBLI_CENTRAL4))
         return seterr(nullptr, OSBLI_EINVAL, "the learned sensor gates the mixed-precision WENO/TENO path");
     for (int d = 0; d < 3; d++)

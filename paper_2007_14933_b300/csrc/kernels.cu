@@ -13,6 +13,7 @@ namespace osb {
 // 2N-storage RK3 of Williamson (the paper's Eqs. 36-38 leave A_i, B_i to the cited scheme).
 // Low-storage 2N Runge-Kutta coefficients (Eqs. 36-38; the paper prints none): row 0 Williamson's
 // 3-stage 3rd-order scheme, row 1 the 5-stage 4th-order scheme of Carpenter & Kennedy (1994).
+// rk = 2 (3rd-order SSP, Gottlieb & Shu 1998) runs its convex form in update_body instead.
 __constant__ double c_rkA[2][5] = {{0.0, -5.0 / 9.0, -153.0 / 128.0, 0.0, 0.0},
                                    {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
      -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0}};
@@ -971,9 +972,19 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
             } else {
                 du = P.dt * (double)r[v];
             }
-            if (STAGE > 0) du = c_rkA[P.rk][STAGE] * dU[v * vs + id] + du;
-            dU[v * vs + id] = du;
-            const double un = U[v * vs + id] + c_rkB[P.rk][STAGE] * du;
+            double un;
+            if (P.rk == 2) {
+                // SSP-RK3, convex form: the second register holds U^n (written at stage 0)
+                const double u = U[v * vs + id];
+                const double u0 = STAGE == 0 ? u : dU[v * vs + id];
+                if (STAGE == 0) dU[v * vs + id] = u;
+                const double a = STAGE == 0 ? 0.0 : (STAGE == 1 ? 0.75 : 1.0 / 3.0);
+                un = a * u0 + (1.0 - a) * (u + du);
+            } else {
+                if (STAGE > 0) du = c_rkA[P.rk][STAGE] * dU[v * vs + id] + du;
+                dU[v * vs + id] = du;
+                un = U[v * vs + id] + c_rkB[P.rk][STAGE] * du;
+            }
             U[v * vs + id] = un;
             bad |= !isfinite(un);
         }

@@ -13,7 +13,7 @@ plain dict:
     bc       bc[d][s]: 0 periodic, 1 zero-gradient, 2 isothermal wall, 3 Dirichlet, 4 inflow,
              5 adiabatic wall
     force    optional body force per unit volume (its work enters the energy equation)
-    rk       0: 3-stage RK3 (default), 1: 5-stage RK4
+    rk       0: 3-stage RK3 (default), 1: 5-stage RK4, 2: 3-stage SSP-RK3
     T_wall, suth (T_s/T_ref of Sutherland's law, <= 0: mu = 1)
     h, L     uniform spacings / periods
     coords   optional [3][nz][ny][nx] node coordinates (curvilinear grids)

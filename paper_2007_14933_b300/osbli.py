@@ -20,7 +20,7 @@ OSBLI_OK, OSBLI_EINVAL, OSBLI_ENOMEM, OSBLI_ECUDA, OSBLI_ENONFINITE, OSBLI_ETIME
 OSBLI_CENTRAL4, OSBLI_WENO5JS, OSBLI_TENO5, OSBLI_WENO5Z, OSBLI_TENO6 = 0, 1, 2, 3, 4
 OSBLI_PERIODIC, OSBLI_ZEROGRAD, OSBLI_WALL, OSBLI_DIRICHLET, OSBLI_INFLOW, OSBLI_ADIABATIC = 0, 1, 2, 3, 4, 5
 OSBLI_FP64, OSBLI_MIXED = 0, 1
-OSBLI_RK3, OSBLI_RK4 = 0, 1
+OSBLI_RK3, OSBLI_RK4, OSBLI_SSPRK3 = 0, 1, 2
 
 EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_set_state",
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",

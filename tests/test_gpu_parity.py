@@ -327,6 +327,31 @@ def test_rk4_five_stage_steps(scheme):
     assert relerr(Ug, Uo) <= TOL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ssprk3_steps(precision):
+    """The 3rd-order SSP integrator (rk = 2, convex form) against the oracle's: Sod with walls of
+    zero-gradient faces (boundary nodes) and the TENO5 TGV; the mixed path by relative L2."""
+    for cfg, U, steps in [(*I.sod()[:2], 200), (*I.tgv(12, Ma=1.25, scheme=I.TENO5), 30)]:
+        cfg = dict(cfg, rk=2)
+        if precision == "fp64":
+            Ug, Uo = run_pair(cfg, U, steps)
+            assert relerr(Ug, Uo) <= TOL
+        else:
+            s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+            s.set_state(U)
+            s.step(steps)
+            Ug = s.get_state()
+            s.close()
+            o = O.Oracle(cfg)
+            o.set_state(U)
+            o.step(steps)
+            Uo = o.get_state()
+            a, b = Ug.reshape(5, -1), Uo.reshape(5, -1)
+            nb = [np.linalg.norm(b[v]) for v in range(5)]
+            nb[1] = nb[2] = nb[3] = max(nb[1:4])
+            assert max(np.linalg.norm(a[v] - b[v]) / nb[v] for v in range(5) if nb[v] > 0) <= 1e-5
+
+
 def test_laminar_channel_adiabatic_wall_and_forcing():
     """Sec. 5.4 channel (isothermal + adiabatic walls, unit body force): the analytic state stays
     steady on the GPU (its residual is rounding noise on both sides), and from a perturbed state

@@ -293,6 +293,42 @@ def test_rk4_amplification_polynomial_and_order():
     assert 3.8 < math.log2(errs[0] / errs[1]) < 4.3
 
 
+def test_ssprk3_amplification_polynomial():
+    """rk = 2 (SSP-RK3): three stages, third order -- on y' = lambda y its amplification factor is
+    the same cubic as any 3-stage 3rd-order scheme's."""
+    for z in (0.3, -0.7, 0.5j, -0.2 + 0.9j, -1.5 + 0.4j):
+        y = O.rk_linear(2, complex(z), 1.0, 1)
+        assert abs(y - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
+
+
+def test_ssprk3_step_equals_its_butcher_form_on_the_euler_residual():
+    """One rk = 2 step of the oracle on a nonlinear problem (TENO5 TGV) equals the same scheme
+    written as a Butcher tableau -- c = (0, 1, 1/2), a21 = 1, a31 = a32 = 1/4, b = (1/6, 1/6, 2/3),
+    the expansion of the convex stages -- evaluated here from the oracle's residual alone; and
+    differs from Williamson's RK3 (same linear behaviour, different nonlinear stages)."""
+    cfg, U = I.tgv(8, Ma=1.25, scheme=O.TENO5)
+    dt = cfg["dt"]
+
+    def R(X):
+        o = O.Oracle(cfg)
+        o.set_state(X)
+        return o.residual()
+    k1 = R(U)
+    k2 = R(U + dt * k1)
+    k3 = R(U + dt * (0.25 * k1 + 0.25 * k2))
+    ref = U + dt * (k1 / 6 + k2 / 6 + 2 * k3 / 3)
+    o = O.Oracle(dict(cfg, rk=2))
+    o.set_state(U)
+    o.step(1)
+    got = o.get_state()
+    scale = np.abs(ref).reshape(5, -1).max(axis=1)[:, None]
+    assert (np.abs(got - ref).reshape(5, -1) / scale).max() < 1e-13
+    w = O.Oracle(cfg)
+    w.set_state(U)
+    w.step(1)
+    assert (np.abs(w.get_state() - got).reshape(5, -1) / scale).max() > 1e-9
+
+
 def test_rk3_third_order_in_time():
     lam = -1.0 + 2.0j
     errs = [abs(O.rk3_linear(lam, 1.0 / n, n) - np.exp(lam)) for n in (20, 40)]
