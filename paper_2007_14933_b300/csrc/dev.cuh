@@ -112,6 +112,19 @@ __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, in
     return ((long long)(k + P.g[2]) * P.np[1] + (j + P.g[1])) * P.np[0] + (i + P.g[0]);
 }
 
+// Interior point number t (x fastest) -> (i, j, k).  t < 2^31 (the largest grid osbli_create
+// accepts), so 32-bit unsigned division suffices; a 64-bit division is a long software sequence
+// that partly runs on the FP64 pipe, which B300 issues at 1/64 of the FP32 rate.
+__device__ __forceinline__ void split_ijk(const Dev &P, long long t, int &i, int &j, int &k)
+{
+    const unsigned u = (unsigned)t, n0 = (unsigned)P.n[0], n1 = (unsigned)P.n[1];
+    const unsigned q = u / n0;
+    i = (int)(u - q * n0);
+    const unsigned k_ = q / n1;
+    j = (int)(q - k_ * n1);
+    k = (int)k_;
+}
+
 // Cartesian unit frame of a direction: n = e_DIR, tangents t1, t2 with the same construction
 // rule as the general case (t1 = normalise(z x n) unless |n_z| >= 0.9, then normalise(n x x);
 // t2 = n x t1): x: (y, z); y: (-x, z); z: (y, -x).

@@ -579,6 +579,7 @@ __device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, con
     // per-direction counts of strong-jump interfaces of this stage start at zero, and so do the
     // interface flags (the convective passes set the bits of their strong-jump interfaces)
     if (bk.x == 0 && threadIdx.x < 3) nstrong[threadIdx.x] = 0;
+    const float gm1 = (float)P.gm1, gam = (float)P.gamma, gM2 = (float)P.gM2;   // once per thread
     for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
          t += (long long)bk.nx * blockDim.x) {
         float h[NV];
@@ -593,15 +594,15 @@ __device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, con
         const float rho = h[0], mx = h[1], my = h[2], mz = h[3], E = h[4];
         const float ir = 1.0f / rho;
         const float u = mx * ir, v = my * ir, w = mz * ir;
-        const float p = (float)P.gm1 * (E - 0.5f * (mx * u + my * v + mz * w));
+        const float p = gm1 * (E - 0.5f * (mx * u + my * v + mz * w));
         Wf[W_U * P.vs + t] = u;
         Wf[W_V * P.vs + t] = v;
         Wf[W_W * P.vs + t] = w;
         Wf[W_P * P.vs + t] = p;
-        Wf[W_A * P.vs + t] = sqrtf((float)P.gamma * p * ir);
+        Wf[W_A * P.vs + t] = sqrtf(gam * p * ir);
         Wf[W_SR * P.vs + t] = sqrtf(rho);
         Wf[W_H * P.vs + t] = (E + p) * ir;
-        Wf[W_T * P.vs + t] = (float)P.gM2 * p * ir;
+        Wf[W_T * P.vs + t] = gM2 * p * ir;
     }
 }
 
@@ -786,14 +787,7 @@ __device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool per)
 }
 
 // Viscous fluxes (Eqs. 2-5) at interior nodes: V[d] = (S~_d . tau_{i.}, S~_d . (u_i tau_{i.} - q)).
-// T = double (plain path) or float (mixed path: gradients, tau and q in FP32, stored as FP64).
-template <typename T>
-__device__ __forceinline__ T viscosity_t(const Dev &P, T Tm)
-{
-    if (P.suth <= 0.0) return T(1);
-    const T s = T(P.suth);
-    return Tm * sqrt(Tm) * (T(1) + s) / (Tm + s);
-}
+// T = double (plain path) or float (mixed path: gradients, tau and q in FP32, stored as FP32).
 
 template <bool CURV, typename T, typename S>
 __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ W,
@@ -801,12 +795,14 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const long long vs = P.vs;
+    // the FP64 parameters in the arithmetic type, converted once per thread (a conversion from
+    // double issues on the FP64 pipe)
+    const bool suth_on = P.suth > 0.0;
+    const T sth = T(P.suth), Re_ = T(P.Re), kq_ = T(P.kq);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % P.n[0]);
-        const long long q = t / P.n[0];
-        const int j = (int)(q % P.n[1]);
-        const int k = (int)(q / P.n[1]);
+        int i, j, k;
+        split_ijk(P, t, i, j, k);
         const int ijk[3] = {i, j, k};
         const long long id = node_index(P, i, j, k);
         T dxi[3][4];
@@ -845,8 +841,8 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
                     gr[v][c] = (sizeof(T) == 4 ? T(line_facf(P, c, ijk[c])) : T(line_fac(P, c, ijk[c]))) * dxi[c][v];
         }
         const T Tm = T(W[W_T * vs + id]);
-        const T mu = viscosity_t<T>(P, Tm);
-        const T mr = mu / T(P.Re);
+        const T mu = suth_on ? Tm * sqrt(Tm) * (T(1) + sth) / (Tm + sth) : T(1);   // Eq. 6
+        const T mr = mu / Re_;
         const T div = gr[0][0] + gr[1][1] + gr[2][2];
         T tau[3][3];
 #pragma unroll
@@ -854,7 +850,7 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
 #pragma unroll
             for (int b = 0; b < 3; b++)
                 tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? T(2.0 / 3.0) * div : T(0)));
-        const T kq = mu * T(P.kq);
+        const T kq = mu * kq_;
         const T uu[3] = {T(W[W_U * vs + id]), T(W[W_V * vs + id]), T(W[W_W * vs + id])};
         T e4[3];
 #pragma unroll
@@ -896,10 +892,8 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
     const long long vs = P.vs;
     for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < N;
          t += (long long)bk.nx * blockDim.x) {
-        const int i = (int)(t % P.n[0]);
-        const long long q = t / P.n[0];
-        const int j = (int)(q % P.n[1]);
-        const int k = (int)(q / P.n[1]);
+        int i, j, k;
+        split_ijk(P, t, i, j, k);
         const int ijk[3] = {i, j, k};
         const long long id = node_index(P, i, j, k);
         RT r[NV];
