@@ -72,9 +72,12 @@ HBM_GBS = _measured_hbm()
 # dram__bytes_read.sum + dram__bytes_write.sum per interior point of one launch, from ncu captures
 # of the same kernel on a smaller grid (traffic grows with the points processed)
 DRAM_BYTES_PER_POINT = {
-    "k_conv_delta_tile": (102.9, "ncu capture of k_conv_delta_tile<2,2> (register-window version) on "
-                                 "TGV 160^3: dram__bytes.sum.per_second x gpu__time_duration.sum = "
-                                 "421.4 MB per launch over 4.096 M points, scaled to this grid"),
+    "k_conv_delta_tile": (100.8, "ncu capture of k_conv_delta_tile<2,2> on TGV 160^3 (gated mixed form): "
+                                 "dram__bytes_read.sum 346.3 MB + dram__bytes_write.sum 66.4 MB per launch "
+                                 "over 4.096 M points, scaled to this grid"),
+    "k_conv_delta_x_win": (76.3, "ncu capture of k_conv_delta_x_win<2> on TGV 160^3 (gated mixed form): "
+                                 "dram__bytes_read.sum 247.9 MB + dram__bytes_write.sum 64.5 MB per launch "
+                                 "over 4.096 M points, scaled to this grid"),
 }
 
 

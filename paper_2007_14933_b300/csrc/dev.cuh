@@ -37,6 +37,8 @@ struct Dev {
     float dthi, dtlo;  // dt = dthi + dtlo (FP32 parts, mixed path register update)
     int mixed;         // OSBLI_MIXED: FP32 reconstruction arithmetic
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
+    float gm1f;        // gamma - 1 rounded to FP32 (an FP32 kernel converting it per thread would
+                       // issue the conversion on the FP64 pipe)
     int sensor;        // learned gate active (mixed path, Cartesian or rectilinear grids)
     int rk, nstage;    // time integrator: 0 RK3 (3 stages), 1 RK4 (5 stages), low-storage 2N
     double force[3];   // body force per unit volume; its work f.u enters the energy equation

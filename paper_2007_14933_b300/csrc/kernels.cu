@@ -1221,7 +1221,7 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
 {
     const long long vs = P.vs;
     const long long mr = m + st;
-    const float gm1 = (float)P.gm1;
+    const float gm1 = P.gm1f;
     // Roe average of nodes m, m+1 (FP32 node values)
     const float sl = Wf[W_SR * vs + m], sr = Wf[W_SR * vs + mr];
     const float inv = __fdividef(1.f, sl + sr);
@@ -1352,7 +1352,7 @@ __device__ __forceinline__ void node_dflux(const Dev &P, const float *__restrict
                                            float dF[NV])
 {
     const long long vs = P.vs;
-    const float gm1 = (float)P.gm1;
+    const float gm1 = P.gm1f;
     float dU[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) dU[v] = (Uf[v * vs + id] - Uf[v * vs + m]) + (Uf[(NV + v) * vs + id] - Uf[(NV + v) * vs + m]);
@@ -1600,7 +1600,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
     cp_async_wait_all();
     __syncthreads();
     if (!xin) return;
-    const float gm1 = (float)P.gm1;
+    const float gm1 = P.gm1f;
     const float jump = P.jump;
     if (first >= n) return;
     // staged row of node y is y - (y0 - 3); interface y lies between nodes y and y + 1.  The four
@@ -1704,7 +1704,7 @@ __global__ void __launch_bounds__(256) k_conv_delta_x_win(Dev P, const float *__
     }
     cp_async_wait_all();
     __syncthreads();
-    const float gm1 = (float)P.gm1;
+    const float gm1 = P.gm1f;
     const float jump = P.jump;
     const int ncell = min(XSEG, P.n[0] - x0);
     float d1[NV];

@@ -111,6 +111,7 @@ extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, 
     P.curv = 0;
     P.gamma = p->gamma;
     P.gm1 = p->gamma - 1.0;
+    P.gm1f = (float)P.gm1;
     P.Re = p->Re;
     P.Pr = p->Pr;
     P.Ma = p->Ma;
