@@ -52,11 +52,13 @@ UNIT = "Mpoint-stage/s"
 # Algorithmic FP64 operations per grid point per direction of one convective launch (interface
 # flux + flux difference), counted from the arithmetic of the method (fma = 2, div/sqrt/rsqrt =
 # 1; comparisons and abs not counted).  Breakdown in the design notes.
-FLOPS_CONV_POINT_DIR = {I.TENO5: 1379.0, I.WENO5JS: 1279.0, I.WENO5Z: 1359.0, I.CENTRAL4: 63.0}
+FLOPS_CONV_POINT_DIR = {I.TENO5: 1379.0, I.WENO5JS: 1279.0, I.WENO5Z: 1359.0, I.CENTRAL4: 63.0,
+                        I.TENO6: 1889.0}
 # central 4th-order interface flux in delta form (three node flux differences by the product
 # rule, the 5-point combination) + flux difference
 FLOPS_CENTRAL_DELTA = 135.0
-SCHEME_NAME = {I.TENO5: "TENO5", I.WENO5JS: "WENO5-JS", I.WENO5Z: "WENO5-Z", I.CENTRAL4: "central4"}
+SCHEME_NAME = {I.TENO5: "TENO5", I.WENO5JS: "WENO5-JS", I.WENO5Z: "WENO5-Z", I.CENTRAL4: "central4",
+               I.TENO6: "TENO6"}
 
 
 def _measured_hbm():
