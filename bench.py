@@ -74,12 +74,12 @@ HBM_GBS = _measured_hbm()
 # dram__bytes_read.sum + dram__bytes_write.sum per interior point of one launch, from ncu captures
 # of the same kernel on a smaller grid (traffic grows with the points processed)
 DRAM_BYTES_PER_POINT = {
-    "k_conv_delta_tile": (100.8, "ncu capture of k_conv_delta_tile<2,2> on TGV 160^3 (gated mixed form): "
-                                 "dram__bytes_read.sum 346.3 MB + dram__bytes_write.sum 66.4 MB per launch "
-                                 "over 4.096 M points, scaled to this grid"),
-    "k_conv_delta_x_win": (76.3, "ncu capture of k_conv_delta_x_win<2> on TGV 160^3 (gated mixed form): "
-                                 "dram__bytes_read.sum 247.9 MB + dram__bytes_write.sum 64.5 MB per launch "
-                                 "over 4.096 M points, scaled to this grid"),
+    "k_conv_delta_tile": (102.7, "ncu capture of k_conv_delta_tile<2,2> in the bench at --n 160 (learned "
+                                 "form): dram__bytes_read.sum 350.2 MB + dram__bytes_write.sum 70.6 MB per "
+                                 "launch over 4.096 M points, scaled to this grid"),
+    "k_conv_delta_x_win": (78.2, "ncu capture of k_conv_delta_x_win<2> in the bench at --n 160 (learned "
+                                 "form): dram__bytes_read.sum 251.0 MB + dram__bytes_write.sum 69.1 MB per "
+                                 "launch over 4.096 M points, scaled to this grid"),
 }
 
 
