@@ -534,18 +534,20 @@ def main():
     prof = sh.profile_residual(reps=2)
     conv = [(nm, t_) for nm, t_ in prof if nm.startswith("conv_")]
     dom_name, dom_ms = max(conv, key=lambda x: x[1])
-    flops = FLOPS_CONV_POINT_DIR[args.scheme] * npts
+    # directions the dominant launch forms (the learned form's fused x + y pass: two)
+    ndir = len(dom_name) - len("conv_")
+    flops = FLOPS_CONV_POINT_DIR[args.scheme] * npts * ndir
     gated = None
     if head == "learned":
         dg = sh.diagnostics()
         gated = {"cells": float(dg[9]), "interfaces_x": float(dg[10]),
                  "interfaces_y": float(dg[11]), "interfaces_z": float(dg[12])}
-        f_int = float(dg[10 + "xyz".index(dom_name[-1])])
-        flops = (f_int * FLOPS_CONV_POINT_DIR[args.scheme] + (1.0 - f_int) * FLOPS_CENTRAL_DELTA) * npts
+        f_int = sum(float(dg[10 + "xyz".index(c)]) for c in dom_name[5:]) / ndir
+        flops = (f_int * FLOPS_CONV_POINT_DIR[args.scheme] + (1.0 - f_int) * FLOPS_CENTRAL_DELTA) * npts * ndir
     if head in ("mixed", "learned"):
         peak, pdt = osbli.osbli_fp32_peak(), "fp32"
         if head == "learned":
-            kern = "k_conv_delta_tile" if dom_name != "conv_x" else "k_conv_delta_x_win"
+            kern = {"conv_x": "k_conv_delta_x_win", "conv_xy": "k_conv_delta_xy"}.get(dom_name, "k_conv_delta_tile")
         else:
             kern = "k_conv_char_delta" if dom_name != "conv_x" else "k_conv_char_delta_x"
         src = "FP32 FMA throughput measured in this run (osbli_fp32_peak)"
@@ -558,12 +560,12 @@ def main():
            "dtype": pdt, "peak_source": src, "flops_per_launch": flops}
     roofline = alu
     if head in ("mixed", "learned"):
-        # the same launch against HBM: algorithmic bytes per point of one delta-form direction
-        # pass = FP32 hi/lo state (40 B) + u, v, w, p (16 B) + residual write (20 B) and read when
-        # it accumulates (20 B, not the first direction) + gate byte; a, sqrt(rho), H (12 B) only
-        # for characteristic interfaces (fraction f_int)
+        # the same launch against HBM: algorithmic bytes per point of one delta-form pass (one
+        # direction, or x and y fused) = FP32 hi/lo state (40 B) + u, v, w, p (16 B) + residual
+        # write (20 B) and read when it accumulates (20 B, not the first pass) + gate byte;
+        # a, sqrt(rho), H (12 B) only for characteristic interfaces (fraction f_int)
         f_c = f_int if head == "learned" else 1.0
-        acc = 0 if dom_name == "conv_x" else 1
+        acc = 0 if dom_name in ("conv_x", "conv_xy") else 1
         bpp = 40.0 + 16.0 + 20.0 + 20.0 * acc + (1.0 if head == "learned" else 0.0) + 12.0 * f_c
         hbm_bytes = bpp * npts
         gbs = hbm_bytes / (dom_ms * 1e-3) / 1e9

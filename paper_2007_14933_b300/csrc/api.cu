@@ -506,6 +506,8 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
         }
     }
     if (P.viscous) per_stage++;
+    // gated mixed path with x and y active: one fused x + y pass (see fused_xy)
+    if (P.mixed && P.sensor && !general(P) && P.scheme != OSBLI_CENTRAL4 && P.active[0] && P.active[1]) per_stage--;
     return P.nstage * per_stage + (P.sensor ? 2 : 0);
 }
 

@@ -117,6 +117,24 @@ __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, in
 // Interior point number t (x fastest) -> (i, j, k).  t < 2^31 (the largest grid osbli_create
 // accepts), so 32-bit unsigned division suffices; a 64-bit division is a long software sequence
 // that partly runs on the FP64 pipe, which B300 issues at 1/64 of the FP32 rate.
+// Padded node index m -> interior coordinates (negative or >= n in the ghost layers), in 32-bit
+// unsigned arithmetic whenever the padded grid has fewer than 2^32 nodes.
+__device__ __forceinline__ void split_node(const Dev &P, long long m, int c[3])
+{
+    if (P.ntot < (1LL << 32)) {
+        const unsigned u = (unsigned)m, n0 = (unsigned)P.np[0], n1 = (unsigned)P.np[1];
+        const unsigned q = u / n0, k = q / n1;
+        c[0] = (int)(u - q * n0) - P.g[0];
+        c[1] = (int)(q - k * n1) - P.g[1];
+        c[2] = (int)k - P.g[2];
+    } else {
+        const long long q = m / P.np[0];
+        c[0] = (int)(m - q * P.np[0]) - P.g[0];
+        c[1] = (int)(q % P.np[1]) - P.g[1];
+        c[2] = (int)(q / P.np[1]) - P.g[2];
+    }
+}
+
 __device__ __forceinline__ void split_ijk(const Dev &P, long long t, int &i, int &j, int &k)
 {
     const unsigned u = (unsigned)t, n0 = (unsigned)P.n[0], n1 = (unsigned)P.n[1];

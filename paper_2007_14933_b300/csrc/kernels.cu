@@ -1658,6 +1658,213 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
 
 constexpr size_t TILE_SMEM = (size_t)14 * TYR * 32 * sizeof(float) + (size_t)TYR * 32;
 
+// Gated x and y passes in one kernel (x and y active).  The block stages a 38 x 38 tile of nodes
+// (32 x lanes and 32 y rows, each with a 3-node halo; FP32 hi, lo, u, v, w, p and the gate byte),
+// then
+//   phase 1 -- lane tx forms the central D of interface x + 1/2 of each of its four rows; the
+//   left neighbour's interface comes by a warp shuffle, the tile's left edge x0 - 1/2 of row q
+//   from lane q (one extra round on four lanes); the x part of the residual stays in registers;
+//   phase 2 -- the y march of k_conv_delta_tile<1> on the same staged tile adds the y part,
+// and the residual is written once: the x pass's reads of the node arrays and its residual
+// round trip through HBM are gone.  Strong-jump and gated interfaces of both directions are
+// recorded as the separate passes record them.
+constexpr int TXR = 32 + 6;        // staged columns (x0 - 3 .. x0 + 34)
+
+__device__ __forceinline__ void xnode(const float (*sT)[TYR][TXR], int r, int c, NodeW &w)
+{
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        w.h[v] = sT[v][r][c];
+        w.l[v] = sT[NV + v][r][c];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++) w.u[q] = sT[10 + q][r][c];
+    w.p = sT[13][r][c];
+}
+
+// Central D of the x interface between staged columns c and c + 1 of row r, its left node's
+// flux difference dl, and whether it must be recorded (gate on either side or a strong jump).
+__device__ __forceinline__ bool x_interface(const float (*sT)[TYR][TXR], const unsigned char (*sG)[TXR],
+                                            int r, int c, float gm1, float jump, float D[NV], float dl[NV])
+{
+    NodeW w0, w1, w2, w3;
+    xnode(sT, r, c - 1, w0);
+    xnode(sT, r, c, w1);
+    xnode(sT, r, c + 1, w2);
+    xnode(sT, r, c + 2, w3);
+    const bool cha = sG[r][c] || sG[r][c + 1] || jump2(jump, sT[13][r][c - 2], sT[0][r][c - 2], w0.p, w0.h[0]) ||
+                     jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                     jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                     jump2(jump, w3.p, w3.h[0], sT[13][r][c + 3], sT[0][r][c + 3]);
+    float fp1[NV], fp2[NV];
+    dflux_w<0>(gm1, w1, w0, dl);
+    dflux_w<0>(gm1, w1, w2, fp1);
+    dflux_w<0>(gm1, w1, w3, fp2);
+#pragma unroll
+    for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - dl[v] - fp2[v]) * (1.f / 12.f);
+    return cha;
+}
+
+__device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj, int dir, long long m,
+                                                 const float D[NV])
+{
+    sj.flag[m] |= (unsigned char)(1u << dir);
+    const int kk = atomicAdd(sj.count + dir, 1);
+    if (kk < sj.cap) sj.list[(long long)dir * sj.cap + kk] = m;
+    float *Ds = sj.Dst + (long long)dir * NV * P.vs;
+#pragma unroll
+    for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D[v];
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__restrict__ Uf,
+                                                         const float *__restrict__ Wf, float *__restrict__ Rf,
+                                                         Strong sj, const unsigned char *__restrict__ gate)
+{
+    extern __shared__ float smem_tile[];
+    float (*sT)[TYR][TXR] = reinterpret_cast<float (*)[TYR][TXR]>(smem_tile);             // [14][TYR][TXR]
+    unsigned char (*sG)[TXR] = reinterpret_cast<unsigned char (*)[TXR]>(smem_tile + 14 * TYR * TXR);
+    __shared__ float sE[8][TPT][NV];   // the tile's left-edge x interface of each row
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * 32;
+    const int x = x0 + tx;
+    const int kz = blockIdx.y;
+    const int y0 = blockIdx.z * TY;
+    const long long st = P.st[1];
+    const long long vs = P.vs;
+    const bool xin = x < P.n[0];
+    const long long zbase = node_index(P, 0, 0, kz);
+    const int n = P.n[1];
+    // stage columns x0 - 3 .. x0 + 34 (up to the row's last ghost) of rows y0 - 3 .. y0 + TY + 2
+    // (clamped to the last ghost n + 2)
+    for (int r = ty; r < TYR; r += 8) {
+        const long long rb = zbase + (long long)min(y0 - 3 + r, n + 2) * st;
+        for (int c = tx; c < TXR; c += 32) {
+            const int xx = x0 - 3 + c;
+            if (xx > P.n[0] + 2) continue;
+            const long long id = rb + xx;
+#pragma unroll
+            for (int v = 0; v < 2 * NV; v++) cp_async4(&sT[v][r][c], Uf + v * vs + id);
+#pragma unroll
+            for (int q = 0; q < 4; q++) cp_async4(&sT[10 + q][r][c], Wf + (W_U + q) * vs + id);
+            sG[r][c] = gate[id];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const float gm1 = P.gm1f;
+    const float jump = P.jump;
+    const int first = y0 + TPT * ty;             // first row of this warp (uniform per warp)
+    if (first >= n) return;
+    const int last = min(first + TPT, n);
+    // ---- phase 1: x interfaces of the warp's rows
+    if (tx < last - first) {
+        // lane q: the left-edge interface x0 - 1/2 of row first + q (staged columns 2 | 3)
+        const int r = first + tx - (y0 - 3);
+        float D[NV], dl[NV];
+        const bool cha = x_interface(sT, sG, r, 2, gm1, jump, D, dl);
+#pragma unroll
+        for (int v = 0; v < NV; v++) sE[ty][tx][v] = D[v];
+        if (cha && x0 == 0)                      // else the tile to the left owns it
+            record_interface(P, sj, 0, zbase + (long long)(first + tx) * st - 1, D);
+    }
+    __syncwarp();
+    float racc[TPT][NV];
+#pragma unroll
+    for (int q = 0; q < TPT; q++)
+#pragma unroll
+        for (int v = 0; v < NV; v++) racc[q][v] = 0.f;
+    const float facx = xin ? line_facf<0>(P, x) : 0.f;
+#pragma unroll 1
+    for (int q = 0; q < last - first; q++) {
+        const int y = first + q;
+        const int r = y - (y0 - 3);
+        float D[NV], dl[NV];
+        bool cha = false;
+        if (xin) cha = x_interface(sT, sG, r, tx + 3, gm1, jump, D, dl);
+        else {
+#pragma unroll
+            for (int v = 0; v < NV; v++) { D[v] = 0.f; dl[v] = 0.f; }
+        }
+        if (cha) record_interface(P, sj, 0, zbase + (long long)y * st + x, D);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            float Dl = __shfl_up_sync(0xffffffffu, D[v], 1);
+            if (tx == 0) Dl = sE[ty][q][v];
+            const float rx = -facx * ((D[v] - Dl) - dl[v]);
+#pragma unroll
+            for (int qq = 0; qq < TPT; qq++) racc[qq][v] = (qq == q) ? rx : racc[qq][v];   // static indexing
+        }
+    }
+    if (!xin) return;
+    // ---- phase 2: the y march of k_conv_delta_tile<1> on the staged tile (column tx + 3)
+    const int cx = tx + 3;
+    const long long base = zbase + x;
+    int r = first - 1 - (y0 - 3);
+    NodeW w0, w1, w2, w3;
+    xnode(sT, r - 1, cx, w0);
+    xnode(sT, r, cx, w1);
+    xnode(sT, r + 1, cx, w2);
+    xnode(sT, r + 2, cx, w3);
+    float Dm[NV];
+#pragma unroll 1
+    for (int y = first - 1; y < last; y++, r++) {
+        bool cha = sG[r][cx] || sG[r + 1][cx] || jump2(jump, sT[13][r - 2][cx], sT[0][r - 2][cx], w0.p, w0.h[0]) ||
+                   jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                   jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                   jump2(jump, w3.p, w3.h[0], sT[13][r + 3][cx], sT[0][r + 3][cx]);
+        float D[NV], d1[NV], fp1[NV], fp2[NV];
+        dflux_w<1>(gm1, w1, w0, d1);
+        dflux_w<1>(gm1, w1, w2, fp1);
+        dflux_w<1>(gm1, w1, w3, fp2);
+#pragma unroll
+        for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
+        const long long m = base + (long long)y * st;
+        // the interface below a warp's first row is recorded by the warp (or tile) owning the
+        // row below it, except the line's first interface
+        if (cha && (y >= first || y < 0)) record_interface(P, sj, 1, m, D);
+        if (y >= first) {
+            const float fac = line_facf<1>(P, y);
+            const int q = y - first;
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
+                float acc = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
+                Rf[v * vs + m] = acc + rr;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) Dm[v] = D[v];
+        if (y + 1 < last) {
+            w0 = w1; w1 = w2; w2 = w3;
+            xnode(sT, r + 3, cx, w3);
+        }
+    }
+}
+
+constexpr size_t XY_SMEM = (size_t)14 * TYR * TXR * sizeof(float) + (size_t)TYR * TXR;
+
+// Launch of the fused gated x + y pass (replaces the x pass and the y pass of the stage).
+template <int SCHEME>
+static void launch_delta_xy(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    static bool smem_set = false;   // one attribute call per instantiation
+    if (!smem_set) {
+        cudaFuncSetAttribute(k_conv_delta_xy<SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XY_SMEM);
+        smem_set = true;
+    }
+    dim3 g((P.n[0] + 31) / 32, P.n[2], (P.n[1] + TY - 1) / TY);
+    k_conv_delta_xy<SCHEME><<<g, dim3(32, 8), XY_SMEM, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), B.gate);
+}
+
+// The fused pass runs for the gated mixed path on Cartesian / rectilinear grids with x and y active.
+static bool fused_xy(const Dev &P)
+{
+    return P.mixed && P.sensor && !general(P) && P.scheme != SCH_CENTRAL4 && P.active[0] && P.active[1];
+}
+
 // Gated x pass: one block per row segment of XSEG nodes stages the segment's nodes with a
 // 3-node halo (FP32 hi, lo, u, v, w, p) in shared memory with coalesced loads; thread t forms the
 // central D of interface x0 + t (thread 0 also x0 - 1) from the staged nodes and records the
@@ -1846,8 +2053,8 @@ __device__ __noinline__ void fix_interface(const Dev &P, const double *__restric
                                            float *__restrict__ Dst, long long m)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
-    const long long pa = m % P.np[0], q = m / P.np[0];
-    const int c3[3] = {(int)pa - P.g[0], (int)(q % P.np[1]) - P.g[1], (int)(q / P.np[1]) - P.g[2]};
+    int c3[3];
+    split_node(P, m, c3);
     const double es = line_eps<DIR>(P, c3[DA], c3[DB]);
     const long long st = P.st[DIR];
     float Dn[NV], unused[NV];
@@ -2227,10 +2434,17 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     }
     int acc = 0;
     const bool patch = P.mixed && !general(P) && P.scheme != SCH_CENTRAL4;
+    const bool fxy = fused_xy(P);
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
-        if (tap) (*tap)(conv_names[d], s);
-        if (d == 0) conv_dir<0>(P, B, acc, s);
+        if (fxy && d == 1) continue;                     // formed with x by the fused pass
+        if (tap) (*tap)(fxy && d == 0 ? "conv_xy" : conv_names[d], s);
+        if (fxy && d == 0) {
+            if (P.scheme == SCH_WENO5JS) launch_delta_xy<SCH_WENO5JS>(P, B, s);
+            else if (P.scheme == SCH_WENO5Z) launch_delta_xy<SCH_WENO5Z>(P, B, s);
+            else if (P.scheme == SCH_TENO6) launch_delta_xy<SCH_TENO6>(P, B, s);
+            else launch_delta_xy<SCH_TENO5>(P, B, s);
+        } else if (d == 0) conv_dir<0>(P, B, acc, s);
         else if (d == 1) conv_dir<1>(P, B, acc, s);
         else conv_dir<2>(P, B, acc, s);
         acc = 1;

@@ -94,6 +94,33 @@ def test_mixed_residual_on_jumps_and_walls():
         assert err < 1e-4, err
 
 
+@pytest.mark.parametrize("scheme", [I.TENO5, I.TENO6])
+def test_gate_on_every_cell_is_the_mixed_path(scheme):
+    """With every cell flagged (threshold 1e-9) the gated passes record every interface and
+    k_patch_fix recomputes each with the characteristic flux: the state after 20 steps matches
+    the ungated mixed path (FP32 rounding order differs) and the oracle within the mixed bar."""
+    from paper_2007_14933_b300 import sensor as SN
+    cfg, U = I.tgv(n=(24, 20, 16), Ma=1.25, scheme=scheme)
+    steps = 20
+    s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+    s.set_state(U)
+    s.step(steps)
+    Um = s.get_state()
+    s.close()
+    g = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    g.set_state(U)
+    g.set_sensor(SN.default_weights(0), 1e-9)
+    g.step(steps)
+    Ug = g.get_state()
+    assert g.diagnostics()[9] > 0.99          # gated fraction of cells
+    g.close()
+    assert l2rel(Ug, Um) <= 1e-6
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(steps)
+    assert l2rel(Ug, o.get_state()) <= L2_TOL
+
+
 def test_mixed_rejects_central_scheme():
     cfg, U = I.tgv(12, Ma=0.1, scheme=I.CENTRAL4)
     with pytest.raises(osbli.OsbliError) as e:
