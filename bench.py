@@ -77,6 +77,9 @@ DRAM_BYTES_PER_POINT = {
     "k_conv_delta_tile": (102.7, "ncu capture of k_conv_delta_tile<2,2> in the bench at --n 160 (learned "
                                  "form): dram__bytes_read.sum 350.2 MB + dram__bytes_write.sum 70.6 MB per "
                                  "launch over 4.096 M points, scaled to this grid"),
+    "k_conv_delta_xy": (85.0, "ncu capture of k_conv_delta_xy<2> in the bench at --n 160 (learned form): "
+                              "dram__bytes_read.sum 272.5 MB + dram__bytes_write.sum 75.5 MB per launch "
+                              "over 4.096 M points, scaled to this grid"),
     "k_conv_delta_x_win": (78.2, "ncu capture of k_conv_delta_x_win<2> in the bench at --n 160 (learned "
                                  "form): dram__bytes_read.sum 251.0 MB + dram__bytes_write.sum 69.1 MB per "
                                  "launch over 4.096 M points, scaled to this grid"),
