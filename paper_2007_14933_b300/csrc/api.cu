@@ -184,6 +184,7 @@ extern "C" int osbli_create(const osbli_params *p, const double *coords, void *c
     P.nstage = p->rk == OSBLI_RK4 ? 5 : 3;
     P.jump = 1.5f;
     P.gm1f = (float)P.gm1;
+    for (int d = 0; d < 2; d++) set_divisor((unsigned)P.n[d], P.dvm[d], P.dvs[d]);
     if (!P.curv) {
         double hh[3];
         for (int d = 0; d < 3; d++) hh[d] = P.active[d] ? p->h[d] : 1.0;

@@ -39,6 +39,8 @@ struct Dev {
     float jump;        // mixed path: FP64 kept where max/min of p or rho over a stencil exceeds this
     float gm1f;        // gamma - 1 rounded to FP32 (an FP32 kernel converting it per thread would
                        // issue the conversion on the FP64 pipe)
+    unsigned dvm[2];   // n[0], n[1] as invariant divisors: multiplier and shifts (set_divisor;
+    int dvs[2][2];     // dvm[d] == 0: not set, plain division)
     int sensor;        // learned gate active (mixed path, Cartesian or rectilinear grids)
     int rk, nstage;    // time integrator: 0 RK3 (3 stages), 1 RK4 (5 stages), low-storage 2N
     double force[3];   // body force per unit volume; its work f.u enters the energy equation
@@ -135,12 +137,31 @@ __device__ __forceinline__ void split_node(const Dev &P, long long m, int c[3])
     }
 }
 
+// Unsigned 32-bit division by an invariant divisor d as a multiply-high and two shifts
+// (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994,
+// Fig. 4.1): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> s1)) >> s2
+// with t = mulhi(m, n), s1 = min(l, 1), s2 = max(l - 1, 0); exact for every 32-bit n.
+inline void set_divisor(unsigned d, unsigned &m, int s[2])
+{
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    s[0] = l < 1 ? l : 1;
+    s[1] = l > 1 ? l - 1 : 0;
+}
+__device__ __forceinline__ unsigned div_inv(unsigned n, unsigned m, const int s[2])
+{
+    const unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s[0])) >> s[1];
+}
+
 __device__ __forceinline__ void split_ijk(const Dev &P, long long t, int &i, int &j, int &k)
 {
     const unsigned u = (unsigned)t, n0 = (unsigned)P.n[0], n1 = (unsigned)P.n[1];
-    const unsigned q = u / n0;
+    const bool inv = P.dvm[0] != 0 && P.dvm[1] != 0;
+    const unsigned q = inv ? div_inv(u, P.dvm[0], P.dvs[0]) : u / n0;
     i = (int)(u - q * n0);
-    const unsigned k_ = q / n1;
+    const unsigned k_ = inv ? div_inv(q, P.dvm[1], P.dvs[1]) : q / n1;
     j = (int)(q - k_ * n1);
     k = (int)k_;
 }
