@@ -61,6 +61,22 @@ SCHEME_NAME = {I.TENO5: "TENO5", I.WENO5JS: "WENO5-JS", I.WENO5Z: "WENO5-Z", I.C
                I.TENO6: "TENO6"}
 
 
+def max_over_ranks(x, dist, device):
+    """The job's time is its slowest rank's: the largest x over the ranks (x itself when dist is
+    None).  device: where the reduction tensor lives (cuda for NCCL, cpu for gloo)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(points_per_rank, steps, world, seconds, stages=3):
+    """Whole-job Mpoint-stage/s: every rank advances its own replica of points_per_rank points
+    (weak scaling) by `steps` RK steps of `stages` stages in `seconds` (the slowest rank's)."""
+    return points_per_rank * stages * steps * world / seconds / 1e6
+
+
 def _measured_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -338,10 +354,7 @@ def run_ensemble(args, world, rank, local):
         e1.record(stream)
         e1.synchronize()
         barrier()
-        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
 
     gpu_index = torch.cuda.current_device()
     res = {}
@@ -365,7 +378,7 @@ def run_ensemble(args, world, rank, local):
         e64 = make(osbli.OSBLI_FP64)
         res["fp64"] = timed(e64.step)
     clocks = clk.summary()
-    forms = {f: {"value": npts * 3 * args.steps * world / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps}
+    forms = {f: {"value": job_rate(npts, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps}
              for f, ms in res.items()}
     l2 = 0.0
     for p in range(len(cfgs)):
@@ -386,9 +399,9 @@ def run_ensemble(args, world, rank, local):
             ens.step(1)
             for p, o in enumerate(outs):
                 osbli.osbli_ensemble_get_state(ens.e, p, o)
-        el = time.perf_counter() - t0
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         byt = int(sum(h.numel() for h in hosts) * 8)
-        e2e = {"value": npts * 3 * args.steps * world / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": byt,
+        e2e = {"value": job_rate(npts, args.steps, world, el), "unit": UNIT, "h2d_bytes_per_step": byt,
                "d2h_bytes_per_step": byt,
                "api": "osbli_ensemble_set_state(host) x64 + osbli_ensemble_step(1) + osbli_ensemble_get_state(host) x64"}
     ens.close()
@@ -449,10 +462,7 @@ def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sens
     e1.synchronize()
     torch.cuda.synchronize()
     barrier()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return s, float(t.item())
+    return s, max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
 
 
 def main():
@@ -530,7 +540,7 @@ def main():
                                sensor if f == "learned" else None)
     clocks = clk.summary()
     sh, ms_max = res[head]
-    value = npts * 3 * args.steps * world / (ms_max / 1e3) / 1e6
+    value = job_rate(npts, args.steps, world, ms_max / 1e3)
     launches = sh.launches_per_step() * args.steps
 
     # per-kernel durations of one residual evaluation of the headline form (CUDA events)
@@ -586,7 +596,7 @@ def main():
     out_forms = {}
     for f in forms:
         s_, ms_ = res[f]
-        out_forms[f] = {"value": npts * 3 * args.steps * world / (ms_ / 1e3) / 1e6,
+        out_forms[f] = {"value": job_rate(npts, args.steps, world, ms_ / 1e3),
                         "ms_per_step": ms_ / args.steps}
     extra = {"forms": out_forms}
     if "fp64" in forms and len(forms) > 1:
@@ -623,12 +633,8 @@ def main():
             osbli.osbli_set_state(sh.h, Uh)
             osbli.osbli_rk_step(sh.h, 1)
             osbli.osbli_get_state(sh.h, Uo)
-        el = time.perf_counter() - t0
-        tt = torch.tensor([el], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        el = float(tt.item())
-        e2e = {"value": npts * 3 * args.steps * world / el / 1e6, "unit": UNIT,
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": job_rate(npts, args.steps, world, el), "unit": UNIT,
                "h2d_bytes_per_step": int(Uh.numel() * 8), "d2h_bytes_per_step": int(Uo.numel() * 8),
                "api": "osbli_set_state(host) + osbli_rk_step(1) + osbli_get_state(host)"}
         launches_e2e = (sh.launches_per_step() + 2) * args.steps
