@@ -1662,8 +1662,9 @@ constexpr size_t TILE_SMEM = (size_t)14 * TYR * 32 * sizeof(float) + (size_t)TYR
 // (32 x lanes and 32 y rows, each with a 3-node halo; FP32 hi, lo, u, v, w, p and the gate byte),
 // then
 //   phase 1 -- lane tx forms the central D of interface x + 1/2 of each of its four rows; the
-//   left neighbour's interface comes by a warp shuffle, the tile's left edge x0 - 1/2 of row q
-//   from lane q (one extra round on four lanes); the x part of the residual stays in registers;
+//   left neighbour's interface comes by a warp shuffle; the tile's left edges x0 - 1/2 of all 32
+//   rows are formed by warp 0 in one extra round (lane l: row l) and passed through shared
+//   memory after a block barrier; the x part of the residual stays in registers;
 //   phase 2 -- the y march of k_conv_delta_tile<1> on the same staged tile adds the y part,
 // and the residual is written once: the x pass's reads of the node arrays and its residual
 // round trip through HBM are gone.  Strong-jump and gated interfaces of both directions are
@@ -1724,7 +1725,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__
     extern __shared__ float smem_tile[];
     float (*sT)[TYR][TXR] = reinterpret_cast<float (*)[TYR][TXR]>(smem_tile);             // [14][TYR][TXR]
     unsigned char (*sG)[TXR] = reinterpret_cast<unsigned char (*)[TXR]>(smem_tile + 14 * TYR * TXR);
-    __shared__ float sE[8][TPT][NV];   // the tile's left-edge x interface of each row
+    __shared__ float sE[TY][NV];       // the tile's left-edge x interface of each row
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * 32;
     const int x = x0 + tx;
@@ -1755,20 +1756,18 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__
     const float gm1 = P.gm1f;
     const float jump = P.jump;
     const int first = y0 + TPT * ty;             // first row of this warp (uniform per warp)
-    if (first >= n) return;
-    const int last = min(first + TPT, n);
+    const int last = min(first + TPT, n);        // first >= n: no rows (still at the barrier)
     // ---- phase 1: x interfaces of the warp's rows
-    if (tx < last - first) {
-        // lane q: the left-edge interface x0 - 1/2 of row first + q (staged columns 2 | 3)
-        const int r = first + tx - (y0 - 3);
+    if (ty == 0 && y0 + tx < n) {
+        // warp 0, lane l: the left-edge interface x0 - 1/2 of row y0 + l (staged columns 2 | 3)
+        const int r = tx + 3;
         float D[NV], dl[NV];
         const bool cha = x_interface(sT, sG, r, 2, gm1, jump, D, dl);
 #pragma unroll
-        for (int v = 0; v < NV; v++) sE[ty][tx][v] = D[v];
+        for (int v = 0; v < NV; v++) sE[tx][v] = D[v];
         if (cha && x0 == 0)                      // else the tile to the left owns it
-            record_interface(P, sj, 0, zbase + (long long)(first + tx) * st - 1, D);
+            record_interface(P, sj, 0, zbase + (long long)(y0 + tx) * st - 1, D);
     }
-    __syncwarp();
     float racc[TPT][NV];
 #pragma unroll
     for (int q = 0; q < TPT; q++)
@@ -1789,14 +1788,21 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__
         if (cha) record_interface(P, sj, 0, zbase + (long long)y * st + x, D);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            float Dl = __shfl_up_sync(0xffffffffu, D[v], 1);
-            if (tx == 0) Dl = sE[ty][q][v];
-            const float rx = -facx * ((D[v] - Dl) - dl[v]);
+            const float Dl = __shfl_up_sync(0xffffffffu, D[v], 1);   // lane 0: edge added below
+            const float rx = -facx * ((D[v] - (tx == 0 ? 0.f : Dl)) - dl[v]);
 #pragma unroll
             for (int qq = 0; qq < TPT; qq++) racc[qq][v] = (qq == q) ? rx : racc[qq][v];   // static indexing
         }
     }
-    if (!xin) return;
+    __syncthreads();                             // the left edges of warp 0 are in sE
+    if (tx == 0) {
+#pragma unroll
+        for (int q = 0; q < TPT; q++)
+#pragma unroll
+            for (int v = 0; v < NV; v++)
+                racc[q][v] += (first + q < last) ? facx * sE[TPT * ty + q][v] : 0.f;
+    }
+    if (!xin || first >= n) return;
     // ---- phase 2: the y march of k_conv_delta_tile<1> on the staged tile (column tx + 3)
     const int cx = tx + 3;
     const long long base = zbase + x;
