@@ -1599,35 +1599,36 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
             racc[q][v] = (accumulate && xin && first + q < last) ? Rf[v * vs + base + (long long)(first + q) * st] : 0.f;
     cp_async_wait_all();
     __syncthreads();
-    if (!xin) return;
     const float gm1 = P.gm1f;
     const float jump = P.jump;
-    if (first >= n) return;
-    // staged row of node y is y - (y0 - 3); interface y lies between nodes y and y + 1.  The four
-    // nodes of an interface's central flux are kept in registers and shifted by one per node.
-    int r = first - 1 - (y0 - 3);
-    NodeW w0, w1, w2, w3;
-    tnode(sT, r - 1, tx, w0);
-    tnode(sT, r, tx, w1);
-    tnode(sT, r + 1, tx, w2);
-    tnode(sT, r + 2, tx, w3);
-    float Dm[NV];
-#pragma unroll 1
-    for (int y = first - 1; y < last; y++, r++) {
-        bool cha = sG[r][tx] || sG[r + 1][tx] || jump2(jump, sT[13][r - 2][tx], sT[0][r - 2][tx], w0.p, w0.h[0]) ||
-                   jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                   jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                   jump2(jump, w3.p, w3.h[0], sT[13][r + 3][tx], sT[0][r + 3][tx]);
+    // staged row of node y is y - (y0 - 3); interface y + 1/2 lies between nodes y and y + 1.
+    // The four nodes of an interface's central flux are kept in registers and shifted by one
+    // per node.  The interface below a warp's first node is the last one of the warp below,
+    // handed over through shared memory after a barrier; the tile's bottom edge y0 - 1/2 is
+    // formed by warp 0 in one extra round.
+    __shared__ float sY[8][NV][32];
+    const bool work = xin && first < n;
+    if (ty == 0 && xin && y0 < n) {
+        NodeW w0, w1, w2, w3;
+        tnode(sT, 1, tx, w0);
+        tnode(sT, 2, tx, w1);
+        tnode(sT, 3, tx, w2);
+        tnode(sT, 4, tx, w3);
+        const bool cha = sG[2][tx] || sG[3][tx] || jump2(jump, sT[13][0][tx], sT[0][0][tx], w0.p, w0.h[0]) ||
+                         jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                         jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                         jump2(jump, w3.p, w3.h[0], sT[13][5][tx], sT[0][5][tx]);
         float D[NV], d1[NV], fp1[NV], fp2[NV];
         dflux_w<DIR>(gm1, w1, w0, d1);
         dflux_w<DIR>(gm1, w1, w2, fp1);
         dflux_w<DIR>(gm1, w1, w3, fp2);
 #pragma unroll
-        for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
-        const long long m = base + (long long)y * st;
-        // the interface left of a thread's first node is recorded by the thread (or tile) owning
-        // the node to its left, except the line's first interface
-        if (cha && (y >= first || y < 0)) {
+        for (int v = 0; v < NV; v++) {
+            D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
+            sY[0][v][tx] = D[v];
+        }
+        if (cha && y0 == 0) {                        // the line's first interface
+            const long long m = base - st;
             sj.flag[m] |= (unsigned char)(1u << DIR);
             const int kk = atomicAdd(sj.count + DIR, 1);
             if (kk < sj.cap) sj.list[(long long)DIR * sj.cap + kk] = m;
@@ -1635,23 +1636,73 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
 #pragma unroll
             for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
         }
-        if (y >= first) {
+    }
+    float part[NV];                                  // first node's residual without its lower interface
+    if (work) {
+        int r = first - (y0 - 3);
+        NodeW w0, w1, w2, w3;
+        tnode(sT, r - 1, tx, w0);
+        tnode(sT, r, tx, w1);
+        tnode(sT, r + 1, tx, w2);
+        tnode(sT, r + 2, tx, w3);
+        float Dm[NV];
+#pragma unroll 1
+        for (int y = first; y < last; y++, r++) {
+            bool cha = sG[r][tx] || sG[r + 1][tx] || jump2(jump, sT[13][r - 2][tx], sT[0][r - 2][tx], w0.p, w0.h[0]) ||
+                       jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                       jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                       jump2(jump, w3.p, w3.h[0], sT[13][r + 3][tx], sT[0][r + 3][tx]);
+            float D[NV], d1[NV], fp1[NV], fp2[NV];
+            dflux_w<DIR>(gm1, w1, w0, d1);
+            dflux_w<DIR>(gm1, w1, w2, fp1);
+            dflux_w<DIR>(gm1, w1, w3, fp2);
+#pragma unroll
+            for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
+            const long long m = base + (long long)y * st;
+            if (cha) {                               // interface y + 1/2: owned by node y
+                sj.flag[m] |= (unsigned char)(1u << DIR);
+                const int kk = atomicAdd(sj.count + DIR, 1);
+                if (kk < sj.cap) sj.list[(long long)DIR * sj.cap + kk] = m;
+                float *Ds = sj.Dst + (long long)DIR * NV * vs;
+#pragma unroll
+                for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
+            }
             const float fac = line_facf<DIR>(P, y);
             const int q = y - first;
+            if (q == 0) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) {
-                const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
-                float acc = 0.f;
+                for (int v = 0; v < NV; v++) part[v] = -fac * (D[v] - d1[v]);
+            } else {
 #pragma unroll
-                for (int qq = 0; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
-                Rf[v * vs + m] = accumulate ? acc + rr : rr;
+                for (int v = 0; v < NV; v++) {
+                    const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int qq = 1; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
+                    Rf[v * vs + m] = accumulate ? acc + rr : rr;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; v++) Dm[v] = D[v];
+            if (y + 1 < last) {
+                w0 = w1; w1 = w2; w2 = w3;
+                tnode(sT, r + 3, tx, w3);
             }
         }
+        // the warp above (if it has nodes) takes this warp's last interface as its lower one
+        if (ty < 7 && last == first + TPT && last < n) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) Dm[v] = D[v];
-        if (y + 1 < last) {
-            w0 = w1; w1 = w2; w2 = w3;
-            tnode(sT, r + 3, tx, w3);
+            for (int v = 0; v < NV; v++) sY[ty + 1][v][tx] = Dm[v];
+        }
+    }
+    __syncthreads();
+    if (work) {
+        const float fac = line_facf<DIR>(P, first);
+        const long long m = base + (long long)first * st;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const float rr = part[v] + fac * sY[ty][v][tx];
+            Rf[v * vs + m] = accumulate ? racc[0][v] + rr : rr;
         }
     }
 }
@@ -1802,51 +1853,91 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__
             for (int v = 0; v < NV; v++)
                 racc[q][v] += (first + q < last) ? facx * sE[TPT * ty + q][v] : 0.f;
     }
-    if (!xin || first >= n) return;
-    // ---- phase 2: the y march of k_conv_delta_tile<1> on the staged tile (column tx + 3)
+    // ---- phase 2: the y march on the staged tile (column tx + 3).  The interface below a
+    // warp's first row is the last one of the warp below, handed over through shared memory
+    // after a barrier; the tile's bottom edge y0 - 1/2 is formed by warp 0 in one extra round.
+    __shared__ float sY[8][NV][32];
     const int cx = tx + 3;
     const long long base = zbase + x;
-    int r = first - 1 - (y0 - 3);
-    NodeW w0, w1, w2, w3;
-    xnode(sT, r - 1, cx, w0);
-    xnode(sT, r, cx, w1);
-    xnode(sT, r + 1, cx, w2);
-    xnode(sT, r + 2, cx, w3);
-    float Dm[NV];
-#pragma unroll 1
-    for (int y = first - 1; y < last; y++, r++) {
-        bool cha = sG[r][cx] || sG[r + 1][cx] || jump2(jump, sT[13][r - 2][cx], sT[0][r - 2][cx], w0.p, w0.h[0]) ||
-                   jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                   jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                   jump2(jump, w3.p, w3.h[0], sT[13][r + 3][cx], sT[0][r + 3][cx]);
+    const bool work = xin && first < n;
+    if (ty == 0 && xin && y0 < n) {
+        // nodes y0 - 1 (staged row 2) and y0: the interface recorded only at the line's start
+        NodeW w0, w1, w2, w3;
+        xnode(sT, 1, cx, w0);
+        xnode(sT, 2, cx, w1);
+        xnode(sT, 3, cx, w2);
+        xnode(sT, 4, cx, w3);
+        const bool cha = sG[2][cx] || sG[3][cx] || jump2(jump, sT[13][0][cx], sT[0][0][cx], w0.p, w0.h[0]) ||
+                         jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                         jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                         jump2(jump, w3.p, w3.h[0], sT[13][5][cx], sT[0][5][cx]);
         float D[NV], d1[NV], fp1[NV], fp2[NV];
         dflux_w<1>(gm1, w1, w0, d1);
         dflux_w<1>(gm1, w1, w2, fp1);
         dflux_w<1>(gm1, w1, w3, fp2);
 #pragma unroll
-        for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
-        const long long m = base + (long long)y * st;
-        // the interface below a warp's first row is recorded by the warp (or tile) owning the
-        // row below it, except the line's first interface
-        if (cha && (y >= first || y < 0)) record_interface(P, sj, 1, m, D);
-        if (y >= first) {
+        for (int v = 0; v < NV; v++) {
+            D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
+            sY[0][v][tx] = D[v];
+        }
+        if (cha && y0 == 0) record_interface(P, sj, 1, base - st, D);
+    }
+    float part[NV];                              // first row's residual without its lower interface
+    if (work) {
+        int r = first - (y0 - 3);
+        NodeW w0, w1, w2, w3;
+        xnode(sT, r - 1, cx, w0);
+        xnode(sT, r, cx, w1);
+        xnode(sT, r + 1, cx, w2);
+        xnode(sT, r + 2, cx, w3);
+        float Dm[NV];
+#pragma unroll 1
+        for (int y = first; y < last; y++, r++) {
+            bool cha = sG[r][cx] || sG[r + 1][cx] || jump2(jump, sT[13][r - 2][cx], sT[0][r - 2][cx], w0.p, w0.h[0]) ||
+                       jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
+                       jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
+                       jump2(jump, w3.p, w3.h[0], sT[13][r + 3][cx], sT[0][r + 3][cx]);
+            float D[NV], d1[NV], fp1[NV], fp2[NV];
+            dflux_w<1>(gm1, w1, w0, d1);
+            dflux_w<1>(gm1, w1, w2, fp1);
+            dflux_w<1>(gm1, w1, w3, fp2);
+#pragma unroll
+            for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
+            const long long m = base + (long long)y * st;
+            if (cha) record_interface(P, sj, 1, m, D);     // interface y + 1/2: owned by row y
             const float fac = line_facf<1>(P, y);
             const int q = y - first;
+            if (q == 0) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) {
-                const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
-                float acc = 0.f;
+                for (int v = 0; v < NV; v++) part[v] = -fac * (D[v] - d1[v]);
+            } else {
 #pragma unroll
-                for (int qq = 0; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
-                Rf[v * vs + m] = acc + rr;
+                for (int v = 0; v < NV; v++) {
+                    const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int qq = 1; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
+                    Rf[v * vs + m] = acc + rr;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; v++) Dm[v] = D[v];
+            if (y + 1 < last) {
+                w0 = w1; w1 = w2; w2 = w3;
+                xnode(sT, r + 3, cx, w3);
             }
         }
+        // the warp above (if it has rows) takes this warp's last interface as its lower one
+        if (ty < 7 && last == first + TPT && last < n) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) Dm[v] = D[v];
-        if (y + 1 < last) {
-            w0 = w1; w1 = w2; w2 = w3;
-            xnode(sT, r + 3, cx, w3);
+            for (int v = 0; v < NV; v++) sY[ty + 1][v][tx] = Dm[v];
         }
+    }
+    __syncthreads();
+    if (work) {
+        const float fac = line_facf<1>(P, first);
+#pragma unroll
+        for (int v = 0; v < NV; v++) Rf[v * vs + base + (long long)first * st] = racc[0][v] + (part[v] + fac * sY[ty][v][tx]);
     }
 }
 
