@@ -91,10 +91,10 @@ HBM_GBS = _measured_hbm()
 # of the same kernel on a smaller grid (traffic grows with the points processed)
 DRAM_BYTES_PER_POINT = {
     "k_conv_delta_tile": (102.7, "ncu capture of k_conv_delta_tile<2,2> in the bench at --n 160 (learned "
-                                 "form): dram__bytes_read.sum 350.2 MB + dram__bytes_write.sum 70.6 MB per "
+                                 "form): dram__bytes_read.sum 350.8 MB + dram__bytes_write.sum 69.9 MB per "
                                  "launch over 4.096 M points, scaled to this grid"),
-    "k_conv_delta_xy": (85.0, "ncu capture of k_conv_delta_xy<2> in the bench at --n 160 (learned form): "
-                              "dram__bytes_read.sum 272.5 MB + dram__bytes_write.sum 75.5 MB per launch "
+    "k_conv_delta_xy": (84.9, "ncu capture of k_conv_delta_xy<2> in the bench at --n 160 (learned form): "
+                              "dram__bytes_read.sum 272.6 MB + dram__bytes_write.sum 75.2 MB per launch "
                               "over 4.096 M points, scaled to this grid"),
     "k_conv_delta_x_win": (78.2, "ncu capture of k_conv_delta_x_win<2> in the bench at --n 160 (learned "
                                  "form): dram__bytes_read.sum 251.0 MB + dram__bytes_write.sum 69.1 MB per "
