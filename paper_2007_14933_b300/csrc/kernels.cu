@@ -113,12 +113,31 @@ __device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *
     const long long plane = (long long)P.n[da] * P.n[db];
     for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)bk.nx * blockDim.x) {
-        const int ia = (int)(t % npa);
-        long long q = t / npa;
-        const int ib = (int)(q % npb);
-        q /= npb;
-        const int gi = (int)(q % GH) + 1;
-        const int s = (int)(q / GH);
+        int ia, ib, gi, s;
+        if (d == 0) {
+            // x faces: the six ghost layers of a row are the fastest index, so that consecutive
+            // threads touch the three contiguous ghost nodes at each end of one row
+            const int gs = (int)(t % (2 * GH));
+            const long long q = t / (2 * GH);
+            gi = gs % GH + 1;
+            s = gs / GH;
+            if (tot < (1LL << 32)) {
+                const unsigned qq = (unsigned)q, na = (unsigned)npa;
+                const unsigned b = qq / na;
+                ia = (int)(qq - b * na);
+                ib = (int)b;
+            } else {
+                ia = (int)(q % npa);
+                ib = (int)(q / npa);
+            }
+        } else {
+            ia = (int)(t % npa);
+            long long q = t / npa;
+            ib = (int)(q % npb);
+            q /= npb;
+            gi = (int)(q % GH) + 1;
+            s = (int)(q / GH);
+        }
         const int bc = P.bc[d][s];
         int ii[3];
         ii[da] = ia - P.g[da];
