@@ -121,6 +121,31 @@ def test_gate_on_every_cell_is_the_mixed_path(scheme):
     assert l2rel(Ug, o.get_state()) <= L2_TOL
 
 
+def test_gate_on_every_cell_is_the_mixed_path_in_2d():
+    """2D four-quadrant Riemann problem (z inactive, zero-gradient faces, ragged 45 x 38 tiles):
+    with every cell flagged, the fused x + y pass plus the patch pass match the ungated mixed path
+    to FP32 rounding order, shocks and all (strong jumps take the FP64 flux on both paths)."""
+    from paper_2007_14933_b300 import sensor as SN
+    quad = [(1.5, 0.0, 0.0, 1.5), (0.5323, 1.206, 0.0, 0.3), (0.138, 1.206, 1.206, 0.029),
+            (0.5323, 0.0, 1.206, 0.3)]
+    cfg, U = I.riemann2d(45, quad, scheme=I.TENO5, ny=38)
+    steps = 15
+    m = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+    m.set_state(U)
+    m.step(steps)
+    Um = m.get_state()
+    m.close()
+    g = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    g.set_state(U)
+    g.set_sensor(SN.default_weights(0), 1e-9)
+    g.step(steps)
+    Ug = g.get_state()
+    assert g.diagnostics()[9] > 0.99
+    g.close()
+    assert np.isfinite(Ug).all()
+    assert l2rel(Ug, Um) <= 1e-6
+
+
 def test_mixed_rejects_central_scheme():
     cfg, U = I.tgv(12, Ma=0.1, scheme=I.CENTRAL4)
     with pytest.raises(osbli.OsbliError) as e:
