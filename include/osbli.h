@@ -207,13 +207,16 @@ int osbli_launches_per_step(const osbli_t *h);
  * The intermediate arrays live in one static device array of 30 doubles x
  * OSBLI_NOALLOC_MAX_NODES (15.7 MB) that every GPU using the library holds until the process
  * exits.  Same arithmetic as osbli_residual.
- *   p        parameters as for osbli_create; uniform grid only (spacing h), faces PERIODIC,
- *            ZEROGRAD or WALL only (no face data), FP64, no sensor
+ *   p        parameters as for osbli_create (every scheme, Sutherland viscosity, body force);
+ *            restricted to a uniform grid (spacing h), faces PERIODIC, ZEROGRAD or WALL
+ *            (T_wall > 0) only -- no face data, so no DIRICHLET / INFLOW / ADIABATIC faces --,
+ *            precision OSBLI_FP64 and no sensor (the mixed-precision path is not offered here)
  *   d_U      device pointer, [5][nz][ny][nx] FP64 state (read)
  *   d_R      device pointer, [5][nz][ny][nx] FP64 residual (written)
  *   stream   cudaStream_t the work is enqueued on; the call synchronises it before returning.
  * Returns OSBLI_OK, EINVAL (bad parameters, or a grid beyond OSBLI_NOALLOC_MAX_NODES: the message
- * from osbli_last_error(NULL) names both sizes) or ECUDA.  The first call on a device looks up
+ * from osbli_last_error(NULL) names both sizes), ENONFINITE (the residual written to d_R holds a
+ * non-finite value) or ECUDA.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  All calls share the array and it keeps the previous call's
  * contents (the ghosted state is cleared at the start of each call); calls whose GPU work

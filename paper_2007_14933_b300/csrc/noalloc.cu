@@ -63,6 +63,15 @@ int scratch_address(double **out)
     return OSBLI_OK;
 }
 
+// error word bit 0 when any of the n output values is not finite
+__global__ void k_nonfinite(const double *__restrict__ R, long long n, int *__restrict__ err)
+{
+    bool bad = false;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(R[t]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, 1);
+}
+
 }  // namespace
 
 extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, double *d_R,
@@ -82,6 +91,8 @@ extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, 
             const int bc = p->bc[d][s];
             if (bc != OSBLI_PERIODIC && bc != OSBLI_ZEROGRAD && bc != OSBLI_WALL)
                 return fail(OSBLI_EINVAL, "direction %lld: only periodic, zero-gradient and wall faces (bc %lld)", d, bc);
+            if (P.active[d] && bc == OSBLI_WALL && !(p->T_wall > 0.0))
+                return fail(OSBLI_EINVAL, "direction %lld: a wall face needs T_wall > 0", d);
             P.bc[d][s] = bc;
         }
         if (!P.active[d]) continue;
@@ -91,10 +102,10 @@ extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, 
         if (n[d] < (per ? 3 : 5)) return fail(OSBLI_EINVAL, "direction %lld too short (%lld points)", d, n[d]);
         if (!(p->h[d] > 0.0)) return fail(OSBLI_EINVAL, "h[%lld] must be > 0", d);
     }
-    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_WENO5Z) return fail(OSBLI_EINVAL, "unknown scheme");
+    if (p->scheme < OSBLI_CENTRAL4 || p->scheme > OSBLI_TENO6) return fail(OSBLI_EINVAL, "unknown scheme %lld", p->scheme);
     if (!(p->gamma > 1.0) || !(p->Ma > 0.0)) return fail(OSBLI_EINVAL, "need gamma > 1 and Ma > 0");
     if (p->Re > 0.0 && !(p->Pr > 0.0)) return fail(OSBLI_EINVAL, "viscous run needs Pr > 0");
-    if (p->scheme == OSBLI_TENO5 && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))
+    if ((p->scheme == OSBLI_TENO5 || p->scheme == OSBLI_TENO6) && !(p->teno_ct > 0.0 && p->teno_ct < 1.0))
         return fail(OSBLI_EINVAL, "teno_ct must lie in (0, 1)");
     if (p->precision != OSBLI_FP64 || p->sensor != 0) return fail(OSBLI_EINVAL, "FP64 without sensor only");
 
@@ -121,6 +132,10 @@ extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, 
     P.gM2 = p->gamma * p->Ma * p->Ma;
     P.kq = P.viscous ? 1.0 / ((p->gamma - 1.0) * p->Ma * p->Ma * p->Pr * p->Re) : 0.0;
     P.dt = p->dt;
+    for (int d = 0; d < 3; d++) P.force[d] = p->force[d];
+    P.forced = p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0;
+    if (!isfinite(p->force[0]) || !isfinite(p->force[1]) || !isfinite(p->force[2]))
+        return fail(OSBLI_EINVAL, "force must be finite");
     double hh[3];
     for (int d = 0; d < 3; d++) hh[d] = P.active[d] ? p->h[d] : 1.0;
     const double Jinv = hh[0] * (hh[1] * hh[2]);
@@ -145,8 +160,13 @@ extern "C" int osbli_residual_noalloc(const osbli_params *p, const double *d_U, 
     launch_unpack(P, d_U, B.U, NV, s);
     launch_residual(P, B, s);
     launch_pack(P, B.R, d_R, NV, s);
+    const long long nout = (long long)NV * P.n[0] * P.n[1] * P.n[2];
+    k_nonfinite<<<(int)((nout + 255) / 256 < 1024 ? (nout + 255) / 256 : 1024), 256, 0, s>>>(d_R, nout, B.err);
+    int word = 0;
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, B.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(OSBLI_ECUDA, "residual launch failed (%lld)", (long long)e);
+    if (word & 1) return fail(OSBLI_ENONFINITE, "the residual holds non-finite values");
     return OSBLI_OK;
 }
