@@ -71,6 +71,8 @@ def lib():
         for f in (L.orc_set_state, L.orc_get_state):
             f.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_residual.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_residual_ex.argtypes = [ctypes.c_void_p] * 4
+        L.orc_set_gate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]
         L.orc_residual_points.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]
         L.orc_labels.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -184,11 +186,26 @@ class Oracle:
         lib().orc_get_state(self._h, _p(U))
         return U
 
-    def residual(self, with_margin=False):
+    def residual(self, with_margin=False, with_jump_margin=False):
+        """R(U).  with_margin: also the per-node smallest TENO |chi - C_T|/C_T; with_jump_margin
+        (gated form): also the per-node smallest |ratio/jump - 1| of its strong-jump tests."""
         R = np.empty(self.shape)
         m = np.empty(self.shape[1:]) if with_margin else None
-        lib().orc_residual(self._h, _p(R), _p(m) if with_margin else None)
-        return (R, m) if with_margin else R
+        jm = np.empty(self.shape[1:]) if with_jump_margin else None
+        lib().orc_residual_ex(self._h, _p(R), _p(m) if with_margin else None,
+                              _p(jm) if with_jump_margin else None)
+        out = (R,) + ((m,) if with_margin else ()) + ((jm,) if with_jump_margin else ())
+        return out if len(out) > 1 else R
+
+    def set_gate(self, gate, jump=1.5):
+        """Gated convective form: gate [nz][ny][nx] (nonzero = the cell's interfaces take the
+        characteristic flux), interfaces with a strong jump (ratio > jump) too, the others the
+        central 4th-order interface flux.  None returns to the plain scheme."""
+        if gate is None:
+            lib().orc_set_gate(self._h, None, float(jump))
+            return
+        g = np.ascontiguousarray(gate, dtype=np.uint8).reshape(self.shape[1:])
+        lib().orc_set_gate(self._h, _p(g), float(jump))
 
     def residual_points(self, ijk, with_margin=False):
         ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)

@@ -72,6 +72,8 @@ typedef struct {
     double shat[3];
     int active[3];
     double margin_min;  /* smallest TENO |chi - C_T|/C_T seen by the last residual */
+    unsigned char *gate;/* cell gate of the gated convective form ([nz][ny][nx]) or NULL */
+    double jump;        /* strong-jump ratio of the gated form */
 } orc_ctx;
 
 /* ------------------------------------------------------------------------------------------
@@ -958,6 +960,88 @@ void orc_char_flux_1d(double gamma, int scheme, double ct, const double *U6 /* [
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Gated convective form (the learned-sensor extension; the paper has no sensor and runs one
+ * scheme everywhere).  A cell gate g (one byte per interior node, an input) chooses, per
+ * interface i+1/2 of direction d:
+ *   - the characteristic WENO/TENO flux above (Sec. 2.2) when g_i or g_{i+1} is set, or when
+ *     the interface's six-node stencil i-2..i+3 holds two adjacent nodes whose pressure ratio
+ *     or density ratio (larger over smaller) exceeds `jump` (a strong jump);
+ *   - otherwise the central 4th-order interface flux
+ *         F^_{i+1/2} = [7 (F_i + F_{i+1}) - (F_{i-1} + F_{i+2})] / 12
+ *     of each node's contravariant flux: the flux form of the first-derivative operator of
+ *     Sec. 2.6 (Eq. 28 with the sign of the generated kernel of Sec. 4), since
+ *     F^_{i+1/2} - F^_{i-1/2} = (F_{i-2} - 8 F_{i-1} + 8 F_{i+1} - F_{i+2}) / 12.
+ * Reading for ghost nodes (non-periodic ends): the central flux reads the ghost values like the
+ * characteristic one (no one-sided closure), and a ghost node takes the gate of the node its
+ * value comes from -- the periodic image, else the nearest interior node of the line.
+ * ------------------------------------------------------------------------------------------ */
+static int gate_at(const orc_ctx *c, const int *ii)
+{
+    int x[3];
+    for (int d = 0; d < 3; d++) {
+        int n = c->p.n[d], y = ii[d];
+        if (y < 0 || y >= n) {
+            if (c->p.bc[d][0] == ORC_PERIODIC) y = wrapi(y, n);
+            else y = y < 0 ? 0 : n - 1;
+        }
+        x[d] = y;
+    }
+    return c->gate[((long)x[2] * c->p.n[1] + x[1]) * c->p.n[0] + x[0]] != 0;
+}
+
+/* Strong-jump test of the interface between line index ii[d] and ii[d] + 1; *jm receives the
+ * smallest |ratio / jump - 1| over the five adjacent pairs (how close the decision came). */
+static int strong_jump(const orc_ctx *c, int d, const int *ii, double *jm)
+{
+    const orc_params *P = &c->p;
+    double pr[6], rh[6];
+    int jj[3] = {ii[0], ii[1], ii[2]};
+    for (int s = 0; s < 6; s++) {
+        jj[d] = ii[d] + s - 2;
+        double u5[5];
+        prim_t w;
+        load_state(c->U, IDX(c, jj[0], jj[1], jj[2]), c->ntot, u5);
+        primitives(P, u5, &w);
+        pr[s] = w.p;
+        rh[s] = w.rho;
+    }
+    int strong = 0;
+    for (int s = 1; s < 6; s++) {
+        double qa = pr[s] > pr[s - 1] ? pr[s] / pr[s - 1] : pr[s - 1] / pr[s];
+        double qb = rh[s] > rh[s - 1] ? rh[s] / rh[s - 1] : rh[s - 1] / rh[s];
+        if (qa > c->jump || qb > c->jump) strong = 1;
+        double ma = fabs(qa / c->jump - 1.0), mb = fabs(qb / c->jump - 1.0);
+        if (ma < *jm) *jm = ma;
+        if (mb < *jm) *jm = mb;
+    }
+    return strong;
+}
+
+/* Interface flux of the gated form between line index ii[d] and ii[d] + 1 (node id m). */
+static void gated_flux(const orc_ctx *c, int d, const int *ii, double *Fh, double *margin, double *jm)
+{
+    long st = c->st[d];
+    long m = IDX(c, ii[0], ii[1], ii[2]);
+    int ir[3] = {ii[0], ii[1], ii[2]};
+    ir[d] = ii[d] + 1;
+    int strong = strong_jump(c, d, ii, jm);
+    if (strong || gate_at(c, ii) || gate_at(c, ir)) {
+        interface_flux(c, d, m, Fh, margin, NULL);
+        return;
+    }
+    double F[4][NV];
+    for (int s = 0; s < 4; s++) {
+        long id = m + (long)(s - 1) * st;
+        double u5[5], S[3];
+        load_state(c->U, id, c->ntot, u5);
+        for (int cc = 0; cc < 3; cc++) S[cc] = c->S[(d * 3 + cc) * c->ntot + id];
+        orc_flux(c->p.gamma, u5, S, F[s]);
+    }
+    for (int v = 0; v < NV; v++)
+        Fh[v] = (7.0 * (F[1][v] + F[2][v]) - (F[0][v] + F[3][v])) / 12.0;
+}
+
+/* ------------------------------------------------------------------------------------------
  * Viscous and heat-flux terms (Eqs. 2-5, central 4th order of Sec. 2.6 with the metric chain
  * rule d/dx_j = sum_d (s_d/Jinv) S~_{d,j} d/dxi_d).  Reading: the viscous terms are written
  * in flux form, d/dxi_d( S~_d . tau ) etc., with the same first-derivative operator for the
@@ -1060,7 +1144,8 @@ static double cflux_fetch(const void *ud, int s)
 /* ------------------------------------------------------------------------------------------
  * Residual at one interior node: R = conv_x + conv_y + conv_z + viscous  (Eqs. 1-3, 10).
  * ------------------------------------------------------------------------------------------ */
-static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double *margin, int *cut)
+static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double *margin, int *cut,
+                        double *jm)
 {
     const orc_params *P = &c->p;
     long id = IDX(c, i, j, k);
@@ -1069,7 +1154,15 @@ static void residual_at(const orc_ctx *c, int i, int j, int k, double *R, double
     for (int d = 0; d < 3; d++) {
         if (!c->active[d]) continue;
         double fac = c->shat[d] * c->Jr[id];
-        if (P->scheme == ORC_CENTRAL4) {
+        if (c->gate && !cut && P->scheme != ORC_CENTRAL4) {
+            /* gated form: interfaces i+1/2 and i-1/2 of this direction */
+            double Fp[NV], Fm[NV], jdummy = INFINITY;
+            int il[3] = {i, j, k};
+            il[d] = ii[d] - 1;
+            gated_flux(c, d, ii, Fp, margin, jm ? jm : &jdummy);
+            gated_flux(c, d, il, Fm, margin, jm ? jm : &jdummy);
+            for (int v = 0; v < NV; v++) R[v] -= fac * (Fp[v] - Fm[v]);
+        } else if (P->scheme == ORC_CENTRAL4) {
             for (int v = 0; v < NV; v++) {
                 cf_ud ud = {c, d, v, i, j, k};
                 double D = deriv4(cflux_fetch, &ud, ii[d], P->n[d], P->bc[d][0] == ORC_PERIODIC);
@@ -1138,7 +1231,7 @@ void orc_destroy(void *h)
 {
     orc_ctx *c = (orc_ctx *)h;
     if (!c) return;
-    free(c->U); free(c->dU); free(c->Rw); free(c->S); free(c->Jr);
+    free(c->U); free(c->dU); free(c->Rw); free(c->S); free(c->Jr); free(c->gate);
     free(c);
 }
 
@@ -1170,8 +1263,9 @@ void orc_get_state(void *h, double *U)
 
 /* Residual R(U) of the current state on every interior node, [5][nz][ny][nx].  When margin
  * is not NULL it receives, per node, the smallest TENO |chi - C_T|/C_T over the interfaces
- * that node's residual used. */
-void orc_residual(void *h, double *R, double *margin)
+ * that node's residual used; jmargin (gated form, may be NULL) the smallest |ratio/jump - 1|
+ * of the strong-jump tests of those interfaces. */
+void orc_residual_ex(void *h, double *R, double *margin, double *jmargin)
 {
     orc_ctx *c = (orc_ctx *)h;
     const orc_params *P = &c->p;
@@ -1182,12 +1276,33 @@ void orc_residual(void *h, double *R, double *margin)
         int j = (int)(line % P->n[1]), k = (int)(line / P->n[1]);
         for (int i = 0; i < P->n[0]; i++) {
             double r[NV], mg = INFINITY;
-            residual_at(c, i, j, k, r, &mg, NULL);
+            double jm = INFINITY;
+            residual_at(c, i, j, k, r, &mg, NULL, &jm);
             long o = ((long)k * P->n[1] + j) * P->n[0] + i;
             for (int v = 0; v < NV; v++) R[v * plane + o] = r[v];
             if (margin) margin[o] = mg;
+            if (jmargin) jmargin[o] = jm;
         }
     }
+}
+
+void orc_residual(void *h, double *R, double *margin)
+{
+    orc_residual_ex(h, R, margin, NULL);
+}
+
+/* Install the cell gate of the gated convective form (gate: [nz][ny][nx] bytes, copied; NULL
+ * returns to the plain scheme) and its strong-jump ratio.  Later residuals and steps use it. */
+void orc_set_gate(void *h, const unsigned char *gate, double jump)
+{
+    orc_ctx *c = (orc_ctx *)h;
+    free(c->gate);
+    c->gate = NULL;
+    c->jump = jump;
+    if (!gate) return;
+    long n = (long)c->p.n[0] * c->p.n[1] * c->p.n[2];
+    c->gate = (unsigned char *)malloc((size_t)n);
+    memcpy(c->gate, gate, (size_t)n);
 }
 
 /* Residual at listed interior nodes only: ijk[3*p + d], R[5*p + v]. */
@@ -1198,7 +1313,7 @@ void orc_residual_points(void *h, int npts, const int *ijk, double *R, double *m
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < npts; q++) {
         double r[NV], mg = INFINITY;
-        residual_at(c, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r, &mg, NULL);
+        residual_at(c, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r, &mg, NULL, NULL);
         for (int v = 0; v < NV; v++) R[5 * q + v] = r[v];
         if (margin) margin[q] = mg;
     }
@@ -1220,7 +1335,7 @@ void orc_labels(void *h, unsigned char *labels)
         for (int i = 0; i < P->n[0]; i++) {
             double r[NV], mg = INFINITY;
             int cut = 0;
-            residual_at(c, i, j, k, r, &mg, &cut);
+            residual_at(c, i, j, k, r, &mg, &cut, NULL);
             labels[((long)k * P->n[1] + j) * P->n[0] + i] = (unsigned char)cut;
         }
     }
