@@ -161,6 +161,17 @@ const char *osbli_profile_name(const osbli_t *h, int i);
  * params.sensor = 1; required before stepping.  Errors: EINVAL. */
 int osbli_sensor_set_weights(osbli_t *h, const float *w, float threshold);
 
+/* Install a fixed cell gate in place of the network's decision (handle created with
+ * params.sensor = 1): flags [nz][ny][nx] bytes, host or device, nonzero = the cell is flagged.
+ * The gate rule is the learned one -- an interface takes the characteristic flux when either
+ * adjacent cell is flagged (a ghost cell takes the flag of its periodic image, else of the
+ * nearest interior cell of its line) or its six-node stencil holds an adjacent pressure or
+ * density ratio above 1.5, and the central 4th-order interface flux
+ * [7 (F_i + F_{i+1}) - (F_{i-1} + F_{i+2})] / 12 (Sec. 2.6, Eq. 28 in flux form) otherwise --
+ * and stays until the next osbli_sensor_set_gate or osbli_sensor_set_weights; no inference runs
+ * while it holds.  Copied in; synchronises.  Errors: EINVAL (no sensor on the handle), ECUDA. */
+int osbli_sensor_set_gate(osbli_t *h, const uint8_t *flags);
+
 /* Training labels of the current state (TENO5 handles, any precision): 1 for a cell whose FP64
  * TENO5 residual used an interface where a candidate stencil was cut and the cut moved the
  * reconstruction by more than 5 % of the stencil's range and by more than 1e-5 x the interface's

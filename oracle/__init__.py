@@ -8,9 +8,12 @@ Parity pins (see ``tests/test_oracle_pins.py``): ENO coefficients and optimal we
 TENO6) against the polynomial-exactness definition, the printed smoothness indicators against their integral definition
 (Eq. 16), WENO/TENO weights on linear and discontinuous data, eigensystem identities, the RK3
 amplification polynomial, the exact Riemann solution for Sod, the closed-form viscous and heat-flux
-residuals, TGV kinetic-energy pins, discrete conservation and the curvilinear order of convergence.
-Functions without such a pin: the isothermal-wall, Dirichlet and inflow ghost values beyond the
-linear-profile identity ("parity unpinned" for the full config-4 flow field).
+residuals, TGV kinetic-energy pins (initial values and the energy budget over 200 steps), discrete
+conservation, the curvilinear order of convergence, the isothermal-wall ghosts on a linear profile,
+the Dirichlet and inflow faces against their definition (and a uniform stream through them staying
+exact), and the gated convective form against the central and characteristic forms
+(``tests/test_oracle_gated.py``).  Without such a pin: the developed flow field of the
+shock / boundary-layer box ("parity unpinned"; no reference data exist for it).
 """
 import ctypes
 import os

@@ -72,6 +72,10 @@ typedef struct {
     double shat[3];
     int active[3];
     double margin_min;  /* smallest TENO |chi - C_T|/C_T seen by the last residual */
+    double *Vn;         /* [3 dir][4 comp][nz][ny][nx] viscous flux of every interior node of the
+                           current state (filled before each residual; each value is computed
+                           once and read by the divergences that need it) */
+    int vn_valid;       /* Vn holds the current state's fluxes */
     unsigned char *gate;/* cell gate of the gated convective form ([nz][ny][nx]) or NULL */
     double jump;        /* strong-jump ratio of the gated form */
 } orc_ctx;
@@ -1118,11 +1122,40 @@ static double vflux_fetch(const void *ud, int s)
 {
     const vf_ud *a = (const vf_ud *)ud;
     const orc_ctx *c = a->c;
+    const orc_params *P = &c->p;
     int ii[3] = {a->i, a->j, a->k};
-    ii[a->d] = (c->p.bc[a->d][0] == ORC_PERIODIC) ? wrapi(s, c->p.n[a->d]) : s;
-    double out[4];
-    viscous_flux(c, a->d, ii[0], ii[1], ii[2], out);
-    return out[a->comp];
+    ii[a->d] = (P->bc[a->d][0] == ORC_PERIODIC) ? wrapi(s, P->n[a->d]) : s;
+    if (!c->vn_valid) {   /* sampled residuals: the flux of this node only */
+        double out[4];
+        viscous_flux(c, a->d, ii[0], ii[1], ii[2], out);
+        return out[a->comp];
+    }
+    long N = (long)P->n[0] * P->n[1] * P->n[2];
+    long o = ((long)ii[2] * P->n[1] + ii[1]) * P->n[0] + ii[0];
+    return c->Vn[(long)(a->d * 4 + a->comp) * N + o];
+}
+
+/* viscous_flux of every interior node and direction into c->Vn (the values the divergence
+ * differences read; computing them once per residual instead of once per use changes no bit) */
+static void viscous_nodes(orc_ctx *c)
+{
+    const orc_params *P = &c->p;
+    long N = (long)P->n[0] * P->n[1] * P->n[2];
+    if (!c->Vn) c->Vn = (double *)calloc((size_t)12 * N, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long line = 0; line < (long)P->n[1] * P->n[2]; line++) {
+        int j = (int)(line % P->n[1]), k = (int)(line / P->n[1]);
+        for (int i = 0; i < P->n[0]; i++) {
+            long o = ((long)k * P->n[1] + j) * P->n[0] + i;
+            for (int d = 0; d < 3; d++) {
+                if (!c->active[d]) continue;
+                double out[4];
+                viscous_flux(c, d, i, j, k, out);
+                for (int q = 0; q < 4; q++) c->Vn[(long)(d * 4 + q) * N + o] = out[q];
+            }
+        }
+    }
+    c->vn_valid = 1;
 }
 
 /* central convective flux component along direction d at node index s of the line */
@@ -1231,7 +1264,7 @@ void orc_destroy(void *h)
 {
     orc_ctx *c = (orc_ctx *)h;
     if (!c) return;
-    free(c->U); free(c->dU); free(c->Rw); free(c->S); free(c->Jr); free(c->gate);
+    free(c->U); free(c->dU); free(c->Rw); free(c->S); free(c->Jr); free(c->gate); free(c->Vn);
     free(c);
 }
 
@@ -1270,6 +1303,7 @@ void orc_residual_ex(void *h, double *R, double *margin, double *jmargin)
     orc_ctx *c = (orc_ctx *)h;
     const orc_params *P = &c->p;
     ghost_fill(c);
+    if (P->Re > 0.0) viscous_nodes(c);
     long plane = (long)P->n[0] * P->n[1] * P->n[2];
 #pragma omp parallel for schedule(dynamic, 1)
     for (long line = 0; line < (long)P->n[1] * P->n[2]; line++) {
@@ -1310,6 +1344,7 @@ void orc_residual_points(void *h, int npts, const int *ijk, double *R, double *m
 {
     orc_ctx *c = (orc_ctx *)h;
     ghost_fill(c);
+    c->vn_valid = 0;   /* a few points of a possibly large grid: no full-grid table */
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < npts; q++) {
         double r[NV], mg = INFINITY;
@@ -1329,6 +1364,7 @@ void orc_labels(void *h, unsigned char *labels)
     orc_ctx *c = (orc_ctx *)h;
     const orc_params *P = &c->p;
     ghost_fill(c);
+    if (P->Re > 0.0) viscous_nodes(c);
 #pragma omp parallel for schedule(dynamic, 1)
     for (long line = 0; line < (long)P->n[1] * P->n[2]; line++) {
         int j = (int)(line % P->n[1]), k = (int)(line / P->n[1]);

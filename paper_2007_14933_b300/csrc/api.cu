@@ -28,6 +28,7 @@ struct osbli {
     cudaGraphExec_t gexec = nullptr;
     int launches_step = 0;
     bool sensor_ready = false;
+    bool weights_set = false;
     double *lfac[3] = {nullptr, nullptr, nullptr};   // rectilinear grids: per-line factors
     double *lesc[3] = {nullptr, nullptr, nullptr};   // and per-line epsilon scales
     float *lfacf[3] = {nullptr, nullptr, nullptr};   // FP32 copies of the factors
@@ -377,7 +378,7 @@ extern "C" int osbli_get_state(osbli_t *h, double *U)
 static int check_faces(osbli *h)
 {
     if (h->P.sensor && !h->sensor_ready)
-        return seterr(h, OSBLI_ESTATE, "the learned sensor needs osbli_sensor_set_weights");
+        return seterr(h, OSBLI_ESTATE, "the learned sensor needs osbli_sensor_set_weights or osbli_sensor_set_gate");
     for (int f = 0; f < 6; f++)
         if (h->B.bd[f] && !h->bdata_set[f])
             return seterr(h, OSBLI_ESTATE, "face (%d,%d) needs osbli_set_boundary_data", f / 2, f % 2);
@@ -509,7 +510,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     if (P.viscous) per_stage++;
     // gated mixed path with x and y active: one fused x + y pass (see fused_xy)
     if (P.mixed && P.sensor && !general(P) && P.scheme != OSBLI_CENTRAL4 && P.active[0] && P.active[1]) per_stage--;
-    return P.nstage * per_stage + (P.sensor ? 2 : 0);
+    return P.nstage * per_stage + (P.sensor && !h->B.gate_fixed ? 2 : 0);
 }
 
 extern "C" const char *osbli_last_error(const osbli_t *h)
@@ -542,10 +543,34 @@ extern "C" int osbli_sensor_set_weights(osbli_t *h, const float *w, float thresh
     if (sensor_upload(w, h->B.sw, h->stream) != OSBLI_OK) return seterr(h, OSBLI_ECUDA, "weight upload failed");
     h->B.zthresh = logf(threshold / (1.f - threshold));
     h->sensor_ready = true;
+    h->weights_set = true;
+    h->B.gate_fixed = 0;
     if (h->gexec) {   // the captured step holds the old threshold
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
     }
+    h->launches_step = 0;
+    return OSBLI_OK;
+}
+
+extern "C" int osbli_sensor_set_gate(osbli_t *h, const uint8_t *flags)
+{
+    if (!h || !flags) return seterr(h, OSBLI_EINVAL, "null argument");
+    if (!h->P.sensor) return seterr(h, OSBLI_EINVAL, "handle created without the sensor (params.sensor = 0)");
+    const long long N = npoints(h->P);
+    // the compact flags pass through the staging buffer (5 N doubles >= N bytes)
+    unsigned char *dflags = reinterpret_cast<unsigned char *>(h->stage);
+    CK(h, cudaMemcpyAsync(dflags, flags, (size_t)N, cudaMemcpyDefault, h->stream));
+    launch_fixed_gate(h->P, h->B, dflags, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->B.gate_fixed = 1;
+    h->sensor_ready = true;
+    if (h->gexec) {   // the captured step evaluates the network
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    h->launches_step = 0;
     return OSBLI_OK;
 }
 
@@ -588,7 +613,7 @@ extern "C" int osbli_sensor_features(osbli_t *h, void *d_feats)
 extern "C" int osbli_sensor_probs(osbli_t *h, float *probs)
 {
     if (!h || !probs) return seterr(h, OSBLI_EINVAL, "null argument");
-    if (!h->P.sensor || !h->sensor_ready) return seterr(h, OSBLI_ESTATE, "sensor weights not set");
+    if (!h->P.sensor || !h->weights_set) return seterr(h, OSBLI_ESTATE, "sensor weights not set");
     if (!h->state_set) return seterr(h, OSBLI_ESTATE, "osbli_set_state has not been called");
     const long long N = npoints(h->P);
     float *d = nullptr;

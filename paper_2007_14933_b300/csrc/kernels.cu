@@ -2544,7 +2544,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
     else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
     launches++;
-    if (P.sensor && sensor_now) {
+    if (P.sensor && sensor_now && !B.gate_fixed) {
         if (tap) (*tap)("sensor", s);
         launches += launch_sensor_gate(P, B, s);
     }

@@ -22,6 +22,7 @@ struct Bufs {
     void *sw = nullptr;                                // sensor: device weights (BF16 / FP32)
     unsigned char *sflag = nullptr, *gate = nullptr;   // sensor: cell flags, dilated gate [vs]
     float zthresh = 0.f;                               // sensor: logit of the decision threshold
+    int gate_fixed = 0;                                // sensor: gate from caller flags (no inference)
     int *err = nullptr;                                // device error word, then 3 strong-jump counts
 };
 
@@ -43,6 +44,8 @@ void launch_ghosts(const Dev &P, const Bufs &B, cudaStream_t s);
 void launch_prim(const Dev &P, const Bufs &B, cudaStream_t s);
 // sensor (sensor.cu)
 int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s);
+// gate from caller-given cell flags (compact [nz][ny][nx] bytes on the device)
+int launch_fixed_gate(const Dev &P, const Bufs &B, const unsigned char *compact, cudaStream_t s);
 void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s);
 void launch_features(const Dev &P, const Bufs &B, void *X, cudaStream_t s);
 size_t sensor_weights_bytes();

@@ -512,6 +512,32 @@ int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s)
     return 2;
 }
 
+// Caller-given cell flags ([nz][ny][nx] bytes, compact) in place of the network's decision:
+// the flags go to the padded cell-flag array and the gate is formed from them as usual.
+__global__ void k_flags_unpack(Dev P, const unsigned char *__restrict__ src, unsigned char *__restrict__ flag)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % P.n[0]);
+        const long long q = t / P.n[0];
+        const int j = (int)(q % P.n[1]), k = (int)(q / P.n[1]);
+        flag[node_index(P, i, j, k)] = src[t] ? 1 : 0;
+    }
+}
+
+int launch_fixed_gate(const Dev &P, const Bufs &B, const unsigned char *compact, cudaStream_t s)
+{
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    long long ub = (N + 255) / 256;
+    if (ub > (long long)sm_count() * 16) ub = (long long)sm_count() * 16;
+    k_flags_unpack<<<(int)ub, 256, 0, s>>>(P, compact, B.sflag);
+    long long db = (P.ntot + 255) / 256;
+    if (db > (long long)sm_count() * 16) db = (long long)sm_count() * 16;
+    k_dilate<<<(int)db, 256, 0, s>>>(P, B.sflag, B.gate, 0);
+    return 2;
+}
+
 void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s)
 {
     launch_prim(P, B, s);

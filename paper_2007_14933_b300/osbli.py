@@ -26,7 +26,7 @@ EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_s
             "osbli_get_state", "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
             "osbli_launches_per_step", "osbli_last_error", "osbli_profile_residual",
             "osbli_profile_name", "osbli_fp64_peak", "osbli_residual_noalloc",
-            "osbli_fp32_peak", "osbli_sensor_set_weights", "osbli_sensor_labels",
+            "osbli_fp32_peak", "osbli_sensor_set_weights", "osbli_sensor_set_gate", "osbli_sensor_labels",
             "osbli_sensor_features", "osbli_sensor_probs", "osbli_mlp_grad", "osbli_mlp_train",
             "osbli_mlp_forward", "osbli_ensemble_create", "osbli_ensemble_destroy",
             "osbli_ensemble_set_state", "osbli_ensemble_get_state", "osbli_ensemble_member",
@@ -89,6 +89,8 @@ def load():
         L.osbli_residual_noalloc.argtypes = [ctypes.POINTER(osbli_params), vp, vp, vp]
         L.osbli_residual_noalloc.restype = ctypes.c_int
         L.osbli_sensor_set_weights.argtypes = [vp, vp, ctypes.c_float]
+        L.osbli_sensor_set_gate.argtypes = [vp, vp]
+        L.osbli_sensor_set_gate.restype = ctypes.c_int
         L.osbli_sensor_labels.argtypes = [vp, vp]
         L.osbli_sensor_features.argtypes = [vp, vp]
         L.osbli_sensor_probs.argtypes = [vp, vp]
@@ -252,6 +254,10 @@ def osbli_sensor_set_weights(h, w, threshold):
     w = np.ascontiguousarray(w, dtype=np.float32)
     assert w.size == SENSOR_NPARAM
     return _check(h, load().osbli_sensor_set_weights(h, _ptr(w), float(threshold)))
+
+
+def osbli_sensor_set_gate(h, flags):
+    return _check(h, load().osbli_sensor_set_gate(h, _ptr(flags)))
 
 
 def osbli_sensor_labels(h, labels):
@@ -445,6 +451,11 @@ class Solver:
 
     def set_sensor(self, w, threshold=0.5):
         osbli_sensor_set_weights(self.h, w, threshold)
+
+    def set_gate(self, flags):
+        """Fixed cell gate ([nz][ny][nx], nonzero = flagged) in place of the network."""
+        f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(self.shape[1:])
+        osbli_sensor_set_gate(self.h, f)
 
     def launches_per_step(self):
         return osbli_launches_per_step(self.h)

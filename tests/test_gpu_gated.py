@@ -1,0 +1,160 @@
+"""The gated mixed-precision path (the learned-sensor form) against the oracle's gated form, with
+the same explicit partial cell mask on both sides (osbli_sensor_set_gate on the GPU,
+Oracle.set_gate on the CPU): interfaces next to a flagged cell or with a strong jump in their
+six-node stencil take the characteristic flux, all others the central 4th-order interface flux.
+
+Decisions taken in floating point: the strong-jump test runs in FP32 on the GPU and in FP64 in
+the oracle, and TENO cut-offs likewise; nodes whose residual used a decision within rounding of
+its threshold (|ratio/1.5 - 1| < 1e-4, |chi - C_T|/C_T < 1e-3) have two correct answers and are
+left out of the pointwise bound (their count is bounded).  Bars: pointwise 1e-4 of the variable's
+residual scale for single residuals (FP32 reconstruction arithmetic), relative L2 <= 1e-5 on
+smooth flow after many steps, shock position within one cell on the Sod problem.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_14933_b300 import inputs as I
+from paper_2007_14933_b300 import osbli
+
+pytestmark = pytest.mark.gpu
+
+L2_TOL = 1e-5
+PT_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_14933_b300 import build
+    build.build()
+    osbli.load()
+
+
+def l2rel(a, b):
+    a = a.reshape(5, -1)
+    b = b.reshape(5, -1)
+    nb = [np.linalg.norm(b[v]) for v in range(5)]
+    nb[1] = nb[2] = nb[3] = max(nb[1:4])
+    return float(max(np.linalg.norm(a[v] - b[v]) / nb[v] for v in range(5) if nb[v] > 0))
+
+
+def mask(shape, frac, seed):
+    return (np.random.default_rng(seed).random(shape) < frac).astype(np.uint8)
+
+
+def gpu_gated(cfg, U, gate, steps=0):
+    s = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    s.set_state(U)
+    s.set_gate(gate)
+    if steps:
+        s.step(steps)
+        out = s.get_state()
+    else:
+        out = s.residual()
+    frac = s.diagnostics()[9]
+    s.close()
+    return out, frac
+
+
+def oracle_gated(cfg, U, gate, steps=0):
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.set_gate(gate, 1.5)
+    if steps:
+        o.step(steps)
+        return o.get_state()
+    return o.residual(with_margin=True, with_jump_margin=True)
+
+
+def _cases():
+    n3 = (37, 35, 34)       # two tiles in x, y and z, each with a ragged tail
+    cfg1, U1 = I.tgv(n=n3, Ma=1.25, Re=0.0, scheme=I.TENO5)
+    cfg2 = dict(n=n3, gamma=1.4, Re=0.0, Ma=1.0, scheme=I.TENO5, teno_ct=1e-5, bc=[[0, 0]] * 3,
+                h=(0.1, 0.2, 0.3))
+    U2 = I.random_state(n3, seed=11, shocky=True)
+    quad = [(1.5, 0.0, 0.0, 1.5), (0.5323, 1.206, 0.0, 0.3), (0.138, 1.206, 1.206, 0.029),
+            (0.5323, 0.0, 1.206, 0.3)]
+    cfg3, U3 = I.riemann2d(45, quad, scheme=I.WENO5JS, ny=38)
+    cfg4, U4, _ = I.sod(N=100, scheme=I.TENO5)
+    cfg5, U5 = I.tgv(n=(40, 33, 1), Ma=0.8, Re=400.0, scheme=I.TENO6)
+    return [("tgv3d_teno5", cfg1, U1), ("random3d_jumps", cfg2, U2), ("riemann2d_weno", cfg3, U3),
+            ("sod1d_x_only", cfg4, U4), ("tgv2d_teno6_viscous", cfg5, U5)]
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.3, 0.6])
+@pytest.mark.parametrize("case", range(5))
+def test_gated_residual_matches_oracle(case, frac):
+    name, cfg, U = _cases()[case]
+    gate = mask(U.shape[1:], frac, seed=case)
+    Rg, gfrac = gpu_gated(cfg, U, gate)
+    Ro, tm, jm = oracle_gated(cfg, U, gate)
+    assert abs(gfrac - gate.mean()) < 1e-12           # the installed flags are what the gate used
+    sc = np.abs(Ro).reshape(5, -1).max(axis=1)[:, None]
+    sc[sc == 0] = 1.0
+    err = (np.abs(Rg - Ro).reshape(5, -1) / sc).max(axis=0)
+    ambiguous = ((jm < 1e-4) | (tm < 1e-3)).reshape(-1)
+    assert ambiguous.mean() < 0.05, (name, ambiguous.mean())
+    assert err[~ambiguous].max() <= PT_TOL, (name, err[~ambiguous].max())
+
+
+def test_gated_smooth_tgv_steps_l2():
+    """40 steps of the Ma 1.25 TGV (smooth phase) with a fixed 35 % mask: every step mixes
+    central and characteristic interfaces in all three directions."""
+    cfg, U = I.tgv(n=(32, 28, 24), Ma=1.25, scheme=I.TENO5)
+    gate = mask(U.shape[1:], 0.35, seed=21)
+    Ug, _ = gpu_gated(cfg, U, gate, steps=40)
+    Uo = oracle_gated(cfg, U, gate, steps=40)
+    assert l2rel(Ug, Uo) <= L2_TOL
+
+
+def test_gated_sod_shock_position_within_one_cell():
+    """Sod with 30 % of the cells flagged at random (the shock and contact take the FP64
+    characteristic flux through the strong-jump rule wherever they are): the shock stays within
+    one cell of the oracle's; the L2 difference is recorded with a looser bound."""
+    cfg, U, x = I.sod(scheme=I.WENO5JS)
+    gate = mask(U.shape[1:], 0.3, seed=31)
+    Ug, _ = gpu_gated(cfg, U, gate, steps=800)
+    Uo = oracle_gated(cfg, U, gate, steps=800)
+    rg, ro = Ug[0, 0, 0], Uo[0, 0, 0]
+    mid = 0.5 * (0.26557 + 0.125)
+
+    def shock(r):
+        return x[np.where((r[:-1] >= mid) & (r[1:] < mid))[0][-1]]
+    assert abs(shock(rg) - shock(ro)) <= 1.0 / 400 + 1e-12
+    assert l2rel(Ug, Uo) <= 1e-3
+
+
+def test_gated_wall_box_residual():
+    """Rectilinear box with inflow / outlet, isothermal wall / Dirichlet top and periodic span
+    (ghost flags clamp to the nearest interior cell on the non-periodic faces), 40 % mask."""
+    from tests.test_gpu_parity import wall_box
+    cfg, U = wall_box(n=(36, 14, 6))
+    gate = mask(U.shape[1:], 0.4, seed=41)
+    Rg, _ = gpu_gated(cfg, U, gate)
+    Ro, tm, jm = oracle_gated(cfg, U, gate)
+    sc = np.abs(Ro).reshape(5, -1).max(axis=1)[:, None]
+    err = (np.abs(Rg - Ro).reshape(5, -1) / sc).max(axis=0)
+    ambiguous = ((jm < 1e-4) | (tm < 1e-3)).reshape(-1)
+    assert ambiguous.mean() < 0.05
+    assert err[~ambiguous].max() <= PT_TOL
+
+
+def test_gate_mode_switches_back_to_the_network():
+    """osbli_sensor_set_weights after osbli_sensor_set_gate returns the handle to inference: with
+    the flag-everything threshold the gated fraction is 1 again."""
+    from paper_2007_14933_b300 import sensor as SN
+    cfg, U = I.tgv(n=(20, 18, 16), Ma=1.25, scheme=I.TENO5)
+    s = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    s.set_state(U)
+    s.set_gate(np.zeros(U.shape[1:], np.uint8))
+    n_fixed = s.launches_per_step()
+    s.step(1)
+    assert s.diagnostics()[9] == 0.0
+    s.set_sensor(SN.default_weights(0), 1e-9)
+    assert s.launches_per_step() == n_fixed + 2      # inference and gate formation come back
+    s.step(1)
+    assert s.diagnostics()[9] > 0.99
+    s.close()

@@ -192,6 +192,28 @@ def test_tgv_central_100_steps():
     assert relerr(Ug, Uo) <= TOL
 
 
+def test_tgv_central_64_200_steps_and_kinetic_energy():
+    """The C2 configuration as stated: TGV 64^3, Ma 0.1, Re 1600, 4th-order central + viscous,
+    200 RK3 steps at CFL 0.5 (t = 0.32); the state matches the oracle at the FP64 bar and the
+    kinetic-energy history (the GPU's own diagnostic, every 50 steps) the oracle's to 1e-12."""
+    import os
+    O.set_threads(len(os.sched_getaffinity(0)))
+    cfg, U = I.tgv(64, Ma=0.1, scheme=I.CENTRAL4)
+    s = osbli.Solver(cfg)
+    s.set_state(U)
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    for _ in range(4):
+        s.step(50)
+        o.step(50)
+        Uo = o.get_state()
+        ke_o = float((0.5 * (Uo[1] ** 2 + Uo[2] ** 2 + Uo[3] ** 2) / Uo[0]).mean())
+        assert abs(s.diagnostics()[5] - ke_o) <= 1e-12 * ke_o
+    Ug = s.get_state()
+    s.close()
+    assert relerr(Ug, Uo) <= TOL
+
+
 def test_tgv_teno_100_steps():
     cfg, U = I.tgv(12, Ma=1.25, scheme=I.TENO5)
     Ug, Uo = run_pair(cfg, U, 100)

@@ -620,3 +620,156 @@ def test_laminar_channel_wall_conditions_matter():
     o = O.Oracle(dict(cfg, force=(0.0, 0.0, 0.0)))
     o.set_state(U)
     assert np.abs(o.residual()[1]).max() > 0.5
+
+
+# ---------------------------------------------------------------- Sec. 6 set-up: Dirichlet and inflow faces
+def _face_box(viscous=False):
+    """2D box: inflow on the low x face, zero-gradient outlet on the high one, Dirichlet faces in
+    y with face data varying along the face; the interior pressure varies along x so that the
+    pressure taken from node 0 and from node 1 differ."""
+    g, Ma = 1.4, 2.0
+    nx, ny = 10, 9
+    h = (0.5, 0.25, 1.0)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    p = (1.0 + 0.1 * ii + 0.02 * jj) / (g * Ma * Ma)
+    T = 1.0 + 0.05 * jj
+    rho = g * Ma * Ma * p / T
+    u = 1.0 - 0.03 * jj + 0.01 * ii
+    v = 0.02 * np.sin(ii)
+    U = I.prim_to_cons(g, rho, u, v, 0 * u, p).reshape(5, 1, ny, nx)
+    j = np.arange(ny)
+    inflow = np.stack([0 * j, 0.9 + 0.02 * j, 0.01 * j, 0 * j, 1.1 + 0.03 * j]).astype(float)
+    i = np.arange(nx)
+    low = np.stack([1.2 + 0.01 * i, 0.5 + 0 * i, 0.05 + 0 * i, 0 * i, 0.3 + 0.002 * i]).astype(float)
+    top = np.stack([0.8 + 0 * i, 1.1 + 0.01 * i, -0.04 + 0 * i, 0 * i, 0.2 + 0 * i]).astype(float)
+    cfg = dict(n=(nx, ny, 1), gamma=g, Re=500.0 if viscous else 0.0, Pr=0.72, Ma=Ma,
+               scheme=O.TENO5, teno_ct=1e-5,
+               bc=[[O.INFLOW, O.ZEROGRAD], [O.DIRICHLET, O.DIRICHLET], [0, 0]], h=h,
+               bdata={(0, 0): inflow, (1, 0): low, (1, 1): top})
+    return cfg, U, inflow, low, top
+
+
+def _prims(g, Ma, W):
+    r = W[0]
+    u, v, w = W[1] / r, W[2] / r, W[3] / r
+    p = (g - 1) * (W[4] - 0.5 * r * (u * u + v * v + w * w))
+    return r, u, v, w, p, g * Ma * Ma * p / r
+
+
+def test_inflow_and_dirichlet_ghosts_follow_their_definition():
+    """Inflow (Sec. 6 set-up): ghost velocity and temperature are the face data, the pressure is
+    the first interior node's (node 1; node 0 is the face's own boundary node), the density
+    gamma Ma^2 p / T.  Dirichlet: the ghosts carry the face's (rho, u, v, w, p) exactly."""
+    cfg, U, inflow, low, top = _face_box()
+    g, Ma = cfg["gamma"], cfg["Ma"]
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    Ug = o.ghosted()[:, 0]                      # [5][ny+6][nx+6]
+    _, _, _, _, p_int, _ = _prims(g, Ma, U[:, 0])
+    ny, nx = U.shape[2], U.shape[3]
+    for gi in (1, 2, 3):
+        col = Ug[:, 3:3 + ny, 3 - gi]
+        r, u, v, w, p, T = _prims(g, Ma, col)
+        np.testing.assert_allclose(u, inflow[1], rtol=1e-13)
+        np.testing.assert_allclose(v, inflow[2], rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(T, inflow[4], rtol=1e-13)
+        np.testing.assert_allclose(p, p_int[:, 1], rtol=1e-13)
+        assert np.abs(p - p_int[:, 0]).min() > 1e-3 * p.min()     # node 0 would differ
+        np.testing.assert_allclose(r, g * Ma * Ma * p_int[:, 1] / inflow[4], rtol=1e-13)
+        for side, data, row in ((0, low, 3 - gi), (1, top, 3 + ny - 1 + gi)):
+            r, u, v, w, p, T = _prims(g, Ma, Ug[:, row, 3:3 + nx])
+            for got, want in ((r, data[0]), (u, data[1]), (v, data[2]), (p, data[4])):
+                np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
+
+
+def test_inflow_and_dirichlet_boundary_nodes_after_a_stage():
+    """After each stage the face nodes are imposed: with dt = 0 the interior is unchanged, the
+    Dirichlet rows equal their data, and the inflow column has the data's velocity and
+    temperature with node 1's pressure."""
+    cfg, U, inflow, low, top = _face_box()
+    g, Ma = cfg["gamma"], cfg["Ma"]
+    o = O.Oracle(dict(cfg, dt=0.0))
+    o.set_state(U)
+    o.step(1)
+    V = o.get_state()[:, 0]
+    np.testing.assert_array_equal(V[:, 1:-1, 1:], U[:, 0, 1:-1, 1:])
+    for row, data in ((0, low), (-1, top)):
+        r, u, v, w, p, T = _prims(g, Ma, V[:, row, :])
+        for got, want in ((r, data[0]), (u, data[1]), (v, data[2]), (p, data[4])):
+            np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
+    _, _, _, _, p_int, _ = _prims(g, Ma, U[:, 0])
+    r, u, v, w, p, T = _prims(g, Ma, V[:, 1:-1, 0])
+    np.testing.assert_allclose(u, inflow[1][1:-1], rtol=1e-13)
+    np.testing.assert_allclose(T, inflow[4][1:-1], rtol=1e-13)
+    np.testing.assert_allclose(p, p_int[1:-1, 1], rtol=1e-13)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_uniform_stream_through_inflow_and_dirichlet_faces_is_steady(viscous):
+    """A uniform stream whose inflow data and Dirichlet faces carry its own state is an exact
+    steady solution: the residual vanishes to rounding and steps leave the state unchanged."""
+    cfg, U, inflow, low, top = _face_box(viscous)
+    g, Ma = cfg["gamma"], cfg["Ma"]
+    ny, nx = U.shape[2], U.shape[3]
+    r0, u0, v0, p0 = 1.3, 0.8, -0.1, 0.25
+    T0 = g * Ma * Ma * p0 / r0
+    Uu = I.prim_to_cons(g, np.full((1, ny, nx), r0), np.full((1, ny, nx), u0),
+                        np.full((1, ny, nx), v0), np.zeros((1, ny, nx)), np.full((1, ny, nx), p0))
+    face = lambda m, a: np.stack([np.full(m, x) for x in a]).astype(float)
+    cfg["bdata"] = {(0, 0): face(ny, (0.0, u0, v0, 0.0, T0)),
+                    (1, 0): face(nx, (r0, u0, v0, 0.0, p0)), (1, 1): face(nx, (r0, u0, v0, 0.0, p0))}
+    o = O.Oracle(dict(cfg, dt=1e-3))
+    o.set_state(Uu)
+    R = o.residual()
+    assert np.abs(R).max() <= 1e-12 * (r0 * u0 * u0 + p0) / 0.25
+    o.step(5)
+    np.testing.assert_allclose(o.get_state(), Uu, rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------- Sec. 7: TGV kinetic-energy budget
+def _ke_budget(U, g, Re):
+    """Box mean kinetic energy, viscous dissipation <tau : grad u> and pressure work <p div u> of
+    a periodic state, with spectral derivatives (independent of the oracle's operators)."""
+    n = U.shape[1]
+    k = np.fft.fftfreq(n, 1.0 / n)
+
+    def d(f, ax):
+        shp = [1, 1, 1]
+        shp[ax] = n
+        return np.real(np.fft.ifft(1j * k.reshape(shp) * np.fft.fft(f, axis=ax), axis=ax))
+    rho = U[0]
+    u = [U[1 + c] / rho for c in range(3)]
+    p = (g - 1) * (U[4] - 0.5 * rho * sum(x * x for x in u))
+    ax = (2, 1, 0)                        # x, y, z derivative axes of a [z][y][x] array
+    G = [[d(u[i], ax[j]) for j in range(3)] for i in range(3)]
+    div = G[0][0] + G[1][1] + G[2][2]
+    eps = sum((G[i][j] + G[j][i] - (2.0 / 3.0 if i == j else 0.0) * div) / Re * G[i][j]
+              for i in range(3) for j in range(3))
+    return float((0.5 * rho * sum(x * x for x in u)).mean()), float(eps.mean()), float((p * div).mean())
+
+
+def test_tgv_kinetic_energy_history_satisfies_the_energy_budget():
+    """TGV at Ma 0.1, Re 1600, 4th-order central + viscous terms, 200 RK3 steps at CFL 0.5:
+    the box-mean kinetic energy K obeys dK/dt = <p div u> - <tau : grad u> (the mean of the
+    kinetic-energy equation over a periodic box).  Sampled every 10 steps and integrated by the
+    trapezoid rule, the decrease of K matches the integrated dissipation and pressure work to 2 %
+    at 32^3 (t = 0.63), and the mismatch falls with resolution (24^3 over the same time: more
+    than 3x larger), as a 4th-order discretisation's should."""
+    out = {}
+    for N, steps in ((32, 200), (24, 150)):
+        cfg, U = I.tgv(N, Ma=0.1, Re=1600.0, scheme=O.CENTRAL4)
+        g = cfg["gamma"]
+        o = O.Oracle(cfg)
+        o.set_state(U)
+        rows = [(0.0,) + _ke_budget(U, g, 1600.0)]
+        for s in range(steps // 10):
+            o.step(10)
+            rows.append(((s + 1) * 10 * cfg["dt"],) + _ke_budget(o.get_state(), g, 1600.0))
+        t, K, eps, pdil = (np.array(c) for c in zip(*rows))
+        assert abs(K[0] - 0.125) < 1e-12 and abs(eps[0] - 0.75 / 1600.0) < 1e-12
+        dK = K[-1] - K[0]
+        rhs = np.trapezoid(pdil - eps, t)
+        out[N] = abs(dK - rhs) / abs(dK)
+        assert dK < 0
+    assert out[32] <= 0.02, out
+    assert out[24] >= 3.0 * out[32], out
