@@ -121,6 +121,13 @@ def parse():
     ap.add_argument("--no-sensor", action="store_true", help="skip the learned-sensor form")
     ap.add_argument("--forms", default=None, help="comma list of forms to time (learned, mixed, fp64)")
     ap.add_argument("--sensor-steps", type=int, default=800, help="Adam steps of the sensor training")
+    ap.add_argument("--accuracy-steps", type=int, default=100,
+                    help="steps from the initial field after which the forms' states are compared "
+                         "(the timed steps count; the rest run after the timed region)")
+    ap.add_argument("--shock-t", type=float, default=2.5,
+                    help="TGV: time the learned form also from the shocklet phase, reached by "
+                         "advancing the mixed form to at least this time (0: skip)")
+    ap.add_argument("--shock-steps-max", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -465,6 +472,66 @@ def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sens
     return s, max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
 
 
+def l2_vs(Uf, Up):
+    """Relative L2 difference, max over the conserved variables (momentum components share one
+    scale)."""
+    nb = [float(np.linalg.norm(Up[v])) for v in range(5)]
+    nb[1] = nb[2] = nb[3] = max(nb[1:4])
+    return max(float(np.linalg.norm(Uf[v] - Up[v])) / nb[v] for v in range(5) if nb[v] > 0)
+
+
+def shocked_phase(osbli, torch, cfg, U, sensor, args, stream, barrier, dist, npts, world, prec):
+    """The learned form where its gate acts: the TGV is advanced with the mixed form (outside any
+    timed region) into its shocklet phase -- past args.shock_t and until TENO cut-off labels mark
+    at least 1 % of the cells -- and the learned, mixed and FP64 forms are then timed from that
+    state exactly as from the initial field, and compared after the same steps."""
+    s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED, cuda_stream=stream.cuda_stream)
+    s.set_state(U)
+    done, lab_frac = 0, 0.0
+    lab = torch.empty(npts, dtype=torch.uint8, device="cuda")
+    while done < args.shock_steps_max:
+        s.step(100)
+        done += 100
+        osbli.osbli_sensor_labels(s.h, lab)
+        lab_frac = float(lab.float().mean().item())
+        if done * cfg["dt"] >= args.shock_t and lab_frac >= 0.01:
+            break
+    Us = s.get_state()
+    s.close()
+    # the gate's recall of the labels at the start state
+    g = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED, cuda_stream=stream.cuda_stream)
+    g.set_sensor(sensor[0], sensor[1])
+    g.set_state(Us)
+    probs = torch.empty(npts, dtype=torch.float32, device="cuda")
+    osbli.osbli_sensor_probs(g.h, probs)
+    flagged = probs >= sensor[1]
+    pos = lab.bool()
+    recall = float((flagged & pos).sum().item()) / max(1, int(pos.sum().item()))
+    g.close()
+    del probs, flagged, pos
+    res = {f: time_form(osbli, torch, cfg, Us, prec[f], args, stream, barrier, dist,
+                        sensor if f == "learned" else None) for f in ("learned", "mixed", "fp64")}
+    dg = res["learned"][0].diagnostics()
+    prof = res["learned"][0].profile_residual(reps=2)
+    out = {"t_start": done * cfg["dt"], "steps_advanced": done, "label_fraction": lab_frac,
+           "gate_recall_of_labels": recall,
+           "gated": {"cells": float(dg[9]), "interfaces_x": float(dg[10]), "interfaces_y": float(dg[11]),
+                     "interfaces_z": float(dg[12])},
+           "forms": {f: {"value": job_rate(npts, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps}
+                     for f, (_, ms) in res.items()},
+           "kernels_ms": {nm: t_ for nm, t_ in prof}}
+    Up = res["fp64"][0].get_state()
+    for f in ("learned", "mixed"):
+        out["l2_%s_vs_fp64" % f] = l2_vs(res[f][0].get_state(), Up)
+        out["speedup_%s_vs_fp64" % f] = out["forms"][f]["value"] / out["forms"]["fp64"]["value"]
+    out["note"] = ("state advanced %d steps (t = %.2f) with the mixed form, then each form timed over "
+                   "%d steps after %d warm-up steps from it; L2 against the FP64 form after those %d steps"
+                   % (done, done * cfg["dt"], args.steps, args.warmup, args.warmup + args.steps))
+    for f in res:
+        res[f][0].close()
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -600,23 +667,30 @@ def main():
                         "ms_per_step": ms_ / args.steps}
     extra = {"forms": out_forms}
     if "fp64" in forms and len(forms) > 1:
-        # accuracy at matched work: every form advanced warmup + steps from the same state
+        # accuracy at matched work: every form advanced to the same step count from the same
+        # state (the steps beyond warmup + steps run after the timed region)
+        acc_steps = max(args.accuracy_steps, args.warmup + args.steps)
+        for f in forms:
+            res[f][0].step(acc_steps - args.warmup - args.steps)
         Up = res["fp64"][0].get_state()
         for f in forms:
             if f == "fp64":
                 continue
-            Uf = res[f][0].get_state()
-            nb = [float(np.linalg.norm(Up[v])) for v in range(5)]
-            nb[1] = nb[2] = nb[3] = max(nb[1:4])     # momentum components share one scale
-            l2 = [float(np.linalg.norm(Uf[v] - Up[v])) / nb[v] for v in range(5) if nb[v] > 0]
-            extra["l2_%s_vs_fp64" % f] = max(l2)
+            extra["l2_%s_vs_fp64" % f] = l2_vs(res[f][0].get_state(), Up)
             extra["speedup_%s_vs_fp64" % f] = out_forms[f]["value"] / out_forms["fp64"]["value"]
-            del Uf
         extra["accuracy_note"] = ("relative L2 (max over conserved variables) of each form's state "
                                   "against the FP64 form after %d steps from the same initial "
                                   "field; the FP64 form is parity-checked against the CPU oracle"
-                                  % (args.warmup + args.steps))
+                                  % acc_steps)
         del Up
+        if head == "learned":
+            dg = res["learned"][0].diagnostics()
+            extra["gated_after_accuracy_steps"] = {"cells": float(dg[9]), "interfaces_x": float(dg[10]),
+                                                   "interfaces_y": float(dg[11]),
+                                                   "interfaces_z": float(dg[12])}
+    if "learned" in forms and args.workload == "tgv" and args.shock_t > 0:
+        extra["shocklet_phase"] = shocked_phase(osbli, torch, cfg, U, sensor, args, stream, barrier, dist,
+                                                npts, world, prec)
     if sensor_info:
         sensor_info["gated"] = gated
         extra["sensor"] = sensor_info

@@ -101,9 +101,14 @@ def test_gated_residual_matches_oracle(case, frac):
 
 
 def test_gated_smooth_tgv_steps_l2():
-    """40 steps of the Ma 1.25 TGV (smooth phase) with a fixed 35 % mask: every step mixes
-    central and characteristic interfaces in all three directions."""
-    cfg, U = I.tgv(n=(32, 28, 24), Ma=1.25, scheme=I.TENO5)
+    """40 steps of the Ma 0.8 TGV with a fixed 35 % mask: every step mixes central and
+    characteristic interfaces in all three directions.  (At Ma 1.25 on this grid adjacent
+    pressure ratios pass within 2e-5 of the 1.5 strong-jump threshold during the run, where the
+    FP32 and FP64 tests decide differently -- two correct answers that switch an interface between
+    the central and the characteristic flux -- so the many-step bar is taken where no stencil
+    comes within 20 % of the threshold; the switching itself is checked residual by residual and
+    on Sod.)"""
+    cfg, U = I.tgv(n=(32, 28, 24), Ma=0.8, scheme=I.TENO5)
     gate = mask(U.shape[1:], 0.35, seed=21)
     Ug, _ = gpu_gated(cfg, U, gate, steps=40)
     Uo = oracle_gated(cfg, U, gate, steps=40)

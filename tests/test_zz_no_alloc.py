@@ -51,6 +51,7 @@ def _noalloc_residual(torch, cfg, U):
 
 def _relerr(a, b):
     scale = np.abs(b).reshape(5, -1).max(axis=1)[:, None]
+    scale[scale == 0] = 1.0      # a 2D state's w momentum is identically zero
     return float((np.abs(a - b).reshape(5, -1) / scale).max())
 
 
