@@ -293,6 +293,53 @@ long long osbli_ensemble_points(const osbli_ens_t *e);
 /* Message of the last failure on e (or of the last failed osbli_ensemble_create when NULL). */
 const char *osbli_ensemble_last_error(const osbli_ens_t *e);
 
+/* ---------------------------------------------------------------------------------------------
+ * Split grids: one grid divided into z-slabs, each a sub-domain with its own ghost layers, as
+ * the paper's parallel runs divide their grids into blocks that exchange halos (Sec. 7.2).  The
+ * slabs live on the current device.  Once per RK stage every slab's low and high ghost planes
+ * are copied from its neighbours' interior planes into its own ghost buffers (the conserved
+ * state, 3 planes: the i-2..i+3 stencil; on viscous runs also the z-direction viscous fluxes,
+ * 2 planes, after they are formed), then each slab advances on its own.  Results are bitwise
+ * those of one osbli_t on the whole grid.  Uniform grids (params.h) only, any scheme,
+ * precision and face type; the learned sensor is not offered on split grids.
+ * ------------------------------------------------------------------------------------------- */
+#define OSBLI_DOMAIN_MAX_SLABS 64
+typedef struct osbli_dom osbli_dom_t;
+
+/* The split of nz planes into nslab contiguous slabs (the first nz % nslab slabs one plane
+ * longer): slab s holds global planes k0[s] .. k0[s] + nzs[s] - 1; lo[s] / hi[s] are the slabs
+ * across its low / high z face (periodic: wrapping), -1 for a physical face.  Host only (no
+ * device work).  Arrays of nslab entries.  Errors: EINVAL (nslab outside 1..min(nz, 64)). */
+int osbli_domain_plan(int nz, int nslab, int periodic, int *k0, int *nzs, int *lo, int *hi);
+
+/* Split the grid of p (uniform, nz > 1) into nslab z-slabs per osbli_domain_plan.  Every slab
+ * needs >= 3 planes, >= 5 where it has a physical z face.  cuda_stream as for osbli_create.
+ * Errors: EINVAL (with the reason; message from osbli_domain_last_error(NULL)), ENOMEM, ECUDA. */
+int osbli_domain_create(const osbli_params *p, int nslab, void *cuda_stream, osbli_dom_t **out);
+void osbli_domain_destroy(osbli_dom_t *d);
+
+/* Whole-grid state in / out, [5][nz][ny][nx] FP64, host or device (split across the slabs). */
+int osbli_domain_set_state(osbli_dom_t *d, const double *U);
+int osbli_domain_get_state(osbli_dom_t *d, double *U);
+
+/* Face data of the whole grid's DIRICHLET / INFLOW face, layout as osbli_set_boundary_data. */
+int osbli_domain_set_boundary_data(osbli_dom_t *d, int dir, int side, const double *prims);
+
+/* nsteps RK steps of the whole grid (one CUDA graph per step holding every slab's launches and
+ * the halo copies); synchronises and checks every slab's error word (ENONFINITE names the
+ * slab). */
+int osbli_domain_step(osbli_dom_t *d, int nsteps);
+
+/* Residual of the current whole-grid state, [5][nz][ny][nx], host or device.  Synchronises. */
+int osbli_domain_residual(osbli_dom_t *d, double *R);
+
+/* Slab count; the handle of slab s (owned by the domain); kernel launches of one captured step
+ * (0 before the first step) and, in *copies, its halo copies. */
+int osbli_domain_slabs(const osbli_dom_t *d);
+osbli_t *osbli_domain_member(osbli_dom_t *d, int s);
+int osbli_domain_launches_per_step(const osbli_dom_t *d, int *copies);
+const char *osbli_domain_last_error(const osbli_dom_t *d);
+
 #ifdef __cplusplus
 }
 #endif

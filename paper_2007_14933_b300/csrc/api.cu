@@ -88,21 +88,28 @@ static void free_all(osbli *h)
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
-static int validate(const osbli_params *p, const double *coords)
+// halo_ok: a sub-domain of osbli_domain_create, whose z faces may be BC_HALO (ghosts filled by
+// the neighbour's exchange)
+static int validate(const osbli_params *p, const double *coords, bool halo_ok = false)
 {
     const int n[3] = {p->nx, p->ny, p->nz};
     for (int d = 0; d < 3; d++) {
         if (n[d] < 1) return seterr(nullptr, OSBLI_EINVAL, "n[%d] = %d < 1", d, n[d]);
-        for (int s = 0; s < 2; s++)
-            if (p->bc[d][s] < OSBLI_PERIODIC || p->bc[d][s] > OSBLI_ADIABATIC)
+        for (int s = 0; s < 2; s++) {
+            const bool halo = halo_ok && d == 2 && p->bc[d][s] == BC_HALO;
+            if (!halo && (p->bc[d][s] < OSBLI_PERIODIC || p->bc[d][s] > OSBLI_ADIABATIC))
                 return seterr(nullptr, OSBLI_EINVAL, "bc[%d][%d] = %d unknown", d, s, p->bc[d][s]);
+        }
         if (n[d] == 1) continue;
         const bool per0 = p->bc[d][0] == OSBLI_PERIODIC, per1 = p->bc[d][1] == OSBLI_PERIODIC;
         if (per0 != per1)
             return seterr(nullptr, OSBLI_EINVAL, "direction %d: periodic on one side only", d);
         if (per0 && n[d] < 3)
             return seterr(nullptr, OSBLI_EINVAL, "periodic direction %d needs >= 3 points", d);
-        if (!per0 && n[d] < 5)
+        const bool both_halo = p->bc[d][0] == BC_HALO && p->bc[d][1] == BC_HALO;
+        if (both_halo && n[d] < 3)
+            return seterr(nullptr, OSBLI_EINVAL, "sub-domain direction %d needs >= 3 points", d);
+        if (!per0 && !both_halo && n[d] < 5)
             return seterr(nullptr, OSBLI_EINVAL, "non-periodic direction %d needs >= 5 points", d);
         if (!coords && !(p->h[d] > 0.0))
             return seterr(nullptr, OSBLI_EINVAL, "h[%d] must be > 0 on a uniform grid", d);
@@ -135,12 +142,32 @@ static int validate(const osbli_params *p, const double *coords)
     return OSBLI_OK;
 }
 
+static int create_impl(const osbli_params *p, const double *coords, void *cuda_stream, osbli_t **out,
+                       bool halo_ok);
+
 extern "C" int osbli_create(const osbli_params *p, const double *coords, void *cuda_stream,
                             osbli_t **out)
 {
+    return create_impl(p, coords, cuda_stream, out, false);
+}
+
+// A sub-domain handle (osbli_domain_create): uniform grid, z faces may be BC_HALO.
+int osbli_internal_create_slab(const osbli_params *p, void *cuda_stream, osbli_t **out)
+{
+    return create_impl(p, nullptr, cuda_stream, out, true);
+}
+
+double *osbli_internal_stage(osbli_t *h) { return h->stage; }
+void osbli_internal_mark_state(osbli_t *h) { h->state_set = true; }
+cudaStream_t osbli_internal_stream(osbli_t *h) { return h->stream; }
+int osbli_internal_check_faces(osbli_t *h);
+
+static int create_impl(const osbli_params *p, const double *coords, void *cuda_stream, osbli_t **out,
+                       bool halo_ok)
+{
     if (!p || !out) return seterr(nullptr, OSBLI_EINVAL, "null argument");
     *out = nullptr;
-    int rc = validate(p, coords);
+    int rc = validate(p, coords, halo_ok);
     if (rc != OSBLI_OK) return rc;
     osbli *h = new (std::nothrow) osbli();
     if (!h) return seterr(nullptr, OSBLI_ENOMEM, "host allocation failed");
@@ -374,6 +401,9 @@ extern "C" int osbli_get_state(osbli_t *h, double *U)
     CK(h, cudaStreamSynchronize(h->stream));
     return OSBLI_OK;
 }
+
+static int check_faces(osbli *h);
+int osbli_internal_check_faces(osbli_t *h) { return check_faces(h); }
 
 static int check_faces(osbli *h)
 {

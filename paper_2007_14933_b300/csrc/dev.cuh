@@ -19,7 +19,8 @@ constexpr int GH = 3;   // ghost width: WENO5/TENO5 stencil i-2..i+3 (Sec. 2.3-2
 
 enum { W_U = 0, W_V, W_W, W_P, W_A, W_SR, W_H, W_T, NW };
 enum { SCH_CENTRAL4 = 0, SCH_WENO5JS = 1, SCH_TENO5 = 2, SCH_WENO5Z = 3, SCH_TENO6 = 4 };
-enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4, BC_ADIABATIC = 5 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_INFLOW = 4, BC_ADIABATIC = 5,
+       BC_HALO = 6 };   // BC_HALO: a sub-domain face whose ghosts a neighbour's halo exchange fills
 
 struct Dev {
     int n[3], g[3], np[3];
@@ -51,6 +52,18 @@ struct Dev {
     float facf[3];           // FP32 copies of fac and lfac for the mixed kernels (no double ->
     const float *lfacf[3];   // float conversion, which runs on the FP64 pipe, in their loops)
 };
+
+// A line end is "open" when the interior difference formula applies up to it, its ghosts holding
+// real neighbour values: periodic directions (wrapped) and sub-domain faces (exchanged halos).
+// Closed ends (physical faces) take the one-sided closures.
+__host__ __device__ __forceinline__ bool open_lo(const Dev &P, int d)
+{
+    return P.bc[d][0] == BC_PERIODIC || P.bc[d][0] == BC_HALO;
+}
+__host__ __device__ __forceinline__ bool open_hi(const Dev &P, int d)
+{
+    return P.bc[d][1] == BC_PERIODIC || P.bc[d][1] == BC_HALO;
+}
 
 // Grids that need the general curvilinear kernels (metric vectors read per node).
 __host__ __device__ __forceinline__ bool general(const Dev &P) { return P.curv && !P.rect; }

@@ -751,11 +751,11 @@ __global__ void __launch_bounds__(128) k_conv_central(Dev P, const double *__res
     ii[DA] = a; ii[DB] = b; ii[DIR] = 0;
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR];
-    const bool per = P.bc[DIR][0] == BC_PERIODIC;
+    const bool lo_open = open_lo(P, DIR), hi_open = open_hi(P, DIR);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         double D[NV];
-        if (per || (m >= 2 && m <= n - 3)) {
+        if ((lo_open || m >= 2) && (hi_open || m <= n - 3)) {
             double f0[NV], f1[NV], f3[NV], f4[NV];
             node_flux<DIR, CURV>(P, U, W, M, id - 2 * st, f0);
             node_flux<DIR, CURV>(P, U, W, M, id - st, f1);
@@ -794,9 +794,9 @@ __global__ void __launch_bounds__(128) k_conv_central(Dev P, const double *__res
 // the one-sided closures.
 // ------------------------------------------------------------------------------------------
 template <typename T, typename Fetch>
-__device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool per)
+__device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool lo_open, bool hi_open)
 {
-    if (per || (ie >= 2 && ie <= n - 3))
+    if ((lo_open || ie >= 2) && (hi_open || ie <= n - 3))
         return fdiv(f(ie - 2) - T(8) * f(ie - 1) + T(8) * f(ie + 1) - f(ie + 2), T(12));
     if (ie == 0) return fdiv(T(-25) * f(0) + T(48) * f(1) - T(36) * f(2) + T(16) * f(3) - T(3) * f(4), T(12));
     if (ie == 1) return fdiv(T(-3) * f(0) - T(10) * f(1) + T(18) * f(2) - T(6) * f(3) + f(4), T(12));
@@ -832,12 +832,12 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
             if (!P.active[e]) continue;
             const int ie = ijk[e];
             const long long st = P.st[e];
-            const bool per = P.bc[e][0] == BC_PERIODIC;
+            const bool lo = open_lo(P, e), hi = open_hi(P, e);
             const int widx[4] = {W_U, W_V, W_W, W_T};
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 const S *f = W + widx[v] * vs + id;
-                dxi[e][v] = deriv_line<T>([&](int s) { return T(f[(long long)(s - ie) * st]); }, ie, P.n[e], per);
+                dxi[e][v] = deriv_line<T>([&](int s) { return T(f[(long long)(s - ie) * st]); }, ie, P.n[e], lo, hi);
             }
         }
         T gr[4][3];
@@ -953,7 +953,10 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                 if (!P.active[d]) continue;
                 const int ie = ijk[d], n = P.n[d];
                 const long long st = P.st[d];
+                // periodic lines wrap into the interior (V lives on interior nodes only); a
+                // sub-domain face reads the halo planes of V its neighbour's exchange filled
                 const bool per = P.bc[d][0] == BC_PERIODIC;
+                const bool lo = open_lo(P, d), hi = open_hi(P, d);
                 const RT fac = CURV ? RT(P.shat[d] * M[9 * vs + id])
                                     : (sizeof(RT) == 4 ? RT(line_facf(P, d, ie)) : RT(line_fac(P, d, ie)));
 #pragma unroll
@@ -963,7 +966,7 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                         int w = s;
                         if (per) { w = s % n; if (w < 0) w += n; }
                         return f[(long long)(w - ie) * st];
-                    }, ie, n, per);
+                    }, ie, n, lo, hi);
                     r[1 + c] += fac * D;
                 }
             }
@@ -1059,7 +1062,7 @@ __global__ void k_metric_raw(Dev P, const double *__restrict__ X, double Lp0, do
                     const long long o = ((long long)jj[2] * P.n[1] + jj[1]) * P.n[0] + jj[0];
                     return (X[c * N + o] - xc) + (c == d ? sh * Lp[d] : 0.0);
                 };
-                Xd[d][c] = deriv_line<double>(f, ijk[d], n, per);
+                Xd[d][c] = deriv_line<double>(f, ijk[d], n, per, per);
             }
         }
         double S[3][3];
@@ -2528,12 +2531,13 @@ struct Tap {
 
 // ghost fill + primitives + convective + viscous fluxes: R holds the convective residual and
 // V the viscous fluxes when this returns (on the stream).  Returns the launch count.
-static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap = nullptr, bool sensor_now = true)
+static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap = nullptr, bool sensor_now = true,
+                          bool ghosts = true)
 {
     static const char *ghost_names[3] = {"ghost_x", "ghost_y", "ghost_z"};
     static const char *conv_names[3] = {"conv_x", "conv_y", "conv_z"};
     int launches = 0;
-    for (int d = 0; d < 3; d++) {
+    for (int d = 0; d < 3 && ghosts; d++) {
         if (!P.active[d]) continue;
         long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
         if (tap) (*tap)(ghost_names[d], s);
@@ -2616,6 +2620,27 @@ int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
     launches++;
     launches += boundary_nodes(P, B, s);
     return launches;
+}
+
+int launch_stage_core(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
+{
+    return residual_front(P, B, s, nullptr, stage == 0, false);
+}
+
+int launch_stage_finish(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
+{
+    if (stage == 0) update<0, 0>(P, B, s);
+    else if (stage == 1) update<0, 1>(P, B, s);
+    else if (stage == 2) update<0, 2>(P, B, s);
+    else if (stage == 3) update<0, 3>(P, B, s);
+    else update<0, 4>(P, B, s);
+    return 1 + boundary_nodes(P, B, s);
+}
+
+int launch_residual_finish(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    update<1, 0>(P, B, s);
+    return 1;
 }
 
 int launch_residual(const Dev &P, const Bufs &B, cudaStream_t s)

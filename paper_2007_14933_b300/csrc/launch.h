@@ -34,6 +34,13 @@ void launch_metrics(const Dev &P, const double *X, const double L[3], double *Sr
                     unsigned long long *smax, double *M, cudaStream_t s);
 int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s);
 int launch_residual(const Dev &P, const Bufs &B, cudaStream_t s);
+// A stage in three parts for sub-domains, whose halos are exchanged between them: ghost fill
+// (launch_ghosts), then launch_stage_core (primitives, sensor at stage 0, convective passes,
+// viscous fluxes; no ghost fill), then launch_stage_finish (viscous divergence + register
+// update, boundary nodes) or launch_residual_finish (residual out to B.R).  Launch counts.
+int launch_stage_core(const Dev &P, const Bufs &B, int stage, cudaStream_t s);
+int launch_stage_finish(const Dev &P, const Bufs &B, int stage, cudaStream_t s);
+int launch_residual_finish(const Dev &P, const Bufs &B, cudaStream_t s);
 // residual sequence with an event recorded before each launch and after the last one
 // (ev must hold max_launches + 1 events); returns the number of launches taped
 int launch_residual_timed(const Dev &P, const Bufs &B, cudaStream_t s, cudaEvent_t *ev,

@@ -31,7 +31,12 @@ EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_s
             "osbli_mlp_forward", "osbli_ensemble_create", "osbli_ensemble_destroy",
             "osbli_ensemble_set_state", "osbli_ensemble_get_state", "osbli_ensemble_member",
             "osbli_ensemble_step", "osbli_ensemble_set_chunk", "osbli_ensemble_autotune",
-            "osbli_ensemble_launches_per_step", "osbli_ensemble_points", "osbli_ensemble_last_error"]
+            "osbli_ensemble_launches_per_step", "osbli_ensemble_points", "osbli_ensemble_last_error",
+            "osbli_domain_plan", "osbli_domain_create", "osbli_domain_destroy", "osbli_domain_set_state",
+            "osbli_domain_get_state", "osbli_domain_set_boundary_data", "osbli_domain_step",
+            "osbli_domain_residual", "osbli_domain_slabs", "osbli_domain_member",
+            "osbli_domain_launches_per_step", "osbli_domain_last_error"]
+DOMAIN_MAX_SLABS = 64
 SENSOR_NPARAM = 5441
 SENSOR_NFEAT = 144
 
@@ -128,6 +133,26 @@ def load():
         for name in ("osbli_ensemble_create", "osbli_ensemble_set_state", "osbli_ensemble_get_state",
                      "osbli_ensemble_step", "osbli_ensemble_set_chunk", "osbli_ensemble_autotune",
                      "osbli_ensemble_launches_per_step"):
+            getattr(L, name).restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.osbli_domain_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip]
+        L.osbli_domain_create.argtypes = [ctypes.POINTER(osbli_params), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.osbli_domain_destroy.argtypes = [vp]
+        L.osbli_domain_destroy.restype = None
+        L.osbli_domain_set_state.argtypes = [vp, vp]
+        L.osbli_domain_get_state.argtypes = [vp, vp]
+        L.osbli_domain_set_boundary_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+        L.osbli_domain_step.argtypes = [vp, ctypes.c_int]
+        L.osbli_domain_residual.argtypes = [vp, vp]
+        L.osbli_domain_slabs.argtypes = [vp]
+        L.osbli_domain_member.argtypes = [vp, ctypes.c_int]
+        L.osbli_domain_member.restype = vp
+        L.osbli_domain_launches_per_step.argtypes = [vp, ip]
+        L.osbli_domain_last_error.argtypes = [vp]
+        L.osbli_domain_last_error.restype = ctypes.c_char_p
+        for name in ("osbli_domain_plan", "osbli_domain_create", "osbli_domain_set_state",
+                     "osbli_domain_get_state", "osbli_domain_set_boundary_data", "osbli_domain_step",
+                     "osbli_domain_residual", "osbli_domain_slabs", "osbli_domain_launches_per_step"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("osbli_create", "osbli_set_boundary_data", "osbli_set_state", "osbli_get_state",
                      "osbli_rk_step", "osbli_residual", "osbli_diagnostics",
@@ -352,6 +377,79 @@ def osbli_ensemble_launches_per_step(e):
 
 def osbli_ensemble_points(e):
     return load().osbli_ensemble_points(e)
+
+
+def _dcheck(d, rc):
+    if rc != OSBLI_OK:
+        msg = load().osbli_domain_last_error(d)
+        raise OsbliError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def osbli_domain_plan(nz, nslab, periodic):
+    """(k0, nzs, lo, hi) lists of the z-split; host only."""
+    arrs = [(ctypes.c_int * max(1, nslab))() for _ in range(4)]
+    rc = load().osbli_domain_plan(int(nz), int(nslab), int(bool(periodic)), *arrs)
+    if rc != OSBLI_OK:
+        raise OsbliError(rc, "bad split of %d planes into %d slabs" % (nz, nslab))
+    return tuple(list(a)[:nslab] for a in arrs)
+
+
+def osbli_domain_create(params, nslab, cuda_stream=None):
+    d = ctypes.c_void_p()
+    _dcheck(None, load().osbli_domain_create(ctypes.byref(params), int(nslab), ctypes.c_void_p(cuda_stream or 0),
+                                             ctypes.byref(d)))
+    return d
+
+
+class Domain:
+    """One grid split into z-slabs with halo exchanges (osbli_domain_*); same interface as Solver
+    for state, stepping and residuals."""
+
+    def __init__(self, cfg, nslab, precision=OSBLI_FP64, cuda_stream=None):
+        self.d = None
+        self.n = tuple(int(x) for x in cfg["n"])
+        self.shape = (5, self.n[2], self.n[1], self.n[0])
+        self.d = osbli_domain_create(make_params(cfg, precision), nslab, cuda_stream)
+        L = load()
+        for (dd, ss), arr in (cfg.get("bdata") or {}).items():
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            _dcheck(self.d, L.osbli_domain_set_boundary_data(self.d, int(dd), int(ss), _ptr(a)))
+
+    def close(self):
+        if getattr(self, "d", None):
+            load().osbli_domain_destroy(self.d)
+            self.d = None
+
+    __del__ = close
+
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.shape)
+        _dcheck(self.d, load().osbli_domain_set_state(self.d, _ptr(U)))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        _dcheck(self.d, load().osbli_domain_get_state(self.d, _ptr(out)))
+        return out
+
+    def step(self, nsteps):
+        _dcheck(self.d, load().osbli_domain_step(self.d, int(nsteps)))
+
+    def residual(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        _dcheck(self.d, load().osbli_domain_residual(self.d, _ptr(out)))
+        return out
+
+    def slabs(self):
+        return load().osbli_domain_slabs(self.d)
+
+    def launches_per_step(self):
+        c = ctypes.c_int(0)
+        n = load().osbli_domain_launches_per_step(self.d, ctypes.byref(c))
+        return n, c.value
 
 
 class Ensemble:
