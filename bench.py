@@ -578,6 +578,11 @@ def main():
         t0 = time.perf_counter()
         feats, labels, _ = SN.tgv_training_set(N=64, Ma=1.25, nsnap=6, steps_between=12)
         train_set = "TGV 64^3 Ma 1.25, 6 snapshots every 12 steps"
+        if args.workload == "tgv":
+            f2, l2_, desc = SN.tgv_shocklet_training_set(N=128, Ma=1.25)
+            feats, labels = torch.cat([feats, f2]), torch.cat([labels, l2_])
+            train_set += " + " + desc
+            del f2, l2_
         if args.workload == "sbli":
             f2, l2_, _ = SN.sbli_training_set()
             feats, labels = torch.cat([feats, f2]), torch.cat([labels, l2_])

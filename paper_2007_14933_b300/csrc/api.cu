@@ -78,6 +78,7 @@ static void free_all(osbli *h)
     if (h->B.sw) cudaFree(h->B.sw);
     if (h->B.sflag) cudaFree(h->B.sflag);
     if (h->B.gate) cudaFree(h->B.gate);
+    if (h->B.cmp) cudaFree(h->B.cmp);
     for (int d = 0; d < 3; d++) {
         if (h->lfac[d]) cudaFree(h->lfac[d]);
         if (h->lesc[d]) cudaFree(h->lesc[d]);
@@ -267,7 +268,9 @@ static int create_impl(const osbli_params *p, const double *coords, void *cuda_s
         CKC(cudaMalloc(&h->B.Dst, 3 * NV * fsb));
         // flagged-interface lists: 1/16 of the nodes per direction (a longer list overflows into a
         // scan of the flag bits)
-        h->B.scap = (int)(P.vs / 16 + 1024);
+        // (gated path: every node, the lists being built by compaction of the flag bits)
+        h->B.scap = P.sensor ? (int)P.vs : (int)(P.vs / 16 + 1024);
+        if (P.sensor) CKC(cudaMalloc(&h->B.cmp, (size_t)6 * compact_blocks(P) * sizeof(int)));
         CKC(cudaMalloc(&h->B.slist, (size_t)3 * h->B.scap * sizeof(long long)));
         const long long lefts = (long long)n[1] * n[2] * ((n[0] + 255) / 256);
         CKC(cudaMalloc(&h->B.Dl, (size_t)lefts * NV * sizeof(float)));
@@ -528,6 +531,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     const Dev &P = h->P;
     int per_stage = 1 /*prim*/ + 1 /*update*/;
     if (P.mixed && !general(P)) per_stage += 1;   // FP64 fix of strong-jump interfaces
+    if (P.mixed && !general(P) && P.sensor) per_stage += 3;   // flag compaction of the gated path
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction

@@ -1491,9 +1491,10 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
 // registers as it marches, with the pressure and density of m-2 and m+3 for the strong-jump
 // test and the next node prefetched, so every node is loaded once per line instead of once per
 // interface that reads it.  Every interface gets the central D here; an interface that needs the
-// characteristic flux (gate or strong jump) is recorded like a strong jump (flag bit, list, its
-// central D in Dst), and k_patch_fix replaces it (FP32 characteristic flux, or FP64 across a
-// strong jump), the update adding the difference.  The arithmetic of every interface is that of
+// characteristic flux (gate or strong jump) is flagged (flag bit, its central D in Dst); after
+// the passes the flags are compacted into per-direction lists in node order (k_flag_*), and
+// k_patch_fix replaces each listed interface (FP32 characteristic flux, or FP64 across a strong
+// jump), the update adding the difference.  The arithmetic of every interface is that of
 // k_conv_char_delta.
 struct NodeW {
     float h[NV], l[NV], u[3], p;
@@ -1652,8 +1653,6 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
         if (cha && y0 == 0) {                        // the line's first interface
             const long long m = base - st;
             sj.flag[m] |= (unsigned char)(1u << DIR);
-            const int kk = atomicAdd(sj.count + DIR, 1);
-            if (kk < sj.cap) sj.list[(long long)DIR * sj.cap + kk] = m;
             float *Ds = sj.Dst + (long long)DIR * NV * vs;
 #pragma unroll
             for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
@@ -1683,8 +1682,6 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
             const long long m = base + (long long)y * st;
             if (cha) {                               // interface y + 1/2: owned by node y
                 sj.flag[m] |= (unsigned char)(1u << DIR);
-                const int kk = atomicAdd(sj.count + DIR, 1);
-                if (kk < sj.cap) sj.list[(long long)DIR * sj.cap + kk] = m;
                 float *Ds = sj.Dst + (long long)DIR * NV * vs;
 #pragma unroll
                 for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
@@ -1783,8 +1780,6 @@ __device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj,
                                                  const float D[NV])
 {
     sj.flag[m] |= (unsigned char)(1u << dir);
-    const int kk = atomicAdd(sj.count + dir, 1);
-    if (kk < sj.cap) sj.list[(long long)dir * sj.cap + kk] = m;
     float *Ds = sj.Dst + (long long)dir * NV * P.vs;
 #pragma unroll
     for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D[v];
@@ -2065,8 +2060,6 @@ __global__ void __launch_bounds__(256) k_conv_delta_x_win(Dev P, const float *__
         if (cha && (pass == 0 || x0 == 0)) {        // x0 - 1 belongs to the previous segment
             const long long m = base + i;
             sj.flag[m] |= (unsigned char)1u;
-            const int kk = atomicAdd(sj.count, 1);
-            if (kk < sj.cap) sj.list[kk] = m;
             float *Ds = sj.Dst;
 #pragma unroll
             for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
@@ -2231,6 +2224,139 @@ __global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restri
                                                    const float *__restrict__ Wf, Strong sj)
 {
     patch_fix_body<SCHEME>(P, self_blk(), U, Uf, Wf, sj);
+}
+
+// ------------------------------------------------------------------------------------------
+// Gated path: the stage's flagged interfaces as per-direction lists in node order.  The gated
+// passes only set flag bits; three launches turn the bits into lists (capacity: every node):
+// per block of CMP_CHUNK consecutive nodes the count of each direction's bits, an exclusive
+// scan of the block counts (which also gives the totals the patch and update passes read), and
+// the ordered write.  Node order keeps neighbouring threads of k_patch_fix on neighbouring
+// interfaces (coalesced stencil loads) and the result independent of scheduling.
+// ------------------------------------------------------------------------------------------
+constexpr int CMP_T = 256, CMP_PER = 8, CMP_CHUNK = CMP_T * CMP_PER;
+
+int compact_blocks(const Dev &P) { return (int)((P.ntot + CMP_CHUNK - 1) / CMP_CHUNK); }
+
+__global__ void __launch_bounds__(CMP_T) k_flag_count(Dev P, const unsigned char *__restrict__ flag,
+                                                      int *__restrict__ bcnt, int nblk)
+{
+    __shared__ int sred[3][CMP_T / 32];
+    const long long c0 = (long long)blockIdx.x * CMP_CHUNK;
+    int c[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < CMP_PER; q++) {
+        const long long t = c0 + q * CMP_T + threadIdx.x;
+        const unsigned f = t < P.ntot ? flag[t] : 0u;
+        c[0] += f & 1u;
+        c[1] += (f >> 1) & 1u;
+        c[2] += (f >> 2) & 1u;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        int v = c[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sred[d][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int v = 0;
+        for (int i = 0; i < CMP_T / 32; i++) v += sred[threadIdx.x][i];
+        bcnt[threadIdx.x * nblk + blockIdx.x] = v;
+    }
+}
+
+// one block of 1024 threads: exclusive scan of each direction's block counts, totals to count[]
+__global__ void __launch_bounds__(1024) k_flag_scan(const int *__restrict__ bcnt, int *__restrict__ boff,
+                                                    int nblk, int *__restrict__ count)
+{
+    __shared__ int swarp[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = 0; d < 3; d++) {
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (int b0 = 0; b0 < nblk; b0 += 1024) {
+            const int b = b0 + threadIdx.x;
+            const int v = b < nblk ? bcnt[d * nblk + b] : 0;
+            int x = v;   // inclusive scan within the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) swarp[w] = x;
+            __syncthreads();
+            if (w == 0) {
+                int z = swarp[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, z, o);
+                    if (lane >= o) z += y;
+                }
+                swarp[lane] = z;   // inclusive over warps
+            }
+            __syncthreads();
+            const int before = (w > 0 ? swarp[w - 1] : 0) + x - v;
+            if (b < nblk) boff[d * nblk + b] = carry + before;
+            __syncthreads();
+            if (threadIdx.x == 1023) carry += swarp[31];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) count[d] = carry;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(CMP_T) k_flag_write(Dev P, const unsigned char *__restrict__ flag,
+                                                      const int *__restrict__ boff, int nblk,
+                                                      long long *__restrict__ list, int cap)
+{
+    __shared__ int swarp[3][CMP_T / 32];
+    const long long c0 = (long long)blockIdx.x * CMP_CHUNK;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int run[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) run[d] = boff[d * nblk + blockIdx.x];
+    for (int q = 0; q < CMP_PER; q++) {
+        const long long t = c0 + q * CMP_T + threadIdx.x;
+        const unsigned f = t < P.ntot ? flag[t] : 0u;
+        unsigned bal[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            bal[d] = __ballot_sync(0xffffffffu, (f >> d) & 1u);
+            if (lane == 0) swarp[d][w] = __popc(bal[d]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            int before = 0, tot = 0;
+            for (int i = 0; i < CMP_T / 32; i++) {
+                const int c = swarp[d][i];
+                before += i < w ? c : 0;
+                tot += c;
+            }
+            if ((f >> d) & 1u) {
+                const int k = run[d] + before + __popc(bal[d] & lt);
+                if (k < cap) list[(long long)d * cap + k] = t;
+            }
+            run[d] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+static int launch_compact(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    const int nblk = compact_blocks(P);
+    int *bcnt = B.cmp, *boff = B.cmp + 3 * nblk;
+    k_flag_count<<<nblk, CMP_T, 0, s>>>(P, B.flag, bcnt, nblk);
+    k_flag_scan<<<1, 1024, 0, s>>>(bcnt, boff, nblk, B.err + 1);
+    k_flag_write<<<nblk, CMP_T, 0, s>>>(P, B.flag, boff, nblk, B.slist, B.scap);
+    return 3;
 }
 
 int conv_chunk(const Dev &P, int d);
@@ -2570,6 +2696,10 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         acc = 1;
         launches++;
         if (patch && d == 0 && !P.sensor) launches++;   // the x segments' left interfaces
+    }
+    if (patch && P.sensor) {   // the gated passes' flags -> ordered lists
+        if (tap) (*tap)("compact", s);
+        launches += launch_compact(P, B, s);
     }
     if (patch) {   // FP64 recomputation of the stage's strong-jump interfaces (applied by the update)
         if (tap) (*tap)("patch", s);

@@ -24,6 +24,7 @@ struct Bufs {
     float zthresh = 0.f;                               // sensor: logit of the decision threshold
     int gate_fixed = 0;                                // sensor: gate from caller flags (no inference)
     int *err = nullptr;                                // device error word, then 3 strong-jump counts
+    int *cmp = nullptr;                                // gated path: block counts / offsets of the flag compaction
 };
 
 void launch_unpack(const Dev &P, const double *src, double *dst, int nvar, cudaStream_t s);
@@ -86,5 +87,7 @@ int launch_ensemble_stage(const EnsLaunch &L, int stage, cudaStream_t s);
 // out = lowest member index whose error word has the non-finite bit, else -1; clears the words
 void launch_ensemble_errors(const EnsLaunch &L, int *out, cudaStream_t s);
 int conv_chunk(const Dev &P, int d);
+// gated path: blocks of the flag compaction (its scratch holds 6 ints per block)
+int compact_blocks(const Dev &P);
 
 }  // namespace osb

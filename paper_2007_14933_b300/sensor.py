@@ -50,10 +50,39 @@ def train(feats, labels, steps=1500, batch=4096, lr=3e-3, seed=1, pos_weight=Non
     return osbli.osbli_mlp_train(feats, labels, n, steps, batch, lr, pos_weight, seed, w)
 
 
+def collect_at(cfg, U, steps, precision=osbli.OSBLI_MIXED):
+    """As collect(), with snapshots after each cumulative step count in `steps` (ascending)."""
+    import torch
+    s = osbli.Solver(dict(cfg, sensor=0), precision=precision)
+    s.set_state(U)
+    N = int(np.prod(cfg["n"]))
+    feats, labels, done = [], [], 0
+    for k in steps:
+        s.step(int(k) - done)
+        done = int(k)
+        f = torch.empty((N, osbli.SENSOR_NFEAT), dtype=torch.bfloat16, device="cuda")
+        osbli.osbli_sensor_features(s.h, f)
+        lab = torch.empty(N, dtype=torch.uint8, device="cuda")
+        osbli.osbli_sensor_labels(s.h, lab)
+        feats.append(f)
+        labels.append(lab)
+    s.close()
+    return torch.cat(feats), torch.cat(labels)
+
+
 def tgv_training_set(N=48, Ma=1.25, nsnap=6, steps_between=12):
-    """TENO5 TGV snapshots from the analytic field through shocklet formation."""
+    """TENO5 TGV snapshots from the analytic field on (the smooth early phase)."""
     cfg, U = I.tgv(N, Ma=Ma, scheme=I.TENO5)
     return collect(cfg, U, nsnap, steps_between)
+
+
+def tgv_shocklet_training_set(N=128, Ma=1.25, times=(1.5, 2.0, 2.5, 3.0, 3.5)):
+    """TENO5 TGV snapshots in the shocklet phase (Ma 1.25 forms shocklets from t ~ 1.5 on), the
+    state advanced by the mixed form between snapshots."""
+    cfg, U = I.tgv(N, Ma=Ma, scheme=I.TENO5)
+    steps = [int(round(t / cfg["dt"])) for t in times]
+    f, lab = collect_at(cfg, U, steps)
+    return f, lab, "TGV %d^3 Ma %.2f at t = %s" % (N, Ma, ", ".join("%.1f" % t for t in times))
 
 
 SBLI_TRAIN_DESC = ("shock / boundary-layer box 96x48x8 on 60x20x4 (Mach 2, Re 1e4, 10 deg shock from "
