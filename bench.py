@@ -120,7 +120,9 @@ def parse():
     ap.add_argument("--mixed", action="store_true", help="time the mixed form only")
     ap.add_argument("--no-sensor", action="store_true", help="skip the learned-sensor form")
     ap.add_argument("--forms", default=None, help="comma list of forms to time (learned, mixed, fp64)")
-    ap.add_argument("--sensor-steps", type=int, default=800, help="Adam steps of the sensor training")
+    ap.add_argument("--sensor-steps", type=int, default=3000, help="Adam steps of the sensor training")
+    ap.add_argument("--train-fine", type=int, default=1,
+                    help="TGV: add TENO labels of the run's own grid at t = 1.5 and 2.0 to the training set")
     ap.add_argument("--accuracy-steps", type=int, default=100,
                     help="steps from the initial field after which the forms' states are compared "
                          "(the timed steps count; the rest run after the timed region)")
@@ -128,6 +130,9 @@ def parse():
                     help="TGV: time the learned form also from the shocklet phase, reached by "
                          "advancing the mixed form to at least this time (0: skip)")
     ap.add_argument("--shock-steps-max", type=int, default=1500)
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="TGV: also time the grid split into this many z-slabs with halo exchanges "
+                         "(osbli_domain_*, one device), mixed and FP64 forms, against the whole grid")
     return ap.parse_args()
 
 
@@ -370,6 +375,14 @@ def run_ensemble(args, world, rank, local):
         chunk, _ = ens.autotune(reps=2)
         res["ensemble"] = timed(ens.step)
         launches = ens.launches_per_step() * args.steps
+        # the persistent form: one cooperative launch for all the timed steps of every member
+        pers = make(osbli.OSBLI_MIXED)
+        pers.set_chunk(chunk)
+        pers.set_persistent(True)
+        res["persistent"] = timed(pers.step)
+        pers_grid = pers.persistent_grid()
+        pers_same = all(np.array_equal(pers.get_state(p), ens.get_state(p)) for p in range(len(cfgs)))
+        pers.close()
         sep = [osbli.Solver(c, precision=osbli.OSBLI_MIXED, cuda_stream=stream.cuda_stream) for c in cfgs]
         for s_, (_, U) in zip(sep, mem):
             s_.set_state(U)
@@ -425,6 +438,9 @@ def run_ensemble(args, world, rank, local):
            "forms": forms, "autotuned_chunk": chunk,
            "gpu_launches_separate_per_step": sep_launches,
            "speedup_ensemble_vs_separate": forms["ensemble"]["value"] / forms["separate"]["value"],
+           "persistent": {"blocks": pers_grid, "launches_per_call": 1,
+                          "bitwise_equal_to_graph_form": pers_same,
+                          "speed_vs_graph_form": forms["persistent"]["value"] / forms["ensemble"]["value"]},
            "speedup_ensemble_vs_fp64": forms["ensemble"]["value"] / forms["fp64"]["value"],
            "l2_ensemble_vs_fp64": l2,
            "variant": "mixed precision, batched members (osbli_ensemble_step)"}
@@ -532,6 +548,36 @@ def shocked_phase(osbli, torch, cfg, U, sensor, args, stream, barrier, dist, npt
     return out
 
 
+def split_grid(osbli, torch, cfg, U, args, stream, barrier, dist, npts, world, prec, res, done):
+    """The same workload as args.slabs z-slabs with halo exchanges on this device (the layout a
+    decomposed run uses), mixed and FP64 forms, timed like the whole grid; states compared
+    bitwise with the whole grid's after the same steps."""
+    out = {"slabs": args.slabs}
+    for f in ("mixed", "fp64"):
+        if f not in res:
+            continue
+        d = osbli.Domain(cfg, args.slabs, precision=prec[f], cuda_stream=stream.cuda_stream)
+        d.set_state(U)
+        d.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        launches, copies = d.launches_per_step()
+        d.step(done - args.warmup - args.steps)      # as many steps as the whole grid's solver took
+        same = bool(np.array_equal(d.get_state(), res[f][0].get_state()))
+        d.close()
+        out[f] = {"value": job_rate(npts, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps,
+                  "launches_per_step": launches, "halo_copies_per_step": copies,
+                  "bitwise_equal_to_whole_grid": same}
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -579,10 +625,16 @@ def main():
         feats, labels, _ = SN.tgv_training_set(N=64, Ma=1.25, nsnap=6, steps_between=12)
         train_set = "TGV 64^3 Ma 1.25, 6 snapshots every 12 steps"
         if args.workload == "tgv":
-            f2, l2_, desc = SN.tgv_shocklet_training_set(N=128, Ma=1.25)
+            f2, l2_, desc = SN.tgv_shocklet_training_set(N=128, Ma=1.25, times=(1.0, 1.5, 2.0, 2.5, 3.0, 3.5))
             feats, labels = torch.cat([feats, f2]), torch.cat([labels, l2_])
             train_set += " + " + desc
             del f2, l2_
+            if args.n >= 256 and args.train_fine:
+                # the run's own resolution, before the timed windows (t <= 2)
+                f2, l2_, desc = SN.tgv_shocklet_training_set(N=args.n, Ma=1.25, times=(1.5, 2.0))
+                feats, labels = torch.cat([feats, f2]), torch.cat([labels, l2_])
+                train_set += " + " + desc
+                del f2, l2_
         if args.workload == "sbli":
             f2, l2_, _ = SN.sbli_training_set()
             feats, labels = torch.cat([feats, f2]), torch.cat([labels, l2_])
@@ -693,6 +745,11 @@ def main():
             extra["gated_after_accuracy_steps"] = {"cells": float(dg[9]), "interfaces_x": float(dg[10]),
                                                    "interfaces_y": float(dg[11]),
                                                    "interfaces_z": float(dg[12])}
+    if args.slabs > 1 and args.workload == "tgv":
+        done = (max(args.accuracy_steps, args.warmup + args.steps) if ("fp64" in forms and len(forms) > 1)
+                else args.warmup + args.steps)
+        extra["split_grid"] = split_grid(osbli, torch, cfg, U, args, stream, barrier, dist, npts, world, prec, res,
+                                         done)
     if "learned" in forms and args.workload == "tgv" and args.shock_t > 0:
         extra["shocklet_phase"] = shocked_phase(osbli, torch, cfg, U, sensor, args, stream, barrier, dist,
                                                 npts, world, prec)

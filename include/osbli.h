@@ -286,7 +286,21 @@ int osbli_ensemble_set_chunk(osbli_ens_t *e, int chunk);
  * milliseconds per step.  Allocates a copy of the states for the duration of the call. */
 int osbli_ensemble_autotune(osbli_ens_t *e, int reps, int *chunk_out, double *ms_out);
 
-/* Kernel launches of one captured step (0 before the first step), total interior points. */
+/* Persistent form (on = 1): each osbli_ensemble_step call is ONE cooperative kernel launch that
+ * runs all nsteps RK steps of every member.  Its blocks (as many as can be resident at once)
+ * take each phase's virtual blocks over all members from a device ticket counter (the tile
+ * queue) and meet at a grid barrier between phases.  Every barrier wait is bounded by
+ * spin_limit polls of at least 64 ns each (0: the default, 2e7); a wait that runs out makes
+ * every block leave and osbli_ensemble_step return OSBLI_ETIMEOUT, the members' states then
+ * partly advanced (set them again).  Results are bitwise those of the graph form (on = 0, the
+ * default: one launch per phase over all members, one graph per step).  Errors: EINVAL. */
+int osbli_ensemble_set_persistent(osbli_ens_t *e, int on, long long spin_limit);
+
+/* Blocks of the last persistent launch (0 before one). */
+int osbli_ensemble_persistent_grid(const osbli_ens_t *e);
+
+/* Kernel launches of one captured step (0 before the first step; 1 in the persistent form, whose
+ * single launch covers a whole osbli_ensemble_step call), total interior points. */
 int osbli_ensemble_launches_per_step(const osbli_ens_t *e);
 long long osbli_ensemble_points(const osbli_ens_t *e);
 

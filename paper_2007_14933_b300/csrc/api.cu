@@ -531,7 +531,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     const Dev &P = h->P;
     int per_stage = 1 /*prim*/ + 1 /*update*/;
     if (P.mixed && !general(P)) per_stage += 1;   // FP64 fix of strong-jump interfaces
-    if (P.mixed && !general(P) && P.sensor) per_stage += 3;   // flag compaction of the gated path
+    if (P.mixed && !general(P) && P.sensor) per_stage += 4;   // flag compaction, FP32 recomputation
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         per_stage += 2;   // ghost + convective direction

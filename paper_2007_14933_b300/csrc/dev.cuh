@@ -124,6 +124,16 @@ __device__ __forceinline__ Blk self_blk()
     return {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
 }
 
+// Thread coordinates inside a (possibly virtual) 2D block: the marching-line bodies take them
+// from the launch, or from a persistent kernel that runs them on a differently shaped block.
+struct Thr2 {
+    int x, y, nx, ny;
+};
+__device__ __forceinline__ Thr2 self_thr2()
+{
+    return {(int)threadIdx.x, (int)threadIdx.y, (int)blockDim.x, (int)blockDim.y};
+}
+
 __host__ __device__ __forceinline__ long long node_index(const Dev &P, int i, int j, int k)
 {
     return ((long long)(k + P.g[2]) * P.np[1] + (j + P.g[1])) * P.np[0] + (i + P.g[0]);

@@ -32,7 +32,10 @@ struct osbli_ens {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     EnsProb *d_tab = nullptr;
-    int *d_start = nullptr;
+    int *d_start = nullptr, *d_pstart = nullptr;
+    void *d_sync = nullptr;              // persistent form: barrier words, ticket, flag
+    int *h_flag = nullptr;
+    int persistent = 0, pgrid = 0;
     int *d_err = nullptr, *h_err = nullptr;
     EnsLaunch L;
     int chunk = 0;                       // 0: per-member default chunks
@@ -65,7 +68,7 @@ static int build_tables(osbli_ens *e)
 {
     const int np = e->nprob, np1 = np + 1;
     std::vector<EnsProb> tab(np);
-    std::vector<int> start((size_t)ENS_NPH * np1, 0);
+    std::vector<int> start((size_t)ENS_NPH * np1, 0), pstart((size_t)ENS_NPH * np1, 0);
     for (int p = 0; p < np; p++) {
         bool set;
         osbli_internal_view(e->h[p], &tab[p].P, &tab[p].B, &set);
@@ -77,6 +80,17 @@ static int build_tables(osbli_ens *e)
             if (P.active[d]) first = false;
         }
         ens_phase_grids(P, tab[p].chunk, tab[p].g);
+        ens_phase_grids_persistent(P, tab[p].chunk, tab[p].gp);
+    }
+    for (int ph = 0; ph < ENS_NPH; ph++) {
+        long long acc = 0;
+        for (int p = 0; p < np; p++) {
+            pstart[(size_t)ph * np1 + p] = (int)acc;
+            acc += (long long)tab[p].gp[ph][0] * tab[p].gp[ph][1] * tab[p].gp[ph][2];
+        }
+        pstart[(size_t)ph * np1 + np] = (int)acc;
+        if (acc > 0x7fffffffLL) return eseterr(e, OSBLI_EINVAL, "phase %d needs more than 2^31 blocks", ph);
+        e->L.ptotal[ph] = (int)acc;
     }
     for (int ph = 0; ph < ENS_NPH; ph++) {
         long long acc = 0;
@@ -90,6 +104,8 @@ static int build_tables(osbli_ens *e)
     }
     ECK(e, cudaMemcpyAsync(e->d_tab, tab.data(), sizeof(EnsProb) * np, cudaMemcpyHostToDevice, e->stream));
     ECK(e, cudaMemcpyAsync(e->d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
+                           e->stream));
+    ECK(e, cudaMemcpyAsync(e->d_pstart, pstart.data(), sizeof(int) * pstart.size(), cudaMemcpyHostToDevice,
                            e->stream));
     ECK(e, cudaStreamSynchronize(e->stream));
     if (e->gexec) {
@@ -107,6 +123,9 @@ extern "C" void osbli_ensemble_destroy(osbli_ens_t *e)
     for (osbli_t *h : e->h) osbli_destroy(h);
     if (e->d_tab) cudaFree(e->d_tab);
     if (e->d_start) cudaFree(e->d_start);
+    if (e->d_pstart) cudaFree(e->d_pstart);
+    if (e->d_sync) cudaFree(e->d_sync);
+    if (e->h_flag) cudaFreeHost(e->h_flag);
     if (e->d_err) cudaFree(e->d_err);
     if (e->h_err) cudaFreeHost(e->h_err);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
@@ -158,6 +177,9 @@ extern "C" int osbli_ensemble_create(int nprob, const osbli_params *params, void
     if (ce == cudaSuccess) ce = cudaMalloc(&e->d_start, sizeof(int) * ENS_NPH * (nprob + 1));
     if (ce == cudaSuccess) ce = cudaMalloc(&e->d_err, sizeof(int));
     if (ce == cudaSuccess) ce = cudaMallocHost(&e->h_err, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_pstart, sizeof(int) * ENS_NPH * (nprob + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_sync, 64);
+    if (ce == cudaSuccess) ce = cudaMallocHost(&e->h_flag, sizeof(int));
     if (ce != cudaSuccess)
         return fail(eseterr(e, ce == cudaErrorMemoryAllocation ? OSBLI_ENOMEM : OSBLI_ECUDA, "tables: %s",
                             cudaGetErrorString(ce)));
@@ -167,6 +189,10 @@ extern "C" int osbli_ensemble_create(int nprob, const osbli_params *params, void
     e->L.mixed = params[0].precision == OSBLI_MIXED;
     e->L.scheme = params[0].scheme;
     e->L.nstage = params[0].rk == OSBLI_RK4 ? 5 : 3;
+    e->L.pstart = e->d_pstart;
+    e->L.bar = (unsigned *)e->d_sync;                                            // 2 words
+    e->L.ticket = (unsigned long long *)((char *)e->d_sync + 16);
+    e->L.flag = (int *)((char *)e->d_sync + 32);
     int rc = build_tables(e);
     if (rc != OSBLI_OK) return fail(rc);
     *out = e;
@@ -238,11 +264,25 @@ extern "C" int osbli_ensemble_step(osbli_ens_t *e, int nsteps)
         if (!set) return eseterr(e, OSBLI_ESTATE, "member %d: state not set", p);
     }
     if (nsteps == 0) return OSBLI_OK;
-    if (!e->gexec) {
-        int rc = capture(e);
-        if (rc != OSBLI_OK) return rc;
+    if (e->persistent) {
+        const int le = launch_ensemble_persistent(e->L, nsteps, e->stream, &e->pgrid);
+        if (le != (int)cudaSuccess)
+            return eseterr(e, OSBLI_ECUDA, "persistent launch: %s", cudaGetErrorString((cudaError_t)le));
+        ECK(e, cudaMemcpyAsync(e->h_flag, e->L.flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+        ECK(e, cudaStreamSynchronize(e->stream));
+        if (*e->h_flag & 1) {
+            launch_ensemble_errors(e->L, e->d_err, e->stream);   // clear the members' words
+            cudaStreamSynchronize(e->stream);
+            return eseterr(e, OSBLI_ETIMEOUT, "a grid barrier of the persistent step gave up after %lld polls; "
+                           "the members' states are partly advanced", e->L.spin_limit);
+        }
+    } else {
+        if (!e->gexec) {
+            int rc = capture(e);
+            if (rc != OSBLI_OK) return rc;
+        }
+        for (int i = 0; i < nsteps; i++) ECK(e, cudaGraphLaunch(e->gexec, e->stream));
     }
-    for (int i = 0; i < nsteps; i++) ECK(e, cudaGraphLaunch(e->gexec, e->stream));
     launch_ensemble_errors(e->L, e->d_err, e->stream);
     ECK(e, cudaGetLastError());
     ECK(e, cudaMemcpyAsync(e->h_err, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
@@ -334,9 +374,25 @@ extern "C" int osbli_ensemble_autotune(osbli_ens_t *e, int reps, int *chunk_out,
     return OSBLI_OK;
 }
 
+extern "C" int osbli_ensemble_set_persistent(osbli_ens_t *e, int on, long long spin_limit)
+{
+    if (!e) return eseterr(nullptr, OSBLI_EINVAL, "null ensemble");
+    if (on != 0 && on != 1) return eseterr(e, OSBLI_EINVAL, "on must be 0 or 1");
+    if (spin_limit < 0) return eseterr(e, OSBLI_EINVAL, "spin_limit must be >= 0");
+    e->persistent = on;
+    e->L.spin_limit = spin_limit > 0 ? spin_limit : 20000000;
+    return OSBLI_OK;
+}
+
 extern "C" int osbli_ensemble_launches_per_step(const osbli_ens_t *e)
 {
-    return e ? e->launches_step : 0;
+    if (!e) return 0;
+    return e->persistent ? 1 : e->launches_step;
+}
+
+extern "C" int osbli_ensemble_persistent_grid(const osbli_ens_t *e)
+{
+    return e ? e->pgrid : 0;
 }
 
 extern "C" long long osbli_ensemble_points(const osbli_ens_t *e)

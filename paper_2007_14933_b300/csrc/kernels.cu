@@ -505,11 +505,12 @@ template <int DIR, int SCHEME, bool CURV>
 __device__ __forceinline__ void conv_char_body(const Dev &P, const Blk &bk, const double *__restrict__ U,
                                                    const double *__restrict__ W,
                                                    const double *__restrict__ M,
-                                                   double *__restrict__ R, int accumulate, int chunk)
+                                                   double *__restrict__ R, int accumulate, int chunk,
+                                                   const Thr2 &th)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
-    const int a = bk.x * blockDim.x + threadIdx.x;
-    const int b = bk.y * blockDim.y + threadIdx.y;
+    const int a = bk.x * th.nx + th.x;
+    const int b = bk.y * th.ny + th.y;
     if (a >= P.n[DA] || b >= P.n[DB]) return;
     const int s0 = bk.z * chunk;
     const int s1 = min(s0 + chunk, P.n[DIR]);
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(128) k_conv_char(Dev P, const double *__restri
                                                    const double *__restrict__ M,
                                                    double *__restrict__ R, int accumulate, int chunk)
 {
-    conv_char_body<DIR, SCHEME, CURV>(P, self_blk(), U, W, M, R, accumulate, chunk);
+    conv_char_body<DIR, SCHEME, CURV>(P, self_blk(), U, W, M, R, accumulate, chunk, self_thr2());
 }
 
 // ------------------------------------------------------------------------------------------
@@ -794,7 +795,22 @@ __global__ void __launch_bounds__(128) k_conv_central(Dev P, const double *__res
 // the one-sided closures.
 // ------------------------------------------------------------------------------------------
 template <typename T, typename Fetch>
-__device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool lo_open, bool hi_open)
+__device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool per)
+{
+    if (per || (ie >= 2 && ie <= n - 3))
+        return fdiv(f(ie - 2) - T(8) * f(ie - 1) + T(8) * f(ie + 1) - f(ie + 2), T(12));
+    if (ie == 0) return fdiv(T(-25) * f(0) + T(48) * f(1) - T(36) * f(2) + T(16) * f(3) - T(3) * f(4), T(12));
+    if (ie == 1) return fdiv(T(-3) * f(0) - T(10) * f(1) + T(18) * f(2) - T(6) * f(3) + f(4), T(12));
+    if (ie == n - 2)
+        return fdiv(-f(n - 5) + T(6) * f(n - 4) - T(18) * f(n - 3) + T(10) * f(n - 2) + T(3) * f(n - 1), T(12));
+    return fdiv(T(3) * f(n - 5) - T(16) * f(n - 4) + T(36) * f(n - 3) - T(48) * f(n - 2) + T(25) * f(n - 1), T(12));
+}
+
+// The same with each end open or closed on its own: sub-domain (halo) faces take the interior
+// formula up to the face, physical faces the closures.  Kept apart from deriv_line so that the
+// lines of undivided grids compile exactly as before.
+template <typename T, typename Fetch>
+__device__ __forceinline__ T deriv_line_open(Fetch f, int ie, int n, bool lo_open, bool hi_open)
 {
     if ((lo_open || ie >= 2) && (hi_open || ie <= n - 3))
         return fdiv(f(ie - 2) - T(8) * f(ie - 1) + T(8) * f(ie + 1) - f(ie + 2), T(12));
@@ -808,7 +824,7 @@ __device__ __forceinline__ T deriv_line(Fetch f, int ie, int n, bool lo_open, bo
 // Viscous fluxes (Eqs. 2-5) at interior nodes: V[d] = (S~_d . tau_{i.}, S~_d . (u_i tau_{i.} - q)).
 // T = double (plain path) or float (mixed path: gradients, tau and q in FP32, stored as FP32).
 
-template <bool CURV, typename T, typename S>
+template <bool CURV, typename T, typename S, bool HALO = false>
 __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ W,
                                                    const double *__restrict__ M, S *__restrict__ V)
 {
@@ -832,12 +848,14 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
             if (!P.active[e]) continue;
             const int ie = ijk[e];
             const long long st = P.st[e];
-            const bool lo = open_lo(P, e), hi = open_hi(P, e);
+            const bool per = P.bc[e][0] == BC_PERIODIC;
             const int widx[4] = {W_U, W_V, W_W, W_T};
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 const S *f = W + widx[v] * vs + id;
-                dxi[e][v] = deriv_line<T>([&](int s) { return T(f[(long long)(s - ie) * st]); }, ie, P.n[e], lo, hi);
+                auto fe = [&](int s) { return T(f[(long long)(s - ie) * st]); };
+                if constexpr (HALO) dxi[e][v] = deriv_line_open<T>(fe, ie, P.n[e], open_lo(P, e), open_hi(P, e));
+                else dxi[e][v] = deriv_line<T>(fe, ie, P.n[e], per);
             }
         }
         T gr[4][3];
@@ -899,7 +917,7 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
 // MODE 0: RK stage (STAGE selects A_i/B_i; stage 0 has dU^(0) = 0); MODE 1: R_total -> Rout.
 // RT is the storage / arithmetic type of the residual and viscous fluxes (double plain, float
 // mixed); the register update itself is FP64 on both paths.
-template <int MODE, int STAGE, bool VISC, bool CURV, typename RT>
+template <int MODE, int STAGE, bool VISC, bool CURV, typename RT, bool HALO = false>
 __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double *__restrict__ U, double *__restrict__ dU,
                                                 const RT *Rin, const RT *__restrict__ V,
                                                 const double *__restrict__ M, double *Rout,
@@ -956,17 +974,27 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                 // periodic lines wrap into the interior (V lives on interior nodes only); a
                 // sub-domain face reads the halo planes of V its neighbour's exchange filled
                 const bool per = P.bc[d][0] == BC_PERIODIC;
-                const bool lo = open_lo(P, d), hi = open_hi(P, d);
                 const RT fac = CURV ? RT(P.shat[d] * M[9 * vs + id])
                                     : (sizeof(RT) == 4 ? RT(line_facf(P, d, ie)) : RT(line_fac(P, d, ie)));
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
                     const RT *f = V + (d * 4 + c) * vs + id;
-                    const RT D = deriv_line<RT>([&](int s) {
-                        int w = s;
-                        if (per) { w = s % n; if (w < 0) w += n; }
-                        return f[(long long)(w - ie) * st];
-                    }, ie, n, lo, hi);
+                    RT D;
+                    if constexpr (HALO) {
+                        // sub-domain: periodic lines wrap into the interior as below, a halo face
+                        // reads the planes of V its neighbour's exchange filled
+                        D = deriv_line_open<RT>([&](int s) {
+                            int w = s;
+                            if (per) { w = s % n; if (w < 0) w += n; }
+                            return f[(long long)(w - ie) * st];
+                        }, ie, n, open_lo(P, d), open_hi(P, d));
+                    } else {
+                        D = deriv_line<RT>([&](int s) {
+                            int w = s;
+                            if (per) { w = s % n; if (w < 0) w += n; }
+                            return f[(long long)(w - ie) * st];
+                        }, ie, n, per);
+                    }
                     r[1 + c] += fac * D;
                 }
             }
@@ -1008,13 +1036,13 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
     }
 }
 
-template <int MODE, int STAGE, bool VISC, bool CURV, typename RT>
+template <int MODE, int STAGE, bool VISC, bool CURV, typename RT, bool HALO = false>
 __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, double *__restrict__ dU,
                                                 const RT *Rin, const RT *__restrict__ V,
                                                 const double *__restrict__ M, double *Rout,
                                                 int *__restrict__ err, Strong sj)
 {
-    update_body<MODE, STAGE, VISC, CURV, RT>(P, self_blk(), U, dU, Rin, V, M, Rout, err, sj);
+    update_body<MODE, STAGE, VISC, CURV, RT, HALO>(P, self_blk(), U, dU, Rin, V, M, Rout, err, sj);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1062,7 +1090,7 @@ __global__ void k_metric_raw(Dev P, const double *__restrict__ X, double Lp0, do
                     const long long o = ((long long)jj[2] * P.n[1] + jj[1]) * P.n[0] + jj[0];
                     return (X[c * N + o] - xc) + (c == d ? sh * Lp[d] : 0.0);
                 };
-                Xd[d][c] = deriv_line<double>(f, ijk[d], n, per, per);
+                Xd[d][c] = deriv_line<double>(f, ijk[d], n, per);
             }
         }
         double S[3][3];
@@ -1442,11 +1470,11 @@ __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk
                                                          const float *__restrict__ Wf,
                                                          float *__restrict__ Rf, Strong sj,
                                                          const unsigned char *__restrict__ gate,
-                                                         int accumulate, int chunk)
+                                                         int accumulate, int chunk, const Thr2 &th)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
-    const int a = bk.x * blockDim.x + threadIdx.x;
-    const int b = bk.y * blockDim.y + threadIdx.y;
+    const int a = bk.x * th.nx + th.x;
+    const int b = bk.y * th.ny + th.y;
     if (a >= P.n[DA] || b >= P.n[DB]) return;
     const int s0 = bk.z * chunk;
     const int s1 = min(s0 + chunk, P.n[DIR]);
@@ -1483,7 +1511,7 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
                                                          const unsigned char *__restrict__ gate,
                                                          int accumulate, int chunk)
 {
-    conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, accumulate, chunk);
+    conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, accumulate, chunk, self_thr2());
 }
 
 // Gated y / z passes (learned sensor on): most interfaces take the central flux, which needs
@@ -2158,20 +2186,28 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
 // Recomputation of one flagged interface m of direction DIR: across a strong jump the FP64
 // characteristic flux, otherwise (an interface the gated pass gave the central flux) the FP32
 // characteristic flux.  Dst (plane set DIR) receives the correction D_new - D_pass in place of
-// the D the convective pass used.
-template <int DIR, int SCHEME>
+// the D the convective pass used.  PART 0 does both kinds; PART 1 only the FP32 ones and PART 2
+// only the FP64 ones (split so that the FP32 kernel keeps the register budget of the FP32
+// arithmetic: the FP64 flux is a call whose registers a caller has to reserve).
+template <int DIR, int SCHEME, int PART = 0>
 __device__ __noinline__ void fix_interface(const Dev &P, const double *__restrict__ U,
                                            const float *__restrict__ Uf, const float *__restrict__ Wf,
                                            float *__restrict__ Dst, long long m)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
+    const long long st = P.st[DIR];
+    const bool strong = strong_jump(P, Uf, Wf, m, st);
+    if ((PART == 1 && strong) || (PART == 2 && !strong)) return;
     int c3[3];
     split_node(P, m, c3);
     const double es = line_eps<DIR>(P, c3[DA], c3[DB]);
-    const long long st = P.st[DIR];
     float Dn[NV], unused[NV];
-    if (strong_jump(P, Uf, Wf, m, st)) fallback_delta<DIR, SCHEME>(P, U, m, st, es, Dn, unused);
-    else delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, (float)es, Dn, unused);
+    if constexpr (PART == 1) {
+        delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, (float)es, Dn, unused);
+    } else {
+        if (strong) fallback_delta<DIR, SCHEME>(P, U, m, st, es, Dn, unused);
+        else delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, (float)es, Dn, unused);
+    }
     float *Ds = Dst + (long long)DIR * NV * P.vs;
 #pragma unroll
     for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = Dn[v] - Ds[v * P.vs + m];
@@ -2181,7 +2217,7 @@ __device__ __noinline__ void fix_interface(const Dev &P, const double *__restric
 // whose list overflowed (more flagged interfaces than its capacity) is handled by a scan of its
 // flag bits instead: each interior node takes its right interface, the first node of a line
 // also its left one.
-template <int SCHEME>
+template <int SCHEME, int PART = 0>
 __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, const double *__restrict__ U,
                                                const float *__restrict__ Uf, const float *__restrict__ Wf,
                                                Strong sj)
@@ -2192,9 +2228,9 @@ __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, cons
     const long long stride = (long long)bk.nx * blockDim.x;
     const long long t0 = bk.x * (long long)blockDim.x + threadIdx.x;
     for (long long t = t0; t < (long long)l0 + l1 + l2; t += stride) {
-        if (t < l0) fix_interface<0, SCHEME>(P, U, Uf, Wf, sj.Dst, sj.list[t]);
-        else if (t < l0 + l1) fix_interface<1, SCHEME>(P, U, Uf, Wf, sj.Dst, sj.list[(long long)sj.cap + (t - l0)]);
-        else fix_interface<2, SCHEME>(P, U, Uf, Wf, sj.Dst, sj.list[2LL * sj.cap + (t - l0 - l1)]);
+        if (t < l0) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.list[t]);
+        else if (t < l0 + l1) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.list[(long long)sj.cap + (t - l0)]);
+        else fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.list[2LL * sj.cap + (t - l0 - l1)]);
     }
     if (c0 <= sj.cap && c1 <= sj.cap && c2 <= sj.cap) return;
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -2205,16 +2241,16 @@ __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, cons
         const long long id = node_index(P, ijk[0], ijk[1], ijk[2]);
         const unsigned char f = sj.flag[id];
         if (c0 > sj.cap) {
-            if (f & 1) fix_interface<0, SCHEME>(P, U, Uf, Wf, sj.Dst, id);
-            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME>(P, U, Uf, Wf, sj.Dst, id - P.st[0]);
+            if (f & 1) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id);
+            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id - P.st[0]);
         }
         if (c1 > sj.cap) {
-            if (f & 2) fix_interface<1, SCHEME>(P, U, Uf, Wf, sj.Dst, id);
-            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME>(P, U, Uf, Wf, sj.Dst, id - P.st[1]);
+            if (f & 2) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id);
+            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id - P.st[1]);
         }
         if (c2 > sj.cap) {
-            if (f & 4) fix_interface<2, SCHEME>(P, U, Uf, Wf, sj.Dst, id);
-            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME>(P, U, Uf, Wf, sj.Dst, id - P.st[2]);
+            if (f & 4) fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id);
+            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id - P.st[2]);
         }
     }
 }
@@ -2224,6 +2260,22 @@ __global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restri
                                                    const float *__restrict__ Wf, Strong sj)
 {
     patch_fix_body<SCHEME>(P, self_blk(), U, Uf, Wf, sj);
+}
+
+// the two halves of k_patch_fix for single problems: the FP64 recomputation of the strong-jump
+// interfaces, and the FP32 one of the others at the register budget of k_conv_char_delta
+template <int SCHEME>
+__global__ void __launch_bounds__(128) k_patch_fp64(Dev P, const double *__restrict__ U, const float *__restrict__ Uf,
+                                                    const float *__restrict__ Wf, Strong sj)
+{
+    patch_fix_body<SCHEME, 2>(P, self_blk(), U, Uf, Wf, sj);
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(128, 5) k_patch_fp32(Dev P, const double *__restrict__ U, const float *__restrict__ Uf,
+                                                       const float *__restrict__ Wf, Strong sj)
+{
+    patch_fix_body<SCHEME, 1>(P, self_blk(), U, Uf, Wf, sj);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2605,16 +2657,20 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
     }
 }
 
-template <int MODE, int STAGE, bool VISC, bool CURV>
+template <int MODE, int STAGE, bool VISC, bool CURV, bool HALO = false>
 static void update_t(const Dev &P, const Bufs &B, int g, cudaStream_t s)
 {
     const Strong none{nullptr, nullptr, nullptr, nullptr, 0};
     if (P.mixed)
-        k_update<MODE, STAGE, VISC, CURV, float><<<g, 128, 0, s>>>(P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err,
-                                                                    CURV ? none : strong_of(B));
+        k_update<MODE, STAGE, VISC, CURV, float, HALO><<<g, 128, 0, s>>>(P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err,
+                                                                          CURV ? none : strong_of(B));
     else
-        k_update<MODE, STAGE, VISC, CURV, double><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.R, B.err, none);
+        k_update<MODE, STAGE, VISC, CURV, double, HALO><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.R, B.err,
+                                                                           none);
 }
+
+// a sub-domain of a split grid (halo faces along z)
+static bool has_halo(const Dev &P) { return P.bc[2][0] == BC_HALO || P.bc[2][1] == BC_HALO; }
 
 template <int MODE, int STAGE>
 static void update(const Dev &P, const Bufs &B, cudaStream_t s)
@@ -2623,6 +2679,7 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     int g = grid_for(N, 128);
     if (P.viscous) {
         if (general(P)) update_t<MODE, STAGE, true, true>(P, B, g, s);
+        else if (has_halo(P)) update_t<MODE, STAGE, true, false, true>(P, B, g, s);
         else update_t<MODE, STAGE, true, false>(P, B, g, s);
     } else {
         if (general(P)) update_t<MODE, STAGE, false, true>(P, B, g, s);
@@ -2630,14 +2687,24 @@ static void update(const Dev &P, const Bufs &B, cudaStream_t s)
     }
 }
 
-static void launch_patch(const Dev &P, const Bufs &B, cudaStream_t s)
+template <int SCHEME>
+static void launch_patch_t(const Dev &P, const Bufs &B, cudaStream_t s)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const int g = grid_for(N, 128);
-    if (P.scheme == SCH_WENO5JS) k_patch_fix<SCH_WENO5JS><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
-    else if (P.scheme == SCH_WENO5Z) k_patch_fix<SCH_WENO5Z><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
-    else if (P.scheme == SCH_TENO6) k_patch_fix<SCH_TENO6><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
-    else k_patch_fix<SCH_TENO5><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    k_patch_fp64<SCHEME><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    if (P.sensor) k_patch_fp32<SCHEME><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+}
+
+// the stage's recorded interfaces (without the learned gate every recorded one is a strong jump,
+// so only the FP64 half runs); returns the launch count
+static int launch_patch(const Dev &P, const Bufs &B, cudaStream_t s)
+{
+    if (P.scheme == SCH_WENO5JS) launch_patch_t<SCH_WENO5JS>(P, B, s);
+    else if (P.scheme == SCH_WENO5Z) launch_patch_t<SCH_WENO5Z>(P, B, s);
+    else if (P.scheme == SCH_TENO6) launch_patch_t<SCH_TENO6>(P, B, s);
+    else launch_patch_t<SCH_TENO5>(P, B, s);
+    return P.sensor ? 2 : 1;
 }
 
 // Optional per-launch event taps (kernel timing): before each launch an event is recorded and
@@ -2703,8 +2770,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     }
     if (patch) {   // FP64 recomputation of the stage's strong-jump interfaces (applied by the update)
         if (tap) (*tap)("patch", s);
-        launch_patch(P, B, s);
-        launches++;
+        launches += launch_patch(P, B, s);
     }
     if (P.viscous) {
         long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -2712,9 +2778,11 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         const int g = grid_for(N, 128);
         if (P.mixed) {
             if (general(P)) k_visc_flux<true, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
+            else if (has_halo(P)) k_visc_flux<false, float, float, true><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
             else k_visc_flux<false, float, float><<<g, 128, 0, s>>>(P, B.Wf, B.M, B.Vf);
         } else {
             if (general(P)) k_visc_flux<true, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
+            else if (has_halo(P)) k_visc_flux<false, double, double, true><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
             else k_visc_flux<false, double, double><<<g, 128, 0, s>>>(P, B.W, B.M, B.V);
         }
         launches++;
@@ -2884,14 +2952,15 @@ template <int DIR, int SCHEME>
 __global__ void __launch_bounds__(128, 5) k_ens_delta(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(DIR == 1 ? ENS_CY : ENS_CZ)
-    conv_char_delta_body<DIR, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[DIR], e.chunk[DIR]);
+    conv_char_delta_body<DIR, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[DIR], e.chunk[DIR],
+                                      self_thr2());
 }
 
 template <int DIR, int SCHEME>
 __global__ void __launch_bounds__(128) k_ens_char(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(DIR == 0 ? ENS_CX : DIR == 1 ? ENS_CY : ENS_CZ)
-    conv_char_body<DIR, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[DIR], e.chunk[DIR]);
+    conv_char_body<DIR, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[DIR], e.chunk[DIR], self_thr2());
 }
 
 template <int SCHEME>
@@ -2910,6 +2979,197 @@ __global__ void __launch_bounds__(128) k_ens_update(const EnsProb *tab, const in
     else update_body<0, STAGE, false, false, double>(P, bk, B.U, B.dU, B.R, nullptr, B.M, B.R, B.err, none);
 }
 #undef ENS_PROLOGUE
+
+// ------------------------------------------------------------------------------------------
+// Persistent ensemble: one cooperative launch runs nsteps RK steps of every member.  All its
+// blocks are resident at once; in each phase they take the phase's virtual blocks (over all
+// members) from one ticket counter -- the device tile queue -- run the single-problem body on
+// them, and meet at a grid barrier before the next phase.  Ticket bookkeeping needs no reset:
+// every block draws exactly one ticket past the end of each phase, so the next phase's first
+// ticket is known to all.  Every wait is bounded: a block that polls the barrier more than
+// spin_limit times sets bit 0 of L.flag, and every block leaves at its next barrier (the
+// members' states are then partly advanced, and the host reports OSBLI_ETIMEOUT).
+// ------------------------------------------------------------------------------------------
+constexpr int ENS_PT = 256;   // persistent block size
+
+__device__ __forceinline__ bool ens_grid_barrier(const EnsLaunch &L, unsigned nblocks, unsigned &gen, int *sab)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned g = gen;
+        int ab = 0;
+        if (atomicAdd(L.bar, 1u) == nblocks - 1) {
+            atomicExch(L.bar, 0u);
+            __threadfence();
+            atomicAdd(L.bar + 1, 1u);        // release the next generation
+        } else {
+            long long it = 0;
+            while (atomicAdd(L.bar + 1, 0u) == g) {
+                if ((atomicAdd(L.flag, 0) & 1) || ++it > L.spin_limit) {
+                    atomicOr(L.flag, 1);
+                    ab = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (atomicAdd(L.flag, 0) & 1) ab = 1;
+        gen = g + 1;
+        __threadfence();
+        *sab = ab;
+    }
+    __syncthreads();
+    return *sab == 0;
+}
+
+// the problem of virtual block b of phase ph (prefix table st), staged in shared memory
+__device__ __forceinline__ EnsProb &ens_stage_v(const EnsProb *__restrict__ tab, const int *__restrict__ st,
+                                                int nprob, int ph, int b, unsigned char *raw, Blk &bk)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (st[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int *src = reinterpret_cast<const int *>(tab + lo);
+    int *dst = reinterpret_cast<int *>(raw);
+    for (int w = threadIdx.x; w < (int)(sizeof(EnsProb) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    EnsProb &e = *reinterpret_cast<EnsProb *>(raw);
+    const int local = b - st[lo];
+    const int gx = e.gp[ph][0], gy = e.gp[ph][1], gz = e.gp[ph][2];
+    bk = {local % gx, (local / gx) % gy, local / (gx * gy), gx, gy, gz};
+    return e;
+}
+
+template <int SCHEME>
+__device__ __forceinline__ void ens_update_stage(const Dev &P, const Bufs &B, const Blk &bk, int stage)
+{
+    const Strong none{nullptr, nullptr, nullptr, nullptr, 0};
+#define OSB_UP(S_)                                                                                      \
+    if (P.mixed) update_body<0, S_, false, false, float>(P, bk, B.U, B.dU, B.Rf, nullptr, B.M, B.R, B.err, strong_of(B)); \
+    else update_body<0, S_, false, false, double>(P, bk, B.U, B.dU, B.R, nullptr, B.M, B.R, B.err, none);
+    switch (stage) {
+    case 0: OSB_UP(0) break;
+    case 1: OSB_UP(1) break;
+    case 2: OSB_UP(2) break;
+    case 3: OSB_UP(3) break;
+    default: OSB_UP(4) break;
+    }
+#undef OSB_UP
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(ENS_PT) k_ens_persistent(EnsLaunch L, int nsteps)
+{
+    __shared__ __align__(16) unsigned char raw_[sizeof(EnsProb)];
+    __shared__ unsigned long long tk_;
+    __shared__ int sab_;
+    const unsigned G = gridDim.x;
+    const int np1 = L.nprob + 1;
+    const Thr2 th{(int)threadIdx.x & 31, (int)threadIdx.x >> 5, 32, ENS_PT / 32};
+    unsigned gen = 0;
+    unsigned long long base = 0;
+    for (int step = 0; step < nsteps; step++)
+        for (int stage = 0; stage < L.nstage; stage++)
+            for (int ph = 0; ph < ENS_NPH; ph++) {
+                const int total = L.ptotal[ph];
+                if (total == 0) continue;
+                for (;;) {
+                    if (threadIdx.x == 0) tk_ = atomicAdd(L.ticket, 1ull);
+                    __syncthreads();
+                    const unsigned long long t = tk_;
+                    __syncthreads();
+                    if (t >= base + (unsigned long long)total) break;
+                    Blk bk;
+                    EnsProb &e = ens_stage_v(L.tab, L.pstart + ph * np1, L.nprob, ph, (int)(t - base), raw_, bk);
+                    const Dev &P = e.P;
+                    const Bufs &B = e.B;
+                    if (ph <= ENS_G2) {
+                        const int d = ph - ENS_G0;
+                        ghost_body(P, bk, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
+                    } else if (ph == ENS_PRIM) {
+                        if (P.mixed) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
+                        else prim_body(P, bk, B.U, B.W);
+                    } else if (ph == ENS_LX) {
+                        conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), nullptr, B.Dl);
+                    } else if (ph == ENS_CX) {
+                        if (P.mixed) conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, B.Dl, e.acc[0]);
+                        else conv_char_body<0, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[0], e.chunk[0], th);
+                    } else if (ph == ENS_CY) {
+                        if (P.mixed) conv_char_delta_body<1, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[1], e.chunk[1], th);
+                        else conv_char_body<1, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[1], e.chunk[1], th);
+                    } else if (ph == ENS_CZ) {
+                        if (P.mixed) conv_char_delta_body<2, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[2], e.chunk[2], th);
+                        else conv_char_body<2, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[2], e.chunk[2], th);
+                    } else if (ph == ENS_FIX) {
+                        patch_fix_body<SCHEME>(P, bk, B.U, B.Uf, B.Wf, strong_of(B));
+                    } else {
+                        ens_update_stage<SCHEME>(P, B, bk, stage);
+                    }
+                    __syncthreads();   // raw_ is restaged for the next virtual block
+                }
+                base += (unsigned long long)total + G;
+                if (!ens_grid_barrier(L, G, gen, &sab_)) return;
+            }
+}
+
+template <int SCHEME>
+static int ens_persistent_t(const EnsLaunch &L, int nsteps, cudaStream_t s, int *grid_out)
+{
+    static int per_sm = -1;   // co-resident blocks per SM, one occupancy query per instantiation
+    if (per_sm < 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<SCHEME>, ENS_PT, 0) != cudaSuccess) n = 0;
+        per_sm = n;
+    }
+    if (per_sm < 1) return (int)cudaErrorCooperativeLaunchTooLarge;
+    grid_for(1, 1);   // fills g_num_sms
+    const int grid = per_sm * g_num_sms;
+    if (grid_out) *grid_out = grid;
+    cudaError_t e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.ticket, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return (int)e;
+    EnsLaunch Lc = L;
+    void *args[] = {&Lc, &nsteps};
+    return (int)cudaLaunchCooperativeKernel((const void *)k_ens_persistent<SCHEME>, dim3(grid), dim3(ENS_PT), args, 0, s);
+}
+
+int launch_ensemble_persistent(const EnsLaunch &L, int nsteps, cudaStream_t s, int *grid_out)
+{
+    if (L.scheme == SCH_WENO5JS) return ens_persistent_t<SCH_WENO5JS>(L, nsteps, s, grid_out);
+    if (L.scheme == SCH_WENO5Z) return ens_persistent_t<SCH_WENO5Z>(L, nsteps, s, grid_out);
+    if (L.scheme == SCH_TENO6) return ens_persistent_t<SCH_TENO6>(L, nsteps, s, grid_out);
+    return ens_persistent_t<SCH_TENO5>(L, nsteps, s, grid_out);
+}
+
+void ens_phase_grids_persistent(const Dev &P, const int chunk[3], int g[ENS_NPH][3])
+{
+    for (int ph = 0; ph < ENS_NPH; ph++) g[ph][0] = g[ph][1] = g[ph][2] = 0;
+    const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
+    auto cd = [](long long a, long long b) { return (int)((a + b - 1) / b); };
+    auto one = [&](int ph, int x, int y = 1, int z = 1) { g[ph][0] = x; g[ph][1] = y; g[ph][2] = z; };
+    for (int d = 0; d < 3; d++)
+        if (P.active[d]) one(ENS_G0 + d, cd(2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2], ENS_PT));
+    one(ENS_PRIM, cd(P.ntot, ENS_PT));
+    const int cph[3] = {ENS_CX, ENS_CY, ENS_CZ};
+    for (int d = 0; d < 3; d++) {
+        if (!P.active[d]) continue;
+        const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
+        if (P.mixed && d == 0) {
+            const int nseg = cd(P.n[0], XSEG);
+            one(ENS_LX, cd((long long)P.n[1] * P.n[2] * nseg, ENS_PT));
+            one(ENS_CX, P.n[1] * P.n[2], nseg);
+        } else {
+            one(cph[d], cd(P.n[da], 32), cd(P.n[db], ENS_PT / 32), cd(P.n[d], chunk[d]));
+        }
+    }
+    if (P.mixed) one(ENS_FIX, cd(N, ENS_PT * 8));
+    one(ENS_UP, cd(N, ENS_PT));
+}
 
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

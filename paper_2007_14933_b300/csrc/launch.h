@@ -71,6 +71,7 @@ struct EnsProb {
     Dev P;
     Bufs B;
     int g[ENS_NPH][3];   // the problem's local grid of each phase (0 blocks: phase skipped)
+    int gp[ENS_NPH][3];  // the same for the persistent kernel's 256-thread blocks
     int chunk[3];        // marching chunk of the line kernels per direction
     int acc[3];          // 1: the direction adds to the residual written by an earlier one
 };
@@ -80,9 +81,21 @@ struct EnsLaunch {
     int nprob = 0;
     int total[ENS_NPH] = {};           // blocks of each phase over all problems
     int mixed = 0, scheme = 0, nstage = 3;
+    // persistent form: one cooperative launch per call, virtual blocks from a ticket counter
+    const int *pstart = nullptr;       // device, [ENS_NPH][nprob + 1] prefix sums of the gp grids
+    int ptotal[ENS_NPH] = {};
+    unsigned *bar = nullptr;           // device: barrier arrivals, generation
+    unsigned long long *ticket = nullptr;   // device: the tile queue
+    int *flag = nullptr;               // device: bit 0 = a bounded wait gave up
+    long long spin_limit = 20000000;   // polls (each >= 64 ns) before a barrier wait gives up
 };
 // host side: local grid of every phase of one problem for the given line-kernel chunks
 void ens_phase_grids(const Dev &P, const int chunk[3], int g[ENS_NPH][3]);
+// the persistent kernel's grids: 256-thread blocks, marching passes as 32 x 8 thread tiles
+void ens_phase_grids_persistent(const Dev &P, const int chunk[3], int g[ENS_NPH][3]);
+// nsteps RK steps of every problem in one cooperative launch; returns the cudaError_t of the
+// launch (cudaErrorCooperativeLaunchTooLarge when the blocks cannot all be resident)
+int launch_ensemble_persistent(const EnsLaunch &L, int nsteps, cudaStream_t s, int *grid_out);
 int launch_ensemble_stage(const EnsLaunch &L, int stage, cudaStream_t s);
 // out = lowest member index whose error word has the non-finite bit, else -1; clears the words
 void launch_ensemble_errors(const EnsLaunch &L, int *out, cudaStream_t s);

@@ -35,7 +35,8 @@ EXPORTED = ["osbli_create", "osbli_destroy", "osbli_set_boundary_data", "osbli_s
             "osbli_domain_plan", "osbli_domain_create", "osbli_domain_destroy", "osbli_domain_set_state",
             "osbli_domain_get_state", "osbli_domain_set_boundary_data", "osbli_domain_step",
             "osbli_domain_residual", "osbli_domain_slabs", "osbli_domain_member",
-            "osbli_domain_launches_per_step", "osbli_domain_last_error"]
+            "osbli_domain_launches_per_step", "osbli_domain_last_error", "osbli_ensemble_set_persistent",
+            "osbli_ensemble_persistent_grid"]
 DOMAIN_MAX_SLABS = 64
 SENSOR_NPARAM = 5441
 SENSOR_NFEAT = 144
@@ -128,6 +129,10 @@ def load():
         L.osbli_ensemble_launches_per_step.argtypes = [vp]
         L.osbli_ensemble_points.argtypes = [vp]
         L.osbli_ensemble_points.restype = ctypes.c_longlong
+        L.osbli_ensemble_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+        L.osbli_ensemble_set_persistent.restype = ctypes.c_int
+        L.osbli_ensemble_persistent_grid.argtypes = [vp]
+        L.osbli_ensemble_persistent_grid.restype = ctypes.c_int
         L.osbli_ensemble_last_error.argtypes = [vp]
         L.osbli_ensemble_last_error.restype = ctypes.c_char_p
         for name in ("osbli_ensemble_create", "osbli_ensemble_set_state", "osbli_ensemble_get_state",
@@ -483,6 +488,13 @@ class Ensemble:
 
     def set_chunk(self, chunk):
         osbli_ensemble_set_chunk(self.e, chunk)
+
+    def set_persistent(self, on=True, spin_limit=0):
+        """One cooperative launch per step() call (on) or one graph per step (off)."""
+        _echeck(self.e, load().osbli_ensemble_set_persistent(self.e, int(bool(on)), int(spin_limit)))
+
+    def persistent_grid(self):
+        return load().osbli_ensemble_persistent_grid(self.e)
 
     def autotune(self, reps=3):
         return osbli_ensemble_autotune(self.e, reps)

@@ -105,5 +105,8 @@ def calibrate_threshold(w, feats, labels, recall=0.95):
     pos = probs[labels.bool()]
     if pos.numel() == 0:
         return 0.5
-    q = torch.quantile(pos.float().cpu()[:1000000], 1.0 - recall).item()
+    if pos.numel() > 1000000:   # an even sample over the whole set (torch.quantile's size limit)
+        idx = torch.linspace(0, pos.numel() - 1, 1000000, device=pos.device).long()
+        pos = pos[idx]
+    q = torch.quantile(pos.float().cpu(), 1.0 - recall).item()
     return float(min(max(q, 1e-4), 0.9999))

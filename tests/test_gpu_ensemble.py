@@ -152,3 +152,53 @@ def test_full_seed0_ensemble_steps_and_conserves():
         V = ens.get_state(p)
         assert np.isfinite(V).all(), p
         assert V[0].min() > 0.0, p
+
+
+@pytest.mark.parametrize("precision", [osbli.OSBLI_MIXED, osbli.OSBLI_FP64])
+@pytest.mark.parametrize("scheme", [I.TENO5, I.WENO5JS])
+def test_persistent_step_is_bitwise_the_graph_step(precision, scheme):
+    """One cooperative launch for all steps of all members (device tile queue, grid barriers)
+    gives bitwise the states of the per-phase graph form, and of several calls in a row."""
+    mem = small_members(scheme)
+    states = {}
+    for mode in (0, 1):
+        ens = osbli.Ensemble([c for c, _ in mem], precision=precision)
+        for p, (_, U) in enumerate(mem):
+            ens.set_state(p, U)
+        if mode:
+            ens.set_persistent(True)
+            ens.step(7)
+            ens.step(5)
+            assert ens.launches_per_step() == 1 and ens.persistent_grid() >= 148
+        else:
+            ens.step(12)
+        states[mode] = [ens.get_state(p) for p in range(len(mem))]
+        ens.close()
+    for a, b in zip(states[0], states[1]):
+        assert np.array_equal(a, b)
+
+
+def test_persistent_barrier_timeout_is_reported_and_the_context_stays_usable():
+    """A barrier wait limit of one poll makes the first barrier give up (the blocks cannot all
+    arrive that fast): the step returns ETIMEOUT without hanging, and the same ensemble then
+    steps correctly with the default limit."""
+    mem = small_members()
+    ens = osbli.Ensemble([c for c, _ in mem], precision=osbli.OSBLI_MIXED)
+    for p, (_, U) in enumerate(mem):
+        ens.set_state(p, U)
+    ens.set_persistent(True, spin_limit=1)
+    with pytest.raises(osbli.OsbliError) as e:
+        ens.step(3)
+    assert e.value.code == osbli.OSBLI_ETIMEOUT
+    ens.set_persistent(True)
+    for p, (_, U) in enumerate(mem):
+        ens.set_state(p, U)
+    ens.step(4)
+    ref = osbli.Ensemble([c for c, _ in mem], precision=osbli.OSBLI_MIXED)
+    for p, (_, U) in enumerate(mem):
+        ref.set_state(p, U)
+    ref.step(4)
+    for p in range(len(mem)):
+        assert np.array_equal(ens.get_state(p), ref.get_state(p))
+    ens.close()
+    ref.close()
