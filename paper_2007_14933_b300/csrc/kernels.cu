@@ -3061,8 +3061,11 @@ __device__ __forceinline__ void ens_update_stage(const Dev &P, const Bufs &B, co
 #undef OSB_UP
 }
 
-template <int SCHEME>
-__global__ void __launch_bounds__(ENS_PT) k_ens_persistent(EnsLaunch L, int nsteps)
+// MIXED: the members' precision as a template argument, so that each instantiation holds only
+// its own bodies: the mixed one (FP32 passes, the FP64 flux only inside the recompute call) fits
+// two blocks per SM, the FP64 one (FP64 characteristic flux inline) one.
+template <int SCHEME, bool MIXED>
+__global__ void __launch_bounds__(ENS_PT, MIXED ? 2 : 1) k_ens_persistent(EnsLaunch L, int nsteps)
 {
     __shared__ __align__(16) unsigned char raw_[sizeof(EnsProb)];
     __shared__ unsigned long long tk_;
@@ -3091,21 +3094,21 @@ __global__ void __launch_bounds__(ENS_PT) k_ens_persistent(EnsLaunch L, int nste
                         const int d = ph - ENS_G0;
                         ghost_body(P, bk, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
                     } else if (ph == ENS_PRIM) {
-                        if (P.mixed) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
+                        if constexpr (MIXED) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
                         else prim_body(P, bk, B.U, B.W);
                     } else if (ph == ENS_LX) {
-                        conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), nullptr, B.Dl);
+                        if constexpr (MIXED) conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), nullptr, B.Dl);
                     } else if (ph == ENS_CX) {
-                        if (P.mixed) conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, B.Dl, e.acc[0]);
+                        if constexpr (MIXED) conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, B.Dl, e.acc[0]);
                         else conv_char_body<0, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[0], e.chunk[0], th);
                     } else if (ph == ENS_CY) {
-                        if (P.mixed) conv_char_delta_body<1, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[1], e.chunk[1], th);
+                        if constexpr (MIXED) conv_char_delta_body<1, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[1], e.chunk[1], th);
                         else conv_char_body<1, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[1], e.chunk[1], th);
                     } else if (ph == ENS_CZ) {
-                        if (P.mixed) conv_char_delta_body<2, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[2], e.chunk[2], th);
+                        if constexpr (MIXED) conv_char_delta_body<2, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[2], e.chunk[2], th);
                         else conv_char_body<2, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[2], e.chunk[2], th);
                     } else if (ph == ENS_FIX) {
-                        patch_fix_body<SCHEME>(P, bk, B.U, B.Uf, B.Wf, strong_of(B));
+                        if constexpr (MIXED) patch_fix_body<SCHEME>(P, bk, B.U, B.Uf, B.Wf, strong_of(B));
                     } else {
                         ens_update_stage<SCHEME>(P, B, bk, stage);
                     }
@@ -3116,13 +3119,14 @@ __global__ void __launch_bounds__(ENS_PT) k_ens_persistent(EnsLaunch L, int nste
             }
 }
 
-template <int SCHEME>
+template <int SCHEME, bool MIXED>
 static int ens_persistent_t(const EnsLaunch &L, int nsteps, cudaStream_t s, int *grid_out)
 {
     static int per_sm = -1;   // co-resident blocks per SM, one occupancy query per instantiation
     if (per_sm < 0) {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<SCHEME>, ENS_PT, 0) != cudaSuccess) n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<SCHEME, MIXED>, ENS_PT, 0) != cudaSuccess)
+            n = 0;
         per_sm = n;
     }
     if (per_sm < 1) return (int)cudaErrorCooperativeLaunchTooLarge;
@@ -3135,15 +3139,23 @@ static int ens_persistent_t(const EnsLaunch &L, int nsteps, cudaStream_t s, int 
     if (e != cudaSuccess) return (int)e;
     EnsLaunch Lc = L;
     void *args[] = {&Lc, &nsteps};
-    return (int)cudaLaunchCooperativeKernel((const void *)k_ens_persistent<SCHEME>, dim3(grid), dim3(ENS_PT), args, 0, s);
+    return (int)cudaLaunchCooperativeKernel((const void *)k_ens_persistent<SCHEME, MIXED>, dim3(grid), dim3(ENS_PT), args,
+                                            0, s);
+}
+
+template <int SCHEME>
+static int ens_persistent_p(const EnsLaunch &L, int nsteps, cudaStream_t s, int *grid_out)
+{
+    return L.mixed ? ens_persistent_t<SCHEME, true>(L, nsteps, s, grid_out)
+                   : ens_persistent_t<SCHEME, false>(L, nsteps, s, grid_out);
 }
 
 int launch_ensemble_persistent(const EnsLaunch &L, int nsteps, cudaStream_t s, int *grid_out)
 {
-    if (L.scheme == SCH_WENO5JS) return ens_persistent_t<SCH_WENO5JS>(L, nsteps, s, grid_out);
-    if (L.scheme == SCH_WENO5Z) return ens_persistent_t<SCH_WENO5Z>(L, nsteps, s, grid_out);
-    if (L.scheme == SCH_TENO6) return ens_persistent_t<SCH_TENO6>(L, nsteps, s, grid_out);
-    return ens_persistent_t<SCH_TENO5>(L, nsteps, s, grid_out);
+    if (L.scheme == SCH_WENO5JS) return ens_persistent_p<SCH_WENO5JS>(L, nsteps, s, grid_out);
+    if (L.scheme == SCH_WENO5Z) return ens_persistent_p<SCH_WENO5Z>(L, nsteps, s, grid_out);
+    if (L.scheme == SCH_TENO6) return ens_persistent_p<SCH_TENO6>(L, nsteps, s, grid_out);
+    return ens_persistent_p<SCH_TENO5>(L, nsteps, s, grid_out);
 }
 
 void ens_phase_grids_persistent(const Dev &P, const int chunk[3], int g[ENS_NPH][3])
