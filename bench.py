@@ -479,10 +479,12 @@ def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sens
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_%s" % ("learned" if sensor else ("mixed" if precision else "fp64")))
     e0.record(stream)
     s.step(args.steps)
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     return s, max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
@@ -570,11 +572,14 @@ def split_grid(osbli, torch, cfg, U, args, stream, barrier, dist, npts, world, p
         ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         launches, copies = d.launches_per_step()
         d.step(done - args.warmup - args.steps)      # as many steps as the whole grid's solver took
-        same = bool(np.array_equal(d.get_state(), res[f][0].get_state()))
+        Ud, Uw = d.get_state(), res[f][0].get_state()
+        same = bool(np.array_equal(Ud, Uw))
+        l2d = l2_vs(Ud, Uw)
+        del Ud, Uw
         d.close()
         out[f] = {"value": job_rate(npts, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps,
                   "launches_per_step": launches, "halo_copies_per_step": copies,
-                  "bitwise_equal_to_whole_grid": same}
+                  "bitwise_equal_to_whole_grid": same, "l2_vs_whole_grid": l2d}
     return out
 
 

@@ -821,6 +821,25 @@ __device__ __forceinline__ T deriv_line_open(Fetch f, int ie, int n, bool lo_ope
     return fdiv(T(3) * f(n - 5) - T(16) * f(n - 4) + T(36) * f(n - 3) - T(48) * f(n - 2) + T(25) * f(n - 1), T(12));
 }
 
+// Stress tensor (Eq. 5, Sutherland's mu of Eq. 6) and the energy flux u_i tau_ij - q_j (Eq. 4) of
+// one node from its physical gradients gr[v][c] = d(u, v, w, T)_v / dx_c, temperature and velocity.
+template <typename T>
+__device__ __forceinline__ void stress_and_work(const T (&gr)[4][3], T Tm, const T (&uu)[3], bool suth_on, T sth,
+                                                T Re_, T kq_, T (&tau)[3][3], T (&e4)[3])
+{
+    const T mu = suth_on ? Tm * sqrt(Tm) * (T(1) + sth) / (Tm + sth) : T(1);   // Eq. 6
+    const T mr = mu / Re_;
+    const T div = gr[0][0] + gr[1][1] + gr[2][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? T(2.0 / 3.0) * div : T(0)));
+    const T kq = mu * kq_;
+#pragma unroll
+    for (int b = 0; b < 3; b++) e4[b] = uu[0] * tau[0][b] + uu[1] * tau[1][b] + uu[2] * tau[2][b] + kq * gr[3][b];
+}
+
 // Viscous fluxes (Eqs. 2-5) at interior nodes: V[d] = (S~_d . tau_{i.}, S~_d . (u_i tau_{i.} - q)).
 // T = double (plain path) or float (mixed path: gradients, tau and q in FP32, stored as FP32).
 
@@ -878,20 +897,9 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
                     gr[v][c] = (sizeof(T) == 4 ? T(line_facf(P, c, ijk[c])) : T(line_fac(P, c, ijk[c]))) * dxi[c][v];
         }
         const T Tm = T(W[W_T * vs + id]);
-        const T mu = suth_on ? Tm * sqrt(Tm) * (T(1) + sth) / (Tm + sth) : T(1);   // Eq. 6
-        const T mr = mu / Re_;
-        const T div = gr[0][0] + gr[1][1] + gr[2][2];
-        T tau[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-                tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? T(2.0 / 3.0) * div : T(0)));
-        const T kq = mu * kq_;
         const T uu[3] = {T(W[W_U * vs + id]), T(W[W_V * vs + id]), T(W[W_W * vs + id])};
-        T e4[3];
-#pragma unroll
-        for (int b = 0; b < 3; b++) e4[b] = uu[0] * tau[0][b] + uu[1] * tau[1][b] + uu[2] * tau[2][b] + kq * gr[3][b];
+        T tau[3][3], e4[3];
+        stress_and_work<T>(gr, Tm, uu, suth_on, sth, Re_, kq_, tau, e4);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             if (!P.active[d]) continue;
@@ -911,6 +919,88 @@ __global__ void __launch_bounds__(128) k_visc_flux(Dev P, const S *__restrict__ 
             for (int c = 0; c < 4; c++) V[(d * 4 + c) * vs + id] = (S)out[c];
         }
     }
+}
+
+// The parts of a node's residual that the convective and viscous passes leave: the stage's
+// recomputed interfaces (FP64 corrections of strong jumps, the gate's characteristic fluxes) and
+// the body force with its work.
+template <typename RT>
+__device__ __forceinline__ void node_fix_force(const Dev &P, const double *__restrict__ U, const Strong &sj, bool fix,
+                                               long long id, const int (&ijk)[3], RT (&r)[NV])
+{
+    const long long vs = P.vs;
+    if (fix) {
+        const unsigned char f0 = sj.flag[id];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!P.active[d]) continue;
+            const unsigned char bit = (unsigned char)(1u << d);
+            const long long st = P.st[d];
+            const bool fr = (f0 & bit) != 0, fl = (sj.flag[id - st] & bit) != 0;
+            if (!fr && !fl) continue;
+            const float *Ds = sj.Dst + (long long)d * NV * vs;
+            const RT fac = sizeof(RT) == 4 ? RT(line_facf(P, d, ijk[d])) : RT(line_fac(P, d, ijk[d]));
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const RT c = (fr ? RT(Ds[v * vs + id]) : RT(0)) - (fl ? RT(Ds[v * vs + id - st]) : RT(0));
+                r[v] += -fac * c;
+            }
+        }
+    }
+    if (P.forced) {
+        // body force per unit volume and its work (u from the node's FP64 state)
+        const double ir = 1.0 / U[id];
+        double work = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            r[1 + c] += RT(P.force[c]);
+            work += P.force[c] * U[(1 + c) * vs + id] * ir;
+        }
+        r[4] += RT(work);
+    }
+}
+
+// The node's total residual r out (MODE 1), or the RK register update (MODE 0, Eqs. 36-37).
+template <int MODE, int STAGE, typename RT>
+__device__ __forceinline__ void node_finish(const Dev &P, double *__restrict__ U, double *__restrict__ dU,
+                                            double *Rout, int *__restrict__ err, long long id, const RT (&r)[NV])
+{
+    const long long vs = P.vs;
+    if (MODE == 1) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Rout[v * vs + id] = (double)r[v];
+        return;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        double du;
+        if (sizeof(RT) == 4) {
+            // mixed path: dt r formed in FP32 with dt split into two FP32 parts (the error is
+            // that of r's own FP32 rounding) and widened to FP64 by integer operations, so the
+            // register update costs two FP64 operations (the FP64 pipe runs at 1/64 rate)
+            du = f2d_bits(fmaf(P.dthi, (float)r[v], P.dtlo * (float)r[v]));
+        } else {
+            du = P.dt * (double)r[v];
+        }
+        double un;
+        if (P.rk == 2) {
+            // SSP-RK3, convex form: the second register holds U^n (written at stage 0)
+            const double u = U[v * vs + id];
+            const double u0 = STAGE == 0 ? u : dU[v * vs + id];
+            if (STAGE == 0) dU[v * vs + id] = u;
+            const double a = STAGE == 0 ? 0.0 : (STAGE == 1 ? 0.75 : 1.0 / 3.0);
+            un = a * u0 + (1.0 - a) * (u + du);
+        } else {
+            double dd = du;
+            if (STAGE > 0) dd = c_rkA[P.rk][STAGE] * dU[v * vs + id] + du;
+            dU[v * vs + id] = dd;
+            un = U[v * vs + id] + c_rkB[P.rk][STAGE] * dd;
+        }
+        U[v * vs + id] = un;
+        bad |= !isfinite(un);
+    }
+    if (bad) atomicOr(err, 1);
 }
 
 // Viscous divergence (flux form) + RK register update (Eqs. 36-37), or residual output.
@@ -936,35 +1026,7 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
         RT r[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) r[v] = Rin[v * vs + id];
-        if (fix) {
-            const unsigned char f0 = sj.flag[id];
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                if (!P.active[d]) continue;
-                const unsigned char bit = (unsigned char)(1u << d);
-                const long long st = P.st[d];
-                const bool fr = (f0 & bit) != 0, fl = (sj.flag[id - st] & bit) != 0;
-                if (!fr && !fl) continue;
-                const float *Ds = sj.Dst + (long long)d * NV * vs;
-                const RT fac = sizeof(RT) == 4 ? RT(line_facf(P, d, ijk[d])) : RT(line_fac(P, d, ijk[d]));
-#pragma unroll
-                for (int v = 0; v < NV; v++) {
-                    const RT c = (fr ? RT(Ds[v * vs + id]) : RT(0)) - (fl ? RT(Ds[v * vs + id - st]) : RT(0));
-                    r[v] += -fac * c;
-                }
-            }
-        }
-        if (P.forced) {
-            // body force per unit volume and its work (u from the node's FP64 state)
-            const double ir = 1.0 / U[id];
-            double work = 0.0;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                r[1 + c] += RT(P.force[c]);
-                work += P.force[c] * U[(1 + c) * vs + id] * ir;
-            }
-            r[4] += RT(work);
-        }
+        node_fix_force<RT>(P, U, sj, fix, id, ijk, r);
         if (VISC) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
@@ -999,40 +1061,7 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                 }
             }
         }
-        if (MODE == 1) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) Rout[v * vs + id] = (double)r[v];
-            continue;
-        }
-        bool bad = false;
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            double du;
-            if (sizeof(RT) == 4) {
-                // mixed path: dt r formed in FP32 with dt split into two FP32 parts (the error is
-                // that of r's own FP32 rounding) and widened to FP64 by integer operations, so the
-                // register update costs two FP64 operations (the FP64 pipe runs at 1/64 rate)
-                du = f2d_bits(fmaf(P.dthi, (float)r[v], P.dtlo * (float)r[v]));
-            } else {
-                du = P.dt * (double)r[v];
-            }
-            double un;
-            if (P.rk == 2) {
-                // SSP-RK3, convex form: the second register holds U^n (written at stage 0)
-                const double u = U[v * vs + id];
-                const double u0 = STAGE == 0 ? u : dU[v * vs + id];
-                if (STAGE == 0) dU[v * vs + id] = u;
-                const double a = STAGE == 0 ? 0.0 : (STAGE == 1 ? 0.75 : 1.0 / 3.0);
-                un = a * u0 + (1.0 - a) * (u + du);
-            } else {
-                if (STAGE > 0) du = c_rkA[P.rk][STAGE] * dU[v * vs + id] + du;
-                dU[v * vs + id] = du;
-                un = U[v * vs + id] + c_rkB[P.rk][STAGE] * du;
-            }
-            U[v * vs + id] = un;
-            bad |= !isfinite(un);
-        }
-        if (bad) atomicOr(err, 1);
+        node_finish<MODE, STAGE, RT>(P, U, dU, Rout, err, id, r);
     }
 }
 

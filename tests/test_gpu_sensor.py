@@ -3,8 +3,8 @@
 Bars: BF16 features within one BF16 rounding of the FP64 features; labels identical to the
 oracle's (ambiguous cut-offs within 1e-9 of C_T excepted); MLP gradients within 2e-2 (relative
 2-norm per parameter block) of the FP64 gradient taken with BF16-rounded inputs and weights;
-probabilities within 2e-2.  Gain: the trained gate sends most interfaces to the central flux
-and stays close to full TENO.
+probabilities within 2e-2.  Gain, against the oracle's FP64 TENO5: on the TGV the gated form is
+closer to it than central fluxes everywhere; on Sod the shock stays within one cell of it.
 """
 import numpy as np
 import pytest
@@ -118,18 +118,30 @@ def test_probs_match_oracle_and_training_lowers_loss(torch):
     assert np.abs(p.ravel() - po).max() <= 2e-2
 
 
-def test_learned_gate_gain_over_full_teno(torch):
-    """Train on 48^3 TGV snapshots, then run 64^3 from the analytic field: the gate keeps the
-    characteristic flux on a minority of cells while the state stays close to the full-TENO
-    (mixed) result; gating nothing (central everywhere but at strong jumps) drifts further."""
+def _l2_vs(Ua, Ub):
+    nb = [np.linalg.norm(Ub[v]) for v in range(5)]
+    nb[1] = nb[2] = nb[3] = max(nb[1:4])
+    return float(max(np.linalg.norm(Ua[v] - Ub[v]) / nb[v] for v in range(5) if nb[v] > 0))
+
+
+def test_learned_gate_gain_against_the_oracle(torch):
+    """Train on 48^3 TGV snapshots, then run 64^3 from the analytic field for 40 steps: against the
+    oracle's FP64 TENO5 state, the learned gate (characteristic flux on a minority of cells) stays
+    within 2e-4 in L2 and closer than gating nothing (central flux everywhere but at strong
+    jumps): measured 1.4e-4 with 36 % of the cells gated against 2.3e-4 ungated.  On this coarse
+    grid the difference between the central and the TENO5 fluxes of smooth regions is itself of
+    that size, so the sensor's gain is a fraction of it, not orders of magnitude."""
+    import os
+    O.set_threads(len(os.sched_getaffinity(0)))
     feats, labels, _ = SN.tgv_training_set(N=48, nsnap=6, steps_between=12)
-    w, _ = SN.train(feats, labels, steps=800, batch=4096)
+    w, _ = SN.train(feats, labels, steps=1500, batch=4096)
+    thr = SN.calibrate_threshold(w, feats, labels, recall=0.9)
     cfg, U = I.tgv(64, Ma=1.25, scheme=I.TENO5)
     steps = 40
-    base = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
-    base.set_state(U)
-    base.step(steps)
-    Ut = base.get_state()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(steps)
+    Uo = o.get_state()
 
     def hybrid(threshold):
         hyb = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
@@ -137,15 +149,48 @@ def test_learned_gate_gain_over_full_teno(torch):
         hyb.set_sensor(w, threshold)
         hyb.step(steps)
         Uh = hyb.get_state()
-        l2 = max(np.linalg.norm(Uh[v] - Ut[v]) / np.linalg.norm(Ut[v]) for v in range(5))
-        return l2, hyb.diagnostics()[9], Uh
+        frac = hyb.diagnostics()[9]
+        hyb.close()
+        return _l2_vs(Uh, Uo), frac, Uh
 
-    thr = SN.calibrate_threshold(w, feats, labels, recall=0.9)
     l2, frac, Uh = hybrid(thr)
     l2_none, frac_none, _ = hybrid(0.999999)
-    print("learned gate: threshold %.3f gated fraction %.3f, L2 vs full TENO %.2e; no gate: %.3f, %.2e"
+    print("learned gate: threshold %.3f gated fraction %.3f, L2 vs oracle %.2e; no gate: %.3f, %.2e"
           % (thr, frac, l2, frac_none, l2_none))
     assert np.isfinite(Uh).all()
-    assert frac < 0.7
-    assert l2 < 5e-3
-    assert l2 < l2_none
+    assert frac < 0.5
+    assert l2 <= 2e-4
+    assert l2 <= 0.8 * l2_none
+
+
+def test_learned_gate_on_sod_keeps_the_shock_within_a_cell(torch):
+    """Sod (TENO5, 400 cells, 800 steps): the sensor trained on TENO cut-off labels of the GPU's
+    own TENO5 run of the tube flags a minority of cells, and the learned form's shock stays within
+    one cell of the oracle's FP64 TENO5 shock, the contact within two."""
+    cfg, U, x = I.sod(scheme=I.TENO5)
+    feats, labels = SN.collect_at(cfg, U, [100, 200, 300, 400, 500, 600, 700, 800])
+    w, _ = SN.train(feats, labels, steps=1500, batch=1024)
+    thr = SN.calibrate_threshold(w, feats, labels, recall=0.95)
+    hyb = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    hyb.set_state(U)
+    hyb.set_sensor(w, thr)
+    hyb.step(800)
+    Uh = hyb.get_state()
+    frac = hyb.diagnostics()[9]
+    hyb.close()
+    o = O.Oracle(cfg)
+    o.set_state(U)
+    o.step(800)
+    Uo = o.get_state()
+    rg, ro = Uh[0, 0, 0], Uo[0, 0, 0]
+
+    def crossing(r, level):
+        return x[np.where((r[:-1] >= level) & (r[1:] < level))[0][-1]]
+    shock = 0.5 * (0.26557 + 0.125)          # between the post-shock and right densities
+    contact = 0.5 * (0.42632 + 0.26557)      # between the two sides of the contact
+    print("Sod learned gate: gated fraction %.3f, shock %.4f vs %.4f, L2 %.2e"
+          % (frac, crossing(rg, shock), crossing(ro, shock), _l2_vs(Uh, Uo)))
+    assert frac < 0.5
+    assert abs(crossing(rg, shock) - crossing(ro, shock)) <= 1.0 / 400 + 1e-12
+    assert abs(crossing(rg, contact) - crossing(ro, contact)) <= 2.0 / 400 + 1e-12
+    assert _l2_vs(Uh, Uo) <= 1e-2
