@@ -2349,14 +2349,16 @@ __global__ void __launch_bounds__(CMP_T) k_flag_count(Dev P, const unsigned char
     }
 }
 
-// one block of 1024 threads: exclusive scan of each direction's block counts, totals to count[]
+// one block of 1024 threads per direction (blockIdx.x): exclusive scan of the direction's block
+// counts, its total to count[d]
 __global__ void __launch_bounds__(1024) k_flag_scan(const int *__restrict__ bcnt, int *__restrict__ boff,
                                                     int nblk, int *__restrict__ count)
 {
     __shared__ int swarp[32];
     __shared__ int carry;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = 0; d < 3; d++) {
+    {
+        const int d = blockIdx.x;
         if (threadIdx.x == 0) carry = 0;
         __syncthreads();
         for (int b0 = 0; b0 < nblk; b0 += 1024) {
@@ -2392,7 +2394,7 @@ __global__ void __launch_bounds__(1024) k_flag_scan(const int *__restrict__ bcnt
 }
 
 __global__ void __launch_bounds__(CMP_T) k_flag_write(Dev P, const unsigned char *__restrict__ flag,
-                                                      const int *__restrict__ boff, int nblk,
+                                                      const int *__restrict__ bcnt, const int *__restrict__ boff, int nblk,
                                                       long long *__restrict__ list, int cap)
 {
     __shared__ int swarp[3][CMP_T / 32];
@@ -2402,6 +2404,8 @@ __global__ void __launch_bounds__(CMP_T) k_flag_write(Dev P, const unsigned char
     int run[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) run[d] = boff[d * nblk + blockIdx.x];
+    // a block whose nodes hold no flag writes nothing (the common case where the gate is sparse)
+    if ((bcnt[blockIdx.x] | bcnt[nblk + blockIdx.x] | bcnt[2 * nblk + blockIdx.x]) == 0) return;
     for (int q = 0; q < CMP_PER; q++) {
         const long long t = c0 + q * CMP_T + threadIdx.x;
         const unsigned f = t < P.ntot ? flag[t] : 0u;
@@ -2435,8 +2439,8 @@ static int launch_compact(const Dev &P, const Bufs &B, cudaStream_t s)
     const int nblk = compact_blocks(P);
     int *bcnt = B.cmp, *boff = B.cmp + 3 * nblk;
     k_flag_count<<<nblk, CMP_T, 0, s>>>(P, B.flag, bcnt, nblk);
-    k_flag_scan<<<1, 1024, 0, s>>>(bcnt, boff, nblk, B.err + 1);
-    k_flag_write<<<nblk, CMP_T, 0, s>>>(P, B.flag, boff, nblk, B.slist, B.scap);
+    k_flag_scan<<<3, 1024, 0, s>>>(bcnt, boff, nblk, B.err + 1);
+    k_flag_write<<<nblk, CMP_T, 0, s>>>(P, B.flag, bcnt, boff, nblk, B.slist, B.scap);
     return 3;
 }
 

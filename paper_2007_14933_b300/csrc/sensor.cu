@@ -262,43 +262,12 @@ __device__ __forceinline__ void cpa4(float *smem, const float *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-__device__ __forceinline__ void cpa8(float *smem, const float *gmem)
-{
-    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
 // stage y-plane jy (clamped to 0 when y is inactive) of the column (x0, k) into ring slot `slot`
 __device__ __forceinline__ void stage_plane(const Dev &P, const float *__restrict__ Uf, const float *__restrict__ Wf,
                                             float *ring, int slot, int x0, int jy, int k, int lane)
 {
     if (!P.active[1]) jy = 0;
     float *dst = ring + slot * PLANE;
-    if (P.active[0] && (P.np[0] & 1) == 0) {
-        // x rows of even length: the staged positions (2m, 2m + 1), nodes x0 - 1 + 2m and x0 + 2m,
-        // sit at an even offset of an even-pitch row, so each pair is one 8-byte copy (half the
-        // copies of single words); a pair reaching past the first ghost node takes the clamped
-        // single-word copies below
-        const float *src[5] = {Uf, Wf + W_U * P.vs, Wf + W_V * P.vs, Wf + W_W * P.vs, Wf + W_P * P.vs};
-        for (int c = lane; c < (SQS / 2) * 15; c += 32) {
-            const int m = c % (SQS / 2), rq = c / (SQS / 2);
-            const int dkr = rq / 5, q = rq % 5;
-            const int dk = P.active[2] ? dkr - 1 : 0;
-            const int pos = 2 * m;
-            float *d = dst + rq * SQS + pos;
-            if (x0 + pos <= P.n[0]) {
-                cpa8(d, src[q] + node_index(P, x0 + pos - 1, jy, k + dk));
-            } else {
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    int dx = pos + h - 1;
-                    if (x0 + dx > P.n[0]) dx = P.n[0] - x0;     // past the first ghost: unused
-                    cpa4(d + h, src[q] + node_index(P, x0 + dx, jy, k + dk));
-                }
-            }
-        }
-        return;
-    }
     for (int pos = lane; pos < SQS; pos += 32) {
         int dx = pos - 1;
         if (!P.active[0]) dx = 0;
