@@ -466,7 +466,7 @@ def run_ensemble(args, world, rank, local):
     return 0
 
 
-def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sensor=None):
+def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sensor=None, tag=""):
     """Warm up, then time args.steps RK steps of one form with CUDA events on its stream."""
     s = osbli.Solver(dict(cfg, sensor=1 if sensor else 0), precision=precision,
                      cuda_stream=stream.cuda_stream)
@@ -479,7 +479,7 @@ def time_form(osbli, torch, cfg, U, precision, args, stream, barrier, dist, sens
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed_%s" % ("learned" if sensor else ("mixed" if precision else "fp64")))
+    torch.cuda.nvtx.range_push("timed%s_%s" % (tag, "learned" if sensor else ("mixed" if precision else "fp64")))
     e0.record(stream)
     s.step(args.steps)
     e1.record(stream)
@@ -538,7 +538,7 @@ def shocked_phase(osbli, torch, cfg, U, sensor, args, stream, barrier, dist, npt
     g.close()
     del probs, flagged, pos
     res = {f: time_form(osbli, torch, cfg, Us, prec[f], args, stream, barrier, dist,
-                        sensor if f == "learned" else None) for f in ("learned", "mixed", "fp64")}
+                        sensor if f == "learned" else None, tag="_shocklet") for f in ("learned", "mixed", "fp64")}
     dg = res["learned"][0].diagnostics()
     prof = res["learned"][0].profile_residual(reps=2)
     out = {"t_start": done * cfg["dt"], "steps_advanced": done, "label_fraction": lab_frac,
@@ -556,7 +556,8 @@ def shocked_phase(osbli, torch, cfg, U, sensor, args, stream, barrier, dist, npt
     # flux, closer to the FP64 result, at its cost
     thr2 = SN_threshold(sensor, 0.99)
     if thr2 is not None:
-        s2, ms2 = time_form(osbli, torch, cfg, Us, prec["learned"], args, stream, barrier, dist, (sensor[0], thr2))
+        s2, ms2 = time_form(osbli, torch, cfg, Us, prec["learned"], args, stream, barrier, dist, (sensor[0], thr2),
+                            tag="_shocklet_strict")
         dg2 = s2.diagnostics()
         out["stricter_gate"] = {"threshold": thr2, "recall_target": 0.99, "gated_cells": float(dg2[9]),
                                 "value": job_rate(npts, args.steps, world, ms2 / 1e3),
