@@ -2218,15 +2218,31 @@ __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *
 // the D the convective pass used.  PART 0 does both kinds; PART 1 only the FP32 ones and PART 2
 // only the FP64 ones (split so that the FP32 kernel keeps the register budget of the FP32
 // arithmetic: the FP64 flux is a call whose registers a caller has to reserve).
+// PART 3 is PART 2 after a PART 1 pass, which marked the strong jumps it skipped (bit 3 + DIR of the
+// interface's flag byte): one byte read per listed interface instead of the jump test's twelve.
 template <int DIR, int SCHEME, int PART = 0>
 __device__ __noinline__ void fix_interface(const Dev &P, const double *__restrict__ U,
                                            const float *__restrict__ Uf, const float *__restrict__ Wf,
-                                           float *__restrict__ Dst, long long m)
+                                           float *__restrict__ Dst, unsigned char *flag, long long m)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
     const long long st = P.st[DIR];
-    const bool strong = strong_jump(P, Uf, Wf, m, st);
-    if ((PART == 1 && strong) || (PART == 2 && !strong)) return;
+    bool strong;
+    if constexpr (PART == 3) {
+        strong = (flag[m] >> (3 + DIR)) & 1u;
+        if (!strong) return;
+    } else {
+        strong = strong_jump(P, Uf, Wf, m, st);
+    }
+    if constexpr (PART == 1) {
+        if (strong) {
+            // mark it for the FP64 half; the byte also holds other directions' bits, hence a word atomic
+            const unsigned long long a = (unsigned long long)(flag + m);
+            atomicOr(reinterpret_cast<unsigned int *>(a & ~3ull), (8u << DIR) << (8u * (unsigned)(a & 3ull)));
+            return;
+        }
+    }
+    if (PART == 2 && !strong) return;
     int c3[3];
     split_node(P, m, c3);
     const double es = line_eps<DIR>(P, c3[DA], c3[DB]);
@@ -2257,9 +2273,9 @@ __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, cons
     const long long stride = (long long)bk.nx * blockDim.x;
     const long long t0 = bk.x * (long long)blockDim.x + threadIdx.x;
     for (long long t = t0; t < (long long)l0 + l1 + l2; t += stride) {
-        if (t < l0) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.list[t]);
-        else if (t < l0 + l1) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.list[(long long)sj.cap + (t - l0)]);
-        else fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.list[2LL * sj.cap + (t - l0 - l1)]);
+        if (t < l0) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, sj.list[t]);
+        else if (t < l0 + l1) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, sj.list[(long long)sj.cap + (t - l0)]);
+        else fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, sj.list[2LL * sj.cap + (t - l0 - l1)]);
     }
     if (c0 <= sj.cap && c1 <= sj.cap && c2 <= sj.cap) return;
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -2270,16 +2286,16 @@ __device__ __forceinline__ void patch_fix_body(const Dev &P, const Blk &bk, cons
         const long long id = node_index(P, ijk[0], ijk[1], ijk[2]);
         const unsigned char f = sj.flag[id];
         if (c0 > sj.cap) {
-            if (f & 1) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id);
-            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id - P.st[0]);
+            if (f & 1) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, id);
+            if (ijk[0] == 0 && (sj.flag[id - P.st[0]] & 1)) fix_interface<0, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, id - P.st[0]);
         }
         if (c1 > sj.cap) {
-            if (f & 2) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id);
-            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id - P.st[1]);
+            if (f & 2) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, id);
+            if (ijk[1] == 0 && (sj.flag[id - P.st[1]] & 2)) fix_interface<1, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, id - P.st[1]);
         }
         if (c2 > sj.cap) {
-            if (f & 4) fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id);
-            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, id - P.st[2]);
+            if (f & 4) fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, id);
+            if (ijk[2] == 0 && (sj.flag[id - P.st[2]] & 4)) fix_interface<2, SCHEME, PART>(P, U, Uf, Wf, sj.Dst, sj.flag, id - P.st[2]);
         }
     }
 }
@@ -2293,11 +2309,11 @@ __global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restri
 
 // the two halves of k_patch_fix for single problems: the FP64 recomputation of the strong-jump
 // interfaces, and the FP32 one of the others at the register budget of k_conv_char_delta
-template <int SCHEME>
+template <int SCHEME, int PART>
 __global__ void __launch_bounds__(128) k_patch_fp64(Dev P, const double *__restrict__ U, const float *__restrict__ Uf,
                                                     const float *__restrict__ Wf, Strong sj)
 {
-    patch_fix_body<SCHEME, 2>(P, self_blk(), U, Uf, Wf, sj);
+    patch_fix_body<SCHEME, PART>(P, self_blk(), U, Uf, Wf, sj);
 }
 
 template <int SCHEME>
@@ -2725,8 +2741,12 @@ static void launch_patch_t(const Dev &P, const Bufs &B, cudaStream_t s)
 {
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     const int g = grid_for(N, 128);
-    k_patch_fp64<SCHEME><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
-    if (P.sensor) k_patch_fp32<SCHEME><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    if (P.sensor) {   // FP32 half first: it marks the strong jumps the FP64 half then takes
+        k_patch_fp32<SCHEME><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+        k_patch_fp64<SCHEME, 3><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    } else {
+        k_patch_fp64<SCHEME, 2><<<g, 128, 0, s>>>(P, B.U, B.Uf, B.Wf, strong_of(B));
+    }
 }
 
 // the stage's recorded interfaces (without the learned gate every recorded one is a strong jump,
