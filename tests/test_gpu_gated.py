@@ -163,3 +163,18 @@ def test_gate_mode_switches_back_to_the_network():
     s.step(1)
     assert s.diagnostics()[9] > 0.99
     s.close()
+
+
+def test_set_gate_needs_a_sensor_handle():
+    cfg, U = I.tgv(n=(12, 10, 8), Ma=1.25, scheme=I.TENO5)
+    s = osbli.Solver(cfg, precision=osbli.OSBLI_MIXED)
+    with pytest.raises(osbli.OsbliError) as e:
+        s.set_gate(np.ones(U.shape[1:], np.uint8))
+    assert e.value.code == osbli.OSBLI_EINVAL
+    s.close()
+    g = osbli.Solver(dict(cfg, sensor=1), precision=osbli.OSBLI_MIXED)
+    g.set_state(U)
+    with pytest.raises(osbli.OsbliError) as e:      # neither weights nor a mask installed yet
+        g.step(1)
+    assert e.value.code == osbli.OSBLI_ESTATE
+    g.close()
