@@ -338,8 +338,12 @@ struct SrcFromState {
 // U_k and the contravariant flux F_k of the six stencil nodes, LLF split with
 // alpha_j = max_k |lambda_j(k)|, WENO/TENO reconstruction of g+ and g-, back-projection.
 // The left eigenvectors are applied in factored form (l_j . w built from u.w, n.w, t.w).
-// T is the arithmetic type (double: plain FP64 path; float: mixed path).
-template <int DIR, int SCHEME, bool CURV, typename T, typename Src, bool LABEL = false>
+// T is the arithmetic type (double: plain FP64 path; float: mixed path).  DELTA32 (with T double,
+// the mixed path across a strong jump): the Roe state, eigenvectors, projections, splitting and
+// back-projection in FP64, the reconstruction in FP32 on the split values relative to node m (the
+// reconstruction is affine, so g = recon(g - g_m) + g_m, and g_m+ + g_m- back-projects to F_m);
+// Fh then receives the flux relative to node m, F_{m+1/2} - F_m.
+template <int DIR, int SCHEME, bool CURV, typename T, typename Src, bool LABEL = false, bool DELTA32 = false>
 __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const double *__restrict__ M,
                                                long long m, long long st, T es, T Fh[NV], bool *label = nullptr)
 {
@@ -474,6 +478,16 @@ __device__ __forceinline__ void interface_flux(const Dev &P, const Src &q, const
             g[j] = vp + vm;
             *label = *label || cut_matters(gp[j][0], gp[j][1], gp[j][2], gp[j][3], gp[j][4], vp, kp, floor_) ||
                      cut_matters(gm[j][4], gm[j][3], gm[j][2], gm[j][1], gm[j][0], vm, km, floor_);
+        } else if constexpr (DELTA32) {
+            // node m is stencil position 2 of g+ and position NS - 4 of g- (nodes m-2.. / ..m+3)
+            float dp[NS], dm[NS];
+            const T rp = gp[j][2], rm = gm[j][NS - 4];
+#pragma unroll
+            for (int k = 0; k < NS; k++) {
+                dp[k] = float(gp[j][k] - rp);
+                dm[k] = float(gm[j][k] - rm);
+            }
+            g[j] = T(recon_pair<SCHEME, float, NS>(dp, dm, float(ct), float(es)));
         } else {
             g[j] = recon_pair<SCHEME, T, NS>(gp[j], gm[j], ct, es);
         }
@@ -1277,18 +1291,21 @@ __device__ __forceinline__ void node_flux_fp64(const Dev &P, const double *__res
     F[4] = (E + p) * un;
 }
 
+// Across a strong jump: the Roe state, eigenvectors and projections in FP64 (where the jump makes
+// them ill-conditioned in FP32), the reconstruction and weights in FP32 on values relative to node
+// m (interface_flux with DELTA32).
 template <int DIR, int SCHEME>
 __device__ __noinline__ void fallback_delta(const Dev &P, const double *__restrict__ U, long long m,
                                             long long st, double es, float *D, float *dF1)
 {
     const SrcFromState q{U, P.vs, P.gamma, P.gm1};
-    double Fh[NV], Fm_[NV], Fl[NV];
-    interface_flux<DIR, SCHEME, false, double>(P, q, nullptr, m, st, es, Fh);
+    double Dh[NV], Fm_[NV], Fl[NV];
+    interface_flux<DIR, SCHEME, false, double, SrcFromState, false, true>(P, q, nullptr, m, st, es, Dh);
     node_flux_fp64<DIR>(P, U, m, Fm_);
     node_flux_fp64<DIR>(P, U, m - st, Fl);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-        D[v] = (float)(Fh[v] - Fm_[v]);
+        D[v] = (float)Dh[v];
         dF1[v] = (float)(Fl[v] - Fm_[v]);
     }
 }
