@@ -1300,9 +1300,17 @@ __device__ __noinline__ void fallback_delta(const Dev &P, const double *__restri
 {
     const SrcFromState q{U, P.vs, P.gamma, P.gm1};
     double Dh[NV], Fm_[NV], Fl[NV];
-    interface_flux<DIR, SCHEME, false, double, SrcFromState, false, true>(P, q, nullptr, m, st, es, Dh);
     node_flux_fp64<DIR>(P, U, m, Fm_);
     node_flux_fp64<DIR>(P, U, m - st, Fl);
+    if constexpr (SCHEME == SCH_TENO6) {
+        // TENO6 keeps its reconstruction in FP64 too: with all four stencils kept it adds no
+        // dissipation, so FP32 cut-off decisions at the jump would not be damped away
+        interface_flux<DIR, SCHEME, false, double>(P, q, nullptr, m, st, es, Dh);
+#pragma unroll
+        for (int v = 0; v < NV; v++) Dh[v] -= Fm_[v];
+    } else {
+        interface_flux<DIR, SCHEME, false, double, SrcFromState, false, true>(P, q, nullptr, m, st, es, Dh);
+    }
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         D[v] = (float)Dh[v];
