@@ -2335,7 +2335,7 @@ __global__ void __launch_bounds__(128) k_patch_fix(Dev P, const double *__restri
 // the two halves of k_patch_fix for single problems: the FP64 recomputation of the strong-jump
 // interfaces, and the FP32 one of the others at the register budget of k_conv_char_delta
 template <int SCHEME, int PART>
-__global__ void __launch_bounds__(128) k_patch_fp64(Dev P, const double *__restrict__ U, const float *__restrict__ Uf,
+__global__ void __launch_bounds__(128, 3) k_patch_fp64(Dev P, const double *__restrict__ U, const float *__restrict__ Uf,
                                                     const float *__restrict__ Wf, Strong sj)
 {
     patch_fix_body<SCHEME, PART>(P, self_blk(), U, Uf, Wf, sj);
