@@ -1568,16 +1568,20 @@ __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *
     conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, accumulate, chunk, self_thr2());
 }
 
-// Gated y / z passes (learned sensor on): most interfaces take the central flux, which needs
-// nodes m-1 .. m+2 only.  Each thread keeps those four nodes' FP32 data (hi, lo, u, v, w, p) in
-// registers as it marches, with the pressure and density of m-2 and m+3 for the strong-jump
-// test and the next node prefetched, so every node is loaded once per line instead of once per
-// interface that reads it.  Every interface gets the central D here; an interface that needs the
-// characteristic flux (gate or strong jump) is flagged (flag bit, its central D in Dst); after
-// the passes the flags are compacted into per-direction lists in node order (k_flag_*), and
-// k_patch_fix replaces each listed interface (FP32 characteristic flux, or FP64 across a strong
-// jump), the update adding the difference.  The arithmetic of every interface is that of
-// k_conv_char_delta.
+// Gated passes (learned sensor on): most interfaces take the central flux.  With one flux
+// difference per interface, G_{m+1/2} = F_{m+1} - F_m (formed relative to node m by the product
+// rule), the central interface flux in delta form and the node's flux difference are
+//   D_{m+1/2} = F_{m+1/2} - F_m = (6 G_{m+1/2} + G_{m-1/2} - G_{m+3/2}) / 12,
+//   F_{m+1/2} - F_{m-1/2} = (7 (G_{m+1/2} + G_{m-1/2}) - (G_{m+3/2} + G_{m-3/2})) / 12,
+// the 4th-order central flux [7 (F_m + F_{m+1}) - (F_{m-1} + F_{m+2})] / 12 and its difference
+// written in differences of neighbours: one product-rule difference per interface and direction
+// instead of three per node (F_{m-1}, F_{m+1} and F_{m+2} each relative to F_m).  Every interface
+// gets the central D here; an interface that needs the characteristic flux (gate on either side
+// or a strong jump between adjacent nodes of its six-node stencil) is flagged (flag bit, its
+// central D in Dst); after the passes the flags are compacted into per-direction lists in node
+// order (k_flag_*), and k_patch_fp32 / k_patch_fp64 replace each listed interface (FP32
+// characteristic flux, or FP64 projections across a strong jump), the update adding the
+// difference to the two adjacent nodes.
 struct NodeW {
     float h[NV], l[NV], u[3], p;
 };
@@ -1625,12 +1629,17 @@ __device__ __forceinline__ bool jump2(float jump, float p0, float r0, float p1, 
     return fmaxf(p0, p1) > jump * fminf(p0, p1) || fmaxf(r0, r1) > jump * fminf(r0, r1);
 }
 
-// Asynchronous 4-byte global -> shared copy (no register staging, so a thread can have all of
-// its tile's copies in flight at once), and the wait for the thread's outstanding copies.
+// Asynchronous 4- and 8-byte global -> shared copies (no register staging, so a thread can have
+// all of its tile's copies in flight at once), and the wait for the thread's outstanding copies.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all()
 {
@@ -1639,9 +1648,12 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 // Tile of the gated y / z passes: 32 lines (lanes along x, coalesced) x TY nodes along DIR, one
 // block of 32 x 8 threads.  The block stages the tile's nodes with a 3-node halo along DIR (FP32
-// hi, lo, u, v, w, p and the gate byte) in shared memory, all loads issued up front; thread
-// (tx, ty) then forms the interfaces of nodes TY/8 * ty .. + TY/8 - 1 of line tx from the staged
-// nodes, and the interface to the left of its first node again (no exchange between threads).
+// hi, lo, u, v, w, p and the gate byte) in shared memory, all loads issued up front.  Thread
+// (tx, ty) forms G of the interfaces above its TY/8 nodes of line tx and the strong-jump bits
+// of those node pairs; threads 0..159 form the tile's edge interfaces (G at y0 - 3/2, y0 - 1/2,
+// y0 + TY + 1/2 and the jump bits of the outermost pairs) in the same round.  After one barrier
+// each thread forms its nodes' flux differences from its own G and its neighbours' (shared
+// memory) and flags the interfaces it owns.
 constexpr int TY = 32;
 constexpr int TYR = TY + 6;         // staged nodes along DIR
 constexpr int TPT = TY / 8;         // nodes per thread
@@ -1669,7 +1681,9 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
     extern __shared__ float smem_tile[];
     float (*sT)[TYR][32] = reinterpret_cast<float (*)[TYR][32]>(smem_tile);          // [14][TYR][32]
     unsigned char (*sG)[32] = reinterpret_cast<unsigned char (*)[32]>(smem_tile + 14 * TYR * 32);
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    __shared__ float sD[TY + 3][NV][32];        // G of interface y0 - 3/2 + j of each line
+    __shared__ unsigned long long sJ[32];       // bit i: strong jump between staged nodes i, i + 1
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
     const int x = blockIdx.x * 32 + tx;
     const int b = blockIdx.y;                     // index along DB
     const int y0 = blockIdx.z * TY;              // first node of the tile along DIR
@@ -1680,18 +1694,26 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
     ii[0] = xin ? x : 0; ii[DB] = b; ii[DIR] = 0;
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const int n = P.n[DIR];
-    // stage nodes y0 - 3 .. y0 + TY + 2 (clamped to the last ghost n + 2)
-    for (int r = ty; r < TYR; r += 8) {
-        const int y = min(y0 - 3 + r, n + 2);
-        const long long id = base + (long long)y * st;
-        if (xin) {
+    if (t < 32) sJ[t] = 0ull;
+    // stage nodes y0 - 3 .. y0 + TY + 2 (clamped to the last ghost n + 2); the gate bytes are
+    // loaded into registers and stored after the loop, so that no round waits for its load
+    constexpr int NRND = (TYR + 7) / 8;
+    unsigned char gv[NRND];
+#pragma unroll
+    for (int k = 0; k < NRND; k++) {
+        const int r = ty + 8 * k;
+        const long long id = base + (long long)min(y0 - 3 + r, n + 2) * st;
+        if (xin && r < TYR) {
 #pragma unroll
             for (int v = 0; v < 2 * NV; v++) cp_async4(&sT[v][r][tx], Uf + v * vs + id);
 #pragma unroll
             for (int c = 0; c < 4; c++) cp_async4(&sT[10 + c][r][tx], Wf + (W_U + c) * vs + id);
-            sG[r][tx] = gate[id];
+            gv[k] = gate[id];
         }
     }
+#pragma unroll
+    for (int k = 0; k < NRND; k++)
+        if (xin && ty + 8 * k < TYR) sG[ty + 8 * k][tx] = gv[k];
     // the residual this pass adds to (earlier directions), for the thread's nodes: loaded now so
     // that its latency overlaps the staging copies
     const int first = y0 + TPT * ty;             // first node of this thread
@@ -1706,105 +1728,82 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
     __syncthreads();
     const float gm1 = P.gm1f;
     const float jump = P.jump;
-    // staged row of node y is y - (y0 - 3); interface y + 1/2 lies between nodes y and y + 1.
-    // The four nodes of an interface's central flux are kept in registers and shifted by one
-    // per node.  The interface below a warp's first node is the last one of the warp below,
-    // handed over through shared memory after a barrier; the tile's bottom edge y0 - 1/2 is
-    // formed by warp 0 in one extra round.
-    __shared__ float sY[8][NV][32];
-    const bool work = xin && first < n;
-    if (ty == 0 && xin && y0 < n) {
-        NodeW w0, w1, w2, w3;
-        tnode(sT, 1, tx, w0);
-        tnode(sT, 2, tx, w1);
-        tnode(sT, 3, tx, w2);
-        tnode(sT, 4, tx, w3);
-        const bool cha = sG[2][tx] || sG[3][tx] || jump2(jump, sT[13][0][tx], sT[0][0][tx], w0.p, w0.h[0]) ||
-                         jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                         jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                         jump2(jump, w3.p, w3.h[0], sT[13][5][tx], sT[0][5][tx]);
-        float D[NV], d1[NV], fp1[NV], fp2[NV];
-        dflux_w<DIR>(gm1, w1, w0, d1);
-        dflux_w<DIR>(gm1, w1, w2, fp1);
-        dflux_w<DIR>(gm1, w1, w3, fp2);
+    // staged node s holds node y0 - 3 + s; interface y0 - 3/2 + j lies between staged nodes j + 1
+    // and j + 2; jump bit i covers the pair (i, i + 1).  Lanes off the grid (x >= n_x) compute on
+    // whatever their shared memory holds and write nothing.
+    if (t < 96) {
+        // tile edges: k = 0 -> y0 - 3/2, 1 -> y0 - 1/2, 2 -> y0 + TY + 1/2
+        const int k = t >> 5;
+        const int sa = (k == 2) ? TY + 3 : k + 1;
+        NodeW a, c;
+        tnode(sT, sa, tx, a);
+        tnode(sT, sa + 1, tx, c);
+        float G[NV];
+        dflux_w<DIR>(gm1, a, c, G);
+        const int j = (k == 2) ? TY + 2 : k;
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-            D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
-            sY[0][v][tx] = D[v];
-        }
-        if (cha && y0 == 0) {                        // the line's first interface
-            const long long m = base - st;
-            sj.flag[m] |= (unsigned char)(1u << DIR);
-            float *Ds = sj.Dst + (long long)DIR * NV * vs;
-#pragma unroll
-            for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
-        }
+        for (int v = 0; v < NV; v++) sD[j][v][tx] = G[v];
+        if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) atomicOr(&sJ[tx], 1ull << sa);
+    } else if (t < 160) {
+        // outermost pairs (0, 1) and (TY + 4, TY + 5): strong-jump bits only
+        const int sa = (t < 128) ? 0 : TY + 4;
+        if (jump2(jump, sT[13][sa][tx], sT[0][sa][tx], sT[13][sa + 1][tx], sT[0][sa + 1][tx]))
+            atomicOr(&sJ[tx], 1ull << sa);
     }
-    float part[NV];                                  // first node's residual without its lower interface
-    if (work) {
-        int r = first - (y0 - 3);
-        NodeW w0, w1, w2, w3;
-        tnode(sT, r - 1, tx, w0);
-        tnode(sT, r, tx, w1);
-        tnode(sT, r + 1, tx, w2);
-        tnode(sT, r + 2, tx, w3);
-        float Dm[NV];
-#pragma unroll 1
-        for (int y = first; y < last; y++, r++) {
-            bool cha = sG[r][tx] || sG[r + 1][tx] || jump2(jump, sT[13][r - 2][tx], sT[0][r - 2][tx], w0.p, w0.h[0]) ||
-                       jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                       jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                       jump2(jump, w3.p, w3.h[0], sT[13][r + 3][tx], sT[0][r + 3][tx]);
-            float D[NV], d1[NV], fp1[NV], fp2[NV];
-            dflux_w<DIR>(gm1, w1, w0, d1);
-            dflux_w<DIR>(gm1, w1, w2, fp1);
-            dflux_w<DIR>(gm1, w1, w3, fp2);
+    const int s0 = TPT * ty + 3;                 // staged node of the thread's first node
+    float Gq[TPT][NV];
+    {
+        unsigned jb = 0;
+        NodeW a, c;
+        tnode(sT, s0, tx, a);
 #pragma unroll
-            for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
-            const long long m = base + (long long)y * st;
-            if (cha) {                               // interface y + 1/2: owned by node y
-                sj.flag[m] |= (unsigned char)(1u << DIR);
-                float *Ds = sj.Dst + (long long)DIR * NV * vs;
+        for (int q = 0; q < TPT; q++) {
+            tnode(sT, s0 + q + 1, tx, c);
+            dflux_w<DIR>(gm1, a, c, Gq[q]);
+            if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) jb |= 1u << q;
 #pragma unroll
-                for (int v = 0; v < NV; v++) Ds[v * vs + m] = D[v];
-            }
-            const float fac = line_facf<DIR>(P, y);
-            const int q = y - first;
-            if (q == 0) {
-#pragma unroll
-                for (int v = 0; v < NV; v++) part[v] = -fac * (D[v] - d1[v]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < NV; v++) {
-                    const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
-                    float acc = 0.f;
-#pragma unroll
-                    for (int qq = 1; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
-                    Rf[v * vs + m] = accumulate ? acc + rr : rr;
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < NV; v++) Dm[v] = D[v];
-            if (y + 1 < last) {
-                w0 = w1; w1 = w2; w2 = w3;
-                tnode(sT, r + 3, tx, w3);
-            }
+            for (int v = 0; v < NV; v++) sD[s0 + q - 1][v][tx] = Gq[q][v];
+            a = c;
         }
-        // the warp above (if it has nodes) takes this warp's last interface as its lower one
-        if (ty < 7 && last == first + TPT && last < n) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) sY[ty + 1][v][tx] = Dm[v];
-        }
+        if (jb) atomicOr(&sJ[tx], (unsigned long long)jb << s0);
     }
     __syncthreads();
-    if (work) {
-        const float fac = line_facf<DIR>(P, first);
-        const long long m = base + (long long)first * st;
+    if (!xin || first >= n) return;
+    const unsigned long long J = sJ[tx];
+    float *Ds = sj.Dst + (long long)DIR * NV * vs;
+#pragma unroll
+    for (int q = 0; q < TPT; q++) {
+        const int y = first + q;
+        if (y >= last) break;
+        const int s = s0 + q, j = s - 1;
+        float Gm[NV], Gmm[NV], Gpp[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            const float rr = part[v] + fac * sY[ty][v][tx];
-            Rf[v * vs + m] = accumulate ? racc[0][v] + rr : rr;
+            Gm[v] = (q >= 1) ? Gq[q - 1][v] : sD[j - 1][v][tx];
+            Gmm[v] = (q >= 2) ? Gq[q - 2][v] : sD[j - 2][v][tx];
+            Gpp[v] = (q + 1 < TPT) ? Gq[q + 1][v] : sD[j + 1][v][tx];
         }
+        const float fac = line_facf<DIR>(P, y);
+        const long long m = base + (long long)y * st;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const float rr = -fac * (7.f * (Gq[q][v] + Gm[v]) - (Gpp[v] + Gmm[v])) * (1.f / 12.f);
+            Rf[v * vs + m] = accumulate ? racc[q][v] + rr : rr;
+        }
+        // interface y + 1/2 (owned by node y): gate on either side, or a strong jump between
+        // adjacent nodes of y - 2 .. y + 3 (pairs s - 2 .. s + 2)
+        if (sG[s][tx] || sG[s + 1][tx] || ((J >> (s - 2)) & 31ull)) {
+            sj.flag[m] |= (unsigned char)(1u << DIR);
+#pragma unroll
+            for (int v = 0; v < NV; v++) Ds[v * vs + m] = (6.f * Gq[q][v] + Gm[v] - Gpp[v]) * (1.f / 12.f);
+        }
+    }
+    if (y0 == 0 && ty == 0 && (sG[2][tx] || sG[3][tx] || (J & 31ull))) {
+        // the line's first interface -1/2 (staged nodes 2 | 3), owned by this tile
+        const long long m = base - st;
+        sj.flag[m] |= (unsigned char)(1u << DIR);
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ds[v * vs + m] = (6.f * sD[1][v][tx] + sD[0][v][tx] - sD[2][v][tx]) * (1.f / 12.f);
     }
 }
 
@@ -1813,14 +1812,15 @@ constexpr size_t TILE_SMEM = (size_t)14 * TYR * 32 * sizeof(float) + (size_t)TYR
 // Gated x and y passes in one kernel (x and y active).  The block stages a 38 x 38 tile of nodes
 // (32 x lanes and 32 y rows, each with a 3-node halo; FP32 hi, lo, u, v, w, p and the gate byte),
 // then
-//   phase 1 -- lane tx forms the central D of interface x + 1/2 of each of its four rows; the
-//   left neighbour's interface comes by a warp shuffle; the tile's left edges x0 - 1/2 of all 32
-//   rows are formed by warp 0 in one extra round (lane l: row l) and passed through shared
-//   memory after a block barrier; the x part of the residual stays in registers;
-//   phase 2 -- the y march of k_conv_delta_tile<1> on the same staged tile adds the y part,
-// and the residual is written once: the x pass's reads of the node arrays and its residual
-// round trip through HBM are gone.  Strong-jump and gated interfaces of both directions are
-// recorded as the separate passes record them.
+//   round 1 -- thread (tx, ty) forms G of the x interface x + 1/2 and of the y interface y + 1/2
+//   of its four nodes (x = x0 + tx, rows y0 + 4 ty ..) and the strong-jump bits of those node
+//   pairs; threads 0..191 form the tile's edge interfaces in the same round (x0 - 3/2, x0 - 1/2,
+//   x0 + 32 + 1/2 of each row, y0 - 3/2, y0 - 1/2, y0 + 32 + 1/2 of each column) and threads
+//   192..255 the jump bits of the outermost pairs;
+//   round 2 -- after one barrier each thread forms its nodes' x and y flux differences (x
+//   neighbours by warp shuffles, y neighbours from registers or shared memory), writes the
+//   residual once and flags the interfaces it owns.
+// The x pass's reads of the node arrays and its residual round trip through HBM are gone.
 constexpr int TXR = 32 + 6;        // staged columns (x0 - 3 .. x0 + 34)
 
 __device__ __forceinline__ void xnode(const float (*sT)[TYR][TXR], int r, int c, NodeW &w)
@@ -1833,29 +1833,6 @@ __device__ __forceinline__ void xnode(const float (*sT)[TYR][TXR], int r, int c,
 #pragma unroll
     for (int q = 0; q < 3; q++) w.u[q] = sT[10 + q][r][c];
     w.p = sT[13][r][c];
-}
-
-// Central D of the x interface between staged columns c and c + 1 of row r, its left node's
-// flux difference dl, and whether it must be recorded (gate on either side or a strong jump).
-__device__ __forceinline__ bool x_interface(const float (*sT)[TYR][TXR], const unsigned char (*sG)[TXR],
-                                            int r, int c, float gm1, float jump, float D[NV], float dl[NV])
-{
-    NodeW w0, w1, w2, w3;
-    xnode(sT, r, c - 1, w0);
-    xnode(sT, r, c, w1);
-    xnode(sT, r, c + 1, w2);
-    xnode(sT, r, c + 2, w3);
-    const bool cha = sG[r][c] || sG[r][c + 1] || jump2(jump, sT[13][r][c - 2], sT[0][r][c - 2], w0.p, w0.h[0]) ||
-                     jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                     jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                     jump2(jump, w3.p, w3.h[0], sT[13][r][c + 3], sT[0][r][c + 3]);
-    float fp1[NV], fp2[NV];
-    dflux_w<0>(gm1, w1, w0, dl);
-    dflux_w<0>(gm1, w1, w2, fp1);
-    dflux_w<0>(gm1, w1, w3, fp2);
-#pragma unroll
-    for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - dl[v] - fp2[v]) * (1.f / 12.f);
-    return cha;
 }
 
 __device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj, int dir, long long m,
@@ -1875,8 +1852,11 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__
     extern __shared__ float smem_tile[];
     float (*sT)[TYR][TXR] = reinterpret_cast<float (*)[TYR][TXR]>(smem_tile);             // [14][TYR][TXR]
     unsigned char (*sG)[TXR] = reinterpret_cast<unsigned char (*)[TXR]>(smem_tile + 14 * TYR * TXR);
-    __shared__ float sE[TY][NV];       // the tile's left-edge x interface of each row
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    __shared__ float sDy[TY + 3][NV][32];    // G of y interface y0 - 3/2 + j of each column
+    __shared__ float sEx[3][NV][TY];         // G of x interfaces x0 - 3/2, x0 - 1/2, x0 + 65/2 of each row
+    __shared__ unsigned long long sJx[TY];   // bit i: strong jump between staged columns i, i + 1 of a row
+    __shared__ unsigned long long sJy[32];   // bit i: strong jump between staged rows i, i + 1 of a column
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
     const int x0 = blockIdx.x * 32;
     const int x = x0 + tx;
     const int kz = blockIdx.y;
@@ -1886,157 +1866,188 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__
     const bool xin = x < P.n[0];
     const long long zbase = node_index(P, 0, 0, kz);
     const int n = P.n[1];
-    // stage columns x0 - 3 .. x0 + 34 (up to the row's last ghost) of rows y0 - 3 .. y0 + TY + 2
-    // (clamped to the last ghost n + 2)
-    for (int r = ty; r < TYR; r += 8) {
-        const long long rb = zbase + (long long)min(y0 - 3 + r, n + 2) * st;
-        for (int c = tx; c < TXR; c += 32) {
-            const int xx = x0 - 3 + c;
-            if (xx > P.n[0] + 2) continue;
-            const long long id = rb + xx;
+    if (t < 32) sJx[t] = 0ull;
+    else if (t < 64) sJy[t - 32] = 0ull;
+    // stage columns x0 - 3 .. x0 + 34 of rows y0 - 3 .. y0 + TY + 2, both clamped to the last
+    // ghost (n + 2) so that every staged value is a node of the grid.  The tile is walked in
+    // row-major order (staged node e = r * TXR + c), 256 copies per round; the gate bytes are
+    // loaded into registers in the same rounds and stored after the copies, so that no round
+    // waits for its gate load.  When the padded row length is even, the staged column pairs
+    // (2i, 2i + 1) start on 8 bytes (x0 - 3 is the row's x0-th padded node) and move as 8-byte
+    // copies, the last real pair (n + 1, n + 2) standing in for pairs past it.
+    constexpr int NST = TYR * TXR;
+    float *sTf = smem_tile;
+    unsigned char *sGf = &sG[0][0];
+    if ((P.np[0] & 1) == 0 && ((reinterpret_cast<uintptr_t>(Uf) | reinterpret_cast<uintptr_t>(Wf)) & 7) == 0 &&
+        (reinterpret_cast<uintptr_t>(gate) & 1) == 0) {
+        constexpr int NPR = TXR / 2, NP = TYR * NPR, NRND = (NP + 255) / 256;
+        unsigned short gv[NRND];
 #pragma unroll
-            for (int v = 0; v < 2 * NV; v++) cp_async4(&sT[v][r][c], Uf + v * vs + id);
+        for (int k = 0; k < NRND; k++) {
+            const int e = t + 256 * k;
+            if (e < NP) {
+                const int r = e / NPR, i = e - r * NPR, se = r * TXR + 2 * i;
+                const long long id = zbase + (long long)min(y0 - 3 + r, n + 2) * st + min(x0 - 3 + 2 * i, P.n[0] + 1);
 #pragma unroll
-            for (int q = 0; q < 4; q++) cp_async4(&sT[10 + q][r][c], Wf + (W_U + q) * vs + id);
-            sG[r][c] = gate[id];
+                for (int v = 0; v < 2 * NV; v++) cp_async8(sTf + v * NST + se, Uf + v * vs + id);
+#pragma unroll
+                for (int q = 0; q < 4; q++) cp_async8(sTf + (10 + q) * NST + se, Wf + (W_U + q) * vs + id);
+                gv[k] = *reinterpret_cast<const unsigned short *>(gate + id);
+            }
         }
+#pragma unroll
+        for (int k = 0; k < NRND; k++) {
+            const int e = t + 256 * k;
+            if (e < NP) {
+                const int r = e / NPR;
+                *reinterpret_cast<unsigned short *>(sGf + r * TXR + 2 * (e - r * NPR)) = gv[k];
+            }
+        }
+    } else {
+        constexpr int NRND = (NST + 255) / 256;
+        unsigned char gv[NRND];
+#pragma unroll
+        for (int k = 0; k < NRND; k++) {
+            const int e = t + 256 * k;
+            if (e < NST) {
+                const int r = e / TXR, c = e - r * TXR;
+                const long long id = zbase + (long long)min(y0 - 3 + r, n + 2) * st + min(x0 - 3 + c, P.n[0] + 2);
+#pragma unroll
+                for (int v = 0; v < 2 * NV; v++) cp_async4(sTf + v * NST + e, Uf + v * vs + id);
+#pragma unroll
+                for (int q = 0; q < 4; q++) cp_async4(sTf + (10 + q) * NST + e, Wf + (W_U + q) * vs + id);
+                gv[k] = gate[id];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NRND; k++)
+            if (t + 256 * k < NST) sGf[t + 256 * k] = gv[k];
     }
     cp_async_wait_all();
     __syncthreads();
     const float gm1 = P.gm1f;
     const float jump = P.jump;
-    const int first = y0 + TPT * ty;             // first row of this warp (uniform per warp)
-    const int last = min(first + TPT, n);        // first >= n: no rows (still at the barrier)
-    // ---- phase 1: x interfaces of the warp's rows
-    if (ty == 0 && y0 + tx < n) {
-        // warp 0, lane l: the left-edge interface x0 - 1/2 of row y0 + l (staged columns 2 | 3)
-        const int r = tx + 3;
-        float D[NV], dl[NV];
-        const bool cha = x_interface(sT, sG, r, 2, gm1, jump, D, dl);
+    // staged row r / column c hold node y0 - 3 + r / x0 - 3 + c; jump bit i covers the pair
+    // (i, i + 1) of staged rows or columns
+    if (t < 96) {
+        // x edges of row l = tx (k = warp): x0 - 3/2 (columns 1 | 2), x0 - 1/2 (2 | 3), x0 + 65/2 (35 | 36)
+        const int k = t >> 5;
+        const int ca = (k == 2) ? 35 : k + 1;
+        NodeW a, c;
+        xnode(sT, tx + 3, ca, a);
+        xnode(sT, tx + 3, ca + 1, c);
+        float G[NV];
+        dflux_w<0>(gm1, a, c, G);
 #pragma unroll
-        for (int v = 0; v < NV; v++) sE[tx][v] = D[v];
-        if (cha && x0 == 0)                      // else the tile to the left owns it
-            record_interface(P, sj, 0, zbase + (long long)(y0 + tx) * st - 1, D);
+        for (int v = 0; v < NV; v++) sEx[k][v][tx] = G[v];
+        if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) atomicOr(&sJx[tx], 1ull << ca);
+    } else if (t < 192) {
+        // y edges of column x0 + tx (k = warp - 3): y0 - 3/2 (rows 1 | 2), y0 - 1/2 (2 | 3), y0 + 65/2 (35 | 36)
+        const int k = (t >> 5) - 3;
+        const int ra = (k == 2) ? TY + 3 : k + 1;
+        NodeW a, c;
+        xnode(sT, ra, tx + 3, a);
+        xnode(sT, ra + 1, tx + 3, c);
+        float G[NV];
+        dflux_w<1>(gm1, a, c, G);
+        const int j = (k == 2) ? TY + 2 : k;
+#pragma unroll
+        for (int v = 0; v < NV; v++) sDy[j][v][tx] = G[v];
+        if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) atomicOr(&sJy[tx], 1ull << ra);
+    } else {
+        // outermost pairs, jump bits only: columns (0, 1) or (36, 37) of row l, rows (0, 1) or
+        // (36, 37) of column l
+        const int l = tx;
+        const int e = (t < 224) ? 0 : TXR - 2;
+        if (jump2(jump, sT[13][l + 3][e], sT[0][l + 3][e], sT[13][l + 3][e + 1], sT[0][l + 3][e + 1]))
+            atomicOr(&sJx[l], 1ull << e);
+        if (jump2(jump, sT[13][e][l + 3], sT[0][e][l + 3], sT[13][e + 1][l + 3], sT[0][e + 1][l + 3]))
+            atomicOr(&sJy[l], 1ull << e);
     }
-    float racc[TPT][NV];
+    const int c = tx + 3;                        // staged column of the lane's node
+    const int r0 = TPT * ty + 3;                 // staged row of the thread's first node
+    float Gx[TPT][NV], Gy[TPT][NV];
+    {
+        unsigned jy = 0;
+        NodeW a, b;
+        xnode(sT, r0, c, a);
 #pragma unroll
-    for (int q = 0; q < TPT; q++)
-#pragma unroll
-        for (int v = 0; v < NV; v++) racc[q][v] = 0.f;
-    const float facx = xin ? line_facf<0>(P, x) : 0.f;
-#pragma unroll 1
-    for (int q = 0; q < last - first; q++) {
-        const int y = first + q;
-        const int r = y - (y0 - 3);
-        float D[NV], dl[NV];
-        bool cha = false;
-        if (xin) cha = x_interface(sT, sG, r, tx + 3, gm1, jump, D, dl);
-        else {
-#pragma unroll
-            for (int v = 0; v < NV; v++) { D[v] = 0.f; dl[v] = 0.f; }
-        }
-        if (cha) record_interface(P, sj, 0, zbase + (long long)y * st + x, D);
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            const float Dl = __shfl_up_sync(0xffffffffu, D[v], 1);   // lane 0: edge added below
-            const float rx = -facx * ((D[v] - (tx == 0 ? 0.f : Dl)) - dl[v]);
-#pragma unroll
-            for (int qq = 0; qq < TPT; qq++) racc[qq][v] = (qq == q) ? rx : racc[qq][v];   // static indexing
-        }
-    }
-    __syncthreads();                             // the left edges of warp 0 are in sE
-    if (tx == 0) {
-#pragma unroll
-        for (int q = 0; q < TPT; q++)
-#pragma unroll
-            for (int v = 0; v < NV; v++)
-                racc[q][v] += (first + q < last) ? facx * sE[TPT * ty + q][v] : 0.f;
-    }
-    // ---- phase 2: the y march on the staged tile (column tx + 3).  The interface below a
-    // warp's first row is the last one of the warp below, handed over through shared memory
-    // after a barrier; the tile's bottom edge y0 - 1/2 is formed by warp 0 in one extra round.
-    __shared__ float sY[8][NV][32];
-    const int cx = tx + 3;
-    const long long base = zbase + x;
-    const bool work = xin && first < n;
-    if (ty == 0 && xin && y0 < n) {
-        // nodes y0 - 1 (staged row 2) and y0: the interface recorded only at the line's start
-        NodeW w0, w1, w2, w3;
-        xnode(sT, 1, cx, w0);
-        xnode(sT, 2, cx, w1);
-        xnode(sT, 3, cx, w2);
-        xnode(sT, 4, cx, w3);
-        const bool cha = sG[2][cx] || sG[3][cx] || jump2(jump, sT[13][0][cx], sT[0][0][cx], w0.p, w0.h[0]) ||
-                         jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                         jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                         jump2(jump, w3.p, w3.h[0], sT[13][5][cx], sT[0][5][cx]);
-        float D[NV], d1[NV], fp1[NV], fp2[NV];
-        dflux_w<1>(gm1, w1, w0, d1);
-        dflux_w<1>(gm1, w1, w2, fp1);
-        dflux_w<1>(gm1, w1, w3, fp2);
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
-            sY[0][v][tx] = D[v];
-        }
-        if (cha && y0 == 0) record_interface(P, sj, 1, base - st, D);
-    }
-    float part[NV];                              // first row's residual without its lower interface
-    if (work) {
-        int r = first - (y0 - 3);
-        NodeW w0, w1, w2, w3;
-        xnode(sT, r - 1, cx, w0);
-        xnode(sT, r, cx, w1);
-        xnode(sT, r + 1, cx, w2);
-        xnode(sT, r + 2, cx, w3);
-        float Dm[NV];
-#pragma unroll 1
-        for (int y = first; y < last; y++, r++) {
-            bool cha = sG[r][cx] || sG[r + 1][cx] || jump2(jump, sT[13][r - 2][cx], sT[0][r - 2][cx], w0.p, w0.h[0]) ||
-                       jump2(jump, w0.p, w0.h[0], w1.p, w1.h[0]) || jump2(jump, w1.p, w1.h[0], w2.p, w2.h[0]) ||
-                       jump2(jump, w2.p, w2.h[0], w3.p, w3.h[0]) ||
-                       jump2(jump, w3.p, w3.h[0], sT[13][r + 3][cx], sT[0][r + 3][cx]);
-            float D[NV], d1[NV], fp1[NV], fp2[NV];
-            dflux_w<1>(gm1, w1, w0, d1);
-            dflux_w<1>(gm1, w1, w2, fp1);
-            dflux_w<1>(gm1, w1, w3, fp2);
-#pragma unroll
-            for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - d1[v] - fp2[v]) * (1.f / 12.f);
-            const long long m = base + (long long)y * st;
-            if (cha) record_interface(P, sj, 1, m, D);     // interface y + 1/2: owned by row y
-            const float fac = line_facf<1>(P, y);
-            const int q = y - first;
-            if (q == 0) {
-#pragma unroll
-                for (int v = 0; v < NV; v++) part[v] = -fac * (D[v] - d1[v]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < NV; v++) {
-                    const float rr = -fac * ((D[v] - Dm[v]) - d1[v]);
-                    float acc = 0.f;
-#pragma unroll
-                    for (int qq = 1; qq < TPT; qq++) acc = (qq == q) ? racc[qq][v] : acc;   // static indexing
-                    Rf[v * vs + m] = acc + rr;
-                }
+        for (int q = 0; q < TPT; q++) {
+            {
+                NodeW e;
+                xnode(sT, r0 + q, c + 1, e);
+                dflux_w<0>(gm1, a, e, Gx[q]);
+                const unsigned bx = __ballot_sync(0xffffffffu, jump2(jump, a.p, a.h[0], e.p, e.h[0]));
+                if (tx == 0 && bx) atomicOr(&sJx[r0 + q - 3], (unsigned long long)bx << 3);
             }
+            xnode(sT, r0 + q + 1, c, b);
+            dflux_w<1>(gm1, a, b, Gy[q]);
+            if (jump2(jump, a.p, a.h[0], b.p, b.h[0])) jy |= 1u << q;
 #pragma unroll
-            for (int v = 0; v < NV; v++) Dm[v] = D[v];
-            if (y + 1 < last) {
-                w0 = w1; w1 = w2; w2 = w3;
-                xnode(sT, r + 3, cx, w3);
-            }
+            for (int v = 0; v < NV; v++) sDy[r0 + q - 1][v][tx] = Gy[q][v];
+            a = b;
         }
-        // the warp above (if it has rows) takes this warp's last interface as its lower one
-        if (ty < 7 && last == first + TPT && last < n) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) sY[ty + 1][v][tx] = Dm[v];
-        }
+        if (jy) atomicOr(&sJy[tx], (unsigned long long)jy << r0);
     }
     __syncthreads();
-    if (work) {
-        const float fac = line_facf<1>(P, first);
+    const int first = y0 + TPT * ty;             // first row of this warp (uniform per warp)
+    const float facx = xin ? line_facf<0>(P, x) : 0.f;
+    const unsigned long long Jy = sJy[tx];
 #pragma unroll
-        for (int v = 0; v < NV; v++) Rf[v * vs + base + (long long)first * st] = racc[0][v] + (part[v] + fac * sY[ty][v][tx]);
+    for (int q = 0; q < TPT; q++) {
+        const int y = first + q;                 // uniform per warp
+        if (y >= n) break;
+        const int r = r0 + q, l = r - 3;
+        // x neighbours: lanes to the left / right, the tile's edges from sEx
+        float Gxm[NV], Gxmm[NV], Gxpp[NV], Gym[NV], Gymm[NV], Gypp[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const float m1 = __shfl_up_sync(0xffffffffu, Gx[q][v], 1);
+            const float m2 = __shfl_up_sync(0xffffffffu, Gx[q][v], 2);
+            const float p1 = __shfl_down_sync(0xffffffffu, Gx[q][v], 1);
+            Gxm[v] = (tx == 0) ? sEx[1][v][l] : m1;
+            Gxmm[v] = (tx == 0) ? sEx[0][v][l] : ((tx == 1) ? sEx[1][v][l] : m2);
+            Gxpp[v] = (tx == 31) ? sEx[2][v][l] : p1;
+            Gym[v] = (q >= 1) ? Gy[q - 1][v] : sDy[r - 2][v][tx];
+            Gymm[v] = (q >= 2) ? Gy[q - 2][v] : sDy[r - 3][v][tx];
+            Gypp[v] = (q + 1 < TPT) ? Gy[q + 1][v] : sDy[r][v][tx];
+        }
+        if (!xin) continue;
+        const float facy = line_facf<1>(P, y);
+        const long long m = zbase + (long long)y * st + x;
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+            Rf[v * vs + m] = -facx * (7.f * (Gx[q][v] + Gxm[v]) - (Gxpp[v] + Gxmm[v])) * (1.f / 12.f) -
+                             facy * (7.f * (Gy[q][v] + Gym[v]) - (Gypp[v] + Gymm[v])) * (1.f / 12.f);
+        // interface x + 1/2 / y + 1/2 (owned by this node): gate on either side, or a strong
+        // jump between adjacent nodes of its six-node stencil (pairs c - 2 .. c + 2 / r - 2 .. r + 2)
+        const unsigned long long Jx = sJx[l];
+        if (sG[r][c] || sG[r][c + 1] || ((Jx >> (c - 2)) & 31ull)) {
+            float D[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) D[v] = (6.f * Gx[q][v] + Gxm[v] - Gxpp[v]) * (1.f / 12.f);
+            record_interface(P, sj, 0, m, D);
+        }
+        if (sG[r][c] || sG[r + 1][c] || ((Jy >> (r - 2)) & 31ull)) {
+            float D[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) D[v] = (6.f * Gy[q][v] + Gym[v] - Gypp[v]) * (1.f / 12.f);
+            record_interface(P, sj, 1, m, D);
+        }
+        if (x0 == 0 && tx == 0 && (sG[r][2] || sG[r][3] || (Jx & 31ull))) {
+            // the row's first interface -1/2 (staged columns 2 | 3), owned by this tile
+            float D[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) D[v] = (6.f * sEx[1][v][l] + sEx[0][v][l] - Gx[q][v]) * (1.f / 12.f);
+            record_interface(P, sj, 0, m - 1, D);
+        }
+    }
+    if (y0 == 0 && ty == 0 && xin && (sG[2][c] || sG[3][c] || (Jy & 31ull))) {
+        // the column's first interface -1/2 (staged rows 2 | 3), owned by this tile
+        float D[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) D[v] = (6.f * sDy[1][v][tx] + sDy[0][v][tx] - sDy[2][v][tx]) * (1.f / 12.f);
+        record_interface(P, sj, 1, zbase + x - st, D);
     }
 }
 
