@@ -1809,31 +1809,24 @@ __global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *
 
 constexpr size_t TILE_SMEM = (size_t)14 * TYR * 32 * sizeof(float) + (size_t)TYR * 32;
 
-// Gated x and y passes in one kernel (x and y active).  The block stages a 38 x 38 tile of nodes
-// (32 x lanes and 32 y rows, each with a 3-node halo; FP32 hi, lo, u, v, w, p and the gate byte),
-// then
-//   round 1 -- thread (tx, ty) forms G of the x interface x + 1/2 and of the y interface y + 1/2
-//   of its four nodes (x = x0 + tx, rows y0 + 4 ty ..) and the strong-jump bits of those node
-//   pairs; threads 0..191 form the tile's edge interfaces in the same round (x0 - 3/2, x0 - 1/2,
-//   x0 + 32 + 1/2 of each row, y0 - 3/2, y0 - 1/2, y0 + 32 + 1/2 of each column) and threads
-//   192..255 the jump bits of the outermost pairs;
-//   round 2 -- after one barrier each thread forms its nodes' x and y flux differences (x
-//   neighbours by warp shuffles, y neighbours from registers or shared memory), writes the
-//   residual once and flags the interfaces it owns.
-// The x pass's reads of the node arrays and its residual round trip through HBM are gone.
-constexpr int TXR = 32 + 6;        // staged columns (x0 - 3 .. x0 + 34)
-
-__device__ __forceinline__ void xnode(const float (*sT)[TYR][TXR], int r, int c, NodeW &w)
-{
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        w.h[v] = sT[v][r][c];
-        w.l[v] = sT[NV + v][r][c];
-    }
-#pragma unroll
-    for (int q = 0; q < 3; q++) w.u[q] = sT[10 + q][r][c];
-    w.p = sT[13][r][c];
-}
+// Gated x and y passes in one kernel (x and y active), streamed through registers.  A warp owns
+// a strip of XS output columns of one z plane: lane l holds column x0 - 3 + l (lanes 0..2 and
+// 29..31 are the strip's halo, their columns clamped to the last ghost), and marches along y
+// over YC rows, rows y0 - 3 .. y0 + YC + 2.  Each step loads the next row into registers
+// (prefetched one step ahead) and
+//   - forms G_y of the interface below the current row (the node pair in the lane's registers)
+//     and its strong-jump bit, kept in a 4-slot ring of interfaces and a bit history;
+//   - forms G_x of the lane's interface x + 1/2 of the current row (right neighbour's node by
+//     warp shuffles) and the row's strong-jump bits by a ballot; the x flux difference of the
+//     row follows from its neighbours' G_x by shuffles, and the x interfaces that need the
+//     characteristic flux are flagged;
+//   - completes the residual of the row two below (its y flux difference needs G_y up to
+//     y + 3/2), adds that row's x part kept from two steps before and writes it once, and flags
+//     the y interface of the row three below (its jump window reaches the current row).
+// No shared memory and no block barriers: every warp streams independently, and the x pass's
+// reads of the node arrays and its residual round trip through HBM are gone.
+constexpr int XS = 26;     // output columns of a strip (lanes 3 .. 28)
+constexpr int YC = 64;     // rows of a warp's march
 
 __device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj, int dir, long long m,
                                                  const float D[NV])
@@ -1844,226 +1837,128 @@ __device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj,
     for (int v = 0; v < NV; v++) Ds[v * P.vs + m] = D[v];
 }
 
-template <int SCHEME>
-__global__ void __launch_bounds__(256, 2) k_conv_delta_xy(Dev P, const float *__restrict__ Uf,
+__device__ __forceinline__ NodeW shfl_node_down(const NodeW &w)
+{
+    NodeW e;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        e.h[v] = __shfl_down_sync(0xffffffffu, w.h[v], 1);
+        e.l[v] = __shfl_down_sync(0xffffffffu, w.l[v], 1);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) e.u[c] = __shfl_down_sync(0xffffffffu, w.u[c], 1);
+    e.p = __shfl_down_sync(0xffffffffu, w.p, 1);
+    return e;
+}
+
+__global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf, float *__restrict__ Rf,
                                                          Strong sj, const unsigned char *__restrict__ gate)
 {
-    extern __shared__ float smem_tile[];
-    float (*sT)[TYR][TXR] = reinterpret_cast<float (*)[TYR][TXR]>(smem_tile);             // [14][TYR][TXR]
-    unsigned char (*sG)[TXR] = reinterpret_cast<unsigned char (*)[TXR]>(smem_tile + 14 * TYR * TXR);
-    __shared__ float sDy[TY + 3][NV][32];    // G of y interface y0 - 3/2 + j of each column
-    __shared__ float sEx[3][NV][TY];         // G of x interfaces x0 - 3/2, x0 - 1/2, x0 + 65/2 of each row
-    __shared__ unsigned long long sJx[TY];   // bit i: strong jump between staged columns i, i + 1 of a row
-    __shared__ unsigned long long sJy[32];   // bit i: strong jump between staged rows i, i + 1 of a column
-    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-    const int x0 = blockIdx.x * 32;
-    const int x = x0 + tx;
-    const int kz = blockIdx.y;
-    const int y0 = blockIdx.z * TY;
-    const long long st = P.st[1];
-    const long long vs = P.vs;
-    const bool xin = x < P.n[0];
-    const long long zbase = node_index(P, 0, 0, kz);
+    const int lane = threadIdx.x & 31;
+    const int nxs = (P.n[0] + XS - 1) / XS, nyc = (P.n[1] + YC - 1) / YC;
+    const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (item >= nxs * nyc * P.n[2]) return;                 // whole warps
+    const int xs = item % nxs, yc = (item / nxs) % nyc, kz = item / (nxs * nyc);
+    const int x0 = xs * XS, y0 = yc * YC;
+    const int x = x0 - 3 + lane;
+    const bool own = lane >= 3 && lane <= 28 && x < P.n[0];          // output column of this strip
+    // x interfaces owned: x + 1/2 of the output columns, and -1/2 (lane 2) on the first strip
+    const bool xrec = own || (x0 == 0 && lane == 2);
+    const long long st = P.st[1], vs = P.vs;
+    const long long cb = node_index(P, min(x, P.n[0] + 2), 0, kz);    // the lane's column, y = 0
     const int n = P.n[1];
-    if (t < 32) sJx[t] = 0ull;
-    else if (t < 64) sJy[t - 32] = 0ull;
-    // stage columns x0 - 3 .. x0 + 34 of rows y0 - 3 .. y0 + TY + 2, both clamped to the last
-    // ghost (n + 2) so that every staged value is a node of the grid.  The tile is walked in
-    // row-major order (staged node e = r * TXR + c), 256 copies per round; the gate bytes are
-    // loaded into registers in the same rounds and stored after the copies, so that no round
-    // waits for its gate load.  When the padded row length is even, the staged column pairs
-    // (2i, 2i + 1) start on 8 bytes (x0 - 3 is the row's x0-th padded node) and move as 8-byte
-    // copies, the last real pair (n + 1, n + 2) standing in for pairs past it.
-    constexpr int NST = TYR * TXR;
-    float *sTf = smem_tile;
-    unsigned char *sGf = &sG[0][0];
-    if ((P.np[0] & 1) == 0 && ((reinterpret_cast<uintptr_t>(Uf) | reinterpret_cast<uintptr_t>(Wf)) & 7) == 0 &&
-        (reinterpret_cast<uintptr_t>(gate) & 1) == 0) {
-        constexpr int NPR = TXR / 2, NP = TYR * NPR, NRND = (NP + 255) / 256;
-        unsigned short gv[NRND];
-#pragma unroll
-        for (int k = 0; k < NRND; k++) {
-            const int e = t + 256 * k;
-            if (e < NP) {
-                const int r = e / NPR, i = e - r * NPR, se = r * TXR + 2 * i;
-                const long long id = zbase + (long long)min(y0 - 3 + r, n + 2) * st + min(x0 - 3 + 2 * i, P.n[0] + 1);
-#pragma unroll
-                for (int v = 0; v < 2 * NV; v++) cp_async8(sTf + v * NST + se, Uf + v * vs + id);
-#pragma unroll
-                for (int q = 0; q < 4; q++) cp_async8(sTf + (10 + q) * NST + se, Wf + (W_U + q) * vs + id);
-                gv[k] = *reinterpret_cast<const unsigned short *>(gate + id);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NRND; k++) {
-            const int e = t + 256 * k;
-            if (e < NP) {
-                const int r = e / NPR;
-                *reinterpret_cast<unsigned short *>(sGf + r * TXR + 2 * (e - r * NPR)) = gv[k];
-            }
-        }
-    } else {
-        constexpr int NRND = (NST + 255) / 256;
-        unsigned char gv[NRND];
-#pragma unroll
-        for (int k = 0; k < NRND; k++) {
-            const int e = t + 256 * k;
-            if (e < NST) {
-                const int r = e / TXR, c = e - r * TXR;
-                const long long id = zbase + (long long)min(y0 - 3 + r, n + 2) * st + min(x0 - 3 + c, P.n[0] + 2);
-#pragma unroll
-                for (int v = 0; v < 2 * NV; v++) cp_async4(sTf + v * NST + e, Uf + v * vs + id);
-#pragma unroll
-                for (int q = 0; q < 4; q++) cp_async4(sTf + (10 + q) * NST + e, Wf + (W_U + q) * vs + id);
-                gv[k] = gate[id];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NRND; k++)
-            if (t + 256 * k < NST) sGf[t + 256 * k] = gv[k];
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    const float gm1 = P.gm1f;
-    const float jump = P.jump;
-    // staged row r / column c hold node y0 - 3 + r / x0 - 3 + c; jump bit i covers the pair
-    // (i, i + 1) of staged rows or columns
-    if (t < 96) {
-        // x edges of row l = tx (k = warp): x0 - 3/2 (columns 1 | 2), x0 - 1/2 (2 | 3), x0 + 65/2 (35 | 36)
-        const int k = t >> 5;
-        const int ca = (k == 2) ? 35 : k + 1;
-        NodeW a, c;
-        xnode(sT, tx + 3, ca, a);
-        xnode(sT, tx + 3, ca + 1, c);
-        float G[NV];
-        dflux_w<0>(gm1, a, c, G);
-#pragma unroll
-        for (int v = 0; v < NV; v++) sEx[k][v][tx] = G[v];
-        if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) atomicOr(&sJx[tx], 1ull << ca);
-    } else if (t < 192) {
-        // y edges of column x0 + tx (k = warp - 3): y0 - 3/2 (rows 1 | 2), y0 - 1/2 (2 | 3), y0 + 65/2 (35 | 36)
-        const int k = (t >> 5) - 3;
-        const int ra = (k == 2) ? TY + 3 : k + 1;
-        NodeW a, c;
-        xnode(sT, ra, tx + 3, a);
-        xnode(sT, ra + 1, tx + 3, c);
-        float G[NV];
-        dflux_w<1>(gm1, a, c, G);
-        const int j = (k == 2) ? TY + 2 : k;
-#pragma unroll
-        for (int v = 0; v < NV; v++) sDy[j][v][tx] = G[v];
-        if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) atomicOr(&sJy[tx], 1ull << ra);
-    } else {
-        // outermost pairs, jump bits only: columns (0, 1) or (36, 37) of row l, rows (0, 1) or
-        // (36, 37) of column l
-        const int l = tx;
-        const int e = (t < 224) ? 0 : TXR - 2;
-        if (jump2(jump, sT[13][l + 3][e], sT[0][l + 3][e], sT[13][l + 3][e + 1], sT[0][l + 3][e + 1]))
-            atomicOr(&sJx[l], 1ull << e);
-        if (jump2(jump, sT[13][e][l + 3], sT[0][e][l + 3], sT[13][e + 1][l + 3], sT[0][e + 1][l + 3]))
-            atomicOr(&sJy[l], 1ull << e);
-    }
-    const int c = tx + 3;                        // staged column of the lane's node
-    const int r0 = TPT * ty + 3;                 // staged row of the thread's first node
-    float Gx[TPT][NV], Gy[TPT][NV];
+    const int nrow = min(YC, n - y0);
+    const int nsteps = nrow + 6;                                    // rows y0 - 3 .. y0 + nrow + 2
+    const float gm1 = P.gm1f, jump = P.jump;
+    const float facx = own ? line_facf<0>(P, x) : 0.f;
+    NodeW row[4];                    // ring: slot i & 3 holds row y0 - 3 + i
+    float Gy[4][NV];                 // ring: slot i & 3 holds G_y of the interface below row y0 - 3 + i
+    float Rx[2][NV];                 // x flux differences of the last two rows with x work
+    unsigned jy = 0;                 // bit b: strong jump between rows s - 1 - b and s - b
+    unsigned gq = 0;                 // byte b: gate of row s - b
+    unsigned gn;                     // gate of the row loaded ahead
     {
-        unsigned jy = 0;
-        NodeW a, b;
-        xnode(sT, r0, c, a);
+        const long long id = cb + (long long)(y0 - 3) * st;
+        load_node(P, Uf, Wf, id, row[0]);
+        gn = gate[id];
+    }
+    for (int i4 = 0; i4 < nsteps; i4 += 4) {
 #pragma unroll
-        for (int q = 0; q < TPT; q++) {
-            {
-                NodeW e;
-                xnode(sT, r0 + q, c + 1, e);
-                dflux_w<0>(gm1, a, e, Gx[q]);
-                const unsigned bx = __ballot_sync(0xffffffffu, jump2(jump, a.p, a.h[0], e.p, e.h[0]));
-                if (tx == 0 && bx) atomicOr(&sJx[r0 + q - 3], (unsigned long long)bx << 3);
+        for (int k = 0; k < 4; k++) {
+            const int i = i4 + k;
+            if (i >= nsteps) break;
+            const int s = y0 - 3 + i;                              // the current row
+            gq = (gq << 8) | gn;
+            if (i + 1 < nsteps) {
+                const long long id = cb + (long long)min(s + 1, n + 2) * st;
+                load_node(P, Uf, Wf, id, row[(k + 1) & 3]);
+                gn = gate[id];
             }
-            xnode(sT, r0 + q + 1, c, b);
-            dflux_w<1>(gm1, a, b, Gy[q]);
-            if (jump2(jump, a.p, a.h[0], b.p, b.h[0])) jy |= 1u << q;
+            const NodeW &cur = row[k];
+            const NodeW &prv = row[(k + 3) & 3];
+            if (i >= 1) jy = (jy << 1) | (jump2(jump, prv.p, prv.h[0], cur.p, cur.h[0]) ? 1u : 0u);
+            // G_y of interface s - 1/2, needed from y0 - 3/2 (i = 2) to y0 + nrow + 1/2 (i = nrow + 4)
+            if (i >= 2 && i <= nrow + 4) dflux_w<1>(gm1, prv, cur, Gy[k]);
+            // residual of row y = s - 2 (i = 5 .. nrow + 4): G_y at y + 3/2, y + 1/2, y - 1/2, y - 3/2
+            if (i >= 5 && i <= nrow + 4 && own) {
+                const int y = s - 2;
+                const float facy = line_facf<1>(P, y);
+                const long long m = cb + (long long)y * st;
 #pragma unroll
-            for (int v = 0; v < NV; v++) sDy[r0 + q - 1][v][tx] = Gy[q][v];
-            a = b;
+                for (int v = 0; v < NV; v++) {
+                    const float ry = -facy * (7.f * (Gy[(k + 3) & 3][v] + Gy[(k + 2) & 3][v]) -
+                                              (Gy[k][v] + Gy[(k + 1) & 3][v])) * (1.f / 12.f);
+                    Rf[v * vs + m] = Rx[k & 1][v] + ry;
+                }
+            }
+            // y interface y + 1/2 of row y = s - 3 (rows y0 .. y0 + nrow - 1, and -1 on the first
+            // chunk): gate of rows y, y + 1, or a strong jump in pairs (y - 2, y - 1) .. (y + 2, y + 3)
+            if (((i >= 6 && i <= nrow + 5) || (i == 5 && y0 == 0)) && own) {
+                if (((gq >> 24) & 0xffu) || ((gq >> 16) & 0xffu) || (jy & 31u)) {
+                    float D[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; v++)
+                        D[v] = (6.f * Gy[(k + 2) & 3][v] + Gy[(k + 1) & 3][v] - Gy[(k + 3) & 3][v]) * (1.f / 12.f);
+                    record_interface(P, sj, 1, cb + (long long)(s - 3) * st, D);
+                }
+            }
+            // x work of row s (i = 3 .. nrow + 2); every lane takes part in the shuffles
+            if (i >= 3 && i <= nrow + 2) {
+                float Gx[NV];
+                unsigned bx;
+                {
+                    const NodeW e = shfl_node_down(cur);
+                    dflux_w<0>(gm1, cur, e, Gx);
+                    bx = __ballot_sync(0xffffffffu, jump2(jump, cur.p, cur.h[0], e.p, e.h[0]));
+                }
+                const unsigned g0 = gq & 0xffu;
+                const unsigned g1 = __shfl_down_sync(0xffffffffu, g0, 1);
+                float Gm[NV], Gpp[NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    Gm[v] = __shfl_up_sync(0xffffffffu, Gx[v], 1);
+                    const float Gmm = __shfl_up_sync(0xffffffffu, Gx[v], 2);
+                    Gpp[v] = __shfl_down_sync(0xffffffffu, Gx[v], 1);
+                    Rx[k & 1][v] = -facx * (7.f * (Gx[v] + Gm[v]) - (Gpp[v] + Gmm)) * (1.f / 12.f);
+                }
+                // interface x + 1/2: pairs (x - 2, x - 1) .. (x + 2, x + 3) are ballot bits lane - 2 .. lane + 2
+                if (xrec && (g0 || g1 || ((bx >> (lane - 2)) & 31u))) {
+                    float D[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; v++) D[v] = (6.f * Gx[v] + Gm[v] - Gpp[v]) * (1.f / 12.f);
+                    record_interface(P, sj, 0, cb + (long long)s * st, D);
+                }
+            }
         }
-        if (jy) atomicOr(&sJy[tx], (unsigned long long)jy << r0);
-    }
-    __syncthreads();
-    const int first = y0 + TPT * ty;             // first row of this warp (uniform per warp)
-    const float facx = xin ? line_facf<0>(P, x) : 0.f;
-    const unsigned long long Jy = sJy[tx];
-#pragma unroll
-    for (int q = 0; q < TPT; q++) {
-        const int y = first + q;                 // uniform per warp
-        if (y >= n) break;
-        const int r = r0 + q, l = r - 3;
-        // x neighbours: lanes to the left / right, the tile's edges from sEx
-        float Gxm[NV], Gxmm[NV], Gxpp[NV], Gym[NV], Gymm[NV], Gypp[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            const float m1 = __shfl_up_sync(0xffffffffu, Gx[q][v], 1);
-            const float m2 = __shfl_up_sync(0xffffffffu, Gx[q][v], 2);
-            const float p1 = __shfl_down_sync(0xffffffffu, Gx[q][v], 1);
-            Gxm[v] = (tx == 0) ? sEx[1][v][l] : m1;
-            Gxmm[v] = (tx == 0) ? sEx[0][v][l] : ((tx == 1) ? sEx[1][v][l] : m2);
-            Gxpp[v] = (tx == 31) ? sEx[2][v][l] : p1;
-            Gym[v] = (q >= 1) ? Gy[q - 1][v] : sDy[r - 2][v][tx];
-            Gymm[v] = (q >= 2) ? Gy[q - 2][v] : sDy[r - 3][v][tx];
-            Gypp[v] = (q + 1 < TPT) ? Gy[q + 1][v] : sDy[r][v][tx];
-        }
-        if (!xin) continue;
-        const float facy = line_facf<1>(P, y);
-        const long long m = zbase + (long long)y * st + x;
-#pragma unroll
-        for (int v = 0; v < NV; v++)
-            Rf[v * vs + m] = -facx * (7.f * (Gx[q][v] + Gxm[v]) - (Gxpp[v] + Gxmm[v])) * (1.f / 12.f) -
-                             facy * (7.f * (Gy[q][v] + Gym[v]) - (Gypp[v] + Gymm[v])) * (1.f / 12.f);
-        // interface x + 1/2 / y + 1/2 (owned by this node): gate on either side, or a strong
-        // jump between adjacent nodes of its six-node stencil (pairs c - 2 .. c + 2 / r - 2 .. r + 2)
-        const unsigned long long Jx = sJx[l];
-        if (sG[r][c] || sG[r][c + 1] || ((Jx >> (c - 2)) & 31ull)) {
-            float D[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) D[v] = (6.f * Gx[q][v] + Gxm[v] - Gxpp[v]) * (1.f / 12.f);
-            record_interface(P, sj, 0, m, D);
-        }
-        if (sG[r][c] || sG[r + 1][c] || ((Jy >> (r - 2)) & 31ull)) {
-            float D[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) D[v] = (6.f * Gy[q][v] + Gym[v] - Gypp[v]) * (1.f / 12.f);
-            record_interface(P, sj, 1, m, D);
-        }
-        if (x0 == 0 && tx == 0 && (sG[r][2] || sG[r][3] || (Jx & 31ull))) {
-            // the row's first interface -1/2 (staged columns 2 | 3), owned by this tile
-            float D[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) D[v] = (6.f * sEx[1][v][l] + sEx[0][v][l] - Gx[q][v]) * (1.f / 12.f);
-            record_interface(P, sj, 0, m - 1, D);
-        }
-    }
-    if (y0 == 0 && ty == 0 && xin && (sG[2][c] || sG[3][c] || (Jy & 31ull))) {
-        // the column's first interface -1/2 (staged rows 2 | 3), owned by this tile
-        float D[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) D[v] = (6.f * sDy[1][v][tx] + sDy[0][v][tx] - sDy[2][v][tx]) * (1.f / 12.f);
-        record_interface(P, sj, 1, zbase + x - st, D);
     }
 }
 
-constexpr size_t XY_SMEM = (size_t)14 * TYR * TXR * sizeof(float) + (size_t)TYR * TXR;
-
 // Launch of the fused gated x + y pass (replaces the x pass and the y pass of the stage).
-template <int SCHEME>
 static void launch_delta_xy(const Dev &P, const Bufs &B, cudaStream_t s)
 {
-    static bool smem_set = false;   // one attribute call per instantiation
-    if (!smem_set) {
-        cudaFuncSetAttribute(k_conv_delta_xy<SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XY_SMEM);
-        smem_set = true;
-    }
-    dim3 g((P.n[0] + 31) / 32, P.n[2], (P.n[1] + TY - 1) / TY);
-    k_conv_delta_xy<SCHEME><<<g, dim3(32, 8), XY_SMEM, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), B.gate);
+    const long long warps = (long long)((P.n[0] + XS - 1) / XS) * ((P.n[1] + YC - 1) / YC) * P.n[2];
+    k_conv_delta_xy<<<(int)((warps + 3) / 4), 128, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), B.gate);
 }
 
 // The fused pass runs for the gated mixed path on Cartesian / rectilinear grids with x and y active.
@@ -2842,10 +2737,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         if (fxy && d == 1) continue;                     // formed with x by the fused pass
         if (tap) (*tap)(fxy && d == 0 ? "conv_xy" : conv_names[d], s);
         if (fxy && d == 0) {
-            if (P.scheme == SCH_WENO5JS) launch_delta_xy<SCH_WENO5JS>(P, B, s);
-            else if (P.scheme == SCH_WENO5Z) launch_delta_xy<SCH_WENO5Z>(P, B, s);
-            else if (P.scheme == SCH_TENO6) launch_delta_xy<SCH_TENO6>(P, B, s);
-            else launch_delta_xy<SCH_TENO5>(P, B, s);
+            launch_delta_xy(P, B, s);
         } else if (d == 0) conv_dir<0>(P, B, acc, s);
         else if (d == 1) conv_dir<1>(P, B, acc, s);
         else conv_dir<2>(P, B, acc, s);
