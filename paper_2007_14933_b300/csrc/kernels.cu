@@ -1646,168 +1646,99 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Tile of the gated y / z passes: 32 lines (lanes along x, coalesced) x TY nodes along DIR, one
-// block of 32 x 8 threads.  The block stages the tile's nodes with a 3-node halo along DIR (FP32
-// hi, lo, u, v, w, p and the gate byte) in shared memory, all loads issued up front.  Thread
-// (tx, ty) forms G of the interfaces above its TY/8 nodes of line tx and the strong-jump bits
-// of those node pairs; threads 0..159 form the tile's edge interfaces (G at y0 - 3/2, y0 - 1/2,
-// y0 + TY + 1/2 and the jump bits of the outermost pairs) in the same round.  After one barrier
-// each thread forms its nodes' flux differences from its own G and its neighbours' (shared
-// memory) and flags the interfaces it owns.
-constexpr int TY = 32;
-constexpr int TYR = TY + 6;         // staged nodes along DIR
-constexpr int TPT = TY / 8;         // nodes per thread
-
-__device__ __forceinline__ void tnode(const float (*sT)[TYR][32], int r, int tx, NodeW &w)
-{
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        w.h[v] = sT[v][r][tx];
-        w.l[v] = sT[NV + v][r][tx];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; c++) w.u[c] = sT[10 + c][r][tx];
-    w.p = sT[13][r][tx];
-}
+// Gated y / z passes streamed through registers: a warp owns 32 lines (lanes along x,
+// coalesced) of one plane index along DB and marches along DIR over ZC nodes, nodes z0 - 3 ..
+// z0 + ZC + 2, loading each node once (prefetched one step ahead).  A step forms G of the
+// interface below the current node and its strong-jump bit (4-slot ring of interfaces, bit
+// history), completes the residual of the node two below (adding the earlier directions'
+// residual, loaded a step ahead) and flags the interface of the node three below, whose jump
+// window reaches the current node.
+constexpr int ZC = 64;     // nodes of a warp's march
 
 template <int DIR, int SCHEME>
-__global__ void __launch_bounds__(256, 2) k_conv_delta_tile(Dev P, const float *__restrict__ Uf,
+__global__ void __launch_bounds__(128, 4) k_conv_delta_tile(Dev P, const float *__restrict__ Uf,
                                                            const float *__restrict__ Wf, float *__restrict__ Rf,
                                                            Strong sj, const unsigned char *__restrict__ gate,
                                                            int accumulate)
 {
     static_assert(DIR != 0, "x uses k_conv_delta_x_win");
     constexpr int DB = (DIR == 2) ? 1 : 2;
-    extern __shared__ float smem_tile[];
-    float (*sT)[TYR][32] = reinterpret_cast<float (*)[TYR][32]>(smem_tile);          // [14][TYR][32]
-    unsigned char (*sG)[32] = reinterpret_cast<unsigned char (*)[32]>(smem_tile + 14 * TYR * 32);
-    __shared__ float sD[TY + 3][NV][32];        // G of interface y0 - 3/2 + j of each line
-    __shared__ unsigned long long sJ[32];       // bit i: strong jump between staged nodes i, i + 1
-    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-    const int x = blockIdx.x * 32 + tx;
-    const int b = blockIdx.y;                     // index along DB
-    const int y0 = blockIdx.z * TY;              // first node of the tile along DIR
-    const long long st = P.st[DIR];
-    const long long vs = P.vs;
+    const int lane = threadIdx.x & 31;
+    const int nxb = (P.n[0] + 31) / 32, nzc = (P.n[DIR] + ZC - 1) / ZC;
+    const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (item >= nxb * nzc * P.n[DB]) return;                // whole warps
+    const int xb = item % nxb, zc = (item / nxb) % nzc, b = item / (nxb * nzc);
+    const int x = xb * 32 + lane;
     const bool xin = x < P.n[0];
+    const int z0 = zc * ZC;
     int ii[3];
-    ii[0] = xin ? x : 0; ii[DB] = b; ii[DIR] = 0;
+    ii[0] = min(x, P.n[0] + 2); ii[DB] = b; ii[DIR] = 0;
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
+    const long long st = P.st[DIR], vs = P.vs;
     const int n = P.n[DIR];
-    if (t < 32) sJ[t] = 0ull;
-    // stage nodes y0 - 3 .. y0 + TY + 2 (clamped to the last ghost n + 2); the gate bytes are
-    // loaded into registers and stored after the loop, so that no round waits for its load
-    constexpr int NRND = (TYR + 7) / 8;
-    unsigned char gv[NRND];
-#pragma unroll
-    for (int k = 0; k < NRND; k++) {
-        const int r = ty + 8 * k;
-        const long long id = base + (long long)min(y0 - 3 + r, n + 2) * st;
-        if (xin && r < TYR) {
-#pragma unroll
-            for (int v = 0; v < 2 * NV; v++) cp_async4(&sT[v][r][tx], Uf + v * vs + id);
-#pragma unroll
-            for (int c = 0; c < 4; c++) cp_async4(&sT[10 + c][r][tx], Wf + (W_U + c) * vs + id);
-            gv[k] = gate[id];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < NRND; k++)
-        if (xin && ty + 8 * k < TYR) sG[ty + 8 * k][tx] = gv[k];
-    // the residual this pass adds to (earlier directions), for the thread's nodes: loaded now so
-    // that its latency overlaps the staging copies
-    const int first = y0 + TPT * ty;             // first node of this thread
-    const int last = min(first + TPT, n);        // one past the last node
-    float racc[TPT][NV];
-#pragma unroll
-    for (int q = 0; q < TPT; q++)
-#pragma unroll
-        for (int v = 0; v < NV; v++)
-            racc[q][v] = (accumulate && xin && first + q < last) ? Rf[v * vs + base + (long long)(first + q) * st] : 0.f;
-    cp_async_wait_all();
-    __syncthreads();
-    const float gm1 = P.gm1f;
-    const float jump = P.jump;
-    // staged node s holds node y0 - 3 + s; interface y0 - 3/2 + j lies between staged nodes j + 1
-    // and j + 2; jump bit i covers the pair (i, i + 1).  Lanes off the grid (x >= n_x) compute on
-    // whatever their shared memory holds and write nothing.
-    if (t < 96) {
-        // tile edges: k = 0 -> y0 - 3/2, 1 -> y0 - 1/2, 2 -> y0 + TY + 1/2
-        const int k = t >> 5;
-        const int sa = (k == 2) ? TY + 3 : k + 1;
-        NodeW a, c;
-        tnode(sT, sa, tx, a);
-        tnode(sT, sa + 1, tx, c);
-        float G[NV];
-        dflux_w<DIR>(gm1, a, c, G);
-        const int j = (k == 2) ? TY + 2 : k;
-#pragma unroll
-        for (int v = 0; v < NV; v++) sD[j][v][tx] = G[v];
-        if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) atomicOr(&sJ[tx], 1ull << sa);
-    } else if (t < 160) {
-        // outermost pairs (0, 1) and (TY + 4, TY + 5): strong-jump bits only
-        const int sa = (t < 128) ? 0 : TY + 4;
-        if (jump2(jump, sT[13][sa][tx], sT[0][sa][tx], sT[13][sa + 1][tx], sT[0][sa + 1][tx]))
-            atomicOr(&sJ[tx], 1ull << sa);
-    }
-    const int s0 = TPT * ty + 3;                 // staged node of the thread's first node
-    float Gq[TPT][NV];
-    {
-        unsigned jb = 0;
-        NodeW a, c;
-        tnode(sT, s0, tx, a);
-#pragma unroll
-        for (int q = 0; q < TPT; q++) {
-            tnode(sT, s0 + q + 1, tx, c);
-            dflux_w<DIR>(gm1, a, c, Gq[q]);
-            if (jump2(jump, a.p, a.h[0], c.p, c.h[0])) jb |= 1u << q;
-#pragma unroll
-            for (int v = 0; v < NV; v++) sD[s0 + q - 1][v][tx] = Gq[q][v];
-            a = c;
-        }
-        if (jb) atomicOr(&sJ[tx], (unsigned long long)jb << s0);
-    }
-    __syncthreads();
-    if (!xin || first >= n) return;
-    const unsigned long long J = sJ[tx];
+    const int nrow = min(ZC, n - z0);
+    const int nsteps = nrow + 6;                             // nodes z0 - 3 .. z0 + nrow + 2
+    const float gm1 = P.gm1f, jump = P.jump;
     float *Ds = sj.Dst + (long long)DIR * NV * vs;
-#pragma unroll
-    for (int q = 0; q < TPT; q++) {
-        const int y = first + q;
-        if (y >= last) break;
-        const int s = s0 + q, j = s - 1;
-        float Gm[NV], Gmm[NV], Gpp[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            Gm[v] = (q >= 1) ? Gq[q - 1][v] : sD[j - 1][v][tx];
-            Gmm[v] = (q >= 2) ? Gq[q - 2][v] : sD[j - 2][v][tx];
-            Gpp[v] = (q + 1 < TPT) ? Gq[q + 1][v] : sD[j + 1][v][tx];
-        }
-        const float fac = line_facf<DIR>(P, y);
-        const long long m = base + (long long)y * st;
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            const float rr = -fac * (7.f * (Gq[q][v] + Gm[v]) - (Gpp[v] + Gmm[v])) * (1.f / 12.f);
-            Rf[v * vs + m] = accumulate ? racc[q][v] + rr : rr;
-        }
-        // interface y + 1/2 (owned by node y): gate on either side, or a strong jump between
-        // adjacent nodes of y - 2 .. y + 3 (pairs s - 2 .. s + 2)
-        if (sG[s][tx] || sG[s + 1][tx] || ((J >> (s - 2)) & 31ull)) {
-            sj.flag[m] |= (unsigned char)(1u << DIR);
-#pragma unroll
-            for (int v = 0; v < NV; v++) Ds[v * vs + m] = (6.f * Gq[q][v] + Gm[v] - Gpp[v]) * (1.f / 12.f);
-        }
+    NodeW row[4];                    // ring: slot i & 3 holds node z0 - 3 + i
+    float G[4][NV];                  // ring: slot i & 3 holds G of the interface below that node
+    float racc[2][NV];               // earlier directions' residual of the next two nodes to finish
+    unsigned jb = 0;                 // bit b: strong jump between nodes s - 1 - b and s - b
+    unsigned gq = 0;                 // byte b: gate of node s - b
+    unsigned gn;
+    {
+        const long long id = base + (long long)(z0 - 3) * st;
+        load_node(P, Uf, Wf, id, row[0]);
+        gn = gate[id];
     }
-    if (y0 == 0 && ty == 0 && (sG[2][tx] || sG[3][tx] || (J & 31ull))) {
-        // the line's first interface -1/2 (staged nodes 2 | 3), owned by this tile
-        const long long m = base - st;
-        sj.flag[m] |= (unsigned char)(1u << DIR);
+    for (int i4 = 0; i4 < nsteps; i4 += 4) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) Ds[v * vs + m] = (6.f * sD[1][v][tx] + sD[0][v][tx] - sD[2][v][tx]) * (1.f / 12.f);
+        for (int k = 0; k < 4; k++) {
+            const int i = i4 + k;
+            if (i >= nsteps) break;
+            const int s = z0 - 3 + i;
+            gq = (gq << 8) | gn;
+            if (i + 1 < nsteps) {
+                const long long id = base + (long long)min(s + 1, n + 2) * st;
+                load_node(P, Uf, Wf, id, row[(k + 1) & 3]);
+                gn = gate[id];
+            }
+            // the earlier directions' residual of node s - 1, finished at the next step
+            if (accumulate && xin && i >= 4 && i <= nrow + 3) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) racc[(k + 1) & 1][v] = Rf[v * vs + base + (long long)(s - 1) * st];
+            }
+            const NodeW &cur = row[k];
+            const NodeW &prv = row[(k + 3) & 3];
+            if (i >= 1) jb = (jb << 1) | (jump2(jump, prv.p, prv.h[0], cur.p, cur.h[0]) ? 1u : 0u);
+            if (i >= 2 && i <= nrow + 4) dflux_w<DIR>(gm1, prv, cur, G[k]);
+            if (!xin) continue;
+            // residual of node y = s - 2: G at y + 3/2, y + 1/2, y - 1/2, y - 3/2
+            if (i >= 5 && i <= nrow + 4) {
+                const int y = s - 2;
+                const float fac = line_facf<DIR>(P, y);
+                const long long m = base + (long long)y * st;
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const float r = -fac * (7.f * (G[(k + 3) & 3][v] + G[(k + 2) & 3][v]) -
+                                            (G[k][v] + G[(k + 1) & 3][v])) * (1.f / 12.f);
+                    Rf[v * vs + m] = accumulate ? racc[k & 1][v] + r : r;
+                }
+            }
+            // interface y + 1/2 of node y = s - 3 (owned nodes z0 .. z0 + nrow - 1, and -1 on the
+            // first chunk): gate of y or y + 1, or a strong jump in pairs (y - 2, y - 1) .. (y + 2, y + 3)
+            if ((i >= 6 && i <= nrow + 5) || (i == 5 && z0 == 0)) {
+                if (((gq >> 24) & 0xffu) || ((gq >> 16) & 0xffu) || (jb & 31u)) {
+                    const long long m = base + (long long)(s - 3) * st;
+                    sj.flag[m] |= (unsigned char)(1u << DIR);
+#pragma unroll
+                    for (int v = 0; v < NV; v++)
+                        Ds[v * vs + m] = (6.f * G[(k + 2) & 3][v] + G[(k + 1) & 3][v] - G[(k + 3) & 3][v]) * (1.f / 12.f);
+                }
+            }
+        }
     }
 }
-
-constexpr size_t TILE_SMEM = (size_t)14 * TYR * 32 * sizeof(float) + (size_t)TYR * 32;
 
 // Gated x and y passes in one kernel (x and y active), streamed through registers.  A warp owns
 // a strip of XS output columns of one z plane: lane l holds column x0 - 3 + l (lanes 0..2 and
@@ -2592,15 +2523,9 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
             k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, B.Dl, acc);
         } else if (gate) {
           if constexpr (DIR != 0) {
-            static bool smem_set = false;   // one attribute call per instantiation
-            if (!smem_set) {
-                cudaFuncSetAttribute(k_conv_delta_tile<DIR, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TILE_SMEM);
-                smem_set = true;
-            }
-            dim3 tg((P.n[0] + 31) / 32, P.n[DIR == 2 ? 1 : 2], (P.n[DIR] + TY - 1) / TY);
-            k_conv_delta_tile<DIR, SCHEME><<<tg, dim3(32, 8), TILE_SMEM, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B),
-                                                                            gate, acc);
+            const long long warps = (long long)((P.n[0] + 31) / 32) * ((P.n[DIR] + ZC - 1) / ZC) * P.n[DIR == 2 ? 1 : 2];
+            k_conv_delta_tile<DIR, SCHEME><<<(int)((warps + 3) / 4), 128, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B),
+                                                                             gate, acc);
           }
         } else {
             k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, acc, chunk);
