@@ -90,12 +90,13 @@ HBM_GBS = _measured_hbm()
 # dram__bytes_read.sum + dram__bytes_write.sum per interior point of one launch, from ncu captures
 # of the same kernel on a smaller grid (traffic grows with the points processed)
 DRAM_BYTES_PER_POINT = {
-    "k_conv_delta_tile": (102.7, "ncu capture of k_conv_delta_tile<2,2> in the bench at --n 160 (learned "
-                                 "form): dram__bytes_read.sum 350.8 MB + dram__bytes_write.sum 69.9 MB per "
-                                 "launch over 4.096 M points, scaled to this grid"),
-    "k_conv_delta_xy": (84.9, "ncu capture of k_conv_delta_xy<2> in the bench at --n 160 (learned form): "
-                              "dram__bytes_read.sum 272.6 MB + dram__bytes_write.sum 75.2 MB per launch "
-                              "over 4.096 M points, scaled to this grid"),
+    "k_conv_delta_tile": (104.8, "ncu capture of k_conv_delta_tile<2,2> in the bench at --n 160 (learned "
+                                 "form, 5.2 % of cells gated): dram__bytes_read.sum 358.8 MB + "
+                                 "dram__bytes_write.sum 70.2 MB per launch over 4.096 M points, scaled to "
+                                 "this grid"),
+    "k_conv_delta_xy": (87.4, "ncu capture of k_conv_delta_xy in the bench at --n 160 (learned form, 5.2 % "
+                              "of cells gated): dram__bytes_read.sum 281.8 MB + dram__bytes_write.sum 76.1 "
+                              "MB per launch over 4.096 M points, scaled to this grid"),
     "k_conv_delta_x_win": (78.2, "ncu capture of k_conv_delta_x_win<2> in the bench at --n 160 (learned "
                                  "form): dram__bytes_read.sum 251.0 MB + dram__bytes_write.sum 69.1 MB per "
                                  "launch over 4.096 M points, scaled to this grid"),
