@@ -1646,37 +1646,70 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Resident warps per SM of a 128-thread streaming kernel, from the runtime's occupancy.
+template <typename K>
+static int warps_per_sm(K kernel)
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 128, 0) != cudaSuccess || blocks < 1) blocks = 1;
+    return blocks * 4;
+}
+
+// March length of a streaming pass over `lines` warps' lines of n nodes: among the candidates
+// (32 .. 256) that fill the GPU's warp slots at least once (the passes are latency-bound, so
+// fewer resident warps run slower), the one with the least whole number of waves times the
+// steps of one warp (its nodes and the 6 halo nodes), so that the last wave is not a small
+// remainder on its own.  A warp's start-up (index set-up, the first loads' latency) counts as
+// ten steps: with it the model picks the lengths measured fastest on TGV 256^3 (128 for both
+// passes; 32 / 64 nodes ran 7 % / 4 % slower in z) and on the 512 x 256 x 64 box (64).
+static int march_length(long long lines, int n, int warps_per_sm)
+{
+    grid_for(1, 1);   // fills g_num_sms
+    const long long slots = (long long)g_num_sms * warps_per_sm;
+    int best = 32;
+    long long best_cost = -1;
+    for (int c = 32; c <= 256; c *= 2) {
+        const long long warps = lines * ((n + c - 1) / c);
+        if (c > 32 && warps < slots) break;
+        const long long cost = (warps + slots - 1) / slots * (long long)(min(c, n) + 6 + 10);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
 // Gated y / z passes streamed through registers: a warp owns 32 lines (lanes along x,
-// coalesced) of one plane index along DB and marches along DIR over ZC nodes, nodes z0 - 3 ..
-// z0 + ZC + 2, loading each node once (prefetched one step ahead).  A step forms G of the
+// coalesced) of one plane index along DB and marches along DIR over zc nodes (from
+// march_length), nodes z0 - 3 .. z0 + zc + 2, loading each node once (prefetched one step ahead).  A step forms G of the
 // interface below the current node and its strong-jump bit (4-slot ring of interfaces, bit
 // history), completes the residual of the node two below (adding the earlier directions'
 // residual, loaded a step ahead) and flags the interface of the node three below, whose jump
 // window reaches the current node.
-constexpr int ZC = 64;     // nodes of a warp's march
 
 template <int DIR, int SCHEME>
 __global__ void __launch_bounds__(128, 4) k_conv_delta_tile(Dev P, const float *__restrict__ Uf,
                                                            const float *__restrict__ Wf, float *__restrict__ Rf,
                                                            Strong sj, const unsigned char *__restrict__ gate,
-                                                           int accumulate)
+                                                           int accumulate, int zc)
 {
     static_assert(DIR != 0, "x uses k_conv_delta_x_win");
     constexpr int DB = (DIR == 2) ? 1 : 2;
     const int lane = threadIdx.x & 31;
-    const int nxb = (P.n[0] + 31) / 32, nzc = (P.n[DIR] + ZC - 1) / ZC;
+    const int nxb = (P.n[0] + 31) / 32, nzc = (P.n[DIR] + zc - 1) / zc;
     const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (item >= nxb * nzc * P.n[DB]) return;                // whole warps
-    const int xb = item % nxb, zc = (item / nxb) % nzc, b = item / (nxb * nzc);
+    const int xb = item % nxb, zk = (item / nxb) % nzc, b = item / (nxb * nzc);
     const int x = xb * 32 + lane;
     const bool xin = x < P.n[0];
-    const int z0 = zc * ZC;
+    const int z0 = zk * zc;
     int ii[3];
     ii[0] = min(x, P.n[0] + 2); ii[DB] = b; ii[DIR] = 0;
     const long long base = node_index(P, ii[0], ii[1], ii[2]);
     const long long st = P.st[DIR], vs = P.vs;
     const int n = P.n[DIR];
-    const int nrow = min(ZC, n - z0);
+    const int nrow = min(zc, n - z0);
     const int nsteps = nrow + 6;                             // nodes z0 - 3 .. z0 + nrow + 2
     const float gm1 = P.gm1f, jump = P.jump;
     float *Ds = sj.Dst + (long long)DIR * NV * vs;
@@ -1743,7 +1776,7 @@ __global__ void __launch_bounds__(128, 4) k_conv_delta_tile(Dev P, const float *
 // Gated x and y passes in one kernel (x and y active), streamed through registers.  A warp owns
 // a strip of XS output columns of one z plane: lane l holds column x0 - 3 + l (lanes 0..2 and
 // 29..31 are the strip's halo, their columns clamped to the last ghost), and marches along y
-// over YC rows, rows y0 - 3 .. y0 + YC + 2.  Each step loads the next row into registers
+// over yc rows (from march_length), rows y0 - 3 .. y0 + yc + 2.  Each step loads the next row into registers
 // (prefetched one step ahead) and
 //   - forms G_y of the interface below the current row (the node pair in the lane's registers)
 //     and its strong-jump bit, kept in a 4-slot ring of interfaces and a bit history;
@@ -1757,7 +1790,6 @@ __global__ void __launch_bounds__(128, 4) k_conv_delta_tile(Dev P, const float *
 // No shared memory and no block barriers: every warp streams independently, and the x pass's
 // reads of the node arrays and its residual round trip through HBM are gone.
 constexpr int XS = 26;     // output columns of a strip (lanes 3 .. 28)
-constexpr int YC = 64;     // rows of a warp's march
 
 __device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj, int dir, long long m,
                                                  const float D[NV])
@@ -1784,14 +1816,14 @@ __device__ __forceinline__ NodeW shfl_node_down(const NodeW &w)
 
 __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf, float *__restrict__ Rf,
-                                                         Strong sj, const unsigned char *__restrict__ gate)
+                                                         Strong sj, const unsigned char *__restrict__ gate, int yc)
 {
     const int lane = threadIdx.x & 31;
-    const int nxs = (P.n[0] + XS - 1) / XS, nyc = (P.n[1] + YC - 1) / YC;
+    const int nxs = (P.n[0] + XS - 1) / XS, nyc = (P.n[1] + yc - 1) / yc;
     const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (item >= nxs * nyc * P.n[2]) return;                 // whole warps
-    const int xs = item % nxs, yc = (item / nxs) % nyc, kz = item / (nxs * nyc);
-    const int x0 = xs * XS, y0 = yc * YC;
+    const int xs = item % nxs, yk = (item / nxs) % nyc, kz = item / (nxs * nyc);
+    const int x0 = xs * XS, y0 = yk * yc;
     const int x = x0 - 3 + lane;
     const bool own = lane >= 3 && lane <= 28 && x < P.n[0];          // output column of this strip
     // x interfaces owned: x + 1/2 of the output columns, and -1/2 (lane 2) on the first strip
@@ -1799,7 +1831,7 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
     const long long st = P.st[1], vs = P.vs;
     const long long cb = node_index(P, min(x, P.n[0] + 2), 0, kz);    // the lane's column, y = 0
     const int n = P.n[1];
-    const int nrow = min(YC, n - y0);
+    const int nrow = min(yc, n - y0);
     const int nsteps = nrow + 6;                                    // rows y0 - 3 .. y0 + nrow + 2
     const float gm1 = P.gm1f, jump = P.jump;
     const float facx = own ? line_facf<0>(P, x) : 0.f;
@@ -1888,8 +1920,12 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
 // Launch of the fused gated x + y pass (replaces the x pass and the y pass of the stage).
 static void launch_delta_xy(const Dev &P, const Bufs &B, cudaStream_t s)
 {
-    const long long warps = (long long)((P.n[0] + XS - 1) / XS) * ((P.n[1] + YC - 1) / YC) * P.n[2];
-    k_conv_delta_xy<<<(int)((warps + 3) / 4), 128, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), B.gate);
+    static int per_sm = 0;         // resident warps per SM, from the runtime's occupancy
+    if (!per_sm) per_sm = warps_per_sm(k_conv_delta_xy);
+    const long long lines = (long long)((P.n[0] + XS - 1) / XS) * P.n[2];
+    const int yc = march_length(lines, P.n[1], per_sm);
+    const long long warps = lines * ((P.n[1] + yc - 1) / yc);
+    k_conv_delta_xy<<<(int)((warps + 3) / 4), 128, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), B.gate, yc);
 }
 
 // The fused pass runs for the gated mixed path on Cartesian / rectilinear grids with x and y active.
@@ -2523,9 +2559,13 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
             k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, B.Dl, acc);
         } else if (gate) {
           if constexpr (DIR != 0) {
-            const long long warps = (long long)((P.n[0] + 31) / 32) * ((P.n[DIR] + ZC - 1) / ZC) * P.n[DIR == 2 ? 1 : 2];
+            static int per_sm = 0;
+            if (!per_sm) per_sm = warps_per_sm(k_conv_delta_tile<DIR, SCHEME>);
+            const long long lines = (long long)((P.n[0] + 31) / 32) * P.n[DIR == 2 ? 1 : 2];
+            const int zc = march_length(lines, P.n[DIR], per_sm);
+            const long long warps = lines * ((P.n[DIR] + zc - 1) / zc);
             k_conv_delta_tile<DIR, SCHEME><<<(int)((warps + 3) / 4), 128, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B),
-                                                                             gate, acc);
+                                                                             gate, acc, zc);
           }
         } else {
             k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, acc, chunk);
