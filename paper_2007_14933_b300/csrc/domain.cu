@@ -38,6 +38,11 @@ struct osbli_dom {
     Bufs B[OSBLI_DOMAIN_MAX_SLABS];
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // one stream per slab, forked from `stream` at every stage and joined at its end, and the
+    // events that order the slabs' work against their neighbours'
+    cudaStream_t ss[OSBLI_DOMAIN_MAX_SLABS] = {};
+    cudaEvent_t e0 = nullptr;
+    cudaEvent_t eg[OSBLI_DOMAIN_MAX_SLABS] = {}, ec[OSBLI_DOMAIN_MAX_SLABS] = {}, ef[OSBLI_DOMAIN_MAX_SLABS] = {};
     cudaGraphExec_t gexec = nullptr;
     int launches = 0, copies = 0;
     int *h_err = nullptr;   // pinned, one word per slab
@@ -87,6 +92,13 @@ static void free_dom(osbli_dom *d)
     if (d->gexec) cudaGraphExecDestroy(d->gexec);
     for (int s = 0; s < d->nslab; s++)
         if (d->slab[s]) osbli_destroy(d->slab[s]);
+    for (int s = 0; s < OSBLI_DOMAIN_MAX_SLABS; s++) {
+        if (d->ss[s]) cudaStreamDestroy(d->ss[s]);
+        if (d->eg[s]) cudaEventDestroy(d->eg[s]);
+        if (d->ec[s]) cudaEventDestroy(d->ec[s]);
+        if (d->ef[s]) cudaEventDestroy(d->ef[s]);
+    }
+    if (d->e0) cudaEventDestroy(d->e0);
     if (d->h_err) cudaFreeHost(d->h_err);
     if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
 }
@@ -130,6 +142,16 @@ extern "C" int osbli_domain_create(const osbli_params *p, int nslab, void *cuda_
     }
     if (cudaMallocHost(&d->h_err, OSBLI_DOMAIN_MAX_SLABS * sizeof(int)) != cudaSuccess)
         return fail(derr(d, OSBLI_ENOMEM, "pinned host allocation failed"));
+    {
+        cudaError_t e = cudaEventCreateWithFlags(&d->e0, cudaEventDisableTiming);
+        for (int s = 0; s < nslab && e == cudaSuccess; s++) {
+            e = cudaStreamCreateWithFlags(&d->ss[s], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->eg[s], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->ec[s], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->ef[s], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return fail(derr(d, OSBLI_ECUDA, "slab streams / events: %s", cudaGetErrorString(e)));
+    }
     for (int s = 0; s < nslab; s++) {
         osbli_params q = *p;
         q.nz = d->nz[s];
@@ -167,66 +189,87 @@ static cudaError_t copy_planes(const Dev &Pa, void *a, const Dev &Pb, const void
                              (size_t)Pb.vs * es, npl * plane, nvar, cudaMemcpyDeviceToDevice, s);
 }
 
-// Conserved-state halos: low ghost planes k = -3..-1 from the low neighbour's k = n-3..n-1, high
-// ghost planes k = n..n+2 from the high neighbour's k = 0..2.
-static int exchange_state(osbli_dom *d)
+// Conserved-state halos of slab s, on its stream: low ghost planes k = -3..-1 from the low
+// neighbour's k = n-3..n-1, high ghost planes k = n..n+2 from the high neighbour's k = 0..2.
+static int exchange_state(osbli_dom *d, int s)
 {
-    int n = 0;
-    for (int s = 0; s < d->nslab; s++) {
-        const int L = d->lo[s], H = d->hi[s];
-        if (L >= 0) {
-            DCK(d, copy_planes(d->P[s], d->B[s].U, d->P[L], d->B[L].U, 0, d->nz[L], GH, NV, sizeof(double), d->stream));
-            n++;
-        }
-        if (H >= 0) {
-            DCK(d, copy_planes(d->P[s], d->B[s].U, d->P[H], d->B[H].U, d->nz[s] + GH, GH, GH, NV, sizeof(double),
-                               d->stream));
-            n++;
-        }
+    const int L = d->lo[s], H = d->hi[s];
+    if (L >= 0) {
+        DCK(d, copy_planes(d->P[s], d->B[s].U, d->P[L], d->B[L].U, 0, d->nz[L], GH, NV, sizeof(double), d->ss[s]));
+        d->copies++;
     }
-    d->copies += n;
+    if (H >= 0) {
+        DCK(d, copy_planes(d->P[s], d->B[s].U, d->P[H], d->B[H].U, d->nz[s] + GH, GH, GH, NV, sizeof(double),
+                           d->ss[s]));
+        d->copies++;
+    }
     return OSBLI_OK;
 }
 
-// z-direction viscous fluxes (components 8..11 of V / Vf): ghost planes k = -2, -1 and n, n+1.
-static int exchange_viscous(osbli_dom *d)
+// z-direction viscous fluxes (components 8..11 of V / Vf) of slab s, on its stream: ghost planes
+// k = -2, -1 and n, n+1.
+static int exchange_viscous(osbli_dom *d, int s)
 {
     if (!d->P[0].viscous) return OSBLI_OK;
     const bool mixed = d->P[0].mixed != 0;
     const size_t es = mixed ? sizeof(float) : sizeof(double);
-    auto base = [&](int s) -> char * {
-        return mixed ? (char *)(d->B[s].Vf + 8 * d->P[s].vs) : (char *)(d->B[s].V + 8 * d->P[s].vs);
+    auto base = [&](int q) -> char * {
+        return mixed ? (char *)(d->B[q].Vf + 8 * d->P[q].vs) : (char *)(d->B[q].V + 8 * d->P[q].vs);
     };
-    int n = 0;
-    for (int s = 0; s < d->nslab; s++) {
-        const int L = d->lo[s], H = d->hi[s];
-        if (L >= 0) {
-            DCK(d, copy_planes(d->P[s], base(s), d->P[L], base(L), GH - 2, d->nz[L] + GH - 2, 2, 4, es, d->stream));
-            n++;
-        }
-        if (H >= 0) {
-            DCK(d, copy_planes(d->P[s], base(s), d->P[H], base(H), d->nz[s] + GH, GH, 2, 4, es, d->stream));
-            n++;
-        }
+    const int L = d->lo[s], H = d->hi[s];
+    if (L >= 0) {
+        DCK(d, copy_planes(d->P[s], base(s), d->P[L], base(L), GH - 2, d->nz[L] + GH - 2, 2, 4, es, d->ss[s]));
+        d->copies++;
     }
-    d->copies += n;
+    if (H >= 0) {
+        DCK(d, copy_planes(d->P[s], base(s), d->P[H], base(H), d->nz[s] + GH, GH, 2, 4, es, d->ss[s]));
+        d->copies++;
+    }
     return OSBLI_OK;
 }
 
-// One RK stage (stage >= 0) or one residual evaluation (stage < 0) of every slab.
+// stream s waits for the event of slab s's low and high neighbours
+static int wait_neighbours(osbli_dom *d, int s, cudaEvent_t *ev)
+{
+    if (d->lo[s] >= 0 && d->lo[s] != s) DCK(d, cudaStreamWaitEvent(d->ss[s], ev[d->lo[s]], 0));
+    if (d->hi[s] >= 0 && d->hi[s] != s && d->hi[s] != d->lo[s]) DCK(d, cudaStreamWaitEvent(d->ss[s], ev[d->hi[s]], 0));
+    return OSBLI_OK;
+}
+
+// One RK stage (stage >= 0) or one residual evaluation (stage < 0) of every slab.  The slabs run
+// on their own streams, forked from the domain stream and joined back at the end, so that their
+// launches overlap; the events keep the order the data needs:
+//   a slab's ghost fill  ->  the state copies into its neighbours (they read its planes, x / y
+//                            ghost columns included);
+//   the state copies into a slab  ->  its convective / viscous passes (same stream);
+//   the neighbours' passes  ->  the viscous-flux copies into a slab and its update (the copies
+//                            read the neighbours' fluxes; the update overwrites the planes the
+//                            neighbours' state copies read).
 static int enqueue(osbli_dom *d, int stage)
 {
     int rc;
-    for (int s = 0; s < d->nslab; s++) {
-        launch_ghosts(d->P[s], d->B[s], d->stream);   // x, y and physical z faces
+    const int ns = d->nslab;
+    DCK(d, cudaEventRecord(d->e0, d->stream));
+    for (int s = 0; s < ns; s++) {
+        DCK(d, cudaStreamWaitEvent(d->ss[s], d->e0, 0));
+        launch_ghosts(d->P[s], d->B[s], d->ss[s]);   // x, y and physical z faces
         d->launches += d->P[s].active[0] + d->P[s].active[1] + d->P[s].active[2];
+        DCK(d, cudaEventRecord(d->eg[s], d->ss[s]));
     }
-    if ((rc = exchange_state(d)) != OSBLI_OK) return rc;
-    for (int s = 0; s < d->nslab; s++) d->launches += launch_stage_core(d->P[s], d->B[s], stage < 0 ? 0 : stage, d->stream);
-    if ((rc = exchange_viscous(d)) != OSBLI_OK) return rc;
-    for (int s = 0; s < d->nslab; s++)
-        d->launches += stage < 0 ? launch_residual_finish(d->P[s], d->B[s], d->stream)
-                                 : launch_stage_finish(d->P[s], d->B[s], stage, d->stream);
+    for (int s = 0; s < ns; s++) {
+        if ((rc = wait_neighbours(d, s, d->eg)) != OSBLI_OK) return rc;
+        if ((rc = exchange_state(d, s)) != OSBLI_OK) return rc;
+        d->launches += launch_stage_core(d->P[s], d->B[s], stage < 0 ? 0 : stage, d->ss[s]);
+        DCK(d, cudaEventRecord(d->ec[s], d->ss[s]));
+    }
+    for (int s = 0; s < ns; s++) {
+        if ((rc = wait_neighbours(d, s, d->ec)) != OSBLI_OK) return rc;
+        if ((rc = exchange_viscous(d, s)) != OSBLI_OK) return rc;
+        d->launches += stage < 0 ? launch_residual_finish(d->P[s], d->B[s], d->ss[s])
+                                 : launch_stage_finish(d->P[s], d->B[s], stage, d->ss[s]);
+        DCK(d, cudaEventRecord(d->ef[s], d->ss[s]));
+    }
+    for (int s = 0; s < ns; s++) DCK(d, cudaStreamWaitEvent(d->stream, d->ef[s], 0));
     DCK(d, cudaGetLastError());
     return OSBLI_OK;
 }
