@@ -256,6 +256,17 @@ __device__ __forceinline__ void ldsm_x4(const void *p, uint32_t &r0, uint32_t &r
                  : "r"(a));
 }
 
+// (d0, d1) = (a0, a1) * b + c, both lanes one round-to-nearest FMA (the packed FP32 FMA of this
+// GPU: one instruction for the two features of an A-fragment register)
+__device__ __forceinline__ void fma2(float a0, float a1, float b, float c, float &d0, float &d1)
+{
+    asm("{\n\t.reg .b64 a, b, c, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %4};\n\tmov.b64 c, {%5, %5};\n\t"
+        "fma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b), "f"(c));
+}
+
 __device__ __forceinline__ void cpa4(float *smem, const float *gmem)
 {
     const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
@@ -371,6 +382,9 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
                     const float *r0 = live0 ? pb[rn0 % 3] + ((rn0 / 3) * 5 + q0) * SQS : ring;
                     const float *r1 = live1 ? pb[rn1 % 3] + ((rn1 / 3) * 5 + q1) * SQS : ring;
                     const float *rowp = (hb ? r1 : r0) + g + xo;
+                    // odd lanes' second column is W1r's zero pad column: they re-read v0 (a finite
+                    // value inside the row), whose product with the zero weight adds nothing
+                    const float *rowq = rowp + (odd ? 0 : 1);
                     const bool live = hb ? live1 : live0;
 #pragma unroll
                     for (int h = 0; h < 4; h++) {
@@ -380,11 +394,9 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
                         };
                         const float M = (q0 == q1) ? Mq(q0) : (hb ? Mq(q1) : Mq(q0));
                         const float A = (q0 == q1) ? Aq(q0) : (hb ? Aq(q1) : Aq(q0));
-                        // odd lanes' second column is the zero pad: re-read v0 (stays inside the row)
-                        const float v0 = rowp[8 * h], v1 = rowp[8 * h + (odd ? 0 : 1)];
-                        const float f0 = live ? fmaf(v0, M, -A) : 0.f;
-                        const float f1 = (live && !odd) ? fmaf(v1, M, -A) : 0.f;
-                        a[h >> 1][(h & 1) + 2 * half] = pack2(f0, f1);
+                        float f0, f1;
+                        fma2(rowp[8 * h], rowq[8 * h], M, -A, f0, f1);
+                        a[h >> 1][(h & 1) + 2 * half] = live ? pack2(f0, f1) : 0u;
                     }
                 }
 #pragma unroll
