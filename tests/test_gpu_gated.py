@@ -80,12 +80,17 @@ def _cases():
     cfg3, U3 = I.riemann2d(45, quad, scheme=I.WENO5JS, ny=38)
     cfg4, U4, _ = I.sod(N=100, scheme=I.TENO5)
     cfg5, U5 = I.tgv(n=(40, 33, 1), Ma=0.8, Re=400.0, scheme=I.TENO6)
+    # x inactive: y and z take the streamed single-direction pass (no fused x + y pass)
+    n6 = (1, 35, 34)
+    cfg6 = dict(n=n6, gamma=1.4, Re=0.0, Ma=1.0, scheme=I.TENO5, teno_ct=1e-5, bc=[[0, 0]] * 3,
+                h=(1.0, 0.2, 0.3))
+    U6 = I.random_state(n6, seed=12, shocky=True)
     return [("tgv3d_teno5", cfg1, U1), ("random3d_jumps", cfg2, U2), ("riemann2d_weno", cfg3, U3),
-            ("sod1d_x_only", cfg4, U4), ("tgv2d_teno6_viscous", cfg5, U5)]
+            ("sod1d_x_only", cfg4, U4), ("tgv2d_teno6_viscous", cfg5, U5), ("yz2d_jumps", cfg6, U6)]
 
 
 @pytest.mark.parametrize("frac", [0.0, 0.3, 0.6])
-@pytest.mark.parametrize("case", range(5))
+@pytest.mark.parametrize("case", range(6))
 def test_gated_residual_matches_oracle(case, frac):
     name, cfg, U = _cases()[case]
     gate = mask(U.shape[1:], frac, seed=case)
