@@ -1447,50 +1447,6 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
     D[4] = H * s04 + a * un * d40 + 0.5f * q2 * g[1] + ut1 * g[2] + ut2 * g[3];
 }
 
-// Central 4th-order interface flux in delta form (the cheap flux of interfaces the learned
-// sensor leaves ungated): F_{m+1/2} = [7 (F_m + F_{m+1}) - (F_{m-1} + F_{m+2})] / 12, i.e.
-// D = (7 dF_{m+1} - dF_{m-1} - dF_{m+2}) / 12 with dF_k = F_k - F_m from the product rule.
-template <int DIR>
-__device__ __forceinline__ void node_dflux(const Dev &P, const float *__restrict__ Uf,
-                                           const float *__restrict__ Wf, long long m, long long id,
-                                           float dF[NV])
-{
-    const long long vs = P.vs;
-    const float gm1 = P.gm1f;
-    float dU[NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) dU[v] = (Uf[v * vs + id] - Uf[v * vs + m]) + (Uf[(NV + v) * vs + id] - Uf[(NV + v) * vs + m]);
-    const float irk = __fdividef(1.f, Uf[id]);
-    float du[3], uk[3], uc[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        uc[c] = Wf[(W_U + c) * vs + m];
-        du[c] = (dU[1 + c] - uc[c] * dU[0]) * irk;
-        uk[c] = uc[c] + du[c];
-    }
-    const float dmu = dU[1] * uk[0] + dU[2] * uk[1] + dU[3] * uk[2] + Uf[1 * vs + m] * du[0] +
-                      Uf[2 * vs + m] * du[1] + Uf[3 * vs + m] * du[2];
-    const float dp = gm1 * (dU[4] - 0.5f * dmu);
-    const float unk = uk[DIR], dun = du[DIR];
-#pragma unroll
-    for (int v = 0; v < NV; v++) dF[v] = unk * dU[v] + dun * Uf[v * vs + m];
-    dF[1 + DIR] += dp;
-    dF[4] += (Wf[W_P * vs + m] + dp) * dun + dp * uc[DIR];
-}
-
-template <int DIR>
-__device__ __forceinline__ void central_delta(const Dev &P, const float *__restrict__ Uf,
-                                              const float *__restrict__ Wf, long long m, long long st,
-                                              float D[NV], float dF1[NV])
-{
-    float fp1[NV], fp2[NV];
-    node_dflux<DIR>(P, Uf, Wf, m, m - st, dF1);
-    node_dflux<DIR>(P, Uf, Wf, m, m + st, fp1);
-    node_dflux<DIR>(P, Uf, Wf, m, m + 2 * st, fp2);
-#pragma unroll
-    for (int v = 0; v < NV; v++) D[v] = (7.f * fp1[v] - dF1[v] - fp2[v]) * (1.f / 12.f);
-}
-
 // One interface of the delta-form mixed path.  An interface whose stencil holds a strong jump is
 // flagged (bit DIR of flag[m], m = left node), its FP32 D kept in Dst (plane set DIR) and its
 // index appended to the direction's list; after the convective passes k_patch_fix recomputes the
@@ -1502,11 +1458,10 @@ template <int DIR, int SCHEME>
 __device__ __forceinline__ void delta_flagged(const Dev &P, const float *__restrict__ Uf,
                                               const float *__restrict__ Wf, long long m, long long st,
                                               float es, float D[NV], float dF1[NV], const Strong &sj,
-                                              bool own, const unsigned char *__restrict__ gate)
+                                              bool own)
 {
     const bool strong = strong_jump(P, Uf, Wf, m, st);
-    if (!gate || strong || gate[m] || gate[m + st]) delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, es, D, dF1);
-    else central_delta<DIR>(P, Uf, Wf, m, st, D, dF1);
+    delta_flux<DIR, SCHEME>(P, Uf, Wf, m, st, es, D, dF1);
     if (!own || !strong) return;
     // the stage's flags were cleared by the primitives pass; one owner per interface, and the
     // directions run one after another, so this read-modify-write of the byte is unshared
@@ -1523,7 +1478,6 @@ template <int DIR, int SCHEME>
 __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf,
                                                          float *__restrict__ Rf, Strong sj,
-                                                         const unsigned char *__restrict__ gate,
                                                          int accumulate, int chunk, const Thr2 &th)
 {
     constexpr int DA = (DIR == 0) ? 1 : 0, DB = (DIR == 2) ? 1 : 2;
@@ -1538,7 +1492,7 @@ __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk
     const long long st = P.st[DIR];
     const float es = (float)line_eps<DIR>(P, a, b);
     float Dm[NV], dF1[NV];
-    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, es, Dm, dF1, sj, s0 == 0, gate);
+    delta_flagged<DIR, SCHEME>(P, Uf, Wf, base + (long long)(s0 - 1) * st, st, es, Dm, dF1, sj, s0 == 0);
     for (int m = s0; m < s1; m++) {
         const long long id = base + (long long)m * st;
         // the residual of the earlier directions, loaded before the interface arithmetic
@@ -1546,7 +1500,7 @@ __device__ __forceinline__ void conv_char_delta_body(const Dev &P, const Blk &bk
 #pragma unroll
         for (int v = 0; v < NV; v++) racc[v] = accumulate ? Rf[v * P.vs + id] : 0.f;
         float Dp[NV];
-        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, sj, true, gate);
+        delta_flagged<DIR, SCHEME>(P, Uf, Wf, id, st, es, Dp, dF1, sj, true);
         const float fac = line_facf<DIR>(P, m);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -1562,10 +1516,9 @@ template <int DIR, int SCHEME>
 __global__ void __launch_bounds__(128, 5) k_conv_char_delta(Dev P, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf,
                                                          float *__restrict__ Rf, Strong sj,
-                                                         const unsigned char *__restrict__ gate,
                                                          int accumulate, int chunk)
 {
-    conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, accumulate, chunk, self_thr2());
+    conv_char_delta_body<DIR, SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, accumulate, chunk, self_thr2());
 }
 
 // Gated passes (learned sensor on): most interfaces take the central flux.  With one flux
@@ -1600,7 +1553,9 @@ __device__ __forceinline__ void load_node(const Dev &P, const float *__restrict_
     w.p = Wf[W_P * vs + id];
 }
 
-// F_k - F_c of node k relative to node c by the product rule (the expressions of node_dflux)
+// F_k - F_c of node k relative to node c by the product rule: dU from the hi/lo pairs (accurate
+// to FP32 relative to the difference itself), du = u_k - u_c and dp from dU, and
+// F_k - F_c = u_k (U_k - U_c) + (u_k - u_c) U_c plus the pressure terms dp and p_k u_k - p_c u_c
 template <int DIR>
 __device__ __forceinline__ void dflux_w(float gm1, const NodeW &c, const NodeW &k, float dF[NV])
 {
@@ -1629,17 +1584,12 @@ __device__ __forceinline__ bool jump2(float jump, float p0, float r0, float p1, 
     return fmaxf(p0, p1) > jump * fminf(p0, p1) || fmaxf(r0, r1) > jump * fminf(r0, r1);
 }
 
-// Asynchronous 4- and 8-byte global -> shared copies (no register staging, so a thread can have
-// all of its tile's copies in flight at once), and the wait for the thread's outstanding copies.
+// Asynchronous 4-byte global -> shared copy (no register staging, so a thread can have all of
+// its segment's copies in flight at once), and the wait for the thread's outstanding copies.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
-{
-    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all()
 {
@@ -2038,7 +1988,6 @@ __global__ void __launch_bounds__(256) k_conv_delta_x_win(Dev P, const float *__
 template <int SCHEME>
 __device__ __forceinline__ void conv_left_x_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
                                                      const float *__restrict__ Wf, Strong sj,
-                                                     const unsigned char *__restrict__ gate,
                                                      float *__restrict__ Dl)
 {
     const int nseg = (P.n[0] + XSEG - 1) / XSEG;
@@ -2051,7 +2000,7 @@ __device__ __forceinline__ void conv_left_x_body(const Dev &P, const Blk &bk, co
     const long long base = node_index(P, 0, j, k);
     float D[NV], unused[NV];
     const float es = (float)line_eps<0>(P, j, k);
-    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, es, D, unused, sj, seg == 0, gate);
+    delta_flagged<0, SCHEME>(P, Uf, Wf, base + seg * XSEG - 1, 1, es, D, unused, sj, seg == 0);
 #pragma unroll
     for (int v = 0; v < NV; v++) Dl[t * NV + v] = D[v];
 }
@@ -2059,17 +2008,15 @@ __device__ __forceinline__ void conv_left_x_body(const Dev &P, const Blk &bk, co
 template <int SCHEME>
 __global__ void __launch_bounds__(128) k_conv_left_x(Dev P, const float *__restrict__ Uf,
                                                      const float *__restrict__ Wf, Strong sj,
-                                                     const unsigned char *__restrict__ gate,
                                                      float *__restrict__ Dl)
 {
-    conv_left_x_body<SCHEME>(P, self_blk(), Uf, Wf, sj, gate, Dl);
+    conv_left_x_body<SCHEME>(P, self_blk(), Uf, Wf, sj, Dl);
 }
 
 template <int SCHEME>
 __device__ __forceinline__ void conv_char_delta_x_body(const Dev &P, const Blk &bk, const float *__restrict__ Uf,
                                                             const float *__restrict__ Wf,
                                                             float *__restrict__ Rf, Strong sj,
-                                                            const unsigned char *__restrict__ gate,
                                                             const float *__restrict__ Dl, int accumulate)
 {
     __shared__ float sD[NV][XSEG + 1];
@@ -2084,7 +2031,7 @@ __device__ __forceinline__ void conv_char_delta_x_body(const Dev &P, const Blk &
     if (i < P.n[0]) {
         float D[NV];
         const float es = (float)line_eps<0>(P, j, k);
-        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, es, D, dF1, sj, true, gate);
+        delta_flagged<0, SCHEME>(P, Uf, Wf, base + i, 1, es, D, dF1, sj, true);
 #pragma unroll
         for (int v = 0; v < NV; v++) sD[v][t + 1] = D[v];
     }
@@ -2104,10 +2051,9 @@ template <int SCHEME>
 __global__ void __launch_bounds__(XSEG) k_conv_char_delta_x(Dev P, const float *__restrict__ Uf,
                                                             const float *__restrict__ Wf,
                                                             float *__restrict__ Rf, Strong sj,
-                                                            const unsigned char *__restrict__ gate,
                                                             const float *__restrict__ Dl, int accumulate)
 {
-    conv_char_delta_x_body<SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, gate, Dl, accumulate);
+    conv_char_delta_x_body<SCHEME>(P, self_blk(), Uf, Wf, Rf, sj, Dl, accumulate);
 }
 
 // Recomputation of one flagged interface m of direction DIR: across a strong jump the FP64
@@ -2553,10 +2499,9 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
         } else if (DIR == 0) {
             const int nseg = (P.n[0] + XSEG - 1) / XSEG;
             const long long lefts = (long long)P.n[1] * P.n[2] * nseg;
-            k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, strong_of(B), gate,
-                                                                             B.Dl);
+            k_conv_left_x<SCHEME><<<(int)((lefts + 127) / 128), 128, 0, s>>>(P, B.Uf, B.Wf, strong_of(B), B.Dl);
             dim3 g(P.n[1] * P.n[2], nseg);
-            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, B.Dl, acc);
+            k_conv_char_delta_x<SCHEME><<<g, XSEG, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), B.Dl, acc);
         } else if (gate) {
           if constexpr (DIR != 0) {
             static int per_sm = 0;
@@ -2568,7 +2513,7 @@ static void conv_char_launch(const Dev &P, const Bufs &B, int acc, int chunk, di
                                                                              gate, acc, zc);
           }
         } else {
-            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), gate, acc, chunk);
+            k_conv_char_delta<DIR, SCHEME><<<grd, blk, 0, s>>>(P, B.Uf, B.Wf, B.Rf, strong_of(B), acc, chunk);
         }
     } else if (P.mixed) {
         k_conv_char_mixed<DIR, SCHEME, CURV><<<grd, blk, 0, s>>>(P, B.U, B.Uf, B.Wf, B.M, B.Rf, acc, chunk);
@@ -2884,21 +2829,21 @@ template <int SCHEME>
 __global__ void __launch_bounds__(128) k_ens_left_x(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(ENS_LX)
-    conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), nullptr, B.Dl);
+    conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), B.Dl);
 }
 
 template <int SCHEME>
 __global__ void __launch_bounds__(XSEG) k_ens_delta_x(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(ENS_CX)
-    conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, B.Dl, e.acc[0]);
+    conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), B.Dl, e.acc[0]);
 }
 
 template <int DIR, int SCHEME>
 __global__ void __launch_bounds__(128, 5) k_ens_delta(const EnsProb *tab, const int *start, int nprob)
 {
     ENS_PROLOGUE(DIR == 1 ? ENS_CY : ENS_CZ)
-    conv_char_delta_body<DIR, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[DIR], e.chunk[DIR],
+    conv_char_delta_body<DIR, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), e.acc[DIR], e.chunk[DIR],
                                       self_thr2());
 }
 
@@ -3043,15 +2988,15 @@ __global__ void __launch_bounds__(ENS_PT, MIXED ? 2 : 1) k_ens_persistent(EnsLau
                         if constexpr (MIXED) prim_mixed_body(P, bk, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
                         else prim_body(P, bk, B.U, B.W);
                     } else if (ph == ENS_LX) {
-                        if constexpr (MIXED) conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), nullptr, B.Dl);
+                        if constexpr (MIXED) conv_left_x_body<SCHEME>(P, bk, B.Uf, B.Wf, strong_of(B), B.Dl);
                     } else if (ph == ENS_CX) {
-                        if constexpr (MIXED) conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, B.Dl, e.acc[0]);
+                        if constexpr (MIXED) conv_char_delta_x_body<SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), B.Dl, e.acc[0]);
                         else conv_char_body<0, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[0], e.chunk[0], th);
                     } else if (ph == ENS_CY) {
-                        if constexpr (MIXED) conv_char_delta_body<1, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[1], e.chunk[1], th);
+                        if constexpr (MIXED) conv_char_delta_body<1, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), e.acc[1], e.chunk[1], th);
                         else conv_char_body<1, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[1], e.chunk[1], th);
                     } else if (ph == ENS_CZ) {
-                        if constexpr (MIXED) conv_char_delta_body<2, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), nullptr, e.acc[2], e.chunk[2], th);
+                        if constexpr (MIXED) conv_char_delta_body<2, SCHEME>(P, bk, B.Uf, B.Wf, B.Rf, strong_of(B), e.acc[2], e.chunk[2], th);
                         else conv_char_body<2, SCHEME, false>(P, bk, B.U, B.W, B.M, B.R, e.acc[2], e.chunk[2], th);
                     } else if (ph == ENS_FIX) {
                         if constexpr (MIXED) patch_fix_body<SCHEME>(P, bk, B.U, B.Uf, B.Wf, strong_of(B));
