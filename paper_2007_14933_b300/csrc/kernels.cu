@@ -1809,7 +1809,7 @@ __device__ __forceinline__ NodeW shfl_node_down(const NodeW &w)
     return e;
 }
 
-__global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__restrict__ Uf,
+__global__ void __launch_bounds__(128, 4) k_conv_delta_xy(Dev P, const float *__restrict__ Uf,
                                                          const float *__restrict__ Wf, float *__restrict__ Rf,
                                                          Strong sj, const unsigned char *__restrict__ gate, int yc)
 {
@@ -1831,8 +1831,11 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
     const float gm1 = P.gm1f, jump = P.jump;
     const float facx = own ? line_facf<0>(P, x) : 0.f;
     NodeW row[4];                    // ring: slot i & 3 holds row y0 - 3 + i
-    float Gy[4][NV];                 // ring: slot i & 3 holds G_y of the interface below row y0 - 3 + i
-    float Rx[2][NV];                 // x flux differences of the last two rows with x work
+    // each thread's rings live in shared memory (its own slots, no exchange between threads), so
+    // that the march fits 128 registers (16 warps per SM)
+    __shared__ float sG[4][NV][128];    // slot i & 3: G_y of the interface below row y0 - 3 + i
+    __shared__ float sR[2][NV][128];    // x flux differences of the last two rows with x work
+    const int tid = threadIdx.x;
     unsigned jy = 0;                 // bit b: strong jump between rows s - 1 - b and s - b
     unsigned gq = 0;                 // byte b: gate of row s - b
     unsigned gn;                     // gate of the row loaded ahead
@@ -1857,7 +1860,12 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
             const NodeW &prv = row[(k + 3) & 3];
             if (i >= 1) jy = (jy << 1) | (jump2(jump, prv.p, prv.h[0], cur.p, cur.h[0]) ? 1u : 0u);
             // G_y of interface s - 1/2, needed from y0 - 3/2 (i = 2) to y0 + nrow + 1/2 (i = nrow + 4)
-            if (i >= 2 && i <= nrow + 4) dflux_w<1>(gm1, prv, cur, Gy[k]);
+            float Gk[NV];
+            if (i >= 2 && i <= nrow + 4) {
+                dflux_w<1>(gm1, prv, cur, Gk);
+#pragma unroll
+                for (int v = 0; v < NV; v++) sG[k][v][tid] = Gk[v];
+            }
             // residual of row y = s - 2 (i = 5 .. nrow + 4): G_y at y + 3/2, y + 1/2, y - 1/2, y - 3/2
             if (i >= 5 && i <= nrow + 4 && own) {
                 const int y = s - 2;
@@ -1865,9 +1873,9 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
                 const long long m = cb + (long long)y * st;
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
-                    const float ry = -facy * (7.f * (Gy[(k + 3) & 3][v] + Gy[(k + 2) & 3][v]) -
-                                              (Gy[k][v] + Gy[(k + 1) & 3][v])) * (1.f / 12.f);
-                    Rf[v * vs + m] = Rx[k & 1][v] + ry;
+                    const float ry = -facy * (7.f * (sG[(k + 3) & 3][v][tid] + sG[(k + 2) & 3][v][tid]) -
+                                              (Gk[v] + sG[(k + 1) & 3][v][tid])) * (1.f / 12.f);
+                    Rf[v * vs + m] = sR[k & 1][v][tid] + ry;
                 }
             }
             // y interface y + 1/2 of row y = s - 3 (rows y0 .. y0 + nrow - 1, and -1 on the first
@@ -1877,7 +1885,8 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
                     float D[NV];
 #pragma unroll
                     for (int v = 0; v < NV; v++)
-                        D[v] = (6.f * Gy[(k + 2) & 3][v] + Gy[(k + 1) & 3][v] - Gy[(k + 3) & 3][v]) * (1.f / 12.f);
+                        D[v] = (6.f * sG[(k + 2) & 3][v][tid] + sG[(k + 1) & 3][v][tid] - sG[(k + 3) & 3][v][tid]) *
+                               (1.f / 12.f);
                     record_interface(P, sj, 1, cb + (long long)(s - 3) * st, D);
                 }
             }
@@ -1898,7 +1907,7 @@ __global__ void __launch_bounds__(128, 3) k_conv_delta_xy(Dev P, const float *__
                     Gm[v] = __shfl_up_sync(0xffffffffu, Gx[v], 1);
                     const float Gmm = __shfl_up_sync(0xffffffffu, Gx[v], 2);
                     Gpp[v] = __shfl_down_sync(0xffffffffu, Gx[v], 1);
-                    Rx[k & 1][v] = -facx * (7.f * (Gx[v] + Gm[v]) - (Gpp[v] + Gmm)) * (1.f / 12.f);
+                    sR[k & 1][v][tid] = -facx * (7.f * (Gx[v] + Gm[v]) - (Gpp[v] + Gmm)) * (1.f / 12.f);
                 }
                 // interface x + 1/2: pairs (x - 2, x - 1) .. (x + 2, x + 3) are ballot bits lane - 2 .. lane + 2
                 if (xrec && (g0 || g1 || ((bx >> (lane - 2)) & 31u))) {
