@@ -1494,7 +1494,7 @@ __device__ __forceinline__ void delta_flux(const Dev &P, const float *__restrict
 
 // One interface of the delta-form mixed path.  An interface whose stencil holds a strong jump is
 // flagged (bit DIR of flag[m], m = left node), its FP32 D kept in Dst (plane set DIR) and its
-// index appended to the direction's list; after the convective passes k_patch_fix recomputes the
+// index appended to the direction's list; after the convective passes the patch pass recomputes the
 // listed interfaces in FP64 and leaves the corrections D64 - D32 in Dst, and the update kernel
 // adds them to the two adjacent nodes' residuals (fixed order: deterministic).  The FP32 pass
 // carries no FP64 code and keeps its register budget.  Interfaces computed twice (the carried
@@ -1771,8 +1771,8 @@ __global__ void __launch_bounds__(128, 4) k_conv_delta_tile(Dev P, const float *
 // Gated x and y passes in one kernel (x and y active), streamed through registers.  A warp owns
 // a strip of XS output columns of one z plane: lane l holds column x0 - 3 + l (lanes 0..2 and
 // 29..31 are the strip's halo, their columns clamped to the last ghost), and marches along y
-// over yc rows (from march_length), rows y0 - 3 .. y0 + yc + 2.  Each step loads the next row into registers
-// (prefetched one step ahead) and
+// over yc rows (from march_length), rows y0 - 3 .. y0 + yc + 2.  Each step loads the next row
+// into registers (prefetched one step ahead) and
 //   - forms G_y of the interface below the current row (the node pair in the lane's registers)
 //     and its strong-jump bit, kept in a 4-slot ring of interfaces and a bit history;
 //   - forms G_x of the lane's interface x + 1/2 of the current row (right neighbour's node by
@@ -1782,8 +1782,9 @@ __global__ void __launch_bounds__(128, 4) k_conv_delta_tile(Dev P, const float *
 //   - completes the residual of the row two below (its y flux difference needs G_y up to
 //     y + 3/2), adds that row's x part kept from two steps before and writes it once, and flags
 //     the y interface of the row three below (its jump window reaches the current row).
-// No shared memory and no block barriers: every warp streams independently, and the x pass's
-// reads of the node arrays and its residual round trip through HBM are gone.
+// No block barriers and no data shared between threads (each thread keeps its two rings in its
+// own shared-memory slots): every warp streams independently, and the x pass's reads of the node
+// arrays and its residual round trip through HBM are gone.
 constexpr int XS = 26;     // output columns of a strip (lanes 3 .. 28)
 
 __device__ __forceinline__ void record_interface(const Dev &P, const Strong &sj, int dir, long long m,
@@ -1941,7 +1942,7 @@ static bool fused_xy(const Dev &P)
 // Gated x pass: one block per row segment of XSEG nodes stages the segment's nodes with a
 // 3-node halo (FP32 hi, lo, u, v, w, p) in shared memory with coalesced loads; thread t forms the
 // central D of interface x0 + t (thread 0 also x0 - 1) from the staged nodes and records the
-// interfaces that need the characteristic flux for k_patch_fix, as the gated y / z passes do.
+// interfaces that need the characteristic flux for the patch pass, as the gated y / z passes do.
 constexpr int XSEG = 256;   // x segment length of the x passes
 constexpr int XH = 3;
 constexpr int XNS = XSEG + 2 * XH;
