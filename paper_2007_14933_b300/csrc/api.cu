@@ -544,10 +544,7 @@ extern "C" int osbli_launches_per_step(const osbli_t *h)
     if (P.viscous) per_stage++;
     // gated mixed path with x and y active: one fused x + y pass (see fused_xy)
     if (P.mixed && P.sensor && !general(P) && P.scheme != OSBLI_CENTRAL4 && P.active[0] && P.active[1]) per_stage--;
-    // the mixed path's stages after the first take their FP32 copies from the previous update
-    // (no primitives pass)
-    const int carried = P.mixed ? P.nstage - 1 : 0;
-    return P.nstage * per_stage - carried + (P.sensor && !h->B.gate_fixed ? 2 : 0);
+    return P.nstage * per_stage + (P.sensor && !h->B.gate_fixed ? 2 : 0);
 }
 
 extern "C" const char *osbli_last_error(const osbli_t *h)

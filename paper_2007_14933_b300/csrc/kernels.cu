@@ -103,17 +103,9 @@ __device__ __forceinline__ long long face_plane_index(const Dev &P, int d, int c
     return (long long)cb * na + ca;
 }
 
-// FP32 hi/lo copies and primitives of one node of the mixed path (defined with the primitives pass)
-__device__ __forceinline__ void prim_mixed_node(const Dev &P, const double (&u)[NV], float gm1, float gam, float gM2,
-                                                float *__restrict__ Uf, float *__restrict__ Wf, long long t);
-
-// Ghost fill of direction d.  With Uf / Wf given (the mixed path's stages after the first, whose
-// primitives pass is skipped) each ghost node written also gets its FP32 copies and primitives.
 __device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *__restrict__ U, int d, const double *__restrict__ bd0,
-                        const double *__restrict__ bd1, float *__restrict__ Uf = nullptr,
-                        float *__restrict__ Wf = nullptr)
+                        const double *__restrict__ bd1)
 {
-    const float gm1f = (float)P.gm1, gamf = (float)P.gamma, gM2f = (float)P.gM2;
     const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
     const long long npa = P.np[da], npb = P.np[db];
     const long long tot = 2LL * GH * npa * npb;
@@ -152,7 +144,6 @@ __device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *
         ii[db] = ib - P.g[db];
         ii[d] = (s == 0) ? -gi : n - 1 + gi;
         const long long idg = node_index(P, ii[0], ii[1], ii[2]);
-        bool wrote = true;
         if (bc == BC_PERIODIC || bc == BC_ZEROGRAD) {
             if (bc == BC_PERIODIC) ii[d] = (s == 0) ? n - gi : gi - 1;
             else ii[d] = (s == 0) ? 0 : n - 1;
@@ -188,30 +179,20 @@ __device__ __forceinline__ void ghost_body(const Dev &P, const Blk &bk, double *
             const double T = bd[4 * plane + pid];
             set_prim(P, U, idg, P.gM2 * p1 / T, bd[1 * plane + pid], bd[2 * plane + pid],
                      bd[3 * plane + pid], p1);
-        } else {
-            wrote = false;   // sub-domain faces: filled by the halo exchange
-        }
-        if (Uf && wrote) {
-            double u[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) u[v] = U[v * P.vs + idg];
-            prim_mixed_node(P, u, gm1f, gamf, gM2f, Uf, Wf, idg);
         }
     }
 }
 
 __global__ void k_ghost(Dev P, double *__restrict__ U, int d, const double *__restrict__ bd0,
-                        const double *__restrict__ bd1, float *__restrict__ Uf, float *__restrict__ Wf)
+                        const double *__restrict__ bd1)
 {
-    ghost_body(P, self_blk(), U, d, bd0, bd1, Uf, Wf);
+    ghost_body(P, self_blk(), U, d, bd0, bd1);
 }
 
 // After-stage boundary nodes: wall (rho u = 0, rho E = rho_w T_w / (M^2 gamma (gamma-1)),
 // Eq. 41), Dirichlet and inflow nodes.
-__global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const double *__restrict__ bd,
-                         float *__restrict__ Uf, float *__restrict__ Wf)
+__global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const double *__restrict__ bd)
 {
-    const float gm1f = (float)P.gm1, gamf = (float)P.gamma, gM2f = (float)P.gM2;
     const int da = (d == 0) ? 1 : 0, db = (d == 2) ? 1 : 2;
     const long long plane = (long long)P.n[da] * P.n[db];
     const int n = P.n[d];
@@ -254,12 +235,6 @@ __global__ void k_bnodes(Dev P, double *__restrict__ U, int d, int s, const doub
             cons_prim(P, U, node_index(P, ii[0], ii[1], ii[2]), r1, u1, v1, w1, p1);
             set_prim(P, U, idb, P.gM2 * p1 / bd[4 * plane + t], bd[1 * plane + t],
                      bd[2 * plane + t], bd[3 * plane + t], p1);
-        }
-        if (Uf) {   // the node's FP32 copies for the next stage (boundary faces only reach here)
-            double u[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) u[v] = U[v * P.vs + idb];
-            prim_mixed_node(P, u, gm1f, gamf, gM2f, Uf, Wf, idb);
         }
     }
 }
@@ -632,31 +607,6 @@ __device__ __forceinline__ void split_hi_lo(double x, float &hi, float &lo)
     lo = sign ? -r : r;
 }
 
-__device__ __forceinline__ void prim_mixed_node(const Dev &P, const double (&u)[NV], float gm1, float gam, float gM2,
-                                                float *__restrict__ Uf, float *__restrict__ Wf, long long t)
-{
-    float h[NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        float lo;
-        split_hi_lo(u[v], h[v], lo);
-        Uf[v * P.vs + t] = h[v];
-        Uf[(NV + v) * P.vs + t] = lo;
-    }
-    const float rho = h[0], mx = h[1], my = h[2], mz = h[3], E = h[4];
-    const float ir = 1.0f / rho;
-    const float uu = mx * ir, vv = my * ir, ww = mz * ir;
-    const float p = gm1 * (E - 0.5f * (mx * uu + my * vv + mz * ww));
-    Wf[W_U * P.vs + t] = uu;
-    Wf[W_V * P.vs + t] = vv;
-    Wf[W_W * P.vs + t] = ww;
-    Wf[W_P * P.vs + t] = p;
-    Wf[W_A * P.vs + t] = sqrtf(gam * p * ir);
-    Wf[W_SR * P.vs + t] = sqrtf(rho);
-    Wf[W_H * P.vs + t] = (E + p) * ir;
-    Wf[W_T * P.vs + t] = gM2 * p * ir;
-}
-
 __device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, const double *__restrict__ U, float *__restrict__ Uf,
                              float *__restrict__ Wf, int *__restrict__ nstrong, unsigned char *__restrict__ flag)
 {
@@ -666,11 +616,27 @@ __device__ __forceinline__ void prim_mixed_body(const Dev &P, const Blk &bk, con
     const float gm1 = (float)P.gm1, gam = (float)P.gamma, gM2 = (float)P.gM2;   // once per thread
     for (long long t = bk.x * (long long)blockDim.x + threadIdx.x; t < P.ntot;
          t += (long long)bk.nx * blockDim.x) {
-        double u[NV];
+        float h[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = U[v * P.vs + t];
-        prim_mixed_node(P, u, gm1, gam, gM2, Uf, Wf, t);
+        for (int v = 0; v < NV; v++) {
+            float lo;
+            split_hi_lo(U[v * P.vs + t], h[v], lo);
+            Uf[v * P.vs + t] = h[v];
+            Uf[(NV + v) * P.vs + t] = lo;
+        }
         if (flag) flag[t] = 0;
+        const float rho = h[0], mx = h[1], my = h[2], mz = h[3], E = h[4];
+        const float ir = 1.0f / rho;
+        const float u = mx * ir, v = my * ir, w = mz * ir;
+        const float p = gm1 * (E - 0.5f * (mx * u + my * v + mz * w));
+        Wf[W_U * P.vs + t] = u;
+        Wf[W_V * P.vs + t] = v;
+        Wf[W_W * P.vs + t] = w;
+        Wf[W_P * P.vs + t] = p;
+        Wf[W_A * P.vs + t] = sqrtf(gam * p * ir);
+        Wf[W_SR * P.vs + t] = sqrtf(rho);
+        Wf[W_H * P.vs + t] = (E + p) * ir;
+        Wf[W_T * P.vs + t] = gM2 * p * ir;
     }
 }
 
@@ -1009,13 +975,9 @@ __device__ __forceinline__ void node_fix_force(const Dev &P, const double *__res
 }
 
 // The node's total residual r out (MODE 1), or the RK register update (MODE 0, Eqs. 36-37).
-// PRIM: the mixed path's next stage skips its primitives pass, so the update also writes the
-// node's FP32 hi/lo copies and primitives from the new state (gm1f, gamf, gM2f in FP32).
-template <int MODE, int STAGE, typename RT, bool PRIM = false>
+template <int MODE, int STAGE, typename RT>
 __device__ __forceinline__ void node_finish(const Dev &P, double *__restrict__ U, double *__restrict__ dU,
-                                            double *Rout, int *__restrict__ err, long long id, const RT (&r)[NV],
-                                            float *__restrict__ Uf = nullptr, float *__restrict__ Wf = nullptr,
-                                            float gm1f = 0.f, float gamf = 0.f, float gM2f = 0.f)
+                                            double *Rout, int *__restrict__ err, long long id, const RT (&r)[NV])
 {
     const long long vs = P.vs;
     if (MODE == 1) {
@@ -1024,7 +986,6 @@ __device__ __forceinline__ void node_finish(const Dev &P, double *__restrict__ U
         return;
     }
     bool bad = false;
-    double unv[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         double du;
@@ -1051,26 +1012,21 @@ __device__ __forceinline__ void node_finish(const Dev &P, double *__restrict__ U
             un = U[v * vs + id] + c_rkB[P.rk][STAGE] * dd;
         }
         U[v * vs + id] = un;
-        unv[v] = un;
         bad |= !isfinite(un);
     }
     if (bad) atomicOr(err, 1);
-    if constexpr (PRIM) prim_mixed_node(P, unv, gm1f, gamf, gM2f, Uf, Wf, id);
 }
 
 // Viscous divergence (flux form) + RK register update (Eqs. 36-37), or residual output.
 // MODE 0: RK stage (STAGE selects A_i/B_i; stage 0 has dU^(0) = 0); MODE 1: R_total -> Rout.
 // RT is the storage / arithmetic type of the residual and viscous fluxes (double plain, float
 // mixed); the register update itself is FP64 on both paths.
-template <int MODE, int STAGE, bool VISC, bool CURV, typename RT, bool HALO = false, bool PRIM = false>
+template <int MODE, int STAGE, bool VISC, bool CURV, typename RT, bool HALO = false>
 __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double *__restrict__ U, double *__restrict__ dU,
                                                 const RT *Rin, const RT *__restrict__ V,
                                                 const double *__restrict__ M, double *Rout,
-                                                int *__restrict__ err, Strong sj,
-                                                float *__restrict__ Uf = nullptr, float *__restrict__ Wf = nullptr)
+                                                int *__restrict__ err, Strong sj)
 {
-    const float gm1f = PRIM ? (float)P.gm1 : 0.f, gamf = PRIM ? (float)P.gamma : 0.f,
-                gM2f = PRIM ? (float)P.gM2 : 0.f;   // once per thread
     // FP64 corrections of strong-jump interfaces (mixed delta path; sj.flag null otherwise)
     const bool fix = sj.flag && (sj.count[0] | sj.count[1] | sj.count[2]);
     const long long N = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -1119,18 +1075,17 @@ __device__ __forceinline__ void update_body(const Dev &P, const Blk &bk, double 
                 }
             }
         }
-        node_finish<MODE, STAGE, RT, PRIM>(P, U, dU, Rout, err, id, r, Uf, Wf, gm1f, gamf, gM2f);
+        node_finish<MODE, STAGE, RT>(P, U, dU, Rout, err, id, r);
     }
 }
 
-template <int MODE, int STAGE, bool VISC, bool CURV, typename RT, bool HALO = false, bool PRIM = false>
+template <int MODE, int STAGE, bool VISC, bool CURV, typename RT, bool HALO = false>
 __global__ void __launch_bounds__(128) k_update(Dev P, double *__restrict__ U, double *__restrict__ dU,
                                                 const RT *Rin, const RT *__restrict__ V,
                                                 const double *__restrict__ M, double *Rout,
-                                                int *__restrict__ err, Strong sj, float *__restrict__ Uf,
-                                                float *__restrict__ Wf)
+                                                int *__restrict__ err, Strong sj)
 {
-    update_body<MODE, STAGE, VISC, CURV, RT, HALO, PRIM>(P, self_blk(), U, dU, Rin, V, M, Rout, err, sj, Uf, Wf);
+    update_body<MODE, STAGE, VISC, CURV, RT, HALO>(P, self_blk(), U, dU, Rin, V, M, Rout, err, sj);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2418,7 +2373,7 @@ void launch_labels(const Dev &P, const Bufs &B, unsigned char *labd[3], unsigned
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
-        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1], nullptr, nullptr);
+        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
     }
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
@@ -2602,38 +2557,26 @@ static void conv_dir(const Dev &P, const Bufs &B, int acc, cudaStream_t s)
     }
 }
 
-template <int MODE, int STAGE, bool VISC, bool CURV, bool HALO = false, bool PRIM = false>
+template <int MODE, int STAGE, bool VISC, bool CURV, bool HALO = false>
 static void update_t(const Dev &P, const Bufs &B, int g, cudaStream_t s)
 {
     const Strong none{nullptr, nullptr, nullptr, nullptr, 0};
     if (P.mixed)
-        k_update<MODE, STAGE, VISC, CURV, float, HALO, PRIM><<<g, 128, 0, s>>>(
-            P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err, CURV ? none : strong_of(B), B.Uf, B.Wf);
+        k_update<MODE, STAGE, VISC, CURV, float, HALO><<<g, 128, 0, s>>>(P, B.U, B.dU, B.Rf, B.Vf, B.M, B.R, B.err,
+                                                                          CURV ? none : strong_of(B));
     else
         k_update<MODE, STAGE, VISC, CURV, double, HALO><<<g, 128, 0, s>>>(P, B.U, B.dU, B.R, B.V, B.M, B.R, B.err,
-                                                                           none, nullptr, nullptr);
+                                                                           none);
 }
 
 // a sub-domain of a split grid (halo faces along z)
 static bool has_halo(const Dev &P) { return P.bc[2][0] == BC_HALO || P.bc[2][1] == BC_HALO; }
 
 template <int MODE, int STAGE>
-static void update(const Dev &P, const Bufs &B, cudaStream_t s, bool carry = false)
+static void update(const Dev &P, const Bufs &B, cudaStream_t s)
 {
     long long N = (long long)P.n[0] * P.n[1] * P.n[2];
     int g = grid_for(N, 128);
-    if constexpr (MODE == 0) {
-        if (carry) {   // mixed path, undivided grid: the update carries the FP32 copies to the next stage
-            if (P.viscous) {
-                if (general(P)) update_t<0, STAGE, true, true, false, true>(P, B, g, s);
-                else update_t<0, STAGE, true, false, false, true>(P, B, g, s);
-            } else {
-                if (general(P)) update_t<0, STAGE, false, true, false, true>(P, B, g, s);
-                else update_t<0, STAGE, false, false, false, true>(P, B, g, s);
-            }
-            return;
-        }
-    }
     if (P.viscous) {
         if (general(P)) update_t<MODE, STAGE, true, true>(P, B, g, s);
         else if (has_halo(P)) update_t<MODE, STAGE, true, false, true>(P, B, g, s);
@@ -2685,11 +2628,8 @@ struct Tap {
 
 // ghost fill + primitives + convective + viscous fluxes: R holds the convective residual and
 // V the viscous fluxes when this returns (on the stream).  Returns the launch count.
-// carried: the stage's FP32 copies and primitives were written by the previous stage's update and
-// boundary-node kernels (mixed path, stages after the first); its ghost fill writes those of the
-// ghost nodes, and the primitives pass is replaced by clearing the interface flags and counts.
 static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap = nullptr, bool sensor_now = true,
-                          bool ghosts = true, bool carried = false)
+                          bool ghosts = true)
 {
     static const char *ghost_names[3] = {"ghost_x", "ghost_y", "ghost_z"};
     static const char *conv_names[3] = {"conv_x", "conv_y", "conv_z"};
@@ -2698,19 +2638,13 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
         if (!P.active[d]) continue;
         long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
         if (tap) (*tap)(ghost_names[d], s);
-        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1],
-                                                     carried ? B.Uf : nullptr, carried ? B.Wf : nullptr);
+        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
         launches++;
     }
-    if (carried) {
-        if (B.flag) cudaMemsetAsync(B.flag, 0, (size_t)P.vs, s);
-        cudaMemsetAsync(B.err + 1, 0, 3 * sizeof(int), s);
-    } else {
-        if (tap) (*tap)("prim", s);
-        if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
-        else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
-        launches++;
-    }
+    if (tap) (*tap)("prim", s);
+    if (P.mixed) k_prim_mixed<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.Uf, B.Wf, B.err + 1, B.flag);
+    else k_prim<<<grid_for(P.ntot, 256), 256, 0, s>>>(P, B.U, B.W);
+    launches++;
     if (P.sensor && sensor_now && !B.gate_fixed) {
         if (tap) (*tap)("sensor", s);
         launches += launch_sensor_gate(P, B, s);
@@ -2757,7 +2691,7 @@ static int residual_front(const Dev &P, const Bufs &B, cudaStream_t s, Tap *tap 
     return launches;
 }
 
-static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s, bool carry = false)
+static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s)
 {
     int launches = 0;
     for (int d = 0; d < 3; d++) {
@@ -2766,8 +2700,7 @@ static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s, bool carr
             int bc = P.bc[d][sd];
             if (bc != BC_WALL && bc != BC_DIRICHLET && bc != BC_INFLOW && bc != BC_ADIABATIC) continue;
             long long plane = (long long)P.n[(d == 0) ? 1 : 0] * P.n[(d == 2) ? 1 : 2];
-            k_bnodes<<<grid_for(plane, 256), 256, 0, s>>>(P, B.U, d, sd, B.bd[2 * d + sd], carry ? B.Uf : nullptr,
-                                                           carry ? B.Wf : nullptr);
+            k_bnodes<<<grid_for(plane, 256), 256, 0, s>>>(P, B.U, d, sd, B.bd[2 * d + sd]);
             launches++;
         }
     }
@@ -2776,18 +2709,15 @@ static int boundary_nodes(const Dev &P, const Bufs &B, cudaStream_t s, bool carr
 
 int launch_stage(const Dev &P, const Bufs &B, int stage, cudaStream_t s)
 {
-    // mixed path: the update of every stage but the last also writes its nodes' FP32 copies and
-    // primitives (and so do the boundary-node kernels for theirs), so the stages after the first
-    // skip the primitives pass; the learned gate is evaluated once per RK step, at its first stage
-    const bool carry_in = P.mixed && stage > 0, carry_out = P.mixed && stage < P.nstage - 1;
-    int launches = residual_front(P, B, s, nullptr, stage == 0, true, carry_in);
-    if (stage == 0) update<0, 0>(P, B, s, carry_out);
-    else if (stage == 1) update<0, 1>(P, B, s, carry_out);
-    else if (stage == 2) update<0, 2>(P, B, s, carry_out);
-    else if (stage == 3) update<0, 3>(P, B, s, carry_out);
-    else update<0, 4>(P, B, s, carry_out);
+    // the learned gate is evaluated once per RK step, at its first stage
+    int launches = residual_front(P, B, s, nullptr, stage == 0);
+    if (stage == 0) update<0, 0>(P, B, s);
+    else if (stage == 1) update<0, 1>(P, B, s);
+    else if (stage == 2) update<0, 2>(P, B, s);
+    else if (stage == 3) update<0, 3>(P, B, s);
+    else update<0, 4>(P, B, s);
     launches++;
-    launches += boundary_nodes(P, B, s, carry_out);
+    launches += boundary_nodes(P, B, s);
     return launches;
 }
 
@@ -2844,7 +2774,7 @@ void launch_ghosts(const Dev &P, const Bufs &B, cudaStream_t s)
     for (int d = 0; d < 3; d++) {
         if (!P.active[d]) continue;
         long long work = 2LL * GH * P.np[(d == 0) ? 1 : 0] * P.np[(d == 2) ? 1 : 2];
-        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1], nullptr, nullptr);
+        k_ghost<<<grid_for(work, 256), 256, 0, s>>>(P, B.U, d, B.bd[2 * d], B.bd[2 * d + 1]);
     }
 }
 
