@@ -94,8 +94,8 @@ DRAM_BYTES_PER_POINT = {
                                  "form, 5.2 % of cells gated): dram__bytes_read.sum 358.8 MB + "
                                  "dram__bytes_write.sum 70.2 MB per launch over 4.096 M points, scaled to "
                                  "this grid"),
-    "k_conv_delta_xy": (87.4, "ncu capture of k_conv_delta_xy in the bench at --n 160 (learned form, 5.2 % "
-                              "of cells gated): dram__bytes_read.sum 281.8 MB + dram__bytes_write.sum 76.1 "
+    "k_conv_delta_xy": (90.4, "ncu capture of k_conv_delta_xy in the bench at --n 160 (learned form, 5.2 % "
+                              "of cells gated): dram__bytes_read.sum 294.0 MB + dram__bytes_write.sum 76.3 "
                               "MB per launch over 4.096 M points, scaled to this grid"),
     "k_conv_delta_x_win": (78.2, "ncu capture of k_conv_delta_x_win<2> in the bench at --n 160 (learned "
                                  "form): dram__bytes_read.sum 251.0 MB + dram__bytes_write.sum 69.1 MB per "
