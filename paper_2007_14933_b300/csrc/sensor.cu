@@ -222,7 +222,7 @@ __global__ void k_features(Dev P, const double *__restrict__ U, __nv_bfloat16 *_
 constexpr int INF_WARPS = 4;
 
 // A warp owns a column of tiles: 32 consecutive x-cells (two 16-row tensor-core tiles) at one
-// z index, marching along y over up to YCH tiles.  The three z-rows (dk = -1, 0, 1) of each y-plane over x-positions
+// z index, marching along y over up to ych tiles (infer_march).  The three z-rows (dk = -1, 0, 1) of each y-plane over x-positions
 // x0-1 .. x0+32 (rho, u, v, w, p) are staged in shared memory by asynchronous copies into a ring
 // of four y-planes: while tile j is computed from planes j-1, j, j+1, plane j+2 is in flight, and
 // every node's values are fetched once per column instead of once per tile that reads them.
@@ -234,7 +234,6 @@ constexpr int INF_WARPS = 4;
 constexpr int SEG = 32;
 constexpr int SQS = SEG + 2;
 constexpr int NSLOT = 4;
-constexpr int YCH = 64;                   // y extent of one warp's march (32 and 128: 1.2 % and 1.4 % slower at 256^3)
 // floats of one staged y-plane: 3 z-rows x 5 quantities x SQS, plus a pad of 14 that puts the two
 // staged rows one fragment load reads (groups C and C + 1 of a k-step) in disjoint banks -- with
 // no pad 128 of the 192 loads of a tile are 2-way bank conflicts
@@ -302,7 +301,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
                                                                  const SensorW *__restrict__ W,
                                                                  float zthresh,
                                                                  unsigned char *__restrict__ flag,
-                                                                 float *__restrict__ probs)
+                                                                 float *__restrict__ probs, int ych)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
@@ -325,7 +324,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
     const int lm = lane >> 3, lr = lane & 7;
     const int nseg = (P.n[0] + SEG - 1) / SEG;
     const int ny = P.n[1];
-    const int nyc = (ny + YCH - 1) / YCH;
+    const int nyc = (ny + ych - 1) / ych;
     const long long nitem = (long long)nseg * P.n[2] * nyc;
     const float gam = (float)P.gamma;
     for (long long it = blockIdx.x * (long long)INF_WARPS + warp; it < nitem;
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_sensor_infer(Dev P, const fl
         const int seg = (int)(it % nseg);
         const long long rest = it / nseg;
         const int k = (int)(rest % P.n[2]);
-        const int j0 = (int)(rest / P.n[2]) * YCH, j1 = min(j0 + YCH, ny);
+        const int j0 = (int)(rest / P.n[2]) * ych, j1 = min(j0 + ych, ny);
         const int x0 = seg * SEG;
         const int ncell = min(SEG, P.n[0] - x0);
         // ring slot of y-plane jy: (jy + 1) & 3
@@ -505,14 +504,25 @@ static int sm_count()
     return n > 0 ? n : 148;
 }
 
-static int infer_blocks(const Dev &P)
+// y extent of one warp's march: 64 tile rows where that still gives three waves of the resident
+// warps (4 blocks of 4 warps per SM), else 32.  Same-box A/B at 256^3 (3.5 waves): 64 rows
+// 1.145 ms, 32 rows 1.163, 128 rows 1.161; at 160^3 64 rows leave 1.01 waves and ran 12 % slower
+// than 32.
+static int infer_march(const Dev &P)
+{
+    const long long segs = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[2];
+    const long long warps64 = segs * ((P.n[1] + 63) / 64);
+    return warps64 >= 3LL * sm_count() * 4 * INF_WARPS ? 64 : 32;
+}
+
+static int infer_blocks(const Dev &P, int ych)
 {
     static bool attr = false;   // dynamic shared memory above the 48 KB default, set once
     if (!attr) {
         cudaFuncSetAttribute(k_sensor_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
         attr = true;
     }
-    const long long cols = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[2] * ((P.n[1] + YCH - 1) / YCH);
+    const long long cols = (long long)((P.n[0] + SEG - 1) / SEG) * P.n[2] * ((P.n[1] + ych - 1) / ych);
     long long blocks = (cols + INF_WARPS - 1) / INF_WARPS;
     if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
     return (int)blocks;
@@ -520,8 +530,9 @@ static int infer_blocks(const Dev &P)
 
 int launch_sensor_gate(const Dev &P, const Bufs &B, cudaStream_t s)
 {
-    k_sensor_infer<<<infer_blocks(P), 32 * INF_WARPS, INFER_SMEM, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw,
-                                                                       B.zthresh, B.sflag, nullptr);
+    const int ych = infer_march(P);
+    k_sensor_infer<<<infer_blocks(P, ych), 32 * INF_WARPS, INFER_SMEM, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw,
+                                                                             B.zthresh, B.sflag, nullptr, ych);
     long long db = (P.ntot + 255) / 256;
     if (db > (long long)sm_count() * 16) db = (long long)sm_count() * 16;
     k_dilate<<<(int)db, 256, 0, s>>>(P, B.sflag, B.gate, 0);
@@ -557,8 +568,9 @@ int launch_fixed_gate(const Dev &P, const Bufs &B, const unsigned char *compact,
 void launch_sensor_probs(const Dev &P, const Bufs &B, float *probs, cudaStream_t s)
 {
     launch_prim(P, B, s);
-    k_sensor_infer<<<infer_blocks(P), 32 * INF_WARPS, INFER_SMEM, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw,
-                                                                       B.zthresh, nullptr, probs);
+    const int ych = infer_march(P);
+    k_sensor_infer<<<infer_blocks(P, ych), 32 * INF_WARPS, INFER_SMEM, s>>>(P, B.Uf, B.Wf, (const SensorW *)B.sw,
+                                                                       B.zthresh, nullptr, probs, ych);
 }
 
 void launch_features(const Dev &P, const Bufs &B, void *X, cudaStream_t s)
